@@ -1,0 +1,211 @@
+/*
+ * slu.h -- C ABI of the irregular-block sparse LU library for B300 (sm_103a).
+ *
+ * The library factors a square sparse matrix A = L U (L unit lower, U upper,
+ * no row exchanges) over the structure-aware irregular 2-D block grid of
+ * "A Structure-Aware Irregular Blocking Method for Sparse LU Factorization"
+ * (Hu et al.), and solves with the factors.
+ *
+ *   slu_analyze  host only: symmetric pattern, symbolic factorization,
+ *                diagonal block pointer (Section 4.2, Algorithm 2),
+ *                percentage sampling and irregular blocking (Section 4.3,
+ *                Algorithm 3) or regular blocking, and the block task plan
+ *                of the right-looking blocked LU (Section 2.2, Algorithm 1).
+ *   slu_factor   GPU: value scatter, then per level of the block dependency
+ *                structure GETRF / GESSM / TSTRF / SSSSM (Algorithm 1's four
+ *                block operations), each block sparse or dense by density.
+ *   slu_solve    GPU: block forward / backward substitution, optionally
+ *                wrapped in FP64 iterative refinement.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are CSC, 0-based: colptr int64[n+1], rowidx int32[nnz].
+ *     Row indices inside a column may come in any order; duplicates are an
+ *     error (SLU_ERR_INVALID_ARG).
+ *   - "host" pointers are read during the call only; the library copies what
+ *     it keeps.  "device" pointers are CUDA device memory owned by the caller
+ *     and must stay valid until the work enqueued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  All device work of a call is enqueued on it.  Calls return
+ *     after enqueueing unless stated otherwise.
+ *   - Dense right-hand sides are column-major with a leading dimension.
+ *   - No call throws.  On failure a call returns a status other than SLU_OK
+ *     and slu_last_error() describes the failure (thread-local string).
+ *   - Plans and handles are opaque and freed only by their destroy call.
+ *     A handle refers to its plan, which must outlive it.
+ */
+#ifndef SLU_H
+#define SLU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SLU_OK = 0,
+    SLU_ERR_INVALID_ARG = 1,     /* bad size, pointer, pattern or option   */
+    SLU_ERR_OUT_OF_MEMORY = 2,   /* host or device allocation failed       */
+    SLU_ERR_CUDA = 3,            /* a CUDA runtime call or launch failed   */
+    SLU_ERR_SINGULAR = 4,        /* zero pivot with perturbation disabled  */
+    SLU_ERR_NOT_CONVERGED = 5,   /* refinement missed its tolerance        */
+    SLU_ERR_TIMEOUT = 6,         /* a bounded device-side wait expired     */
+    SLU_ERR_NOT_SUPPORTED = 7    /* option combination not implemented     */
+} slu_status;
+
+typedef enum {
+    SLU_BLOCKING_IRREGULAR = 0,  /* Algorithm 3 on the sampled curve        */
+    SLU_BLOCKING_REGULAR = 1     /* fixed-size blocks of regular_block rows */
+} slu_blocking;
+
+typedef enum {
+    SLU_PREC_FP64 = 0,           /* factors stored and computed in FP64     */
+    SLU_PREC_FP32 = 1            /* factors in FP32 (diagonal-block pivots
+                                    in FP64), solves refined in FP64        */
+} slu_precision;
+
+typedef struct {
+    int32_t blocking;            /* slu_blocking                            */
+    int32_t regular_block;       /* block size for SLU_BLOCKING_REGULAR     */
+    int32_t sample_points;       /* Algorithm 3: samples S (paper: 1000)    */
+    int32_t step;                /* Algorithm 3: window width (paper: 2)    */
+    int32_t max_num;             /* Algorithm 3: forced boundary after this
+                                    many skips (paper: 3)                   */
+    int32_t stride;              /* window advance (1 = the listed loop)    */
+    int32_t b_min;               /* S = min(sample_points, n / b_min)       */
+    int32_t precision;           /* slu_precision                           */
+    double dense_threshold;      /* block stored dense if nnz >= thr*bI*bJ  */
+    int32_t pivot_perturb;       /* 1: |pivot| < tau -> +-tau and counted   */
+    double pivot_tau_rel;        /* tau = pivot_tau_rel * max|A|; 0 = the
+                                    default (2^-26 FP64, 2^-12 FP32)        */
+    double refine_tol;           /* stop when backward error <= this        */
+    int32_t refine_max_iter;     /* < 0 never refine; 0 = default (none for
+                                    FP64, 30 for FP32); > 0 that many       */
+    int64_t wait_budget_ms;      /* bound on any device-side wait           */
+} slu_opts;
+
+typedef struct {
+    int64_t n;
+    int64_t nnz_a;               /* entries of the input pattern            */
+    int64_t nnz_sym;             /* entries of pattern(A + A^T) + diagonal  */
+    int64_t nnz_lu;              /* entries of the filled L+U pattern       */
+    int64_t flops;               /* sum_k (l_k + 2 l_k u_k)                 */
+    int32_t nblocks_1d;          /* p: blocks per dimension                 */
+    int32_t nlevels;             /* levels of the block dependency DAG      */
+    int64_t nblocks;             /* non-empty 2-D blocks                    */
+    int64_t ndense;              /* blocks stored dense                     */
+    int64_t storage_elems;       /* value slots incl. explicit zeros        */
+    int64_t n_getrf, n_gessm, n_tstrf;
+    int64_t n_ssssm_targets, n_ssssm_pairs;
+    int32_t max_block;           /* largest block dimension                 */
+    int32_t samples;             /* S actually used                         */
+    double analyze_ms;           /* host time of slu_analyze                */
+} slu_plan_info;
+
+typedef struct {
+    int64_t nperturb;            /* pivots replaced by +-tau                */
+    double tau;                  /* perturbation threshold used             */
+} slu_factor_info;
+
+typedef struct {
+    int32_t iterations;          /* refinement steps taken                  */
+    double backward_error;       /* max over RHS of ||b-Ax||_inf /
+                                    (||A||_inf ||x||_inf + ||b||_inf); -1
+                                    when not computed                       */
+} slu_solve_info;
+
+typedef struct slu_plan slu_plan;
+typedef struct slu_handle slu_handle;
+
+/* Fill *opts with the defaults: irregular blocking, S = 1000, step 2,
+ * max_num 3, stride 1, b_min 32, regular_block 128, FP64, dense threshold
+ * 0.6, perturbation on, refine_tol 1e-14, refine_max_iter 0 (the
+ * precision's default), wait budget 2000 ms. */
+void slu_opts_default(slu_opts *opts);
+
+/* Host-only analysis (Sections 4.2-4.3, Algorithms 2 and 3; Algorithm 1's
+ * block task lists).  colptr/rowidx: host, CSC of A's pattern (n x n).
+ * opts: host, NULL for defaults.  *out receives a new plan on success. */
+slu_status slu_analyze(int64_t n, const int64_t *colptr, const int32_t *rowidx,
+                       const slu_opts *opts, slu_plan **out);
+
+slu_status slu_plan_query(const slu_plan *plan, slu_plan_info *info);
+
+/* Copies of the plan's host arrays, for bit-exact checks.  Every output is
+ * host memory sized from slu_plan_query:
+ *   blockptr int64[n+1]  diagonal block pointer of the filled pattern
+ *   ptr      int64[p+1]  block boundaries
+ *   colptr   int64[n+1], rowidx int32[nnz_lu]: filled L+U pattern, rows
+ *            sorted; this is also the order of slu_export_factors' values
+ * Any output pointer may be NULL to skip it. */
+slu_status slu_plan_export(const slu_plan *plan, int64_t *blockptr,
+                           int64_t *ptr, int64_t *colptr, int32_t *rowidx);
+
+/* Block list (sorted by block column, then block row) and levels:
+ *   bi, bj int32[nblocks], bnnz int64[nblocks], dense uint8[nblocks],
+ *   level int32[p]. */
+slu_status slu_plan_export_blocks(const slu_plan *plan, int32_t *bi,
+                                  int32_t *bj, int64_t *bnnz, uint8_t *dense,
+                                  int32_t *level);
+
+/* Task lists, per level concatenated; level l owns entries
+ * [off[l], off[l+1]) of each list (off arrays int64[nlevels+1]).
+ *   getrf  int32[n_getrf]              diagonal block I
+ *   gessm  int32[2*n_gessm]            (I, J)
+ *   tstrf  int32[2*n_tstrf]            (J, I)
+ *   tgt    int32[2*n_ssssm_targets]    (K, J), sorted per level
+ *   srcoff int64[n_ssssm_targets+1], src int32[n_ssssm_pairs]: sources I of
+ *          each target, ascending. */
+slu_status slu_plan_export_tasks(const slu_plan *plan, int64_t *getrf_off,
+                                 int32_t *getrf, int64_t *gessm_off,
+                                 int32_t *gessm, int64_t *tstrf_off,
+                                 int32_t *tstrf, int64_t *tgt_off,
+                                 int32_t *tgt, int64_t *srcoff, int32_t *src);
+
+/* GPU numerical factorization.  values: device, float64[nnz_a] in the CSC
+ * order of the pattern given to slu_analyze.  Allocates the factor storage
+ * (device memory on the current device) and enqueues the factorization on
+ * `stream`.  The call synchronizes the stream before returning (it reads
+ * the perturbation count), so *info is final.  *out receives a new handle;
+ * with SLU_ERR_SINGULAR a handle is still returned (factors not usable). */
+slu_status slu_factor(const slu_plan *plan, const double *values,
+                      void *stream, slu_handle **out, slu_factor_info *info);
+
+/* Re-run the factorization into an existing handle with new values of the
+ * same pattern; no allocation.  Enqueues only (info may be NULL; if not
+ * NULL the call synchronizes and fills it). */
+slu_status slu_refactor(slu_handle *h, const double *values, void *stream,
+                        slu_factor_info *info);
+
+/* X = A^{-1} B.  B, X: device, float64, column-major n x nrhs with leading
+ * dimensions ldb, ldx >= n, 1 <= nrhs <= 64; X may alias B.  With
+ * refinement (FP32 factors by default, or refine_max_iter > 0) the call
+ * iterates r = b - A x in FP64 until the backward error is <= refine_tol,
+ * synchronizing once per iteration, and returns SLU_ERR_NOT_CONVERGED (X
+ * holding the last iterate) if it stops at the iteration limit.  A non-NULL
+ * info also makes an unrefined solve compute the backward error (one
+ * residual, synchronizing).  Refinement and info use a workspace that the
+ * handle allocates on first use. */
+slu_status slu_solve(const slu_handle *h, const double *B, int64_t ldb,
+                     int32_t nrhs, double *X, int64_t ldx, void *stream,
+                     slu_solve_info *info);
+
+/* Lam = A^{-T} G through the stored factors (U^T then L^T); no refinement.
+ * Same layout rules as slu_solve. */
+slu_status slu_solve_transpose(const slu_handle *h, const double *G,
+                               int64_t ldg, int32_t nrhs, double *Lam,
+                               int64_t ldl, void *stream);
+
+/* Factor values in the order of the plan's filled pattern (slu_plan_export
+ * colptr/rowidx): rows < col hold U, the diagonal holds U's, rows > col hold
+ * L.  out: device float64[nnz_lu]. */
+slu_status slu_export_factors(const slu_handle *h, double *out, void *stream);
+
+void slu_plan_destroy(slu_plan *plan);
+void slu_handle_destroy(slu_handle *h);
+const char *slu_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLU_H */

@@ -1,0 +1,749 @@
+// Host analysis: pattern -> plan.
+//
+//   1. pattern(A + A^T) plus the full diagonal (the diagonal block pointer of
+//      Section 4.2 relies on a structurally symmetric pattern);
+//   2. elimination tree and symbolic factorization (the second phase named
+//      in Section 1): struct L(:,j) = struct S(j+1:, j) united with the
+//      structures of j's children in the elimination tree, minus j;
+//   3. Algorithm 2: diagonal block pointer of the filled L+U pattern;
+//   4. Section 4.3: S samples of the percentage curve and Algorithm 3, or a
+//      regular blocking;
+//   5. the block plan of Algorithm 1 restricted to non-empty blocks:
+//      storage layout, levels of the block dependency DAG, task lists,
+//      intra-block column schedules, value maps.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "slu_internal.hpp"
+
+namespace slu {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+slu_status fail(slu_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+namespace {
+
+struct Sym {                      // symmetric pattern with diagonal
+    std::vector<int64_t> p;
+    std::vector<int32_t> i;
+};
+
+void symmetrize(int64_t n, const int64_t *cp, const int32_t *ri, Sym &S) {
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
+            const int32_t r = ri[q];
+            cnt[j + 1]++;                       // (r, j)
+            if (r != j) cnt[r + 1]++;           // (j, r)
+        }
+    for (int64_t j = 0; j < n; ++j) cnt[j + 1] += 1;   // diagonal
+    for (int64_t j = 0; j < n; ++j) cnt[j + 1] += cnt[j];
+    std::vector<int32_t> tmp(cnt[n]);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
+            const int32_t r = ri[q];
+            tmp[fill[j]++] = r;
+            if (r != j) tmp[fill[r]++] = (int32_t)j;
+        }
+        tmp[fill[j]++] = (int32_t)j;
+    }
+    S.p.assign(n + 1, 0);
+    S.i.clear();
+    S.i.reserve(cnt[n]);
+    for (int64_t j = 0; j < n; ++j) {
+        auto b = tmp.begin() + cnt[j], e = tmp.begin() + cnt[j + 1];
+        std::sort(b, e);
+        auto u = std::unique(b, e);
+        S.i.insert(S.i.end(), b, u);
+        S.p[j + 1] = (int64_t)S.i.size();
+    }
+}
+
+// Liu's elimination tree of a symmetric pattern (upper part used), with
+// path compression through the `anc` array.
+void etree(int64_t n, const Sym &S, std::vector<int32_t> &parent) {
+    parent.assign(n, -1);
+    std::vector<int32_t> anc(n, -1);
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t q = S.p[j]; q < S.p[j + 1]; ++q) {
+            int32_t r = S.i[q];
+            if (r >= j) break;                  // rows sorted
+            while (anc[r] != -1 && anc[r] != j) {
+                const int32_t nx = anc[r];
+                anc[r] = (int32_t)j;
+                r = nx;
+            }
+            if (anc[r] == -1) {
+                anc[r] = (int32_t)j;
+                parent[r] = (int32_t)j;
+            }
+        }
+    }
+}
+
+// struct L(:,j) (strictly lower, sorted), columns in increasing order so
+// that children (always < parent) are complete before their parent.
+void symbolic(int64_t n, const Sym &S, const std::vector<int32_t> &par,
+              std::vector<int64_t> &Lp, std::vector<int32_t> &Li) {
+    std::vector<int64_t> chp(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j)
+        if (par[j] >= 0) chp[par[j] + 1]++;
+    for (int64_t j = 0; j < n; ++j) chp[j + 1] += chp[j];
+    std::vector<int32_t> ch(chp[n]);
+    {
+        std::vector<int64_t> f(chp.begin(), chp.end() - 1);
+        for (int64_t j = 0; j < n; ++j)
+            if (par[j] >= 0) ch[f[par[j]]++] = (int32_t)j;
+    }
+    std::vector<int64_t> mark(n, -1);
+    Lp.assign(n + 1, 0);
+    Li.clear();
+    std::vector<int32_t> col;
+    for (int64_t j = 0; j < n; ++j) {
+        col.clear();
+        mark[j] = j;
+        for (int64_t q = S.p[j]; q < S.p[j + 1]; ++q) {
+            const int32_t r = S.i[q];
+            if (r > j && mark[r] != j) { mark[r] = j; col.push_back(r); }
+        }
+        for (int64_t c = chp[j]; c < chp[j + 1]; ++c) {
+            const int32_t k = ch[c];
+            for (int64_t q = Lp[k]; q < Lp[k + 1]; ++q) {
+                const int32_t r = Li[q];
+                if (mark[r] != j) { mark[r] = j; col.push_back(r); }
+            }
+        }
+        std::sort(col.begin(), col.end());
+        Li.insert(Li.end(), col.begin(), col.end());
+        Lp[j + 1] = (int64_t)Li.size();
+    }
+}
+
+int64_t idx_of(int64_t s, int64_t N, int64_t S) { return (s * N) / S; }
+
+}  // namespace
+
+// Algorithm 2 (Section 4.2): count, for each row, the entries left of the
+// diagonal; growing the leading submatrix from i x i to (i+1) x (i+1) adds
+// row i's and (by symmetry) column i's off-diagonal entries plus the
+// diagonal, so blockptr[i+1] = blockptr[i] + 2 num[i] + 1.
+void diagonal_block_pointer(int64_t n, const int64_t *colptr,
+                            const int32_t *rowidx, int64_t *blockptr) {
+    std::vector<int64_t> num(n, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = colptr[i]; j < colptr[i + 1]; ++j) {
+            const int64_t index = rowidx[j];
+            if (index > i) num[index] += 1;
+        }
+    blockptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        num[i] = 2 * num[i] + 1;
+        blockptr[i + 1] = blockptr[i] + num[i];
+    }
+}
+
+// Section 4.3, Algorithm 3 over S samples of the percentage curve
+// pct(s) = bp[idx(s)] / bp[N], idx(s) = floor(s N / S).  The threshold is
+// the linear-profile slope step / S; the test
+// pct(i+step) - pct(i) >= step / S is evaluated exactly as
+// (bp[idx(i+step)] - bp[idx(i)]) * S >= step * bp[N].
+void irregular_blocking(int64_t N, const int64_t *bp, int32_t S, int32_t step,
+                        int32_t max_num, int32_t stride,
+                        std::vector<int64_t> &ptr) {
+    ptr.clear();
+    ptr.push_back(0);
+    const int64_t total = bp[N];
+    int32_t l = 0;
+    for (int64_t i = 0; i + step <= S; i += stride) {
+        const int64_t a = bp[idx_of(i, N, S)];
+        const int64_t b = bp[idx_of(i + step, N, S)];
+        bool mark;
+        if ((b - a) * (int64_t)S >= (int64_t)step * total) {
+            mark = true;                         // dense region
+        } else if (l >= max_num) {
+            mark = true;                         // bound the block size
+        } else {
+            mark = false;
+            ++l;
+        }
+        if (mark) {
+            const int64_t pos = idx_of(i + step, N, S);
+            if (pos > ptr.back()) ptr.push_back(pos);
+            l = 0;
+        }
+    }
+    if (ptr.back() < N) ptr.push_back(N);
+}
+
+}  // namespace slu
+
+using namespace slu;
+
+extern "C" void slu_opts_default(slu_opts *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->blocking = SLU_BLOCKING_IRREGULAR;
+    o->regular_block = 128;
+    o->sample_points = 1000;
+    o->step = 2;
+    o->max_num = 3;
+    o->stride = 1;
+    o->b_min = 32;
+    o->precision = SLU_PREC_FP64;
+    o->dense_threshold = 0.6;
+    o->pivot_perturb = 1;
+    o->pivot_tau_rel = 0.0;
+    o->refine_tol = 1e-14;
+    o->refine_max_iter = 0;
+    o->wait_budget_ms = 2000;
+}
+
+extern "C" const char *slu_last_error(void) { return g_err.c_str(); }
+
+static slu_status build_blocks(slu_plan &P) {
+    const int64_t n = P.n;
+    const int32_t p = P.p;
+    P.rowblk.assign(n, 0);
+    for (int32_t b = 0; b < p; ++b)
+        for (int64_t r = P.ptr[b]; r < P.ptr[b + 1]; ++r) P.rowblk[r] = b;
+    P.maxb = 0;
+    for (int32_t b = 0; b < p; ++b)
+        P.maxb = std::max<int32_t>(P.maxb, (int32_t)(P.ptr[b + 1] - P.ptr[b]));
+    if (P.maxb > 65535)
+        return fail(SLU_ERR_NOT_SUPPORTED, "block larger than 65535 rows");
+    // pass 1: non-empty blocks and their counts, block column by column
+    std::vector<int64_t> cnt(p, 0);
+    std::vector<int32_t> touched;
+    P.blocks.clear();
+    P.bnnz.clear();
+    std::vector<int64_t> bcol_first(p + 1, 0);   // first block id of col J
+    for (int32_t J = 0; J < p; ++J) {
+        touched.clear();
+        for (int64_t j = P.ptr[J]; j < P.ptr[J + 1]; ++j)
+            for (int64_t q = P.f_colptr[j]; q < P.f_colptr[j + 1]; ++q) {
+                const int32_t I = P.rowblk[P.f_rowidx[q]];
+                if (cnt[I]++ == 0) touched.push_back(I);
+            }
+        std::sort(touched.begin(), touched.end());
+        bcol_first[J] = (int64_t)P.blocks.size();
+        for (int32_t I : touched) {
+            BlockDesc d;
+            std::memset(&d, 0, sizeof(d));
+            d.I = I;
+            d.J = J;
+            d.rows = (int32_t)(P.ptr[I + 1] - P.ptr[I]);
+            d.cols = (int32_t)(P.ptr[J + 1] - P.ptr[J]);
+            d.r0 = (int32_t)P.ptr[I];
+            d.c0 = (int32_t)P.ptr[J];
+            d.dense = (double)cnt[I] >= P.opts.dense_threshold *
+                                            ((double)d.rows * (double)d.cols);
+            d.doff = d.goff = -1;
+            P.blocks.push_back(d);
+            P.bnnz.push_back(cnt[I]);
+            cnt[I] = 0;
+        }
+    }
+    bcol_first[p] = (int64_t)P.blocks.size();
+    const int64_t nb = (int64_t)P.blocks.size();
+    {
+        int64_t ncol = 0;
+        for (const BlockDesc &d : P.blocks)
+            if (!d.dense) ncol += d.cols + 1;
+        if (ncol > INT32_MAX)
+            return fail(SLU_ERR_NOT_SUPPORTED, "too many sparse block columns");
+    }
+    // storage layout
+    int64_t voff = 0, roff = 0, coff = 0, ndiag_slots = 0;
+    P.ndense = 0;
+    P.diagblk.assign(p, -1);
+    for (int64_t b = 0; b < nb; ++b) {
+        BlockDesc &d = P.blocks[b];
+        d.voff = voff;
+        if (d.dense) {
+            d.ld = d.rows;
+            d.roff = -1;
+            d.coff = -1;
+            voff += (int64_t)d.rows * d.cols;
+            P.ndense++;
+        } else {
+            d.ld = 0;
+            d.roff = roff;
+            d.coff = (int32_t)coff;
+            voff += P.bnnz[b];
+            roff += P.bnnz[b];
+            coff += d.cols + 1;
+        }
+        voff = (voff + 3) & ~int64_t(3);        // 32-byte aligned blocks
+        if (d.I == d.J) {
+            P.diagblk[d.I] = (int32_t)b;
+            d.doff = (int32_t)ndiag_slots;
+            ndiag_slots += d.rows;
+        }
+    }
+    P.storage = voff;
+    P.lcolptr.assign(coff, 0);
+    P.lrow.assign(roff, 0);
+    P.f2s.assign(P.f_colptr[n], 0);
+    P.dpos.assign(ndiag_slots, 0);
+    // pass 2: local CSC, filled -> storage map, diagonal positions
+    std::vector<int64_t> run(p, 0);             // running local position
+    std::vector<int32_t> bid(p, -1);
+    for (int32_t J = 0; J < p; ++J) {
+        for (int64_t b = bcol_first[J]; b < bcol_first[J + 1]; ++b) {
+            bid[P.blocks[b].I] = (int32_t)b;
+            run[P.blocks[b].I] = 0;
+        }
+        for (int64_t j = P.ptr[J]; j < P.ptr[J + 1]; ++j) {
+            const int32_t jj = (int32_t)(j - P.ptr[J]);
+            for (int64_t b = bcol_first[J]; b < bcol_first[J + 1]; ++b) {
+                const BlockDesc &d = P.blocks[b];
+                if (!d.dense) P.lcolptr[d.coff + jj] = (int32_t)run[d.I];
+            }
+            for (int64_t q = P.f_colptr[j]; q < P.f_colptr[j + 1]; ++q) {
+                const int32_t r = P.f_rowidx[q];
+                const int32_t I = P.rowblk[r];
+                const BlockDesc &d = P.blocks[bid[I]];
+                const int32_t rl = r - d.r0;
+                int64_t t;
+                if (d.dense) {
+                    t = (int64_t)jj * d.ld + rl;
+                } else {
+                    t = run[I]++;
+                    P.lrow[d.roff + t] = (uint16_t)rl;
+                }
+                P.f2s[q] = d.voff + t;
+                if (I == J && rl == jj)
+                    P.dpos[d.doff + jj] =
+                        d.dense ? rl : (int32_t)(t - P.lcolptr[d.coff + jj]);
+            }
+        }
+        for (int64_t b = bcol_first[J]; b < bcol_first[J + 1]; ++b) {
+            const BlockDesc &d = P.blocks[b];
+            if (!d.dense) P.lcolptr[d.coff + d.cols] = (int32_t)run[d.I];
+            bid[d.I] = -1;
+        }
+    }
+    // intra-diagonal-block column schedule: height(jj) = 1 + max height of
+    // the columns m < jj with U(m, jj) stored (0 if none); a column only
+    // reads columns of smaller height, so each height is one parallel group.
+    P.sched.assign(ndiag_slots, 0);
+    P.sgrp.clear();
+    std::vector<int32_t> h, order;
+    for (int32_t I = 0; I < p; ++I) {
+        BlockDesc &d = P.blocks[P.diagblk[I]];
+        const int32_t m = d.rows;
+        h.assign(m, 0);
+        int32_t hmax = 0;
+        for (int32_t jj = 0; jj < m; ++jj) {
+            int32_t best = -1;
+            if (d.dense) {
+                best = jj - 1;                  // dense: a chain
+            } else {
+                const int32_t s = P.lcolptr[d.coff + jj];
+                const int32_t dp = P.dpos[d.doff + jj];
+                for (int32_t t = 0; t < dp; ++t)
+                    best = std::max(best, h[P.lrow[d.roff + s + t]]);
+            }
+            h[jj] = best + 1;
+            hmax = std::max(hmax, h[jj]);
+        }
+        order.resize(m);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return h[a] < h[b]; });
+        d.goff = (int32_t)P.sgrp.size();
+        d.ngroups = m ? hmax + 1 : 0;
+        int32_t g = 0;
+        for (int32_t t = 0; t < m; ++t) {
+            P.sched[d.doff + t] = order[t];
+            while (g <= h[order[t]]) {
+                P.sgrp.push_back(t);
+                ++g;
+            }
+        }
+        P.sgrp.push_back(m);
+    }
+    return SLU_OK;
+}
+
+// Levels: level(I) = 0 if block row I has no non-empty block left of the
+// diagonal, else 1 + max level(I') over non-empty (I, I'), I' < I: the
+// longest chain of the task graph of Algorithm 1 restricted to non-empty
+// blocks (step I' writes into block row/column I exactly when (I, I') is
+// non-empty, the pattern being symmetric).  Tasks of a level:
+//   GETRF(I), GESSM(I,J) for non-empty (I,J), TSTRF(J,I) for non-empty
+//   (J,I), and SSSSM into every non-empty (K,J) with (K,I) and (I,J)
+//   non-empty, the sources of one target gathered in ascending I.
+static void build_levels_and_tasks(slu_plan &P) {
+    const int32_t p = P.p;
+    const int64_t nb = (int64_t)P.blocks.size();
+    std::vector<std::vector<int32_t>> lower_row(p), upper_row(p),
+        lower_col(p), upper_col(p);
+    for (int64_t b = 0; b < nb; ++b) {
+        const BlockDesc &d = P.blocks[b];
+        if (d.I > d.J) {
+            lower_row[d.I].push_back((int32_t)b);
+            lower_col[d.J].push_back((int32_t)b);
+        } else if (d.I < d.J) {
+            upper_row[d.I].push_back((int32_t)b);
+            upper_col[d.J].push_back((int32_t)b);
+        }
+    }
+    // blocks are sorted by (J, I): lower_col[J] and upper_col[J] ascend in
+    // I, lower_row[I] and upper_row[I] ascend in J.
+    P.level.assign(p, 0);
+    int32_t maxlev = -1;
+    for (int32_t I = 0; I < p; ++I) {
+        int32_t best = -1;
+        for (int32_t b : lower_row[I])
+            best = std::max(best, P.level[P.blocks[b].J]);
+        P.level[I] = best + 1;
+        maxlev = std::max(maxlev, P.level[I]);
+    }
+    P.nlevels = maxlev + 1;
+    auto find = [&](int32_t K, int32_t J) -> int32_t {
+        if (K == J) return P.diagblk[J];
+        const auto &w = (K > J) ? lower_col[J] : upper_col[J];
+        auto it = std::lower_bound(
+            w.begin(), w.end(), K,
+            [&](int32_t b, int32_t key) { return P.blocks[b].I < key; });
+        if (it != w.end() && P.blocks[*it].I == K) return *it;
+        return -1;
+    };
+    const int32_t L = P.nlevels;
+    std::vector<std::vector<int32_t>> lv_getrf(L), lv_gessm(L), lv_tstrf(L);
+    struct Tgt {
+        int32_t K, J, tb;
+        std::vector<int32_t> srcs;
+    };
+    std::vector<std::vector<Tgt>> lv_ss(L);
+    // walk block rows level by level (ascending I inside a level), so that
+    // a target's slot is only ever looked up within its own level
+    std::vector<std::vector<int32_t>> rows_of(L);
+    for (int32_t I = 0; I < p; ++I) rows_of[P.level[I]].push_back(I);
+    std::vector<int32_t> slot(nb, -1);
+    for (int32_t lv = 0; lv < L; ++lv) {
+        auto &vec = lv_ss[lv];
+        for (int32_t I : rows_of[lv]) {
+            const int32_t db = P.diagblk[I];
+            lv_getrf[lv].push_back(db);
+            for (int32_t b : upper_row[I]) {
+                lv_gessm[lv].push_back(b);
+                lv_gessm[lv].push_back(db);
+            }
+            for (int32_t b : lower_col[I]) {
+                lv_tstrf[lv].push_back(b);
+                lv_tstrf[lv].push_back(db);
+            }
+            for (int32_t lb : lower_col[I]) {
+                const int32_t K = P.blocks[lb].I;
+                for (int32_t ub : upper_row[I]) {
+                    const int32_t J = P.blocks[ub].J;
+                    const int32_t tb = find(K, J);
+                    if (tb < 0) continue;
+                    if (slot[tb] < 0) {
+                        slot[tb] = (int32_t)vec.size();
+                        vec.push_back(Tgt{K, J, tb, {}});
+                    }
+                    vec[slot[tb]].srcs.push_back(lb);
+                    vec[slot[tb]].srcs.push_back(ub);
+                }
+            }
+        }
+        for (const Tgt &t : vec) slot[t.tb] = -1;
+    }
+    P.getrf_off.assign(L + 1, 0);
+    P.gessm_off.assign(L + 1, 0);
+    P.tstrf_off.assign(L + 1, 0);
+    P.tgt_off.assign(L + 1, 0);
+    P.getrf.clear();
+    P.gessm.clear();
+    P.tstrf.clear();
+    P.tgt.clear();
+    P.src.clear();
+    P.srcoff.assign(1, 0);
+    for (int32_t lv = 0; lv < L; ++lv) {
+        P.getrf.insert(P.getrf.end(), lv_getrf[lv].begin(), lv_getrf[lv].end());
+        P.gessm.insert(P.gessm.end(), lv_gessm[lv].begin(), lv_gessm[lv].end());
+        P.tstrf.insert(P.tstrf.end(), lv_tstrf[lv].begin(), lv_tstrf[lv].end());
+        auto &vec = lv_ss[lv];
+        std::sort(vec.begin(), vec.end(), [](const Tgt &a, const Tgt &b) {
+            return a.K != b.K ? a.K < b.K : a.J < b.J;
+        });
+        for (auto &t : vec) {
+            P.tgt.push_back(t.tb);
+            P.src.insert(P.src.end(), t.srcs.begin(), t.srcs.end());
+            P.srcoff.push_back((int64_t)P.src.size() / 2);
+        }
+        P.getrf_off[lv + 1] = (int64_t)P.getrf.size();
+        P.gessm_off[lv + 1] = (int64_t)P.gessm.size() / 2;
+        P.tstrf_off[lv + 1] = (int64_t)P.tstrf.size() / 2;
+        P.tgt_off[lv + 1] = (int64_t)P.tgt.size();
+    }
+    auto flat = [&](std::vector<std::vector<int32_t>> &v,
+                    std::vector<int64_t> &off, std::vector<int32_t> &ids) {
+        off.assign(p + 1, 0);
+        ids.clear();
+        for (int32_t I = 0; I < p; ++I) {
+            ids.insert(ids.end(), v[I].begin(), v[I].end());
+            off[I + 1] = (int64_t)ids.size();
+        }
+    };
+    flat(lower_row, P.lrow_off, P.lrow_blk);
+    flat(upper_row, P.urow_off, P.urow_blk);
+    flat(upper_col, P.ucol_off, P.ucol_blk);
+    flat(lower_col, P.lcol_off, P.lcol_blk);
+}
+
+extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,
+                                  const int32_t *rowidx, const slu_opts *opts,
+                                  slu_plan **out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) return fail(SLU_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > INT32_MAX - 1)
+        return fail(SLU_ERR_INVALID_ARG, "n out of range");
+    if (!colptr || (n > 0 && !rowidx))
+        return fail(SLU_ERR_INVALID_ARG, "NULL pattern array");
+    slu_opts o;
+    if (opts) o = *opts;
+    else slu_opts_default(&o);
+    if (o.blocking != SLU_BLOCKING_IRREGULAR &&
+        o.blocking != SLU_BLOCKING_REGULAR)
+        return fail(SLU_ERR_INVALID_ARG, "unknown blocking");
+    if (o.blocking == SLU_BLOCKING_REGULAR && o.regular_block <= 0)
+        return fail(SLU_ERR_INVALID_ARG, "regular_block must be positive");
+    if (o.sample_points <= 0 || o.step <= 0 || o.max_num < 0 ||
+        o.stride <= 0 || o.b_min <= 0)
+        return fail(SLU_ERR_INVALID_ARG, "bad blocking parameters");
+    if (o.precision != SLU_PREC_FP64 && o.precision != SLU_PREC_FP32)
+        return fail(SLU_ERR_INVALID_ARG, "unknown precision");
+    if (!(o.dense_threshold >= 0.0))
+        return fail(SLU_ERR_INVALID_ARG, "dense_threshold must be >= 0");
+    if (colptr[0] != 0) return fail(SLU_ERR_INVALID_ARG, "colptr[0] must be 0");
+    for (int64_t j = 0; j < n; ++j)
+        if (colptr[j + 1] < colptr[j])
+            return fail(SLU_ERR_INVALID_ARG, "colptr not monotone");
+    const int64_t nnz = colptr[n];
+    {
+        std::vector<int64_t> seen(n, -1);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
+                const int32_t r = rowidx[q];
+                if (r < 0 || r >= n)
+                    return fail(SLU_ERR_INVALID_ARG, "row index out of range");
+                if (seen[r] == j)
+                    return fail(SLU_ERR_INVALID_ARG, "duplicate entry");
+                seen[r] = j;
+            }
+    }
+    slu_plan *P = new (std::nothrow) slu_plan();
+    if (!P) return fail(SLU_ERR_OUT_OF_MEMORY, "plan allocation");
+    try {
+        P->opts = o;
+        P->n = n;
+        P->nnz_a = nnz;
+        P->a_colptr.assign(colptr, colptr + n + 1);
+        P->a_rowidx.assign(rowidx, rowidx + nnz);
+        // CSR view of A for the residual
+        P->a_rowptr.assign(n + 1, 0);
+        for (int64_t q = 0; q < nnz; ++q) P->a_rowptr[rowidx[q] + 1]++;
+        for (int64_t i = 0; i < n; ++i) P->a_rowptr[i + 1] += P->a_rowptr[i];
+        P->a_colidx.resize(nnz);
+        P->a_vpos.resize(nnz);
+        {
+            std::vector<int64_t> f(P->a_rowptr.begin(), P->a_rowptr.end() - 1);
+            for (int64_t j = 0; j < n; ++j)
+                for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
+                    const int64_t at = f[rowidx[q]]++;
+                    P->a_colidx[at] = (int32_t)j;
+                    P->a_vpos[at] = q;
+                }
+        }
+        std::vector<int64_t> Lp;
+        std::vector<int32_t> Li;
+        {
+            Sym S;
+            symmetrize(n, colptr, rowidx, S);
+            P->nnz_sym = S.p[n];
+            std::vector<int32_t> parent;
+            etree(n, S, parent);
+            symbolic(n, S, parent, Lp, Li);
+        }
+        // filled L+U pattern: column j = U rows (k < j with j in L(:,k),
+        // ascending), the diagonal j, then L rows (ascending)
+        std::vector<int64_t> ucnt(n + 1, 0);
+        for (int64_t q = 0; q < Lp[n]; ++q) ucnt[Li[q] + 1]++;
+        P->f_colptr.assign(n + 1, 0);
+        for (int64_t j = 0; j < n; ++j)
+            P->f_colptr[j + 1] =
+                P->f_colptr[j] + ucnt[j + 1] + 1 + (Lp[j + 1] - Lp[j]);
+        P->f_rowidx.resize(P->f_colptr[n]);
+        {
+            std::vector<int64_t> f(P->f_colptr.begin(), P->f_colptr.end() - 1);
+            for (int64_t k = 0; k < n; ++k)
+                for (int64_t q = Lp[k]; q < Lp[k + 1]; ++q)
+                    P->f_rowidx[f[Li[q]]++] = (int32_t)k;
+            for (int64_t j = 0; j < n; ++j) {
+                P->f_rowidx[f[j]++] = (int32_t)j;
+                for (int64_t q = Lp[j]; q < Lp[j + 1]; ++q)
+                    P->f_rowidx[f[j]++] = Li[q];
+            }
+        }
+        // flops = sum_k (l_k + 2 l_k u_k); by symmetry u_k = l_k
+        P->flops = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t l = Lp[k + 1] - Lp[k];
+            P->flops += l + 2 * l * l;
+        }
+        std::vector<int64_t>().swap(Lp);
+        std::vector<int32_t>().swap(Li);
+        // Algorithm 2 on the filled pattern
+        P->blockptr.assign(n + 1, 0);
+        diagonal_block_pointer(n, P->f_colptr.data(), P->f_rowidx.data(),
+                               P->blockptr.data());
+        if (n == 0) {
+            P->ptr.assign(1, 0);
+            P->samples = 0;
+        } else if (o.blocking == SLU_BLOCKING_IRREGULAR) {
+            int64_t S_ = std::min<int64_t>(o.sample_points, n / o.b_min);
+            if (S_ < 1) S_ = 1;
+            P->samples = (int32_t)S_;
+            irregular_blocking(n, P->blockptr.data(), (int32_t)S_, o.step,
+                               o.max_num, o.stride, P->ptr);
+        } else {
+            P->ptr.clear();
+            for (int64_t r = 0; r < n; r += o.regular_block) P->ptr.push_back(r);
+            P->ptr.push_back(n);
+            P->samples = 0;
+        }
+        P->p = (int32_t)P->ptr.size() - 1;
+        const slu_status st = build_blocks(*P);
+        if (st != SLU_OK) {
+            delete P;
+            return st;
+        }
+        build_levels_and_tasks(*P);
+        // A entry -> storage slot, through the filled pattern
+        P->a2s.resize(nnz);
+        for (int64_t j = 0; j < n; ++j) {
+            const int32_t *b = P->f_rowidx.data() + P->f_colptr[j];
+            const int32_t *e = P->f_rowidx.data() + P->f_colptr[j + 1];
+            for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
+                const int32_t *it = std::lower_bound(b, e, rowidx[q]);
+                P->a2s[q] = P->f2s[P->f_colptr[j] + (it - b)];
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        delete P;
+        return fail(SLU_ERR_OUT_OF_MEMORY, "host allocation in analyze");
+    }
+    P->analyze_ms = std::chrono::duration<double, std::milli>(
+                        std::chrono::steady_clock::now() - t0).count();
+    *out = P;
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_plan_query(const slu_plan *P, slu_plan_info *info) {
+    if (!P || !info) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n = P->n;
+    info->nnz_a = P->nnz_a;
+    info->nnz_sym = P->nnz_sym;
+    info->nnz_lu = P->f_colptr.empty() ? 0 : P->f_colptr.back();
+    info->flops = P->flops;
+    info->nblocks_1d = P->p;
+    info->nlevels = P->nlevels;
+    info->nblocks = (int64_t)P->blocks.size();
+    info->ndense = P->ndense;
+    info->storage_elems = P->storage;
+    info->n_getrf = (int64_t)P->getrf.size();
+    info->n_gessm = (int64_t)P->gessm.size() / 2;
+    info->n_tstrf = (int64_t)P->tstrf.size() / 2;
+    info->n_ssssm_targets = (int64_t)P->tgt.size();
+    info->n_ssssm_pairs = (int64_t)P->src.size() / 2;
+    info->max_block = P->maxb;
+    info->samples = P->samples;
+    info->analyze_ms = P->analyze_ms;
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_plan_export(const slu_plan *P, int64_t *blockptr,
+                                      int64_t *ptr, int64_t *colptr,
+                                      int32_t *rowidx) {
+    if (!P) return fail(SLU_ERR_INVALID_ARG, "NULL plan");
+    if (blockptr)
+        std::memcpy(blockptr, P->blockptr.data(), P->blockptr.size() * 8);
+    if (ptr) std::memcpy(ptr, P->ptr.data(), P->ptr.size() * 8);
+    if (colptr) std::memcpy(colptr, P->f_colptr.data(), P->f_colptr.size() * 8);
+    if (rowidx) std::memcpy(rowidx, P->f_rowidx.data(), P->f_rowidx.size() * 4);
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_plan_export_blocks(const slu_plan *P, int32_t *bi,
+                                             int32_t *bj, int64_t *bnnz,
+                                             uint8_t *dense, int32_t *level) {
+    if (!P) return fail(SLU_ERR_INVALID_ARG, "NULL plan");
+    for (size_t b = 0; b < P->blocks.size(); ++b) {
+        if (bi) bi[b] = P->blocks[b].I;
+        if (bj) bj[b] = P->blocks[b].J;
+        if (bnnz) bnnz[b] = P->bnnz[b];
+        if (dense) dense[b] = (uint8_t)P->blocks[b].dense;
+    }
+    if (level) std::memcpy(level, P->level.data(), P->level.size() * 4);
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_plan_export_tasks(
+    const slu_plan *P, int64_t *getrf_off, int32_t *getrf, int64_t *gessm_off,
+    int32_t *gessm, int64_t *tstrf_off, int32_t *tstrf, int64_t *tgt_off,
+    int32_t *tgt, int64_t *srcoff, int32_t *src) {
+    if (!P) return fail(SLU_ERR_INVALID_ARG, "NULL plan");
+    const auto &B = P->blocks;
+    auto cp = [](int64_t *dst, const std::vector<int64_t> &v) {
+        if (dst) std::memcpy(dst, v.data(), v.size() * 8);
+    };
+    cp(getrf_off, P->getrf_off);
+    cp(gessm_off, P->gessm_off);
+    cp(tstrf_off, P->tstrf_off);
+    cp(tgt_off, P->tgt_off);
+    cp(srcoff, P->srcoff);
+    if (getrf)
+        for (size_t i = 0; i < P->getrf.size(); ++i) getrf[i] = B[P->getrf[i]].I;
+    if (gessm)
+        for (size_t i = 0; i < P->gessm.size() / 2; ++i) {
+            gessm[2 * i] = B[P->gessm[2 * i]].I;
+            gessm[2 * i + 1] = B[P->gessm[2 * i]].J;
+        }
+    if (tstrf)
+        for (size_t i = 0; i < P->tstrf.size() / 2; ++i) {
+            tstrf[2 * i] = B[P->tstrf[2 * i]].I;
+            tstrf[2 * i + 1] = B[P->tstrf[2 * i]].J;
+        }
+    if (tgt)
+        for (size_t i = 0; i < P->tgt.size(); ++i) {
+            tgt[2 * i] = B[P->tgt[i]].I;
+            tgt[2 * i + 1] = B[P->tgt[i]].J;
+        }
+    if (src)
+        for (size_t i = 0; i < P->src.size() / 2; ++i)
+            src[i] = B[P->src[2 * i]].J;
+    return SLU_OK;
+}
+
+extern "C" void slu_plan_destroy(slu_plan *P) {
+    if (!P) return;
+    free_dev_plan(P);
+    delete P;
+}

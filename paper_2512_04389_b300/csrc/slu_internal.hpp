@@ -1,0 +1,102 @@
+// Internal structures of the irregular-block sparse LU library.
+//
+// Host analysis (analyze.cpp) builds an `slu_plan`; the device code
+// (factor.cu, solve.cu) uploads its flat arrays once per plan and walks them.
+//
+// Storage of the factors.  The filled L+U pattern is cut by the block
+// boundaries `ptr` (Algorithm 3, or regular) into 2-D blocks; only non-empty
+// blocks are stored (Section 2.2: empty blocks are skipped).  Each block owns
+// a contiguous run of value slots starting at `voff`:
+//   dense  : column-major b_I x b_J tile, leading dimension `ld`; slots that
+//            are not in the symbolic pattern hold exact zeros, which stay
+//            zero through the factorization because the pattern is closed
+//            under fill;
+//   sparse : block-local CSC; column jj occupies local positions
+//            [lcolptr[coff+jj], lcolptr[coff+jj+1]) with 16-bit local row
+//            indices lrow[roff + pos] sorted ascending.
+// A diagonal block keeps L's strict lower part and U's upper part (with the
+// diagonal) of its rows and columns.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/slu.h"
+
+namespace slu {
+
+struct BlockDesc {         // 64 bytes, read by every kernel
+    int32_t I, J;          // block row, block column
+    int32_t rows, cols;    // b_I, b_J
+    int64_t voff;          // first value slot
+    int64_t roff;          // sparse: first local row index slot
+    int32_t coff;          // sparse: first local colptr slot (cols+1 of them)
+    int32_t ld;            // dense: leading dimension (== rows)
+    int32_t dense;         // 1 = dense tile
+    int32_t r0, c0;        // first global row / column of the block
+    int32_t doff;          // diagonal block: first dpos / sched slot
+    int32_t goff;          // diagonal block: first height-group slot
+    int32_t ngroups;       // diagonal block: number of height groups
+};
+static_assert(sizeof(BlockDesc) == 64, "BlockDesc layout");
+
+struct DevPlan;            // device mirror, defined in device_common.cuh
+
+}  // namespace slu
+
+struct slu_plan {
+    slu_opts opts;
+    int64_t n = 0, nnz_a = 0, nnz_sym = 0;
+    double analyze_ms = 0;
+    // input pattern (copied) and its CSR view for the FP64 residual
+    std::vector<int64_t> a_colptr;
+    std::vector<int32_t> a_rowidx;
+    std::vector<int64_t> a_rowptr;       // CSR of A
+    std::vector<int32_t> a_colidx;
+    std::vector<int64_t> a_vpos;         // CSR entry -> position in values
+    // filled, structurally symmetric L+U pattern (rows sorted)
+    std::vector<int64_t> f_colptr;
+    std::vector<int32_t> f_rowidx;
+    int64_t flops = 0;
+    // blocking
+    std::vector<int64_t> blockptr;       // Algorithm 2, n+1
+    std::vector<int64_t> ptr;            // boundaries, p+1
+    int32_t p = 0, samples = 0, maxb = 0;
+    std::vector<int32_t> rowblk;         // row -> block index
+    // blocks, sorted by (J, I)
+    std::vector<slu::BlockDesc> blocks;
+    std::vector<int64_t> bnnz;
+    std::vector<int32_t> diagblk;        // I -> block id of (I, I)
+    std::vector<int32_t> lcolptr;
+    std::vector<uint16_t> lrow;
+    std::vector<int32_t> dpos, sched, sgrp;
+    int64_t storage = 0;
+    int64_t ndense = 0;
+    // levels and tasks (block ids; the export calls translate to (I, J))
+    std::vector<int32_t> level;
+    int32_t nlevels = 0;
+    std::vector<int64_t> getrf_off, gessm_off, tstrf_off, tgt_off;
+    std::vector<int32_t> getrf;          // diag block ids
+    std::vector<int32_t> gessm;          // pairs (blk(I,J), blk(I,I))
+    std::vector<int32_t> tstrf;          // pairs (blk(J,I), blk(I,I))
+    std::vector<int32_t> tgt;            // target block ids
+    std::vector<int64_t> srcoff;         // per target, into src pairs
+    std::vector<int32_t> src;            // pairs (blk(K,I), blk(I,J))
+    // per diagonal block I: neighbour block lists for the solves
+    std::vector<int64_t> lrow_off, urow_off, ucol_off, lcol_off;
+    std::vector<int32_t> lrow_blk;       // (I, I'), I' < I
+    std::vector<int32_t> urow_blk;       // (I, J),  J > I
+    std::vector<int32_t> ucol_blk;       // (I', I), I' < I
+    std::vector<int32_t> lcol_blk;       // (K, I),  K > I
+    // value maps
+    std::vector<int64_t> a2s;            // A entry -> storage slot
+    std::vector<int64_t> f2s;            // filled entry -> storage slot
+    // device mirror (lazily uploaded)
+    slu::DevPlan *dev = nullptr;
+};
+
+namespace slu {
+void set_error(const std::string &msg);
+slu_status fail(slu_status st, const std::string &msg);
+void free_dev_plan(slu_plan *plan);
+}  // namespace slu

@@ -1,0 +1,280 @@
+"""Thin Python binding of the C ABI in ``include/slu.h`` (ctypes).
+
+Argument marshalling only: every step of analysis runs in the library's host
+code and every numerical step in its CUDA kernels.  torch supplies device
+memory and the current CUDA stream.  If ``libslu_b300.so`` is missing or
+cannot be loaded the import of this module raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libslu_b300.so")
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA_ERROR",
+          4: "SINGULAR", 5: "NOT_CONVERGED", 6: "TIMEOUT", 7: "NOT_SUPPORTED"}
+BLOCKING = {"irregular": 0, "regular": 1}
+PRECISION = {"fp64": 0, "fp32": 1}
+
+
+class SluError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"slu {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(C.Structure):
+    _fields_ = [("blocking", C.c_int32), ("regular_block", C.c_int32),
+                ("sample_points", C.c_int32), ("step", C.c_int32),
+                ("max_num", C.c_int32), ("stride", C.c_int32),
+                ("b_min", C.c_int32), ("precision", C.c_int32),
+                ("dense_threshold", C.c_double), ("pivot_perturb", C.c_int32),
+                ("pivot_tau_rel", C.c_double), ("refine_tol", C.c_double),
+                ("refine_max_iter", C.c_int32), ("wait_budget_ms", C.c_int64)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz_a", C.c_int64), ("nnz_sym", C.c_int64),
+                ("nnz_lu", C.c_int64), ("flops", C.c_int64),
+                ("nblocks_1d", C.c_int32), ("nlevels", C.c_int32),
+                ("nblocks", C.c_int64), ("ndense", C.c_int64),
+                ("storage_elems", C.c_int64), ("n_getrf", C.c_int64),
+                ("n_gessm", C.c_int64), ("n_tstrf", C.c_int64),
+                ("n_ssssm_targets", C.c_int64), ("n_ssssm_pairs", C.c_int64),
+                ("max_block", C.c_int32), ("samples", C.c_int32),
+                ("analyze_ms", C.c_double)]
+
+
+class FactorInfo(C.Structure):
+    _fields_ = [("nperturb", C.c_int64), ("tau", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("backward_error", C.c_double)]
+
+
+# every entry point declared in include/slu.h
+EXPORTS = ["slu_opts_default", "slu_analyze", "slu_plan_query",
+           "slu_plan_export", "slu_plan_export_blocks", "slu_plan_export_tasks",
+           "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
+           "slu_export_factors", "slu_plan_destroy", "slu_handle_destroy",
+           "slu_last_error"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with "
+            "`python -m paper_2512_04389_b300.build` (there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.slu_opts_default.argtypes = [C.POINTER(Opts)]
+    lib.slu_opts_default.restype = None
+    lib.slu_analyze.argtypes = [C.c_int64, P, P, C.POINTER(Opts), C.POINTER(P)]
+    lib.slu_plan_query.argtypes = [P, C.POINTER(PlanInfo)]
+    lib.slu_plan_export.argtypes = [P, P, P, P, P]
+    lib.slu_plan_export_blocks.argtypes = [P, P, P, P, P, P]
+    lib.slu_plan_export_tasks.argtypes = [P] + [P] * 10
+    lib.slu_factor.argtypes = [P, P, P, C.POINTER(P), C.POINTER(FactorInfo)]
+    lib.slu_refactor.argtypes = [P, P, P, C.POINTER(FactorInfo)]
+    lib.slu_solve.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
+                              C.POINTER(SolveInfo)]
+    lib.slu_solve_transpose.argtypes = [P, P, C.c_int64, C.c_int32, P,
+                                        C.c_int64, P]
+    lib.slu_export_factors.argtypes = [P, P, P]
+    lib.slu_plan_destroy.argtypes = [P]
+    lib.slu_plan_destroy.restype = None
+    lib.slu_handle_destroy.argtypes = [P]
+    lib.slu_handle_destroy.restype = None
+    lib.slu_last_error.argtypes = []
+    lib.slu_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("slu_opts_default", "slu_plan_destroy",
+                        "slu_handle_destroy", "slu_last_error"):
+            getattr(lib, name).restype = C.c_int
+    return lib
+
+
+lib = _load()
+
+
+def _check(st, ok=(0,)):
+    if st not in ok:
+        raise SluError(st, lib.slu_last_error().decode())
+    return st
+
+
+def _np(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_opts(**kw):
+    o = Opts()
+    lib.slu_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "blocking" and isinstance(v, str):
+            v = BLOCKING[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k not in dict(Opts._fields_):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t):
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"expected float64, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _colmajor(B):
+    """(tensor, leading dimension, columns, was_vector) in column-major."""
+    if B.dim() == 1:
+        Bc = B.contiguous()
+        return Bc, max(1, Bc.shape[0]), 1, True
+    n, k = B.shape
+    if B.stride(0) == 1 and (k == 1 or B.stride(1) >= n):
+        return B, (B.stride(1) if k > 1 else max(1, n)), k, False
+    Bc = B.t().contiguous().t()
+    return Bc, max(1, n), k, False
+
+
+def _colmajor_empty(n, k, device):
+    import torch
+    X = torch.empty((k, n), dtype=torch.float64, device=device).t()
+    return X, max(1, n)
+
+
+class Plan:
+    """Result of host analysis (``slu_analyze``) for one sparsity pattern."""
+
+    def __init__(self, n, colptr, rowidx, **opts):
+        self._h = C.c_void_p()
+        self.n = int(n)
+        self.colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+        self.rowidx = np.ascontiguousarray(rowidx, dtype=np.int32)
+        self.opts = default_opts(**opts)
+        _check(lib.slu_analyze(self.n, _np(self.colptr), _np(self.rowidx),
+                               C.byref(self.opts), C.byref(self._h)))
+        i = PlanInfo()
+        _check(lib.slu_plan_query(self._h, C.byref(i)))
+        self.info = {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.slu_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def export(self):
+        n, nnz, p = self.n, self.info["nnz_lu"], self.info["nblocks_1d"]
+        bp = np.empty(n + 1, np.int64)
+        ptr = np.empty(p + 1, np.int64)
+        cp = np.empty(n + 1, np.int64)
+        ri = np.empty(nnz, np.int32)
+        _check(lib.slu_plan_export(self._h, _np(bp), _np(ptr), _np(cp), _np(ri)))
+        return dict(blockptr=bp, ptr=ptr, colptr=cp, rowidx=ri)
+
+    def export_blocks(self):
+        nb, p = self.info["nblocks"], self.info["nblocks_1d"]
+        bi = np.empty(nb, np.int32)
+        bj = np.empty(nb, np.int32)
+        bn = np.empty(nb, np.int64)
+        de = np.empty(nb, np.uint8)
+        lv = np.empty(p, np.int32)
+        _check(lib.slu_plan_export_blocks(self._h, _np(bi), _np(bj), _np(bn),
+                                          _np(de), _np(lv)))
+        return dict(blocks=np.stack([bi, bj], 1), bnnz=bn,
+                    dense=de.astype(bool), level=lv)
+
+    def export_tasks(self):
+        I = self.info
+        L = I["nlevels"]
+        out = {k: np.empty(L + 1, np.int64) for k in
+               ("getrf_off", "gessm_off", "tstrf_off", "tgt_off")}
+        out["getrf"] = np.empty(I["n_getrf"], np.int32)
+        out["gessm"] = np.empty(2 * I["n_gessm"], np.int32)
+        out["tstrf"] = np.empty(2 * I["n_tstrf"], np.int32)
+        out["tgt"] = np.empty(2 * I["n_ssssm_targets"], np.int32)
+        out["srcoff"] = np.empty(I["n_ssssm_targets"] + 1, np.int64)
+        out["src"] = np.empty(I["n_ssssm_pairs"], np.int32)
+        _check(lib.slu_plan_export_tasks(
+            self._h, _np(out["getrf_off"]), _np(out["getrf"]),
+            _np(out["gessm_off"]), _np(out["gessm"]), _np(out["tstrf_off"]),
+            _np(out["tstrf"]), _np(out["tgt_off"]), _np(out["tgt"]),
+            _np(out["srcoff"]), _np(out["src"])))
+        return out
+
+
+class Factor:
+    """Factors of one matrix on the GPU (``slu_factor``)."""
+
+    def __init__(self, plan, values, stream=None, allow_singular=False):
+        self.plan = plan
+        self._h = C.c_void_p()
+        info = FactorInfo()
+        st = lib.slu_factor(plan._h, _dev_ptr(values), _stream_ptr(stream),
+                            C.byref(self._h), C.byref(info))
+        _check(st, (0, 4) if allow_singular else (0,))
+        self.singular = st == 4
+        self.values = values
+        self.nperturb = info.nperturb
+        self.tau = info.tau
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.slu_handle_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def refactor(self, values, stream=None, sync_info=False):
+        info = FactorInfo() if sync_info else None
+        _check(lib.slu_refactor(self._h, _dev_ptr(values), _stream_ptr(stream),
+                                C.byref(info) if info is not None else None))
+        self.values = values
+        if info is not None:
+            self.nperturb = info.nperturb
+
+    def solve(self, B, stream=None, info=False, allow_not_converged=False):
+        """X = A^{-1} B for a CUDA float64 tensor B of shape (n,) or (n, k)."""
+        Bc, ldb, k, vec = _colmajor(B)
+        X, ldx = _colmajor_empty(Bc.shape[0], k, Bc.device)
+        si = SolveInfo()
+        st = lib.slu_solve(self._h, _dev_ptr(Bc), ldb, k, _dev_ptr(X), ldx,
+                           _stream_ptr(stream), C.byref(si) if info else None)
+        _check(st, (0, 5) if allow_not_converged else (0,))
+        out = X.reshape(-1) if vec else X
+        if info:
+            return out, {"iterations": si.iterations,
+                         "backward_error": si.backward_error,
+                         "converged": st == 0}
+        return out
+
+    def solve_transpose(self, G, stream=None):
+        """Lam = A^{-T} G through the stored factors."""
+        Gc, ldg, k, vec = _colmajor(G)
+        L, ldl = _colmajor_empty(Gc.shape[0], k, Gc.device)
+        _check(lib.slu_solve_transpose(self._h, _dev_ptr(Gc), ldg, k,
+                                       _dev_ptr(L), ldl, _stream_ptr(stream)))
+        return L.reshape(-1) if vec else L
+
+    def export_factors(self, stream=None):
+        """Factor values (FP64) in the order of ``plan.export()``'s pattern."""
+        import torch
+        out = torch.empty(self.plan.info["nnz_lu"], dtype=torch.float64,
+                          device="cuda")
+        _check(lib.slu_export_factors(self._h, _dev_ptr(out),
+                                      _stream_ptr(stream)))
+        return out

@@ -11,6 +11,13 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line(
         "markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+    # build the in-tree library (git-ignored) and the oracle's C part
+    import shutil
+    from oracle.build import build as build_oracle
+    build_oracle()
+    if shutil.which("nvcc"):
+        from paper_2512_04389_b300.build import build as build_lib
+        build_lib()
 
 
 def brute_fill(P):

@@ -1,0 +1,118 @@
+"""Host analysis of the library (C ABI, no GPU needed) against the oracle's
+independent plan code: filled pattern, diagonal block pointer (Algorithm 2),
+block boundaries (Algorithm 3 / regular), block list, dense flags, levels and
+every task list must be bit-exact."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import lu as OL, plan as OP
+
+S = pytest.importorskip("paper_2512_04389_b300.slu")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "slu.h")).read()
+    declared = set(re.findall(r"\b(slu_[a-z_]+)\s*\(", hdr))
+    assert declared == set(S.EXPORTS)
+    for name in declared:
+        assert hasattr(S.lib, name), name
+
+
+CASES = [
+    ("grid5_48 irregular", lambda: workloads.grid5(48), {}),
+    ("grid5_48 regular64", lambda: workloads.grid5(48),
+     dict(blocking="regular", regular_block=64)),
+    ("grid5_48 stride2", lambda: workloads.grid5(48), dict(stride=2)),
+    ("grid7cd_12 bmin8", lambda: workloads.grid7_cd(12, nrhs=1), dict(b_min=8)),
+    ("grid7theta_10", lambda: workloads.grid7_theta(10), dict(b_min=16)),
+    ("circuit_3000", lambda: workloads.circuit_bbd(
+        n=3000, border=60, block_lo=16, block_hi=64), dict(b_min=16)),
+    ("grid5_7 tiny", lambda: workloads.grid5(7), dict(b_min=4)),
+    ("dense threshold 0", lambda: workloads.grid5(20), dict(dense_threshold=0.0,
+                                                             b_min=8)),
+]
+
+
+@pytest.mark.parametrize("name,mk,opts", CASES, ids=[c[0] for c in CASES])
+def test_plan_bit_exact(name, mk, opts):
+    s = mk()
+    P = S.Plan(s.n, s.colptr, s.rowidx, **opts)
+    o = S.default_opts(**opts)
+    F = OL.lu(s.n, s.colptr, s.rowidx, s.values)
+    pp, pr, _ = OL.lu_pattern(F)
+    e = P.export()
+    assert np.array_equal(e["colptr"], pp)
+    assert np.array_equal(e["rowidx"], pr)
+    bp = OP.blockptr(s.n, pp, pr)
+    assert np.array_equal(e["blockptr"], bp)
+    if o.blocking == 0:
+        ptr = OP.irregular_ptr(bp, s.n, o.sample_points, o.step, o.max_num,
+                               o.stride, o.b_min)
+        assert P.info["samples"] == OP.num_samples(s.n, o.sample_points,
+                                                  o.b_min)
+    else:
+        ptr = OP.regular_ptr(s.n, o.regular_block)
+    assert np.array_equal(e["ptr"], ptr)
+    assert P.info["flops"] == OL.flops(F)
+    pl = OP.block_plan(s.n, pp, pr, ptr, o.dense_threshold)
+    b = P.export_blocks()
+    assert np.array_equal(b["blocks"], pl["blocks"])
+    assert np.array_equal(b["bnnz"], pl["bnnz"])
+    assert np.array_equal(b["dense"], pl["dense"])
+    assert np.array_equal(b["level"], pl["level"])
+    t = P.export_tasks()
+    assert P.info["nlevels"] == pl["nlevels"]
+    for lv in range(pl["nlevels"]):
+        g = t["getrf"][t["getrf_off"][lv]:t["getrf_off"][lv + 1]]
+        assert g.tolist() == pl["getrf"][lv]
+        ge = t["gessm"][2 * t["gessm_off"][lv]:2 * t["gessm_off"][lv + 1]]
+        assert [tuple(x) for x in ge.reshape(-1, 2).tolist()] == pl["gessm"][lv]
+        ts = t["tstrf"][2 * t["tstrf_off"][lv]:2 * t["tstrf_off"][lv + 1]]
+        # tasks of one level are independent: compare as sorted lists
+        assert sorted(tuple(x) for x in ts.reshape(-1, 2).tolist()) == \
+            pl["tstrf"][lv]
+        tg = t["tgt"].reshape(-1, 2)
+        got = []
+        for k in range(t["tgt_off"][lv], t["tgt_off"][lv + 1]):
+            srcs = t["src"][t["srcoff"][k]:t["srcoff"][k + 1]].tolist()
+            got.append((tuple(tg[k].tolist()), srcs))
+        assert got == pl["ssssm"][lv]
+
+
+@pytest.mark.parametrize("bad", ["dup", "range", "colptr"])
+def test_analyze_rejects_bad_patterns(bad):
+    cp = np.array([0, 2, 3], np.int64)
+    ri = np.array([0, 1, 1], np.int32)
+    if bad == "dup":
+        ri = np.array([0, 0, 1], np.int32)
+    elif bad == "range":
+        ri = np.array([0, 2, 1], np.int32)
+    else:
+        cp = np.array([0, 3, 2], np.int64)
+    with pytest.raises(S.SluError) as e:
+        S.Plan(2, cp, ri)
+    assert e.value.status == 1
+
+
+def test_analyze_rejects_bad_options():
+    s = workloads.grid5(4)
+    with pytest.raises(S.SluError):
+        S.Plan(s.n, s.colptr, s.rowidx, step=0)
+    with pytest.raises(S.SluError):
+        S.Plan(s.n, s.colptr, s.rowidx, blocking="regular", regular_block=0)
+
+
+def test_empty_and_single():
+    P = S.Plan(0, np.zeros(1, np.int64), np.zeros(0, np.int32))
+    assert P.info["nblocks_1d"] == 0 and P.info["nlevels"] == 0
+    P = S.Plan(1, np.array([0, 1]), np.array([0]))
+    assert P.info["nnz_lu"] == 1 and P.info["nblocks_1d"] == 1
+    # an entirely empty column still gets its diagonal
+    P = S.Plan(3, np.array([0, 1, 1, 2]), np.array([0, 2]))
+    assert P.info["nnz_sym"] == 3
