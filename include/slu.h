@@ -114,6 +114,23 @@ typedef struct {
                                     when not computed                       */
 } slu_solve_info;
 
+/* Kernel classes for slu_stats. */
+enum {
+    SLU_KC_PREP = 0,             /* max|A|, ||A||_inf, value scatter        */
+    SLU_KC_GETRF = 1,
+    SLU_KC_PANEL = 2,            /* GESSM + TSTRF                           */
+    SLU_KC_SSSSM = 3,
+    SLU_KC_SOLVE = 4,            /* triangular sweeps                       */
+    SLU_KC_RESID = 5,            /* residual, norms, update                 */
+    SLU_KC_COUNT = 6
+};
+
+typedef struct {
+    int64_t launches;            /* kernels launched through this handle    */
+    int64_t calls[SLU_KC_COUNT]; /* launches per class while profiling      */
+    double ms[SLU_KC_COUNT];     /* summed CUDA-event durations per class   */
+} slu_stats;
+
 typedef struct slu_plan slu_plan;
 typedef struct slu_handle slu_handle;
 
@@ -200,6 +217,20 @@ slu_status slu_solve_transpose(const slu_handle *h, const double *G,
  * colptr/rowidx): rows < col hold U, the diagonal holds U's, rows > col hold
  * L.  out: device float64[nnz_lu]. */
 slu_status slu_export_factors(const slu_handle *h, double *out, void *stream);
+
+/* Profiling: while enabled, every kernel launch of the handle is bracketed
+ * by a pair of CUDA events on its stream, and slu_handle_stats sums their
+ * durations per kernel class (it synchronizes on the last event).  Enabling
+ * clears the accumulated figures; the launch counter runs always. */
+slu_status slu_set_profiling(slu_handle *h, int32_t enable);
+slu_status slu_handle_stats(slu_handle *h, slu_stats *out);
+
+/* Algorithmic flops of the factorization by kernel class, from the filled
+ * pattern: with l_k the entries of L(:,k) inside k's diagonal block and
+ * l'_k those below it, GETRF does l_k + 2 l_k^2, GESSM + TSTRF
+ * l'_k + 4 l_k l'_k and SSSSM 2 l'_k^2 (they sum to l + 2 l^2 per column).
+ * out: host double[3] = {getrf, panel, ssssm}. */
+slu_status slu_plan_flops(const slu_plan *plan, double *out);
 
 void slu_plan_destroy(slu_plan *plan);
 void slu_handle_destroy(slu_handle *h);

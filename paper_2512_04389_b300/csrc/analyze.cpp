@@ -635,6 +635,19 @@ extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,
             return st;
         }
         build_levels_and_tasks(*P);
+        // flops per kernel class from the block of each column's rows
+        for (int64_t k = 0; k < n; ++k) {
+            const int32_t I = P->rowblk[k];
+            double lin = 0, lout = 0;
+            for (int64_t q = P->f_colptr[k]; q < P->f_colptr[k + 1]; ++q) {
+                const int32_t r = P->f_rowidx[q];
+                if (r <= k) continue;
+                if (P->rowblk[r] == I) lin += 1; else lout += 1;
+            }
+            P->flops_cls[0] += lin + 2 * lin * lin;
+            P->flops_cls[1] += lout + 4 * lin * lout;
+            P->flops_cls[2] += 2 * lout * lout;
+        }
         // A entry -> storage slot, through the filled pattern
         P->a2s.resize(nnz);
         for (int64_t j = 0; j < n; ++j) {
@@ -739,6 +752,12 @@ extern "C" slu_status slu_plan_export_tasks(
     if (src)
         for (size_t i = 0; i < P->src.size() / 2; ++i)
             src[i] = B[P->src[2 * i]].J;
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_plan_flops(const slu_plan *P, double *out) {
+    if (!P || !out) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
+    for (int c = 0; c < 3; ++c) out[c] = P->flops_cls[c];
     return SLU_OK;
 }
 

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "slu_internal.hpp"
 
@@ -87,4 +88,37 @@ struct slu_handle {
     double *work = nullptr;
     int64_t work_elems = 0;
     double *red = nullptr;               // reduction scratch for refinement
+    // launch accounting and optional per-launch event timing
+    int64_t launches = 0;
+    bool profiling = false;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    int64_t calls[SLU_KC_COUNT] = {0};
+    double ms[SLU_KC_COUNT] = {0};
 };
+
+namespace slu {
+// Brackets one kernel launch: counts it and, when profiling, records a
+// pair of events around it on `st`.
+struct LaunchScope {
+    slu_handle *h;
+    int cls;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchScope(const slu_handle *hc, int c, cudaStream_t s)
+        : h(const_cast<slu_handle *>(hc)), cls(c), st(s) {
+        h->launches++;
+        if (h->profiling) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~LaunchScope() {
+        if (a) {
+            cudaEventRecord(b, st);
+            h->recs.push_back({cls, a, b});
+        }
+    }
+};
+}  // namespace slu

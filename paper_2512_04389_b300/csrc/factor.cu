@@ -381,17 +381,26 @@ static slu_status run_factor(slu_handle *h, const double *values,
                  "cudaMemsetAsync(cnt)"))
         return SLU_ERR_CUDA;
     if (P->nnz_a > 0) {
-        k_maxabs<<<grid_for(P->nnz_a, 256), 256, 0, st>>>(
-            P->nnz_a, values, reinterpret_cast<unsigned long long *>(h->scal));
-        k_anorm<<<(int)((P->n + 255) / 256), 256, 0, st>>>(
-            P->n, D->a_rowptr, D->a_vpos, values,
-            reinterpret_cast<unsigned long long *>(h->scal + 1));
+        {
+            LaunchScope ls_(h, SLU_KC_PREP, st);
+            k_maxabs<<<grid_for(P->nnz_a, 256), 256, 0, st>>>(
+                P->nnz_a, values, reinterpret_cast<unsigned long long *>(h->scal));
+        }
+        {
+            LaunchScope ls_(h, SLU_KC_PREP, st);
+            k_anorm<<<(int)((P->n + 255) / 256), 256, 0, st>>>(
+                P->n, D->a_rowptr, D->a_vpos, values,
+                reinterpret_cast<unsigned long long *>(h->scal + 1));
+        }
         if (!cuda_ok(cudaMemcpyAsync(h->a_vals, values, P->nnz_a * sizeof(double),
                                      cudaMemcpyDeviceToDevice, st),
                      "cudaMemcpyAsync(A)"))
             return SLU_ERR_CUDA;
-        k_scatter<T><<<grid_for(P->nnz_a, 256), 256, 0, st>>>(P->nnz_a, D->a2s,
-                                                            values, val);
+        {
+            LaunchScope ls_(h, SLU_KC_PREP, st);
+            k_scatter<T><<<grid_for(P->nnz_a, 256), 256, 0, st>>>(P->nnz_a, D->a2s,
+                                                                values, val);
+        }
     }
     const size_t smem_f = (size_t)kWarps * P->maxb * sizeof(double);
     const size_t smem_a = (size_t)kWarps * P->maxb * sizeof(Acc);
@@ -399,18 +408,24 @@ static slu_status run_factor(slu_handle *h, const double *values,
         return SLU_ERR_CUDA;
     for (int lv = 0; lv < P->nlevels; ++lv) {
         const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
-        if (g1 > g0)
-            k_getrf<T><<<(int)(g1 - g0), kThreads, smem_f, st>>>(
-                D->getrf + g0, a, val, h->scal, h->tau_rel, h->cnt);
+        if (g1 > g0) {
+                LaunchScope ls_(h, SLU_KC_GETRF, st);
+                k_getrf<T><<<(int)(g1 - g0), kThreads, smem_f, st>>>(
+                    D->getrf + g0, a, val, h->scal, h->tau_rel, h->cnt);
+            }
         const int64_t e0 = P->gessm_off[lv], e1 = P->gessm_off[lv + 1];
         const int64_t t0 = P->tstrf_off[lv], t1 = P->tstrf_off[lv + 1];
-        if (e1 - e0 + t1 - t0 > 0)
-            k_panel<T, Acc><<<(int)(e1 - e0 + t1 - t0), kThreads, smem_a, st>>>(
-                D->gessm + 2 * e0, (int)(e1 - e0), D->tstrf + 2 * t0, a, val);
+        if (e1 - e0 + t1 - t0 > 0) {
+                LaunchScope ls_(h, SLU_KC_PANEL, st);
+                k_panel<T, Acc><<<(int)(e1 - e0 + t1 - t0), kThreads, smem_a, st>>>(
+                    D->gessm + 2 * e0, (int)(e1 - e0), D->tstrf + 2 * t0, a, val);
+            }
         const int64_t s0 = P->tgt_off[lv], s1 = P->tgt_off[lv + 1];
-        if (s1 > s0)
-            k_ssssm<T, Acc><<<(int)(s1 - s0), kThreads, smem_a, st>>>(
-                D->tgt + s0, D->srcoff + s0, D->src, a, val);
+        if (s1 > s0) {
+                LaunchScope ls_(h, SLU_KC_SSSSM, st);
+                k_ssssm<T, Acc><<<(int)(s1 - s0), kThreads, smem_a, st>>>(
+                    D->tgt + s0, D->srcoff + s0, D->src, a, val);
+            }
     }
     if (!cuda_ok(cudaGetLastError(), "factor launch")) return SLU_ERR_CUDA;
     return SLU_OK;
@@ -448,6 +463,10 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (h->device >= 0) cudaSetDevice(h->device);
+    for (auto &r : h->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
     void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -508,6 +527,44 @@ extern "C" slu_status slu_refactor(slu_handle *h, const double *values,
     return SLU_OK;
 }
 
+extern "C" slu_status slu_set_profiling(slu_handle *h, int32_t enable) {
+    if (!h) return fail(SLU_ERR_INVALID_ARG, "NULL handle");
+    for (auto &r : h->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    h->recs.clear();
+    for (int c = 0; c < SLU_KC_COUNT; ++c) {
+        h->calls[c] = 0;
+        h->ms[c] = 0.0;
+    }
+    h->profiling = enable != 0;
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_handle_stats(slu_handle *h, slu_stats *out) {
+    if (!h || !out) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
+    if (!h->recs.empty() &&
+        !cuda_ok(cudaEventSynchronize(h->recs.back().b), "cudaEventSynchronize"))
+        return SLU_ERR_CUDA;
+    for (auto &r : h->recs) {
+        float t = 0.f;
+        if (!cuda_ok(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime"))
+            return SLU_ERR_CUDA;
+        h->calls[r.cls]++;
+        h->ms[r.cls] += t;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    h->recs.clear();
+    out->launches = h->launches;
+    for (int c = 0; c < SLU_KC_COUNT; ++c) {
+        out->calls[c] = h->calls[c];
+        out->ms[c] = h->ms[c];
+    }
+    return SLU_OK;
+}
+
 extern "C" slu_status slu_export_factors(const slu_handle *h, double *out,
                                          void *stream) {
     if (!h || !out) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
@@ -515,6 +572,7 @@ extern "C" slu_status slu_export_factors(const slu_handle *h, double *out,
     const int64_t nnz = P->f_colptr[P->n];
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (nnz == 0) return SLU_OK;
+    LaunchScope ls_(h, SLU_KC_PREP, s);
     if (h->prec == SLU_PREC_FP64)
         k_export<double><<<grid_for(nnz, 256), 256, 0, s>>>(
             nnz, P->dev->f2s, static_cast<const double *>(h->storage), out);

@@ -58,6 +58,7 @@ struct slu_plan {
     std::vector<int64_t> f_colptr;
     std::vector<int32_t> f_rowidx;
     int64_t flops = 0;
+    double flops_cls[3] = {0, 0, 0};     // getrf, panel, ssssm
     // blocking
     std::vector<int64_t> blockptr;       // Algorithm 2, n+1
     std::vector<int64_t> ptr;            // boundaries, p+1

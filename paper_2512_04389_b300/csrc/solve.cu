@@ -338,9 +338,11 @@ static slu_status sweep(const slu_handle *h, Sweep sw, double *X, int64_t ldx,
     for (int k = 0; k < P->nlevels; ++k) {
         const int lv = up ? k : P->nlevels - 1 - k;
         const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
-        if (g1 > g0)
+        if (g1 > g0) {
+            LaunchScope ls_(h, SLU_KC_SOLVE, st);
             kern<<<(int)(g1 - g0), kThreads, smem, st>>>(D->getrf + g0, a, val,
                                                        off, blk, X, ldx, nrhs);
+        }
     }
     return cuda_ok(cudaGetLastError(), "solve launch") ? SLU_OK : SLU_ERR_CUDA;
 }
@@ -391,14 +393,21 @@ static slu_status backward_error(slu_handle *h, const double *B, int64_t ldb,
     const slu_plan *P = h->plan;
     const DevPlan *D = P->dev;
     const int64_t n = P->n;
-    k_residual<<<(int)((n * 32 + 255) / 256), 256, 0, st>>>(
+    {
+        LaunchScope ls_(h, SLU_KC_RESID, st);
+        k_residual<<<(int)((n * 32 + 255) / 256), 256, 0, st>>>(
         n, nrhs, D->a_rowptr, D->a_colidx, D->a_vpos, h->a_vals, B, ldb, X, ldx,
         R, n);
+    }
     if (!cuda_ok(cudaMemsetAsync(h->red, 0, 3 * nrhs * sizeof(double), st),
                  "cudaMemsetAsync"))
         return SLU_ERR_CUDA;
-    k_norms<<<148 * 2, 256, 0, st>>>(n, nrhs, R, n, X, ldx, B, ldb,
-                                     reinterpret_cast<unsigned long long *>(h->red));
+    {
+        LaunchScope ls_(h, SLU_KC_RESID, st);
+        k_norms<<<148 * 2, 256, 0, st>>>(
+            n, nrhs, R, n, X, ldx, B, ldb,
+            reinterpret_cast<unsigned long long *>(h->red));
+    }
     double hr[3 * 64 + 1];
     if (!cuda_ok(cudaMemcpyAsync(hr, h->red, 3 * nrhs * sizeof(double),
                                  cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
@@ -469,7 +478,10 @@ extern "C" slu_status slu_solve(const slu_handle *ch, const double *B,
         if (be <= P->opts.refine_tol || it >= maxit) break;
         s = solve_inplace(h, R, n, nrhs, false, st);
         if (s != SLU_OK) return s;
-        k_add_cols<<<148 * 4, 256, 0, st>>>(n, nrhs, R, n, X, ldx);
+        {
+            LaunchScope ls_(h, SLU_KC_RESID, st);
+            k_add_cols<<<148 * 4, 256, 0, st>>>(n, nrhs, R, n, X, ldx);
+        }
         ++it;
     }
     if (info) {

@@ -57,11 +57,20 @@ class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("backward_error", C.c_double)]
 
 
+KERNEL_CLASSES = ["prep", "getrf", "panel", "ssssm", "solve", "resid"]
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("calls", C.c_int64 * 6),
+                ("ms", C.c_double * 6)]
+
+
 # every entry point declared in include/slu.h
 EXPORTS = ["slu_opts_default", "slu_analyze", "slu_plan_query",
            "slu_plan_export", "slu_plan_export_blocks", "slu_plan_export_tasks",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
-           "slu_export_factors", "slu_plan_destroy", "slu_handle_destroy",
+           "slu_export_factors", "slu_set_profiling", "slu_handle_stats",
+           "slu_plan_flops", "slu_plan_destroy", "slu_handle_destroy",
            "slu_last_error"]
 
 
@@ -86,6 +95,9 @@ def _load():
     lib.slu_solve_transpose.argtypes = [P, P, C.c_int64, C.c_int32, P,
                                         C.c_int64, P]
     lib.slu_export_factors.argtypes = [P, P, P]
+    lib.slu_set_profiling.argtypes = [P, C.c_int32]
+    lib.slu_handle_stats.argtypes = [P, C.POINTER(Stats)]
+    lib.slu_plan_flops.argtypes = [P, P]
     lib.slu_plan_destroy.argtypes = [P]
     lib.slu_plan_destroy.restype = None
     lib.slu_handle_destroy.argtypes = [P]
@@ -179,6 +191,12 @@ class Plan:
             lib.slu_plan_destroy(self._h)
             self._h = C.c_void_p()
 
+    def flops_by_class(self):
+        """Algorithmic flops {getrf, panel, ssssm} of the factorization."""
+        out = np.zeros(3)
+        _check(lib.slu_plan_flops(self._h, _np(out)))
+        return dict(zip(("getrf", "panel", "ssssm"), out.tolist()))
+
     def export(self):
         n, nnz, p = self.n, self.info["nnz_lu"], self.info["nblocks_1d"]
         bp = np.empty(n + 1, np.int64)
@@ -269,6 +287,17 @@ class Factor:
         _check(lib.slu_solve_transpose(self._h, _dev_ptr(Gc), ldg, k,
                                        _dev_ptr(L), ldl, _stream_ptr(stream)))
         return L.reshape(-1) if vec else L
+
+    def set_profiling(self, enable=True):
+        _check(lib.slu_set_profiling(self._h, 1 if enable else 0))
+
+    def stats(self):
+        """Launch count and, while profiling, per-class event times (ms)."""
+        st = Stats()
+        _check(lib.slu_handle_stats(self._h, C.byref(st)))
+        return {"launches": st.launches,
+                "calls": dict(zip(KERNEL_CLASSES, list(st.calls))),
+                "ms": dict(zip(KERNEL_CLASSES, list(st.ms)))}
 
     def export_factors(self, stream=None):
         """Factor values (FP64) in the order of ``plan.export()``'s pattern."""

@@ -1,0 +1,210 @@
+"""GPU parity: the library's factors and solves against the CPU oracle on the
+same seeded inputs, through the C ABI.
+
+Tolerances (FP64 path): max|dL, dU| / max|L, U| <= 1e-10 and solve backward
+error <= 1e-13; FP32 factors refined in FP64 must reach backward error
+<= 1e-14 (their factor error against the oracle is reported, not bounded
+beyond what refinement needs)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import lu as OL
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+S = pytest.importorskip("paper_2512_04389_b300.slu")
+
+FP64_TOL = 1e-10
+
+
+def _dev(x):
+    return torch.as_tensor(np.asarray(x), dtype=torch.float64, device="cuda")
+
+
+def gpu_factor(s, **opts):
+    P = S.Plan(s.n, s.colptr, s.rowidx, **opts)
+    F = S.Factor(P, _dev(s.values))
+    return P, F
+
+
+def oracle_factor(s):
+    F = OL.lu(s.n, s.colptr, s.rowidx, s.values)
+    pp, pr, pv = OL.lu_pattern(F)
+    return F, pp, pr, pv
+
+
+def factor_error(P, F, pv):
+    got = F.export_factors().cpu().numpy()
+    return np.abs(got - pv).max() / np.abs(pv).max()
+
+
+CASES = [
+    ("grid5_48", lambda: workloads.grid5(48), {}),
+    ("grid5_48 regular64", lambda: workloads.grid5(48),
+     dict(blocking="regular", regular_block=64)),
+    ("grid5_48 stride2", lambda: workloads.grid5(48), dict(stride=2)),
+    ("grid5_48 all dense", lambda: workloads.grid5(48),
+     dict(dense_threshold=0.0)),
+    ("grid5_48 all sparse", lambda: workloads.grid5(48),
+     dict(dense_threshold=2.0)),
+    ("grid7cd_14", lambda: workloads.grid7_cd(14, nrhs=4), dict(b_min=16)),
+    ("grid7theta_12", lambda: workloads.grid7_theta(12), dict(b_min=16)),
+    ("circuit_4000", lambda: workloads.circuit_bbd(
+        n=4000, border=80, block_lo=16, block_hi=64), dict(b_min=16)),
+    ("grid5_7 ragged", lambda: workloads.grid5(7), dict(b_min=3)),
+    ("grid5_30 regular37", lambda: workloads.grid5(30),
+     dict(blocking="regular", regular_block=37)),
+]
+
+
+@pytest.mark.parametrize("name,mk,opts", CASES, ids=[c[0] for c in CASES])
+def test_fp64_factor_and_solve_parity(name, mk, opts):
+    s = mk()
+    P, F = gpu_factor(s, **opts)
+    Fo, pp, pr, pv = oracle_factor(s)
+    e = P.export()
+    assert np.array_equal(e["colptr"], pp) and np.array_equal(e["rowidx"], pr)
+    assert factor_error(P, F, pv) <= FP64_TOL
+    assert F.nperturb == 0
+    X, info = F.solve(_dev(s.rhs), info=True)
+    Xo = OL.solve(Fo, s.rhs)
+    Xg = X.cpu().numpy()
+    assert np.abs(Xg - Xo).max() / np.abs(Xo).max() <= 1e-10
+    be = OL.backward_error(s.n, s.colptr, s.rowidx, s.values, Xg, s.rhs)
+    assert be <= 1e-13
+    assert abs(info["backward_error"] - be) <= 1e-15 + 0.01 * be
+    G = np.random.default_rng(1).standard_normal((s.n, 2))
+    Lam = F.solve_transpose(_dev(G)).cpu().numpy()
+    Lo = OL.solve_transpose(Fo, G)
+    assert np.abs(Lam - Lo).max() / np.abs(Lo).max() <= 1e-10
+
+
+@pytest.mark.parametrize("name,mk,opts", CASES[:1] + CASES[5:8],
+                         ids=[c[0] for c in CASES[:1] + CASES[5:8]])
+def test_fp32_factor_with_fp64_refinement(name, mk, opts):
+    s = mk()
+    P, F = gpu_factor(s, precision="fp32", **opts)
+    _, _, _, pv = oracle_factor(s)
+    err = factor_error(P, F, pv)
+    assert err <= 1e-4          # reported; single-precision factors
+    X, info = F.solve(_dev(s.rhs), info=True)
+    be = OL.backward_error(s.n, s.colptr, s.rowidx, s.values,
+                           X.cpu().numpy(), s.rhs)
+    assert info["converged"] and info["backward_error"] <= 1e-14
+    assert be <= 1e-14
+    assert 1 <= info["iterations"] <= 10
+
+
+def test_deterministic_and_refactor_identical():
+    s = workloads.grid7_cd(12, nrhs=1)
+    P, F = gpu_factor(s, b_min=16)
+    a = F.export_factors().cpu().numpy()
+    F2 = S.Factor(P, _dev(s.values))
+    b = F2.export_factors().cpu().numpy()
+    assert np.array_equal(a, b)
+    v2 = s.values * 1.5
+    F.refactor(_dev(v2))
+    F.refactor(_dev(s.values))
+    c = F.export_factors().cpu().numpy()
+    assert np.array_equal(a, c)
+
+
+def test_refactor_new_values_match_oracle():
+    s = workloads.grid5(40)
+    P, F = gpu_factor(s)
+    rng = np.random.default_rng(7)
+    v2 = s.values * rng.uniform(0.5, 1.5, s.values.size)
+    F.refactor(_dev(v2))
+    Fo = OL.lu(s.n, s.colptr, s.rowidx, v2)
+    _, _, pv = OL.lu_pattern(Fo)
+    assert factor_error(P, F, pv) <= FP64_TOL
+
+
+def test_pivot_perturbation_and_singular():
+    """A zero leading pivot: with perturbation the pivot becomes +tau
+    (tau = 2^-26 max|A|) and is counted; without it the factor reports
+    SINGULAR."""
+    A = np.array([[0.0, 1.0, 0.0], [1.0, 1.0, 1.0], [0.0, 1.0, 3.0]])
+    from conftest import dense_to_csc
+    cp, ri, v = dense_to_csc(A, np.ones((3, 3), bool))
+    P = S.Plan(3, cp, ri, b_min=1)
+    F = S.Factor(P, _dev(v))
+    assert F.nperturb == 1
+    tau = 2.0 ** -26 * 3.0
+    assert F.tau == pytest.approx(tau)
+    Fo = OL.lu(3, cp, ri, v, tau=tau)
+    _, _, pv = OL.lu_pattern(Fo)
+    got = F.export_factors().cpu().numpy()
+    assert np.abs(got - pv).max() / np.abs(pv).max() <= 1e-12
+    P2 = S.Plan(3, cp, ri, b_min=1, pivot_perturb=0)
+    with pytest.raises(S.SluError) as e:
+        S.Factor(P2, _dev(v))
+    assert e.value.status == 4
+
+
+def test_empty_rhs_and_vector_rhs():
+    s = workloads.grid5(16)
+    P, F = gpu_factor(s, b_min=8)
+    x = F.solve(_dev(s.rhs[:, 0]))
+    assert x.shape == (s.n,)
+    Fo = OL.lu(s.n, s.colptr, s.rowidx, s.values)
+    xo = OL.solve(Fo, s.rhs[:, :1])[:, 0]
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-12 * np.abs(xo).max()
+
+
+@pytest.mark.parametrize("name,mk", [
+    ("grid5_48 (2304)", lambda: workloads.grid5(48)),
+    ("grid7theta_32 (32768)", lambda: workloads.grid7_theta(32)),
+])
+def test_full_size_parity(name, mk):
+    """Full-size configurations the oracle factors in seconds: element-wise."""
+    s = mk()
+    P, F = gpu_factor(s)
+    _, _, _, pv = oracle_factor(s)
+    assert factor_error(P, F, pv) <= FP64_TOL
+    X, info = F.solve(_dev(s.rhs), info=True)
+    assert info["backward_error"] <= 1e-13
+
+
+def test_full_size_grid7cd_40_properties():
+    """40^3 convection-diffusion (n = 64,000) in the benchmark's
+    configuration: backward error of the solve, and A = L U checked on 2000
+    sampled entries of A, each recomputed in FP64 from the exported factors."""
+    s = workloads.grid7_cd(40)
+    P, F = gpu_factor(s)
+    X, info = F.solve(_dev(s.rhs), info=True)
+    be = OL.backward_error(s.n, s.colptr, s.rowidx, s.values,
+                           X.cpu().numpy(), s.rhs)
+    assert be <= 1e-13
+    e = P.export()
+    vals = F.export_factors().cpu().numpy()
+    cp, ri = e["colptr"], e["rowidx"]
+    rng = np.random.default_rng(3)
+    cols = np.repeat(np.arange(s.n), np.diff(s.colptr))
+    pick = rng.choice(s.values.size, 2000, replace=False)
+    # L(i, :) by rows: gather strictly-lower entries by row once
+    lower = ri > np.repeat(np.arange(s.n), np.diff(cp))
+    lr = ri[lower]
+    lc = np.repeat(np.arange(s.n), np.diff(cp))[lower]
+    lv = vals[lower]
+    order = np.argsort(lr, kind="stable")
+    lr, lc, lv = lr[order], lc[order], lv[order]
+    lptr = np.searchsorted(lr, np.arange(s.n + 1))
+    scale = np.abs(s.values).max()
+    worst = 0.0
+    for q in pick:
+        i, j = s.rowidx[q], cols[q]
+        ucol_r = ri[cp[j]:cp[j + 1]]
+        ucol_v = vals[cp[j]:cp[j + 1]]
+        um = ucol_r <= j
+        u = dict(zip(ucol_r[um].tolist(), ucol_v[um].tolist()))
+        acc = u.get(i, 0.0) if i <= j else 0.0          # L(i,i) = 1
+        for k, lik in zip(lc[lptr[i]:lptr[i + 1]], lv[lptr[i]:lptr[i + 1]]):
+            if k <= j and k in u:
+                acc += lik * u[k]
+        worst = max(worst, abs(acc - s.values[q]) / scale)
+    assert worst <= 1e-12
