@@ -77,7 +77,8 @@ typedef struct {
     double dense_threshold;      /* block stored dense if nnz >= thr*bI*bJ  */
     int32_t pivot_perturb;       /* 1: |pivot| < tau -> +-tau and counted   */
     double pivot_tau_rel;        /* tau = pivot_tau_rel * max|A|; 0 = the
-                                    default (2^-26 FP64, 2^-12 FP32)        */
+                                    default 2^-26 (pivots are FP64 in both
+                                    precisions)                             */
     double refine_tol;           /* stop when backward error <= this        */
     int32_t refine_max_iter;     /* < 0 never refine; 0 = default (none for
                                     FP64, 30 for FP32); > 0 that many       */

@@ -488,10 +488,11 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
     cudaGetDevice(&h->device);
     h->prec = P->opts.precision;
     const bool fp64 = h->prec == SLU_PREC_FP64;
+    // Diagonal-block pivots are formed in FP64 for both storage precisions,
+    // so one threshold serves both: sqrt(eps64) ~ 2^-26 of max|A|.
     if (P->opts.pivot_perturb)
-        h->tau_rel = P->opts.pivot_tau_rel > 0
-                         ? P->opts.pivot_tau_rel
-                         : (fp64 ? std::ldexp(1.0, -26) : std::ldexp(1.0, -12));
+        h->tau_rel = P->opts.pivot_tau_rel > 0 ? P->opts.pivot_tau_rel
+                                               : std::ldexp(1.0, -26);
     const size_t esz = fp64 ? sizeof(double) : sizeof(float);
     const bool ok =
         cuda_ok(cudaMalloc(&h->storage, std::max<int64_t>(1, P->storage) * esz),
