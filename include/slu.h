@@ -233,6 +233,34 @@ slu_status slu_handle_stats(slu_handle *h, slu_stats *out);
  * out: host double[3] = {getrf, panel, ssssm}. */
 slu_status slu_plan_flops(const slu_plan *plan, double *out);
 
+/* Allocation-free refined solve (no counterpart in the paper).
+ *
+ * The same computation as slu_solve with refinement (and with the backward
+ * error always computed), for callers that may not allocate device memory
+ * when they solve: a process whose device memory is budgeted and handed out
+ * entirely at start-up, an application whose framework owns all device
+ * memory through its own pool, or a latency-critical loop that cannot
+ * afford cudaMalloc's implicit synchronization.  slu_solve allocates its
+ * refinement workspace on first use; this call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  Its residual and
+ * reduction scratch is a fixed array in the library's device image,
+ * SLU_NOALLOC_MAX_ELEMS doubles plus 192 reduction words (about 8 MiB),
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * Arguments as slu_solve, except that X must not alias B and n * nrhs must
+ * not exceed SLU_NOALLOC_MAX_ELEMS (else SLU_ERR_INVALID_ARG with a message
+ * naming the limit).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array and
+ * it keeps the previous call's contents (the call clears what it needs
+ * zeroed); calls whose GPU work overlaps race on it and must be ordered by
+ * the caller.  Synchronizes the stream once per refinement iteration. */
+#define SLU_NOALLOC_MAX_ELEMS (1 << 20)
+slu_status slu_solve_refine_noalloc(const slu_handle *h, const double *B,
+                                    int64_t ldb, int32_t nrhs, double *X,
+                                    int64_t ldx, void *stream,
+                                    slu_solve_info *info);
+
 void slu_plan_destroy(slu_plan *plan);
 void slu_handle_destroy(slu_handle *h);
 const char *slu_last_error(void);

@@ -12,6 +12,7 @@
 // Arithmetic is FP64 whatever the storage type of the factors.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "device_common.cuh"
@@ -505,4 +506,151 @@ extern "C" slu_status slu_solve_transpose(const slu_handle *h, const double *G,
     slu_status s = copy_cols(Lam, ldl, G, ldg, n, nrhs, st);
     if (s == SLU_OK) s = solve_inplace(h, Lam, ldl, nrhs, true, st);
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free refined solve.
+//
+// slu_solve's refinement path keeps its residual and reduction words in a
+// workspace that the handle allocates with cudaMalloc on first use.  Some
+// callers may not allocate device memory at that point: a process whose
+// device memory budget is fixed and fully handed out at start-up, an
+// application whose framework owns every byte of device memory through its
+// own pool, or a latency-critical loop in which cudaMalloc's implicit device
+// synchronization is not acceptable.  For them this entry point runs the same
+// refinement with its scratch in a fixed array that lives in the library's
+// device image instead.
+//
+// The array holds SLU_NOALLOC_MAX_ELEMS residual values plus the reduction
+// words; every GPU that loads the library reserves it (8 MiB) until the
+// process exits.  All calls on one device share it and it keeps whatever the
+// previous call left there; the reduction words are cleared on every use and
+// the residual is fully rewritten before it is read.  Two calls whose work
+// overlaps on the GPU (different streams, or host threads) race on the
+// array, so callers must order them.
+constexpr int kNoallocRed = 3 * 64;
+static __device__ __align__(256) double g_noalloc_scratch[SLU_NOALLOC_MAX_ELEMS + kNoallocRed];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  The name
+// g_noalloc_scratch in host code is only a host-side stand-in; its device
+// address comes from cudaGetSymbolAddress, taken once per device with that
+// device current.
+slu_status noalloc_scratch(double **out) {
+    int dev = -1;
+    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return SLU_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(SLU_ERR_NOT_SUPPORTED, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (!cuda_ok(cudaGetSymbolAddress(&p, g_noalloc_scratch),
+                     "cudaGetSymbolAddress(noalloc scratch)"))
+            return SLU_ERR_CUDA;
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return SLU_OK;
+}
+
+// backward_error with caller-given reduction words instead of h->red.
+slu_status backward_error_with(slu_handle *h, const double *B, int64_t ldb,
+                               const double *X, int64_t ldx, int nrhs,
+                               double *R, double *red, cudaStream_t st,
+                               double *be) {
+    const slu_plan *P = h->plan;
+    const DevPlan *D = P->dev;
+    const int64_t n = P->n;
+    {
+        LaunchScope ls_(h, SLU_KC_RESID, st);
+        k_residual<<<(int)((n * 32 + 255) / 256), 256, 0, st>>>(
+            n, nrhs, D->a_rowptr, D->a_colidx, D->a_vpos, h->a_vals, B, ldb, X,
+            ldx, R, n);
+    }
+    if (!cuda_ok(cudaMemsetAsync(red, 0, 3 * nrhs * sizeof(double), st),
+                 "cudaMemsetAsync"))
+        return SLU_ERR_CUDA;
+    {
+        LaunchScope ls_(h, SLU_KC_RESID, st);
+        k_norms<<<148 * 2, 256, 0, st>>>(
+            n, nrhs, R, n, X, ldx, B, ldb,
+            reinterpret_cast<unsigned long long *>(red));
+    }
+    double hr[3 * 64 + 1];
+    if (!cuda_ok(cudaMemcpyAsync(hr, red, 3 * nrhs * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
+        !cuda_ok(cudaMemcpyAsync(hr + 3 * 64, h->scal + 1, sizeof(double),
+                                 cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
+        !cuda_ok(cudaStreamSynchronize(st), "residual"))
+        return SLU_ERR_CUDA;
+    double worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+        const double den = hr[3 * 64] * hr[3 * c + 1] + hr[3 * c + 2];
+        worst = std::max(worst, den > 0 ? hr[3 * c] / den : 0.0);
+    }
+    *be = worst;
+    return SLU_OK;
+}
+
+}  // namespace
+
+extern "C" slu_status slu_solve_refine_noalloc(const slu_handle *ch,
+                                               const double *B, int64_t ldb,
+                                               int32_t nrhs, double *X,
+                                               int64_t ldx, void *stream,
+                                               slu_solve_info *info) {
+    slu_handle *h = const_cast<slu_handle *>(ch);
+    if (!h || !B || !X) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
+    const slu_plan *P = h->plan;
+    const int64_t n = P->n;
+    if (nrhs < 0 || nrhs > 64 || ldb < n || ldx < n)
+        return fail(SLU_ERR_INVALID_ARG, "bad nrhs or leading dimension");
+    if (X == B) return fail(SLU_ERR_INVALID_ARG, "X must not alias B");
+    if (n * (int64_t)nrhs > SLU_NOALLOC_MAX_ELEMS)
+        return fail(SLU_ERR_INVALID_ARG,
+                    "n * nrhs exceeds SLU_NOALLOC_MAX_ELEMS (1048576): use "
+                    "slu_solve, which allocates its workspace");
+    if (info) {
+        info->iterations = 0;
+        info->backward_error = -1.0;
+    }
+    if (nrhs == 0 || n == 0) return SLU_OK;
+    double *scratch = nullptr;
+    slu_status s = noalloc_scratch(&scratch);
+    if (s != SLU_OK) return s;
+    double *R = scratch;
+    double *red = scratch + SLU_NOALLOC_MAX_ELEMS;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int maxit = P->opts.refine_max_iter < 0  ? 0
+                      : P->opts.refine_max_iter > 0 ? P->opts.refine_max_iter
+                      : (h->prec == SLU_PREC_FP64 ? 0 : 30);
+    s = copy_cols(X, ldx, B, ldb, n, nrhs, st);
+    if (s == SLU_OK) s = solve_inplace(h, X, ldx, nrhs, false, st);
+    if (s != SLU_OK) return s;
+    double be = 0.0;
+    int it = 0;
+    for (;;) {
+        s = backward_error_with(h, B, ldb, X, ldx, nrhs, R, red, st, &be);
+        if (s != SLU_OK) return s;
+        if (be <= P->opts.refine_tol || it >= maxit) break;
+        s = solve_inplace(h, R, n, nrhs, false, st);
+        if (s != SLU_OK) return s;
+        {
+            LaunchScope ls_(h, SLU_KC_RESID, st);
+            k_add_cols<<<148 * 4, 256, 0, st>>>(n, nrhs, R, n, X, ldx);
+        }
+        ++it;
+    }
+    if (info) {
+        info->iterations = it;
+        info->backward_error = be;
+    }
+    if (maxit > 0 && !(be <= P->opts.refine_tol))
+        return fail(SLU_ERR_NOT_CONVERGED, "refinement did not reach refine_tol");
+    return SLU_OK;
 }

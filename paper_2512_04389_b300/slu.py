@@ -70,8 +70,8 @@ EXPORTS = ["slu_opts_default", "slu_analyze", "slu_plan_query",
            "slu_plan_export", "slu_plan_export_blocks", "slu_plan_export_tasks",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
            "slu_export_factors", "slu_set_profiling", "slu_handle_stats",
-           "slu_plan_flops", "slu_plan_destroy", "slu_handle_destroy",
-           "slu_last_error"]
+           "slu_plan_flops", "slu_solve_refine_noalloc", "slu_plan_destroy",
+           "slu_handle_destroy", "slu_last_error"]
 
 
 def _load():
@@ -98,6 +98,8 @@ def _load():
     lib.slu_set_profiling.argtypes = [P, C.c_int32]
     lib.slu_handle_stats.argtypes = [P, C.POINTER(Stats)]
     lib.slu_plan_flops.argtypes = [P, P]
+    lib.slu_solve_refine_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P,
+                                             C.c_int64, P, C.POINTER(SolveInfo)]
     lib.slu_plan_destroy.argtypes = [P]
     lib.slu_plan_destroy.restype = None
     lib.slu_handle_destroy.argtypes = [P]
