@@ -226,6 +226,14 @@ slu_status slu_export_factors(const slu_handle *h, double *out, void *stream);
 slu_status slu_set_profiling(slu_handle *h, int32_t enable);
 slu_status slu_handle_stats(slu_handle *h, slu_stats *out);
 
+/* Per-launch record of the launches profiled since the last
+ * slu_set_profiling / slu_handle_stats call, in launch order: kernel class
+ * and CUDA-event duration (ms).  Copies min(cap, count) records into the
+ * host arrays cls and ms and the count into *count; synchronizes on the
+ * last event; does not consume the records. */
+slu_status slu_handle_trace(slu_handle *h, int64_t cap, int32_t *cls,
+                            float *ms, int64_t *count);
+
 /* Algorithmic flops of the factorization by kernel class, from the filled
  * pattern: with l_k the entries of L(:,k) inside k's diagonal block and
  * l'_k those below it, GETRF does l_k + 2 l_k^2, GESSM + TSTRF

@@ -491,6 +491,50 @@ static void build_levels_and_tasks(slu_plan &P) {
         P.tstrf_off[lv + 1] = (int64_t)P.tstrf.size() / 2;
         P.tgt_off[lv + 1] = (int64_t)P.tgt.size();
     }
+    // execution split of the SSSSM targets (same updates, same order per
+    // target: the dense tiles of a level run before its generic targets)
+    P.gm_off.assign(L + 1, 0);
+    P.gg_off.assign(L + 1, 0);
+    P.gm_task.clear();
+    P.gm_src.clear();
+    P.gg_tgt.clear();
+    P.gg_src.clear();
+    P.gg_srcoff.assign(1, 0);
+    constexpr int32_t kTile = 64;
+    for (int32_t lv = 0; lv < L; ++lv) {
+        for (int64_t k = P.tgt_off[lv]; k < P.tgt_off[lv + 1]; ++k) {
+            const int32_t tb = P.tgt[k];
+            const BlockDesc &td = P.blocks[tb];
+            std::vector<int32_t> dense_pairs, other;
+            for (int64_t q = P.srcoff[k]; q < P.srcoff[k + 1]; ++q) {
+                const int32_t lb = P.src[2 * q], ub = P.src[2 * q + 1];
+                if (td.dense && P.blocks[lb].dense && P.blocks[ub].dense) {
+                    dense_pairs.push_back(lb);
+                    dense_pairs.push_back(ub);
+                } else {
+                    other.push_back(lb);
+                    other.push_back(ub);
+                }
+            }
+            if (!dense_pairs.empty()) {
+                const int32_t s0 = (int32_t)(P.gm_src.size() / 2);
+                P.gm_src.insert(P.gm_src.end(), dense_pairs.begin(), dense_pairs.end());
+                const int32_t s1 = (int32_t)(P.gm_src.size() / 2);
+                for (int32_t r0 = 0; r0 < td.rows; r0 += kTile)
+                    for (int32_t c0 = 0; c0 < td.cols; c0 += kTile) {
+                        const int32_t t5[5] = {tb, s0, s1, r0, c0};
+                        P.gm_task.insert(P.gm_task.end(), t5, t5 + 5);
+                    }
+            }
+            if (!other.empty()) {
+                P.gg_tgt.push_back(tb);
+                P.gg_src.insert(P.gg_src.end(), other.begin(), other.end());
+                P.gg_srcoff.push_back((int64_t)P.gg_src.size() / 2);
+            }
+        }
+        P.gm_off[lv + 1] = (int64_t)P.gm_task.size() / 5;
+        P.gg_off[lv + 1] = (int64_t)P.gg_tgt.size();
+    }
     auto flat = [&](std::vector<std::vector<int32_t>> &v,
                     std::vector<int64_t> &off, std::vector<int32_t> &ids) {
         off.assign(p + 1, 0);
@@ -504,6 +548,34 @@ static void build_levels_and_tasks(slu_plan &P) {
     flat(upper_row, P.urow_off, P.urow_blk);
     flat(upper_col, P.ucol_off, P.ucol_blk);
     flat(lower_col, P.lcol_off, P.lcol_blk);
+    // solve pull pairs per sweep and level
+    P.part_elems = 0;
+    for (int sw = 0; sw < 4; ++sw) {
+        const auto &off = sw == 0 ? P.lrow_off : sw == 1 ? P.urow_off
+                        : sw == 2 ? P.ucol_off : P.lcol_off;
+        const auto &ids = sw == 0 ? P.lrow_blk : sw == 1 ? P.urow_blk
+                        : sw == 2 ? P.ucol_blk : P.lcol_blk;
+        P.sp_off[sw].assign(L + 1, 0);
+        P.sp_pairs[sw].clear();
+        P.sp_poff[sw].clear();
+        P.sd_pair0[sw].assign(P.getrf.size(), 0);
+        for (int32_t lv = 0; lv < L; ++lv) {
+            int64_t acc = 0;
+            for (int64_t g = P.getrf_off[lv]; g < P.getrf_off[lv + 1]; ++g) {
+                const int32_t db = P.getrf[g];
+                const int32_t I = P.blocks[db].I;
+                P.sd_pair0[sw][g] = (int64_t)P.sp_pairs[sw].size() / 2;
+                for (int64_t q = off[I]; q < off[I + 1]; ++q) {
+                    P.sp_pairs[sw].push_back(ids[q]);
+                    P.sp_pairs[sw].push_back(db);
+                    P.sp_poff[sw].push_back(acc);
+                    acc += P.blocks[db].rows;
+                }
+            }
+            P.sp_off[sw][lv + 1] = (int64_t)P.sp_pairs[sw].size() / 2;
+            P.part_elems = std::max(P.part_elems, acc);
+        }
+    }
 }
 
 extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,

@@ -20,9 +20,15 @@ struct DevPlan {
     int32_t *getrf = nullptr, *gessm = nullptr, *tstrf = nullptr;
     int32_t *tgt = nullptr, *src = nullptr;
     int64_t *srcoff = nullptr;
+    int32_t *gm_task = nullptr, *gm_src = nullptr, *gg_tgt = nullptr,
+            *gg_src = nullptr;
+    int64_t *gg_srcoff = nullptr;
     int64_t *a2s = nullptr, *f2s = nullptr;
     int64_t *a_rowptr = nullptr, *a_vpos = nullptr;
     int32_t *a_colidx = nullptr;
+    int32_t *sp_pairs[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t *sp_poff[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t *sd_pair0[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t *lrow_off = nullptr, *urow_off = nullptr, *ucol_off = nullptr,
             *lcol_off = nullptr;
     int32_t *lrow_blk = nullptr, *urow_blk = nullptr, *ucol_blk = nullptr,
@@ -63,6 +69,105 @@ __device__ __forceinline__ int rowat(const uint16_t *rows, int t) {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
+// Dynamic shared memory given to the kernels that stage blocks (one CTA per
+// SM; the B300 limit per CTA is 227 KB).
+constexpr size_t kStageSmem = 220 * 1024;
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) {
+    return (x + 15) & ~size_t(15);
+}
+
+// One block seen column by column, either in place in global memory or as
+// a copy staged in shared memory.  Column jj holds slots [off, off + cnt)
+// of v with local rows rows[t] (rows == nullptr: dense, row of slot t is t).
+template <typename T>
+struct BlockView {
+    const int32_t *cp;     // local colptr (cols + 1); nullptr when dense
+    const uint16_t *rw;    // local rows of a sparse block
+    T *v;                  // values
+    const int32_t *dp;     // diagonal blocks: diagonal slot of each column
+    int rows, ld;
+    __device__ __forceinline__ void col(int jj, int &off, int &cnt,
+                                        const uint16_t *&r) const {
+        if (cp) {
+            off = cp[jj];
+            cnt = cp[jj + 1] - off;
+            r = rw + off;
+        } else {
+            off = jj * ld;
+            cnt = rows;
+            r = nullptr;
+        }
+    }
+};
+
+// Stage block d into buf (cap bytes): its values, its local pattern and,
+// for a diagonal block, its diagonal slots.  If the values do not fit, only
+// the index data is staged and the values stay in global memory; if that
+// does not fit either, the view is entirely global.  Called by all threads
+// of the CTA; ends with __syncthreads() when anything was staged.
+// *staged tells whether the values were staged (they must then be written
+// back with unstage_block); *used receives the bytes taken from buf.
+template <typename T>
+__device__ BlockView<T> stage_block(const BlockDesc &d, const BlockArgs &a,
+                                    T *val, unsigned char *buf, size_t cap,
+                                    bool diag, bool *staged, size_t *used) {
+    const int64_t nnz = d.dense ? (int64_t)d.ld * d.cols
+                                : (int64_t)a.lcolptr[d.coff + d.cols];
+    const size_t vbytes = align16(nnz * sizeof(T));
+    const size_t ibytes = (diag ? align16((size_t)d.cols * 4) : 0) +
+                          (d.dense ? 0 : align16((size_t)(d.cols + 1) * 4) +
+                                             align16(nnz * 2));
+    BlockView<T> v;
+    v.rows = d.rows;
+    v.ld = d.ld;
+    v.cp = d.dense ? nullptr : a.lcolptr + d.coff;
+    v.rw = d.dense ? nullptr : a.lrow + d.roff;
+    v.v = val + d.voff;
+    v.dp = diag ? a.dpos + d.doff : nullptr;
+    *staged = false;
+    *used = 0;
+    const bool with_vals = vbytes + ibytes <= cap;
+    if (!with_vals && (ibytes == 0 || ibytes > cap)) return v;
+    unsigned char *p = buf;
+    if (with_vals) {
+        T *vv = reinterpret_cast<T *>(p);
+        p += vbytes;
+        for (int64_t e = threadIdx.x; e < nnz; e += blockDim.x) vv[e] = val[d.voff + e];
+        v.v = vv;
+        *staged = true;
+    }
+    if (diag) {
+        int32_t *dp = reinterpret_cast<int32_t *>(p);
+        p += align16((size_t)d.cols * 4);
+        for (int e = threadIdx.x; e < d.cols; e += blockDim.x) dp[e] = a.dpos[d.doff + e];
+        v.dp = dp;
+    }
+    if (!d.dense) {
+        int32_t *cp = reinterpret_cast<int32_t *>(p);
+        p += align16((size_t)(d.cols + 1) * 4);
+        uint16_t *rw = reinterpret_cast<uint16_t *>(p);
+        p += align16(nnz * 2);
+        for (int e = threadIdx.x; e <= d.cols; e += blockDim.x) cp[e] = a.lcolptr[d.coff + e];
+        for (int64_t e = threadIdx.x; e < nnz; e += blockDim.x) rw[e] = a.lrow[d.roff + e];
+        v.cp = cp;
+        v.rw = rw;
+    }
+    __syncthreads();
+    *used = (size_t)(p - buf);
+    return v;
+}
+
+// Copy a staged block's values back to global memory (all threads).
+template <typename T>
+__device__ void unstage_block(const BlockDesc &d, const BlockArgs &a,
+                              const BlockView<T> &v, T *val) {
+    const int64_t nnz = d.dense ? (int64_t)d.ld * d.cols
+                                : (int64_t)a.lcolptr[d.coff + d.cols];
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < nnz; e += blockDim.x) val[d.voff + e] = v.v[e];
+}
+
 inline bool cuda_ok(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return true;
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -88,6 +193,7 @@ struct slu_handle {
     double *work = nullptr;
     int64_t work_elems = 0;
     double *red = nullptr;               // reduction scratch for refinement
+    double *part = nullptr;              // solve partial sums (factor time)
     // launch accounting and optional per-launch event timing
     int64_t launches = 0;
     bool profiling = false;

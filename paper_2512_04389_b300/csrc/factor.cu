@@ -69,6 +69,172 @@ __global__ void k_export(int64_t n, const int64_t *__restrict__ f2s,
         out[i] = (double)val[f2s[i]];
 }
 
+
+// Slot of local row r in a column with sorted local rows (dense: r itself);
+// -1 when absent.
+__device__ __forceinline__ int find_row(const uint16_t *rows, int cnt, int r) {
+    if (!rows) return r < cnt ? r : -1;
+    int lo = 0, hi = cnt - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int v = rows[mid];
+        if (v == r) return mid;
+        if (v < r) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+
+// Column update vj(slot of row rs[t]) -= ls[t] * u for t < n, lanes over t.
+// The source column (rows rs, values ls) sits in shared memory; the target
+// column (rows rj, cj slots, values vj) may be in shared or global memory.
+// Each lane first finds and loads up to 4 target slots, then writes them,
+// so several global round trips are in flight at once.
+template <typename T>
+__device__ __forceinline__ void axpy_rows(T *vj, const uint16_t *rj, int cj,
+                                          const uint16_t *rs, const double *ls,
+                                          int n, double u, int lane) {
+    for (int t0 = 0; t0 < n; t0 += 128) {
+        int pr[4];
+        double bv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = t0 + q * 32 + lane;
+            pr[q] = t < n ? find_row(rj, cj, rs[t]) : -1;
+            bv[q] = pr[q] >= 0 ? (double)vj[pr[q]] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = t0 + q * 32 + lane;
+            if (pr[q] >= 0) vj[pr[q]] = (T)(bv[q] - ls[t] * u);
+        }
+    }
+}
+
+// Dense diagonal block: right-looking LU with the whole CTA.  Step k fixes
+// the pivot (FP64, perturbation as in the sparse path), scales L(k+1:, k)
+// and applies the rank-1 update to the trailing block.  Entries outside the
+// symbolic pattern are exact zeros and stay zero.
+template <typename M>
+__device__ void getrf_dense_core(M *A, int b, int ld, double tau,
+                                 unsigned long long *cnt) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = 0; k < b; ++k) {
+        if (tid == 0) {
+            double piv = (double)A[(int64_t)k * ld + k];
+            if (tau > 0.0 && fabs(piv) < tau) {
+                piv = (piv >= 0.0) ? tau : -tau;
+                atomicAdd(&cnt[0], 1ull);
+            } else if (piv == 0.0) {
+                atomicOr(&cnt[1], 1ull);
+            }
+            A[(int64_t)k * ld + k] = (M)piv;
+        }
+        __syncthreads();
+        const double piv = (double)A[(int64_t)k * ld + k];
+        M *colk = A + (int64_t)k * ld;
+        for (int r = k + 1 + tid; r < b; r += nt) colk[r] = (M)((double)colk[r] / piv);
+        __syncthreads();
+        const int m = b - k - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            const int r = k + 1 + e % m, c = k + 1 + e / m;
+            const M u = A[(int64_t)c * ld + k];
+            if (u != M(0)) A[(int64_t)c * ld + r] -= colk[r] * u;
+        }
+        __syncthreads();
+    }
+}
+
+
+
+// Right-looking LU of a tall m x w panel held column-major in shared
+// memory (leading dimension m); pivots on the first w rows.
+__device__ void getrf_panel_tall(double *P, int m, int w, double tau,
+                                 unsigned long long *cnt) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = 0; k < w; ++k) {
+        if (tid == 0) {
+            double piv = P[k * m + k];
+            if (tau > 0.0 && fabs(piv) < tau) {
+                piv = (piv >= 0.0) ? tau : -tau;
+                atomicAdd(&cnt[0], 1ull);
+            } else if (piv == 0.0) {
+                atomicOr(&cnt[1], 1ull);
+            }
+            P[k * m + k] = piv;
+        }
+        __syncthreads();
+        const double piv = P[k * m + k];
+        for (int r = k + 1 + tid; r < m; r += nt) P[k * m + r] /= piv;
+        __syncthreads();
+        const int mr = m - k - 1, nc = w - k - 1;
+        for (int e = tid; e < mr * nc; e += nt) {
+            const int r = k + 1 + e % mr, c = k + 1 + e / mr;
+            const double u = P[c * m + k];
+            if (u != 0.0) P[c * m + r] -= P[k * m + r] * u;
+        }
+        __syncthreads();
+    }
+}
+
+// Dense diagonal block too large for a shared-memory tile: right-looking LU
+// by column panels of width W.  Per panel: factor the tall panel in shared
+// memory (FP64), form U12 = L11^{-1} A12 in shared memory, then update the
+// trailing block A22 -= L21 U12 in place (each element read and written
+// once per panel).
+template <typename T>
+__device__ void getrf_dense_panels(T *A, int b, int ld, double tau,
+                                   unsigned long long *cnt,
+                                   unsigned char *smem, size_t cap) {
+    constexpr int W = 32;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double *Pn = reinterpret_cast<double *>(smem);          // (b - p0) x W
+    double *U = Pn + (size_t)b * W;                          // W x (b - p0 - w)
+    (void)cap;
+    for (int p0 = 0; p0 < b; p0 += W) {
+        const int w = min(W, b - p0), m = b - p0, n2 = b - p0 - w;
+        for (int e = tid; e < m * w; e += nt) {
+            const int r = e % m, c = e / m;
+            Pn[c * m + r] = (double)A[(int64_t)(p0 + c) * ld + p0 + r];
+        }
+        for (int e = tid; e < w * n2; e += nt) {
+            const int r = e % w, c = e / w;
+            U[c * w + r] = (double)A[(int64_t)(p0 + w + c) * ld + p0 + r];
+        }
+        __syncthreads();
+        getrf_panel_tall(Pn, m, w, tau, cnt);
+        // U12 = L11^{-1} A12: one thread per column
+        for (int c = tid; c < n2; c += nt) {
+            double *u = U + c * w;
+            for (int k = 0; k < w; ++k) {
+                const double x = u[k];
+                if (x == 0.0) continue;
+                for (int r = k + 1; r < w; ++r) u[r] -= Pn[k * m + r] * x;
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < m * w; e += nt) {
+            const int r = e % m, c = e / m;
+            A[(int64_t)(p0 + c) * ld + p0 + r] = (T)Pn[c * m + r];
+        }
+        for (int e = tid; e < w * n2; e += nt) {
+            const int r = e % w, c = e / w;
+            A[(int64_t)(p0 + w + c) * ld + p0 + r] = (T)U[c * w + r];
+        }
+        // A22 -= L21 U12
+        for (int e = tid; e < n2 * n2; e += nt) {
+            const int r = e % n2, c = e / n2;
+            double acc = 0.0;
+#pragma unroll 8
+            for (int k = 0; k < w; ++k) acc += Pn[k * m + w + r] * U[c * w + k];
+            T *q = A + (int64_t)(p0 + w + c) * ld + p0 + w + r;
+            *q = (T)((double)*q - acc);
+        }
+        __syncthreads();
+    }
+}
+
 // GETRF on diagonal blocks.  Columns run in height groups of the block's
 // own column DAG; inside a group one warp per column performs the
 // left-looking update x = B(:,jj); for m in struct U(:,jj) ascending:
@@ -81,53 +247,136 @@ k_getrf(const int32_t *__restrict__ ids, BlockArgs a, T *__restrict__ val,
         unsigned long long *__restrict__ cnt) {
     const BlockDesc d = a.bd[ids[blockIdx.x]];
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *acc = reinterpret_cast<double *>(smem) + warp * d.rows;
-    for (int t = lane; t < d.rows; t += 32) acc[t] = 0.0;
-    __syncwarp();
     const double tau = tau_rel * scal[0];
-    for (int g = 0; g < d.ngroups; ++g) {
-        const int gs = a.sgrp[d.goff + g], ge = a.sgrp[d.goff + g + 1];
-        for (int q = gs + warp; q < ge; q += kWarps) {
-            const int jj = a.sched[d.doff + q];
-            int64_t vb;
-            int cn;
-            const uint16_t *rows;
-            colview(d, jj, a, vb, cn, rows);
-            for (int t = lane; t < cn; t += 32)
-                acc[rowat(rows, t)] = (double)val[vb + t];
-            __syncwarp();
-            const int dp = a.dpos[d.doff + jj];
-            for (int t = 0; t < dp; ++t) {
-                const int m = rowat(rows, t);
-                const double x = acc[m];
-                if (x != 0.0) {
-                    int64_t vm;
-                    int cm;
-                    const uint16_t *rm;
-                    colview(d, m, a, vm, cm, rm);
-                    const int dpm = a.dpos[d.doff + m];
-                    for (int u = dpm + 1 + lane; u < cm; u += 32)
-                        acc[rowat(rm, u)] -= (double)val[vm + u] * x;
-                }
-                __syncwarp();
-            }
-            double piv = acc[jj];
+    if (d.dense) {
+        const int b = d.rows;
+        T *g = val + d.voff;
+        if ((size_t)b * b * sizeof(double) <= kStageSmem) {
+            double *M = reinterpret_cast<double *>(smem);
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x) M[e] = (double)g[e];
+            __syncthreads();
+            getrf_dense_core<double>(M, b, b, tau, cnt);
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x) g[e] = (T)M[e];
+        } else if ((size_t)b * 64 * sizeof(double) <= kStageSmem) {
+            getrf_dense_panels<T>(g, b, d.ld, tau, cnt, smem, kStageSmem);
+        } else {
+            getrf_dense_core<T>(g, b, d.ld, tau, cnt);
+        }
+        return;
+    }
+    // Sparse diagonal block, right-looking with the whole CTA: step k fixes
+    // the pivot, scales L(k+1:, k), and applies the rank-1 update
+    // B(r, j) -= L(r, k) U(k, j) for r, j in the rows of L(:, k) below the
+    // diagonal (the columns of U(k, :) by symmetry of the pattern); one
+    // warp per column j, lanes over rows r, slots found by binary search.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double s_piv;
+    // source column buffer (values, rows), then the staged block
+    double *sv = reinterpret_cast<double *>(smem);
+    uint16_t *sr = reinterpret_cast<uint16_t *>(sv + d.rows);
+    const size_t sbytes = align16((size_t)d.rows * 10);
+    bool staged;
+    size_t used;
+    const BlockView<T> B = stage_block<T>(d, a, val, smem + sbytes,
+                                          kStageSmem - sbytes, true, &staged,
+                                          &used);
+    for (int k = 0; k < d.rows; ++k) {
+        int ok, ck;
+        const uint16_t *rk;
+        B.col(k, ok, ck, rk);
+        const int dk = B.dp[k];
+        const int nL = ck - dk - 1;
+        if (threadIdx.x == 0) {
+            double piv = (double)B.v[ok + dk];
             if (tau > 0.0 && fabs(piv) < tau) {
                 piv = (piv >= 0.0) ? tau : -tau;
-                if (lane == 0) atomicAdd(&cnt[0], 1ull);
+                atomicAdd(&cnt[0], 1ull);
             } else if (piv == 0.0) {
-                if (lane == 0) atomicOr(&cnt[1], 1ull);
+                atomicOr(&cnt[1], 1ull);
             }
-            for (int t = lane; t < cn; t += 32) {
-                const int r = rowat(rows, t);
-                double v = acc[r];
-                if (r > jj) v = v / piv;
-                else if (r == jj) v = piv;
-                val[vb + t] = (T)v;
-                acc[r] = 0.0;
+            B.v[ok + dk] = (T)piv;
+            s_piv = piv;
+        }
+        __syncthreads();
+        if (nL == 0) continue;
+        const double piv = s_piv;
+        for (int e = threadIdx.x; e < nL; e += blockDim.x) {
+            const T l = (T)((double)B.v[ok + dk + 1 + e] / piv);
+            B.v[ok + dk + 1 + e] = l;
+            sv[e] = (double)l;
+            sr[e] = (uint16_t)rowat(rk, dk + 1 + e);
+        }
+        __syncthreads();
+        for (int c = warp; c < nL; c += kWarps) {
+            const int j = sr[c];
+            int oj, cj;
+            const uint16_t *rj;
+            B.col(j, oj, cj, rj);
+            const int pu = find_row(rj, B.dp[j], k);
+            const double u = pu >= 0 ? (double)B.v[oj + pu] : 0.0;
+            if (u == 0.0) continue;
+            axpy_rows<T>(B.v + oj, rj, cj, sr, sv, nL, u, lane);
+        }
+        __syncthreads();
+    }
+    if (staged) unstage_block<T>(d, a, B, val);
+}
+
+
+// Dense GESSM / TSTRF: independent vectors (the columns of B_IJ for GESSM,
+// the rows of B_JI for TSTRF), one thread per vector, solved by substitution
+// against the dense diagonal factor; a chunk of vectors is staged in shared
+// memory as X[i * V + t] (thread t's element i), so accesses are
+// conflict-free and the factor entries are uniform (broadcast) loads.
+template <typename T, typename Acc>
+__device__ void panel_dense(bool gessm, const BlockDesc &d,
+                            const BlockDesc &dd, T *__restrict__ val, Acc *X,
+                            size_t smem_elems) {
+    const int m = dd.rows;
+    const int nvec = gessm ? d.cols : d.rows;
+    // the caller guarantees 32 * m <= smem_elems
+    const int V = (int)min((size_t)blockDim.x, smem_elems / (size_t)m) & ~31;
+    const T *__restrict__ F = val + dd.voff;  // diagonal block, ld = m
+    T *B = val + d.voff;
+    const int ldb = d.ld;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int v0 = 0; v0 < nvec; v0 += V) {
+        const int nv = min(V, nvec - v0);
+        for (int e = tid; e < m * nv; e += nt) {
+            int i, t;
+            if (gessm) { t = e / m; i = e % m; }
+            else       { i = e / nv; t = e % nv; }
+            X[i * V + t] = gessm ? (Acc)B[(int64_t)(v0 + t) * ldb + i]
+                                 : (Acc)B[(int64_t)i * ldb + v0 + t];
+        }
+        __syncthreads();
+        if (tid < nv) {
+            Acc *x = X + tid;
+            if (gessm) {                       // unit lower L_II from the left
+                for (int mm = 0; mm < m; ++mm) {
+                    const Acc xm = x[mm * V];
+                    if (xm == Acc(0)) continue;
+                    const T *Lc = F + (int64_t)mm * m;
+                    for (int r = mm + 1; r < m; ++r) x[r * V] -= (Acc)Lc[r] * xm;
+                }
+            } else {                           // upper U_II from the right
+                for (int mm = 0; mm < m; ++mm) {
+                    const Acc xm = x[mm * V] / (Acc)F[(int64_t)mm * m + mm];
+                    x[mm * V] = xm;
+                    if (xm == Acc(0)) continue;
+                    for (int i = mm + 1; i < m; ++i)
+                        x[i * V] -= (Acc)F[(int64_t)i * m + mm] * xm;
+                }
             }
-            __syncwarp();
+        }
+        __syncthreads();
+        for (int e = tid; e < m * nv; e += nt) {
+            int i, t;
+            if (gessm) { t = e / m; i = e % m; }
+            else       { i = e / nv; t = e % nv; }
+            const T v = (T)X[i * V + t];
+            if (gessm) B[(int64_t)(v0 + t) * ldb + i] = v;
+            else       B[(int64_t)i * ldb + v0 + t] = v;
         }
         __syncthreads();
     }
@@ -145,83 +394,99 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
     const int32_t *pr = is_gessm ? gessm : tstrf;
     const BlockDesc d = a.bd[pr[2 * t0]];
     const BlockDesc dd = a.bd[pr[2 * t0 + 1]];
-    Acc *acc = reinterpret_cast<Acc *>(smem) + warp * d.rows;
-    for (int t = lane; t < d.rows; t += 32) acc[t] = Acc(0);
-    __syncwarp();
-    if (is_gessm) {
-        // U_IJ(:,jj) = L_II^{-1} B_IJ(:,jj); columns independent.
-        for (int jj = warp; jj < d.cols; jj += kWarps) {
-            int64_t vb;
-            int cn;
-            const uint16_t *rows;
-            colview(d, jj, a, vb, cn, rows);
-            for (int t = lane; t < cn; t += 32)
-                acc[rowat(rows, t)] = (Acc)val[vb + t];
-            __syncwarp();
-            for (int t = 0; t < cn; ++t) {
-                const int m = rowat(rows, t);
-                const Acc x = acc[m];
-                if (x != Acc(0)) {
-                    int64_t vm;
-                    int cm;
-                    const uint16_t *rm;
-                    colview(dd, m, a, vm, cm, rm);
-                    const int dpm = a.dpos[dd.doff + m];
-                    for (int u = dpm + 1 + lane; u < cm; u += 32)
-                        acc[rowat(rm, u)] -= (Acc)val[vm + u] * x;
-                }
-                __syncwarp();
+    if (d.dense && dd.dense &&
+        (size_t)dd.rows * 32 <= kStageSmem / sizeof(Acc)) {
+        panel_dense<T, Acc>(is_gessm, d, dd, val, reinterpret_cast<Acc *>(smem),
+                            kStageSmem / sizeof(Acc));
+        return;
+    }
+    // Right-looking over the columns k of the diagonal block, the whole CTA
+    // per step.  Shared memory: a source-column buffer, then the diagonal
+    // factor (read at every step), then the panel block if it also fits.
+    const int mb = max(d.rows, dd.rows);
+    double *sv = reinterpret_cast<double *>(smem);
+    uint16_t *sr = reinterpret_cast<uint16_t *>(sv + mb);
+    const size_t sbytes = align16((size_t)mb * 10);
+    bool staged_f, staged_b;
+    size_t used_f, used_b;
+    const BlockView<T> F = stage_block<T>(dd, a, val, smem + sbytes,
+                                          kStageSmem - sbytes, true,
+                                          &staged_f, &used_f);
+    const size_t o2 = sbytes + used_f;
+    const BlockView<T> Bv = stage_block<T>(d, a, val, smem + o2,
+                                           kStageSmem - o2, false, &staged_b,
+                                           &used_b);
+    for (int k = 0; k < dd.rows; ++k) {
+        int fk, fck;
+        const uint16_t *frk;
+        F.col(k, fk, fck, frk);
+        const int dk = F.dp[k];
+        const int nL = fck - dk - 1;     // rows of L_II(:,k) = cols of U_II(k,:)
+        if (is_gessm) {
+            // U_IJ(r, j) -= L_II(r, k) U_IJ(k, j) for every column j holding
+            // row k (U_IJ(k, :) is final at step k).  Each lane looks for
+            // row k in one column; the warp then walks the hits.
+            if (nL == 0) continue;
+            for (int e = threadIdx.x; e < nL; e += blockDim.x) {
+                sv[e] = (double)F.v[fk + dk + 1 + e];
+                sr[e] = (uint16_t)rowat(frk, dk + 1 + e);
             }
-            for (int t = lane; t < cn; t += 32) {
-                const int r = rowat(rows, t);
-                val[vb + t] = (T)acc[r];
-                acc[r] = Acc(0);
+            __syncthreads();
+            for (int cb = warp * 32; cb < d.cols; cb += kWarps * 32) {
+                const int c = cb + lane;
+                int oc = 0, cc = 0, pk = -1;
+                const uint16_t *rc = nullptr;
+                double x = 0.0;
+                if (c < d.cols) {
+                    Bv.col(c, oc, cc, rc);
+                    pk = find_row(rc, cc, k);
+                    if (pk >= 0) x = (double)Bv.v[oc + pk];
+                }
+                unsigned hits = __ballot_sync(~0u, pk >= 0 && x != 0.0);
+                while (hits) {
+                    const int src = __ffs(hits) - 1;
+                    hits &= hits - 1;
+                    const int c2 = cb + src;
+                    const double x2 = __shfl_sync(~0u, x, src);
+                    int o2c, c2c;
+                    const uint16_t *r2c;
+                    Bv.col(c2, o2c, c2c, r2c);
+                    axpy_rows<T>(Bv.v + o2c, r2c, c2c, sr, sv, nL, x2, lane);
+                }
             }
-            __syncwarp();
-        }
-    } else {
-        // L_JI(:,ii) = (B_JI(:,ii) - sum_{m<ii} L_JI(:,m) U_II(m,ii)) / U_II(ii,ii),
-        // columns in the height groups of the diagonal block.
-        for (int g = 0; g < dd.ngroups; ++g) {
-            const int gs = a.sgrp[dd.goff + g], ge = a.sgrp[dd.goff + g + 1];
-            for (int q = gs + warp; q < ge; q += kWarps) {
-                const int ii = a.sched[dd.doff + q];
-                int64_t vb;
-                int cn;
-                const uint16_t *rows;
-                colview(d, ii, a, vb, cn, rows);
-                for (int t = lane; t < cn; t += 32)
-                    acc[rowat(rows, t)] = (Acc)val[vb + t];
-                __syncwarp();
-                int64_t vu;
-                int cu;
-                const uint16_t *ru;
-                colview(dd, ii, a, vu, cu, ru);
-                const int dp = a.dpos[dd.doff + ii];
-                for (int t = 0; t < dp; ++t) {
-                    const Acc u = (Acc)val[vu + t];
-                    if (u != Acc(0)) {
-                        const int m = rowat(ru, t);
-                        int64_t vm;
-                        int cm;
-                        const uint16_t *rm;
-                        colview(d, m, a, vm, cm, rm);
-                        for (int e = lane; e < cm; e += 32)
-                            acc[rowat(rm, e)] -= (Acc)val[vm + e] * u;
-                    }
-                    __syncwarp();
-                }
-                const Acc piv = (Acc)val[vu + dp];
-                for (int t = lane; t < cn; t += 32) {
-                    const int r = rowat(rows, t);
-                    val[vb + t] = (T)(acc[r] / piv);
-                    acc[r] = Acc(0);
-                }
-                __syncwarp();
+            __syncthreads();
+        } else {
+            // L_JI(:, k) /= U_II(k, k); then L_JI(r, j) -= L_JI(r, k) U_II(k, j)
+            // for the columns j of U_II(k, :).
+            int ok, ck;
+            const uint16_t *rk;
+            Bv.col(k, ok, ck, rk);
+            if (ck == 0) continue;
+            const double ukk = (double)F.v[fk + dk];
+            for (int e = threadIdx.x; e < ck; e += blockDim.x) {
+                const T l = (T)((double)Bv.v[ok + e] / ukk);
+                Bv.v[ok + e] = l;
+                sv[e] = (double)l;
+                sr[e] = (uint16_t)rowat(rk, e);
+            }
+            __syncthreads();
+            for (int c = warp; c < nL; c += kWarps) {
+                const int j = rowat(frk, dk + 1 + c);
+                int fj, fcj;
+                const uint16_t *frj;
+                F.col(j, fj, fcj, frj);
+                const int pu = find_row(frj, F.dp[j], k);
+                const double u = pu >= 0 ? (double)F.v[fj + pu] : 0.0;
+                if (u == 0.0) continue;
+                int oj, cj;
+                const uint16_t *rj;
+                Bv.col(j, oj, cj, rj);
+                axpy_rows<T>(Bv.v + oj, rj, cj, sr, sv, ck, u, lane);
             }
             __syncthreads();
         }
     }
+    if (staged_b) unstage_block<T>(d, a, Bv, val);
 }
 
 // SSSSM: target B_KJ -= sum over the level's sources I of L_KI U_IJ.
@@ -283,6 +548,72 @@ k_ssssm(const int32_t *__restrict__ tgt, const int64_t *__restrict__ srcoff,
     }
 }
 
+
+// SSSSM on dense tiles: a 64 x 64 tile of a dense target B_KJ minus the sum
+// over the level's dense sources of L_KI U_IJ, accumulated in registers
+// (4 x 4 per thread) over all sources and k-slices of 16, written once.
+// Sources run in ascending I, so the result is deterministic.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
+             const BlockDesc *__restrict__ bd, T *__restrict__ val) {
+    constexpr int TM = 64, TN = 64, KT = 16, PAD = 16 / sizeof(T);
+    __shared__ __align__(16) T As[KT][TM];
+    __shared__ __align__(16) T Bs[KT][TN + PAD];
+    const int32_t *tk = task + 5 * (int64_t)blockIdx.x;
+    const BlockDesc d = bd[tk[0]];
+    const int s0 = tk[1], s1 = tk[2], r0 = tk[3], c0 = tk[4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int s = s0; s < s1; ++s) {
+        const BlockDesc dl = bd[src[2 * s]];
+        const BlockDesc du = bd[src[2 * s + 1]];
+        const T *__restrict__ A = val + dl.voff;
+        const T *__restrict__ B = val + du.voff;
+        const int K = dl.cols;
+        for (int k0 = 0; k0 < K; k0 += KT) {
+            for (int e = tid; e < KT * TM; e += 256) {
+                const int r = e % TM, k = e / TM;
+                const int gr = r0 + r, gk = k0 + k;
+                As[k][r] = (gr < d.rows && gk < K) ? A[(int64_t)gk * dl.ld + gr] : T(0);
+            }
+            for (int e = tid; e < KT * TN; e += 256) {
+                const int k = e % KT, c = e / KT;
+                const int gk = k0 + k, gc = c0 + c;
+                Bs[k][c] = (gk < K && gc < d.cols) ? B[(int64_t)gc * du.ld + gk] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                T a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = c0 + tx * 4 + j;
+        if (c >= d.cols) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = r0 + ty * 4 + i;
+            if (r < d.rows) val[d.voff + (int64_t)c * d.ld + r] -= acc[i][j];
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host side
 
 template <typename V>
@@ -304,11 +635,17 @@ void free_dev_plan(slu_plan *P) {
     if (D->device >= 0) cudaSetDevice(D->device);
     void *ptrs[] = {D->bd, D->lcolptr, D->lrow, D->dpos, D->sched, D->sgrp,
                     D->getrf, D->gessm, D->tstrf, D->tgt, D->src, D->srcoff,
+                    D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
                     D->lrow_off, D->urow_off, D->ucol_off, D->lcol_off,
                     D->lrow_blk, D->urow_blk, D->ucol_blk, D->lcol_blk};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (int sw = 0; sw < 4; ++sw) {
+        if (D->sp_pairs[sw]) cudaFree(D->sp_pairs[sw]);
+        if (D->sp_poff[sw]) cudaFree(D->sp_poff[sw]);
+        if (D->sd_pair0[sw]) cudaFree(D->sd_pair0[sw]);
+    }
     if (cur >= 0) cudaSetDevice(cur);
     delete D;
     P->dev = nullptr;
@@ -323,13 +660,16 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
     DevPlan *D = new DevPlan();
     D->device = dev;
     P->dev = D;
-    const bool ok =
+    bool ok =
         upload(P->blocks, &D->bd) && upload(P->lcolptr, &D->lcolptr) &&
         upload(P->lrow, &D->lrow) && upload(P->dpos, &D->dpos) &&
         upload(P->sched, &D->sched) && upload(P->sgrp, &D->sgrp) &&
         upload(P->getrf, &D->getrf) && upload(P->gessm, &D->gessm) &&
         upload(P->tstrf, &D->tstrf) && upload(P->tgt, &D->tgt) &&
         upload(P->src, &D->src) && upload(P->srcoff, &D->srcoff) &&
+        upload(P->gm_task, &D->gm_task) && upload(P->gm_src, &D->gm_src) &&
+        upload(P->gg_tgt, &D->gg_tgt) && upload(P->gg_src, &D->gg_src) &&
+        upload(P->gg_srcoff, &D->gg_srcoff) &&
         upload(P->a2s, &D->a2s) && upload(P->f2s, &D->f2s) &&
         upload(P->a_rowptr, &D->a_rowptr) && upload(P->a_vpos, &D->a_vpos) &&
         upload(P->a_colidx, &D->a_colidx) &&
@@ -337,6 +677,10 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->ucol_off, &D->ucol_off) && upload(P->lcol_off, &D->lcol_off) &&
         upload(P->lrow_blk, &D->lrow_blk) && upload(P->urow_blk, &D->urow_blk) &&
         upload(P->ucol_blk, &D->ucol_blk) && upload(P->lcol_blk, &D->lcol_blk);
+    for (int sw = 0; ok && sw < 4; ++sw)
+        ok = upload(P->sp_pairs[sw], &D->sp_pairs[sw]) &&
+             upload(P->sp_poff[sw], &D->sp_poff[sw]) &&
+             upload(P->sd_pair0[sw], &D->sd_pair0[sw]);
     if (!ok) {
         free_dev_plan(P);
         return SLU_ERR_CUDA;
@@ -355,13 +699,13 @@ static int grid_for(int64_t n, int threads) {
 }
 
 template <typename T, typename Acc>
-static slu_status set_smem_limits(size_t bytes) {
-    if (bytes <= 48 * 1024) return SLU_OK;
-    const int b = (int)bytes;
+static slu_status set_smem_limits(size_t generic) {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    const bool ok = cuda_ok(cudaFuncSetAttribute(k_getrf<T>, attr, b), "smem") &&
-                    cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, b), "smem") &&
-                    cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, b), "smem");
+    const int big = (int)std::max(generic, kStageSmem);
+    bool ok = cuda_ok(cudaFuncSetAttribute(k_getrf<T>, attr, big), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem");
+    if (ok && generic > 48 * 1024)
+        ok = cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, (int)generic), "smem");
     return ok ? SLU_OK : SLU_ERR_CUDA;
 }
 
@@ -406,26 +750,33 @@ static slu_status run_factor(slu_handle *h, const double *values,
     const size_t smem_a = (size_t)kWarps * P->maxb * sizeof(Acc);
     if (set_smem_limits<T, Acc>(std::max(smem_f, smem_a)) != SLU_OK)
         return SLU_ERR_CUDA;
+    const size_t smem_big = std::max(kStageSmem, std::max(smem_f, smem_a));
     for (int lv = 0; lv < P->nlevels; ++lv) {
         const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
         if (g1 > g0) {
                 LaunchScope ls_(h, SLU_KC_GETRF, st);
-                k_getrf<T><<<(int)(g1 - g0), kThreads, smem_f, st>>>(
+                k_getrf<T><<<(int)(g1 - g0), kThreads, smem_big, st>>>(
                     D->getrf + g0, a, val, h->scal, h->tau_rel, h->cnt);
             }
         const int64_t e0 = P->gessm_off[lv], e1 = P->gessm_off[lv + 1];
         const int64_t t0 = P->tstrf_off[lv], t1 = P->tstrf_off[lv + 1];
         if (e1 - e0 + t1 - t0 > 0) {
                 LaunchScope ls_(h, SLU_KC_PANEL, st);
-                k_panel<T, Acc><<<(int)(e1 - e0 + t1 - t0), kThreads, smem_a, st>>>(
+                k_panel<T, Acc><<<(int)(e1 - e0 + t1 - t0), kThreads, smem_big, st>>>(
                     D->gessm + 2 * e0, (int)(e1 - e0), D->tstrf + 2 * t0, a, val);
             }
-        const int64_t s0 = P->tgt_off[lv], s1 = P->tgt_off[lv + 1];
+        const int64_t m0 = P->gm_off[lv], m1 = P->gm_off[lv + 1];
+        if (m1 > m0) {
+            LaunchScope ls_(h, SLU_KC_SSSSM, st);
+            k_ssssm_gemm<T><<<(int)(m1 - m0), 256, 0, st>>>(
+                D->gm_task + 5 * m0, D->gm_src, D->bd, val);
+        }
+        const int64_t s0 = P->gg_off[lv], s1 = P->gg_off[lv + 1];
         if (s1 > s0) {
-                LaunchScope ls_(h, SLU_KC_SSSSM, st);
-                k_ssssm<T, Acc><<<(int)(s1 - s0), kThreads, smem_a, st>>>(
-                    D->tgt + s0, D->srcoff + s0, D->src, a, val);
-            }
+            LaunchScope ls_(h, SLU_KC_SSSSM, st);
+            k_ssssm<T, Acc><<<(int)(s1 - s0), kThreads, smem_a, st>>>(
+                D->gg_tgt + s0, D->gg_srcoff + s0, D->gg_src, a, val);
+        }
     }
     if (!cuda_ok(cudaGetLastError(), "factor launch")) return SLU_ERR_CUDA;
     return SLU_OK;
@@ -467,7 +818,8 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
-    void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red};
+    void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red,
+                    h->part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (cur >= 0) cudaSetDevice(cur);
@@ -500,7 +852,10 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
         cuda_ok(cudaMalloc(&h->scal, 4 * sizeof(double)), "cudaMalloc") &&
         cuda_ok(cudaMalloc(&h->cnt, 2 * sizeof(unsigned long long)), "cudaMalloc") &&
         cuda_ok(cudaMalloc(&h->a_vals, std::max<int64_t>(1, P->nnz_a) * sizeof(double)),
-                "cudaMalloc(A)");
+                "cudaMalloc(A)") &&
+        cuda_ok(cudaMalloc(&h->part, std::max<int64_t>(1, P->part_elems) * 4 *
+                                         sizeof(double)),
+                "cudaMalloc(solve partials)");
     if (!ok) {
         slu_handle_destroy(h);
         return SLU_ERR_OUT_OF_MEMORY;
@@ -562,6 +917,25 @@ extern "C" slu_status slu_handle_stats(slu_handle *h, slu_stats *out) {
     for (int c = 0; c < SLU_KC_COUNT; ++c) {
         out->calls[c] = h->calls[c];
         out->ms[c] = h->ms[c];
+    }
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_handle_trace(slu_handle *h, int64_t cap,
+                                       int32_t *cls, float *ms,
+                                       int64_t *count) {
+    if (!h || !count) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
+    if (!h->recs.empty() &&
+        !cuda_ok(cudaEventSynchronize(h->recs.back().b), "cudaEventSynchronize"))
+        return SLU_ERR_CUDA;
+    *count = (int64_t)h->recs.size();
+    for (int64_t i = 0; i < std::min<int64_t>(cap, *count); ++i) {
+        float t = 0.f;
+        if (!cuda_ok(cudaEventElapsedTime(&t, h->recs[i].a, h->recs[i].b),
+                     "cudaEventElapsedTime"))
+            return SLU_ERR_CUDA;
+        if (cls) cls[i] = h->recs[i].cls;
+        if (ms) ms[i] = t;
     }
     return SLU_OK;
 }

@@ -83,6 +83,24 @@ struct slu_plan {
     std::vector<int32_t> tgt;            // target block ids
     std::vector<int64_t> srcoff;         // per target, into src pairs
     std::vector<int32_t> src;            // pairs (blk(K,I), blk(I,J))
+    // execution split of SSSSM per level: dense tiles (dense target, dense
+    // sources) and the generic remainder
+    std::vector<int64_t> gm_off;         // per level, into gm_task
+    std::vector<int32_t> gm_task;        // 5 per tile: tgt, s0, s1, r0, c0
+    std::vector<int32_t> gm_src;         // pairs (blk(K,I), blk(I,J))
+    std::vector<int64_t> gg_off;         // per level, into gg_tgt
+    std::vector<int32_t> gg_tgt;
+    std::vector<int64_t> gg_srcoff;
+    std::vector<int32_t> gg_src;
+    // solve pull pairs, per sweep (0 L fwd, 1 U bwd, 2 U^T fwd, 3 L^T bwd):
+    // per level the (source block, diagonal block) pairs, each with the
+    // offset (doubles, per right-hand side chunk) of its partial vector,
+    // and for every entry of the getrf list its first pair
+    std::vector<int64_t> sp_off[4];
+    std::vector<int32_t> sp_pairs[4];
+    std::vector<int64_t> sp_poff[4];
+    std::vector<int64_t> sd_pair0[4];
+    int64_t part_elems = 0;              // per right-hand side
     // per diagonal block I: neighbour block lists for the solves
     std::vector<int64_t> lrow_off, urow_off, ucol_off, lcol_off;
     std::vector<int32_t> lrow_blk;       // (I, I'), I' < I

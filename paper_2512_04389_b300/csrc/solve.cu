@@ -24,234 +24,331 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Adds sum over the listed blocks of B(:, jj) * x(c0 + jj) into part (one
-// partial vector per warp; warps split the columns of each block).
+constexpr int RC = 4;   // right-hand sides processed together
+enum Sweep { FWD = 0, BWD = 1, FWD_T = 2, BWD_T = 3 };
+
+// Pull, scatter form (L y = b and U x = y): one CTA per source block B of
+// the level (rows = the diagonal block's rows); part = B * x(B's columns),
+// m x RC, reduced from per-warp partials in a fixed order.
 template <typename T>
-__device__ __forceinline__ void pull_scatter(const BlockArgs &a,
-                                             const T *__restrict__ val,
-                                             const int32_t *__restrict__ blk,
-                                             int64_t b0, int64_t b1,
-                                             const double *__restrict__ x,
-                                             double *pw) {
+__global__ void __launch_bounds__(kThreads)
+k_pull_scatter(const int32_t *__restrict__ pairs,
+               const int64_t *__restrict__ poff, BlockArgs a,
+               const T *__restrict__ val, const double *__restrict__ X,
+               int64_t ldx, int nc, double *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const BlockDesc db = a.bd[pairs[2 * blockIdx.x]];
+    const int m = db.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *pw = reinterpret_cast<double *>(smem);
+    for (int t = threadIdx.x; t < kWarps * m * RC; t += kThreads) pw[t] = 0.0;
+    __syncthreads();
+    double *mine = pw + warp * m * RC;
+    for (int jj = warp; jj < db.cols; jj += kWarps) {
+        double xv[RC];
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+            xv[c] = c < nc ? X[(int64_t)c * ldx + db.c0 + jj] : 0.0;
+            any |= xv[c] != 0.0;
+        }
+        if (any) {
+            int64_t vb;
+            int cn;
+            const uint16_t *rows;
+            colview(db, jj, a, vb, cn, rows);
+            for (int e = lane; e < cn; e += 32) {
+                const double l = (double)val[vb + e];
+                double *q = mine + rowat(rows, e) * RC;
+#pragma unroll
+                for (int c = 0; c < RC; ++c) q[c] += l * xv[c];
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    double *out = part + poff[blockIdx.x] * RC;
+    for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+        double sum = 0.0;
+        for (int w = 0; w < kWarps; ++w) sum += pw[w * m * RC + t];
+        out[t] = sum;
+    }
+}
+
+// Pull, dot form (U^T z = g and L^T lam = z): one CTA per source block B
+// (columns = the diagonal block's columns); part(ii) = B(:, ii) . x(B's rows).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
+           BlockArgs a, const T *__restrict__ val,
+           const double *__restrict__ X, int64_t ldx, int nc,
+           double *__restrict__ part) {
+    const BlockDesc db = a.bd[pairs[2 * blockIdx.x]];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t bi = b0; bi < b1; ++bi) {
-        const BlockDesc db = a.bd[blk[bi]];
-        for (int jj = warp; jj < db.cols; jj += kWarps) {
-            const double xv = x[db.c0 + jj];
-            if (xv != 0.0) {
-                int64_t vb;
-                int cn;
-                const uint16_t *rows;
-                colview(db, jj, a, vb, cn, rows);
-                for (int e = lane; e < cn; e += 32)
-                    pw[rowat(rows, e)] += (double)val[vb + e] * xv;
-            }
-            __syncwarp();
-        }
-    }
-}
-
-// L y = b on the rows of one level's diagonal blocks (levels ascending):
-// pull from blocks (I, I'), I' < I, then unit lower L_II.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_fwd(const int32_t *__restrict__ ids, BlockArgs a, const T *__restrict__ val,
-      const int64_t *__restrict__ boff, const int32_t *__restrict__ blk,
-      double *__restrict__ X, int64_t ldx, int nrhs) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const BlockDesc dd = a.bd[ids[blockIdx.x]];
-    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *y = reinterpret_cast<double *>(smem);
-    double *part = y + m;
-    const int64_t b0 = boff[dd.I], b1 = boff[dd.I + 1];
-    for (int c = 0; c < nrhs; ++c) {
-        double *x = X + (int64_t)c * ldx;
-        for (int t = threadIdx.x; t < m; t += kThreads) y[t] = x[dd.r0 + t];
-        for (int t = threadIdx.x; t < kWarps * m; t += kThreads) part[t] = 0.0;
-        __syncthreads();
-        pull_scatter(a, val, blk, b0, b1, x, part + warp * m);
-        __syncthreads();
-        for (int t = threadIdx.x; t < m; t += kThreads) {
-            double s = 0.0;
-            for (int w = 0; w < kWarps; ++w) s += part[w * m + t];
-            y[t] -= s;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            for (int jj = 0; jj < m; ++jj) {
-                const double xv = y[jj];
-                if (xv != 0.0) {
-                    int64_t vb;
-                    int cn;
-                    const uint16_t *rows;
-                    colview(dd, jj, a, vb, cn, rows);
-                    const int dp = a.dpos[dd.doff + jj];
-                    for (int e = dp + 1 + lane; e < cn; e += 32)
-                        y[rowat(rows, e)] -= (double)val[vb + e] * xv;
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < m; t += kThreads) x[dd.r0 + t] = y[t];
-        __syncthreads();
-    }
-}
-
-// U x = y (levels descending): pull from blocks (I, J), J > I, then U_II.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_bwd(const int32_t *__restrict__ ids, BlockArgs a, const T *__restrict__ val,
-      const int64_t *__restrict__ boff, const int32_t *__restrict__ blk,
-      double *__restrict__ X, int64_t ldx, int nrhs) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const BlockDesc dd = a.bd[ids[blockIdx.x]];
-    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *y = reinterpret_cast<double *>(smem);
-    double *part = y + m;
-    const int64_t b0 = boff[dd.I], b1 = boff[dd.I + 1];
-    for (int c = 0; c < nrhs; ++c) {
-        double *x = X + (int64_t)c * ldx;
-        for (int t = threadIdx.x; t < m; t += kThreads) y[t] = x[dd.r0 + t];
-        for (int t = threadIdx.x; t < kWarps * m; t += kThreads) part[t] = 0.0;
-        __syncthreads();
-        pull_scatter(a, val, blk, b0, b1, x, part + warp * m);
-        __syncthreads();
-        for (int t = threadIdx.x; t < m; t += kThreads) {
-            double s = 0.0;
-            for (int w = 0; w < kWarps; ++w) s += part[w * m + t];
-            y[t] -= s;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            for (int jj = m - 1; jj >= 0; --jj) {
-                int64_t vb;
-                int cn;
-                const uint16_t *rows;
-                colview(dd, jj, a, vb, cn, rows);
-                const int dp = a.dpos[dd.doff + jj];
-                const double xv = y[jj] / (double)val[vb + dp];
-                __syncwarp();
-                if (lane == 0) y[jj] = xv;
-                if (xv != 0.0)
-                    for (int e = lane; e < dp; e += 32)
-                        y[rowat(rows, e)] -= (double)val[vb + e] * xv;
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < m; t += kThreads) x[dd.r0 + t] = y[t];
-        __syncthreads();
-    }
-}
-
-// Dot of column ii of each listed block with x on the block's rows; one warp
-// owns column ii across all blocks, so no partial sums are needed.
-template <typename T>
-__device__ __forceinline__ double pull_dot(const BlockArgs &a,
-                                           const T *__restrict__ val,
-                                           const int32_t *__restrict__ blk,
-                                           int64_t b0, int64_t b1, int ii,
-                                           const double *__restrict__ x) {
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int64_t bi = b0; bi < b1; ++bi) {
-        const BlockDesc db = a.bd[blk[bi]];
+    double *out = part + poff[blockIdx.x] * RC;
+    for (int ii = warp; ii < db.cols; ii += kWarps) {
         int64_t vb;
         int cn;
         const uint16_t *rows;
         colview(db, ii, a, vb, cn, rows);
-        for (int e = lane; e < cn; e += 32)
-            s += (double)val[vb + e] * x[db.r0 + rowat(rows, e)];
-    }
-    return warp_sum(s);
-}
-
-// U^T z = g (levels ascending): z(ii) -= dot of column ii of blocks
-// (I', I), I' < I, with z(I'); then a forward sweep with U_II^T.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_fwd_t(const int32_t *__restrict__ ids, BlockArgs a, const T *__restrict__ val,
-        const int64_t *__restrict__ boff, const int32_t *__restrict__ blk,
-        double *__restrict__ X, int64_t ldx, int nrhs) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const BlockDesc dd = a.bd[ids[blockIdx.x]];
-    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *z = reinterpret_cast<double *>(smem);
-    const int64_t b0 = boff[dd.I], b1 = boff[dd.I + 1];
-    for (int c = 0; c < nrhs; ++c) {
-        double *x = X + (int64_t)c * ldx;
-        for (int t = threadIdx.x; t < m; t += kThreads) z[t] = x[dd.r0 + t];
-        __syncthreads();
-        for (int ii = warp; ii < m; ii += kWarps) {
-            const double s = pull_dot(a, val, blk, b0, b1, ii, x);
-            if (lane == 0) z[ii] -= s;
+        double sv[RC] = {0.0, 0.0, 0.0, 0.0};
+        for (int e = lane; e < cn; e += 32) {
+            const double l = (double)val[vb + e];
+            const int64_t r = db.r0 + rowat(rows, e);
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                if (c < nc) sv[c] += l * X[(int64_t)c * ldx + r];
         }
-        __syncthreads();
-        if (warp == 0) {
-            for (int ii = 0; ii < m; ++ii) {
-                int64_t vb;
-                int cn;
-                const uint16_t *rows;
-                colview(dd, ii, a, vb, cn, rows);
-                const int dp = a.dpos[dd.doff + ii];
-                double s = 0.0;
-                for (int e = lane; e < dp; e += 32)
-                    s += (double)val[vb + e] * z[rowat(rows, e)];
-                s = warp_sum(s);
-                const double zi = (z[ii] - s) / (double)val[vb + dp];
-                __syncwarp();
-                if (lane == 0) z[ii] = zi;
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < m; t += kThreads) x[dd.r0 + t] = z[t];
-        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < RC; ++c) sv[c] = warp_sum(sv[c]);
+        if (lane < RC) out[ii * RC + lane] = sv[lane];
     }
 }
 
-// L^T lam = z (levels descending): pull from blocks (K, I), K > I, then a
-// backward sweep with L_II^T (unit diagonal).
+// One column step of a diagonal-block sweep; cv[e] is entry e of column jj
+// (rows rows[e], diagonal at slot dp), y the m x RC right-hand sides.
+template <int MODE>
+__device__ __forceinline__ void chain_step(int jj, const double *cv,
+                                           const uint16_t *rows, int cn,
+                                           int dp, double *y, int lane) {
+    if (MODE == FWD) {                 // unit lower, scatter below
+        double xv[RC];
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < RC; ++c) { xv[c] = y[jj * RC + c]; any |= xv[c] != 0.0; }
+        if (any)
+            for (int e = dp + 1 + lane; e < cn; e += 32) {
+                double *q = y + rowat(rows, e) * RC;
+#pragma unroll
+                for (int c = 0; c < RC; ++c) q[c] -= cv[e] * xv[c];
+            }
+    } else if (MODE == BWD) {          // upper, divide then scatter above
+        double xv[RC];
+        bool any = false;
+        const double piv = cv[dp];
+#pragma unroll
+        for (int c = 0; c < RC; ++c) { xv[c] = y[jj * RC + c] / piv; any |= xv[c] != 0.0; }
+        __syncwarp();
+        if (lane < RC) y[jj * RC + lane] = xv[lane];
+        if (any)
+            for (int e = lane; e < dp; e += 32) {
+                double *q = y + rowat(rows, e) * RC;
+#pragma unroll
+                for (int c = 0; c < RC; ++c) q[c] -= cv[e] * xv[c];
+            }
+    } else {                           // transposed: gather dot
+        double sv[RC] = {0.0, 0.0, 0.0, 0.0};
+        const int e0 = MODE == FWD_T ? lane : dp + 1 + lane;
+        const int e1 = MODE == FWD_T ? dp : cn;
+        for (int e = e0; e < e1; e += 32) {
+            const double *q = y + rowat(rows, e) * RC;
+#pragma unroll
+            for (int c = 0; c < RC; ++c) sv[c] += cv[e] * q[c];
+        }
+#pragma unroll
+        for (int c = 0; c < RC; ++c) sv[c] = warp_sum(sv[c]);
+        double zi = 0.0;
+        if (lane < RC) {
+            zi = y[jj * RC + lane] - sv[lane];
+            if (MODE == FWD_T) zi /= cv[dp];
+        }
+        __syncwarp();
+        if (lane < RC) y[jj * RC + lane] = zi;
+    }
+    __syncwarp();
+}
+
+// chain_step on values of storage type T (staged copy of the block).
+template <typename T, int MODE>
+__device__ __forceinline__ void chain_step_t(int jj, const T *cv,
+                                             const uint16_t *rows, int cn,
+                                             int dp, double *y, int lane) {
+    if (MODE == FWD) {
+        double xv[RC];
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < RC; ++c) { xv[c] = y[jj * RC + c]; any |= xv[c] != 0.0; }
+        if (any)
+            for (int e = dp + 1 + lane; e < cn; e += 32) {
+                double *q = y + rowat(rows, e) * RC;
+                const double l = (double)cv[e];
+#pragma unroll
+                for (int c = 0; c < RC; ++c) q[c] -= l * xv[c];
+            }
+    } else if (MODE == BWD) {
+        double xv[RC];
+        bool any = false;
+        const double piv = (double)cv[dp];
+#pragma unroll
+        for (int c = 0; c < RC; ++c) { xv[c] = y[jj * RC + c] / piv; any |= xv[c] != 0.0; }
+        __syncwarp();
+        if (lane < RC) y[jj * RC + lane] = xv[lane];
+        if (any)
+            for (int e = lane; e < dp; e += 32) {
+                double *q = y + rowat(rows, e) * RC;
+                const double u = (double)cv[e];
+#pragma unroll
+                for (int c = 0; c < RC; ++c) q[c] -= u * xv[c];
+            }
+    } else {
+        double sv[RC] = {0.0, 0.0, 0.0, 0.0};
+        const int e0 = MODE == FWD_T ? lane : dp + 1 + lane;
+        const int e1 = MODE == FWD_T ? dp : cn;
+        for (int e = e0; e < e1; e += 32) {
+            const double *q = y + rowat(rows, e) * RC;
+            const double l = (double)cv[e];
+#pragma unroll
+            for (int c = 0; c < RC; ++c) sv[c] += l * q[c];
+        }
+#pragma unroll
+        for (int c = 0; c < RC; ++c) sv[c] = warp_sum(sv[c]);
+        double zi = 0.0;
+        if (lane < RC) {
+            zi = y[jj * RC + lane] - sv[lane];
+            if (MODE == FWD_T) zi /= (double)cv[dp];
+        }
+        __syncwarp();
+        if (lane < RC) y[jj * RC + lane] = zi;
+    }
+    __syncwarp();
+}
+
+// Whether two value panels of W columns fit in cap bytes (as doubles).
 template <typename T>
+__device__ bool panels_fit(const BlockView<T> &F, int m, int W, size_t cap) {
+    int64_t maxp = 0;
+    for (int j0 = 0; j0 < m; j0 += W) {
+        const int j1 = min(m, j0 + W);
+        int o0, c0, o1, c1;
+        const uint16_t *r0, *r1;
+        F.col(j0, o0, c0, r0);
+        F.col(j1 - 1, o1, c1, r1);
+        maxp = max(maxp, (int64_t)(o1 + c1 - o0));
+    }
+    return (size_t)(2 * maxp) * sizeof(double) <= cap;
+}
+
+// Diagonal part of a sweep: one CTA per diagonal block of the level.
+// y = x(block rows) minus the level's partials (fixed order), then the
+// chain over the block's columns by warp 0.  The block's index data is
+// staged in shared memory; its values too if they fit, otherwise they are
+// streamed through two column-panel buffers, warps 1-7 loading the next
+// panel while warp 0 works on the current one.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads)
-k_bwd_t(const int32_t *__restrict__ ids, BlockArgs a, const T *__restrict__ val,
-        const int64_t *__restrict__ boff, const int32_t *__restrict__ blk,
-        double *__restrict__ X, int64_t ldx, int nrhs) {
+k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
+       const int64_t *__restrict__ boff, const int64_t *__restrict__ poff,
+       BlockArgs a, const T *__restrict__ val, double *__restrict__ X,
+       int64_t ldx, int nc, const double *__restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int W = 16;
     const BlockDesc dd = a.bd[ids[blockIdx.x]];
     const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *z = reinterpret_cast<double *>(smem);
-    const int64_t b0 = boff[dd.I], b1 = boff[dd.I + 1];
-    for (int c = 0; c < nrhs; ++c) {
-        double *x = X + (int64_t)c * ldx;
-        for (int t = threadIdx.x; t < m; t += kThreads) z[t] = x[dd.r0 + t];
+    double *y = reinterpret_cast<double *>(smem);
+    const size_t ybytes = align16((size_t)m * RC * sizeof(double));
+    const int64_t p0 = pair0[blockIdx.x];
+    const int64_t np = boff[dd.I + 1] - boff[dd.I];
+    for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+        const int r = t / RC, c = t % RC;
+        double v = c < nc ? X[(int64_t)c * ldx + dd.r0 + r] : 0.0;
+        for (int64_t q = 0; q < np; ++q) v -= part[poff[p0 + q] * RC + t];
+        y[t] = v;
+    }
+    // values as double: full copy if it fits, else panel buffers
+    const int64_t nnz = dd.dense ? (int64_t)dd.ld * dd.cols
+                                 : (int64_t)a.lcolptr[dd.coff + dd.cols];
+    bool staged;
+    size_t used;
+    const size_t full = align16(nnz * sizeof(double));
+    const BlockView<T> F = stage_block<T>(dd, a, const_cast<T *>(val),
+                                          smem + ybytes, kStageSmem - ybytes,
+                                          true, &staged, &used);
+    // F.v is T; copy values into a double buffer for the chain
+    unsigned char *vbuf = smem + ybytes + used;
+    const size_t vcap = kStageSmem - ybytes - used;
+    const bool whole = staged ? false : full <= vcap;
+    const bool up = (MODE == FWD || MODE == FWD_T);
+    if (staged || whole) {
+        const T *src = F.v;
+        double *vd = reinterpret_cast<double *>(vbuf);
+        if (whole)
+            for (int64_t e = threadIdx.x; e < nnz; e += kThreads) vd[e] = (double)src[e];
         __syncthreads();
-        for (int ii = warp; ii < m; ii += kWarps) {
-            const double s = pull_dot(a, val, blk, b0, b1, ii, x);
-            if (lane == 0) z[ii] -= s;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            for (int ii = m - 1; ii >= 0; --ii) {
-                int64_t vb;
-                int cn;
+        if (warp == 0)
+            for (int k = 0; k < m; ++k) {
+                const int jj = up ? k : m - 1 - k;
+                int off, cn;
                 const uint16_t *rows;
-                colview(dd, ii, a, vb, cn, rows);
-                const int dp = a.dpos[dd.doff + ii];
-                double s = 0.0;
-                for (int e = dp + 1 + lane; e < cn; e += 32)
-                    s += (double)val[vb + e] * z[rowat(rows, e)];
-                s = warp_sum(s);
-                const double zi = z[ii] - s;
-                __syncwarp();
-                if (lane == 0) z[ii] = zi;
-                __syncwarp();
+                F.col(jj, off, cn, rows);
+                if (whole)
+                    chain_step<MODE>(jj, vd + off, rows, cn, F.dp[jj], y, lane);
+                else {
+                    // staged T values: convert on the fly through registers
+                    chain_step_t<T, MODE>(jj, F.v + off, rows, cn, F.dp[jj], y, lane);
+                }
             }
+    } else if (!panels_fit<T>(F, m, W, vcap)) {
+        // neither the block nor two panels fit: read values in place
+        __syncthreads();
+        if (warp == 0)
+            for (int k = 0; k < m; ++k) {
+                const int jj = up ? k : m - 1 - k;
+                int off, cn;
+                const uint16_t *rows;
+                F.col(jj, off, cn, rows);
+                chain_step_t<T, MODE>(jj, F.v + off, rows, cn, F.dp[jj], y, lane);
+            }
+    } else {
+        // panel streaming: W columns per panel, two buffers
+        const int npan = (m + W - 1) / W;
+        int64_t maxp = 0;
+        for (int pn = 0; pn < npan; ++pn) {
+            const int j0 = pn * W, j1 = min(m, j0 + W);
+            int o0, c0, o1, c1;
+            const uint16_t *r0, *r1;
+            F.col(j0, o0, c0, r0);
+            F.col(j1 - 1, o1, c1, r1);
+            maxp = max(maxp, (int64_t)(o1 + c1 - o0));
         }
+        double *buf[2] = {reinterpret_cast<double *>(vbuf),
+                          reinterpret_cast<double *>(vbuf) + maxp};
+        auto panel_of = [&](int q) { return up ? q : npan - 1 - q; };
+        auto load = [&](int pn, double *dst, int t0, int nt) {
+            const int j0 = pn * W, j1 = min(m, j0 + W);
+            int o0, c0, o1, c1;
+            const uint16_t *r0, *r1;
+            F.col(j0, o0, c0, r0);
+            F.col(j1 - 1, o1, c1, r1);
+            for (int64_t e = t0; e < (int64_t)(o1 + c1 - o0); e += nt)
+                dst[e] = (double)F.v[o0 + e];
+        };
+        load(panel_of(0), buf[0], threadIdx.x, kThreads);
         __syncthreads();
-        for (int t = threadIdx.x; t < m; t += kThreads) x[dd.r0 + t] = z[t];
-        __syncthreads();
+        for (int q = 0; q < npan; ++q) {
+            const int pn = panel_of(q);
+            if (warp == 0) {
+                const int j0 = pn * W, j1 = min(m, j0 + W);
+                int ob, cb;
+                const uint16_t *rb;
+                F.col(j0, ob, cb, rb);
+                for (int k = 0; k < j1 - j0; ++k) {
+                    const int jj = up ? j0 + k : j1 - 1 - k;
+                    int off, cn;
+                    const uint16_t *rows;
+                    F.col(jj, off, cn, rows);
+                    chain_step<MODE>(jj, buf[q & 1] + (off - ob), rows, cn,
+                                     F.dp[jj], y, lane);
+                }
+            } else if (q + 1 < npan) {
+                load(panel_of(q + 1), buf[(q + 1) & 1], threadIdx.x - 32,
+                     kThreads - 32);
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+        const int r = t / RC, c = t % RC;
+        if (c < nc) X[(int64_t)c * ldx + dd.r0 + r] = y[t];
     }
 }
 
@@ -313,39 +410,66 @@ __global__ void k_add_cols(int64_t n, int nrhs, const double *__restrict__ D,
 
 // ---------------------------------------------------------------- host side
 
-enum Sweep { FWD, BWD, FWD_T, BWD_T };
-
-template <typename T>
-static slu_status sweep(const slu_handle *h, Sweep sw, double *X, int64_t ldx,
-                        int nrhs, cudaStream_t st) {
+// One sweep over the levels (ascending for L and U^T, descending for U and
+// L^T), in chunks of RC right-hand sides; per level a pull launch (one CTA
+// per source block) and a diagonal launch (one CTA per diagonal block).
+template <typename T, int MODE>
+static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
+                          int nrhs, cudaStream_t st) {
     const slu_plan *P = h->plan;
     const DevPlan *D = P->dev;
     const T *val = static_cast<const T *>(h->storage);
     const BlockArgs a = block_args(P);
-    const bool scatter = (sw == FWD || sw == BWD);
-    const size_t smem =
-        (size_t)P->maxb * sizeof(double) * (scatter ? 1 + kWarps : 1);
-    auto *kern = sw == FWD ? k_fwd<T> : sw == BWD ? k_bwd<T>
-               : sw == FWD_T ? k_fwd_t<T> : k_bwd_t<T>;
-    const int64_t *off = sw == FWD ? D->lrow_off : sw == BWD ? D->urow_off
-                       : sw == FWD_T ? D->ucol_off : D->lcol_off;
-    const int32_t *blk = sw == FWD ? D->lrow_blk : sw == BWD ? D->urow_blk
-                       : sw == FWD_T ? D->ucol_blk : D->lcol_blk;
-    if (smem > 48 * 1024 &&
-        !cuda_ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem), "cudaFuncSetAttribute"))
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const size_t pull_smem = (size_t)kWarps * P->maxb * RC * sizeof(double);
+    if (pull_smem > kStageSmem)
+        return fail(SLU_ERR_NOT_SUPPORTED, "block too large for the solve");
+    if (!cuda_ok(cudaFuncSetAttribute(k_diag<T, MODE>, attr, (int)kStageSmem),
+                 "cudaFuncSetAttribute") ||
+        !cuda_ok(cudaFuncSetAttribute(k_pull_scatter<T>, attr, (int)kStageSmem),
+                 "cudaFuncSetAttribute"))
         return SLU_ERR_CUDA;
-    const bool up = (sw == FWD || sw == FWD_T);
-    for (int k = 0; k < P->nlevels; ++k) {
-        const int lv = up ? k : P->nlevels - 1 - k;
-        const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
-        if (g1 > g0) {
-            LaunchScope ls_(h, SLU_KC_SOLVE, st);
-            kern<<<(int)(g1 - g0), kThreads, smem, st>>>(D->getrf + g0, a, val,
-                                                       off, blk, X, ldx, nrhs);
+    const int64_t *boff = MODE == FWD ? D->lrow_off : MODE == BWD ? D->urow_off
+                        : MODE == FWD_T ? D->ucol_off : D->lcol_off;
+    const bool up = (MODE == FWD || MODE == FWD_T);
+    for (int c0 = 0; c0 < nrhs; c0 += RC) {
+        const int nc = std::min(RC, nrhs - c0);
+        double *Xc = X + (int64_t)c0 * ldx;
+        for (int k = 0; k < P->nlevels; ++k) {
+            const int lv = up ? k : P->nlevels - 1 - k;
+            const int64_t q0 = P->sp_off[MODE][lv], q1 = P->sp_off[MODE][lv + 1];
+            if (q1 > q0) {
+                LaunchScope ls_(h, SLU_KC_SOLVE, st);
+                if (MODE == FWD || MODE == BWD)
+                    k_pull_scatter<T><<<(int)(q1 - q0), kThreads, pull_smem, st>>>(
+                        D->sp_pairs[MODE] + 2 * q0, D->sp_poff[MODE] + q0, a, val,
+                        Xc, ldx, nc, h->part);
+                else
+                    k_pull_dot<T><<<(int)(q1 - q0), kThreads, 0, st>>>(
+                        D->sp_pairs[MODE] + 2 * q0, D->sp_poff[MODE] + q0, a, val,
+                        Xc, ldx, nc, h->part);
+            }
+            const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
+            if (g1 > g0) {
+                LaunchScope ls_(h, SLU_KC_SOLVE, st);
+                k_diag<T, MODE><<<(int)(g1 - g0), kThreads, kStageSmem, st>>>(
+                    D->getrf + g0, D->sd_pair0[MODE] + g0, boff, D->sp_poff[MODE], a,
+                    val, Xc, ldx, nc, h->part);
+            }
         }
     }
     return cuda_ok(cudaGetLastError(), "solve launch") ? SLU_OK : SLU_ERR_CUDA;
+}
+
+template <typename T>
+static slu_status sweep(const slu_handle *h, Sweep sw, double *X, int64_t ldx,
+                        int nrhs, cudaStream_t st) {
+    switch (sw) {
+        case FWD: return sweep_t<T, FWD>(h, X, ldx, nrhs, st);
+        case BWD: return sweep_t<T, BWD>(h, X, ldx, nrhs, st);
+        case FWD_T: return sweep_t<T, FWD_T>(h, X, ldx, nrhs, st);
+        default: return sweep_t<T, BWD_T>(h, X, ldx, nrhs, st);
+    }
 }
 
 static slu_status solve_inplace(const slu_handle *h, double *X, int64_t ldx,

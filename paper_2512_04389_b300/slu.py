@@ -70,7 +70,7 @@ EXPORTS = ["slu_opts_default", "slu_analyze", "slu_plan_query",
            "slu_plan_export", "slu_plan_export_blocks", "slu_plan_export_tasks",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
            "slu_export_factors", "slu_set_profiling", "slu_handle_stats",
-           "slu_plan_flops", "slu_solve_refine_noalloc", "slu_plan_destroy",
+           "slu_plan_flops", "slu_handle_trace", "slu_solve_refine_noalloc", "slu_plan_destroy",
            "slu_handle_destroy", "slu_last_error"]
 
 
@@ -98,6 +98,7 @@ def _load():
     lib.slu_set_profiling.argtypes = [P, C.c_int32]
     lib.slu_handle_stats.argtypes = [P, C.POINTER(Stats)]
     lib.slu_plan_flops.argtypes = [P, P]
+    lib.slu_handle_trace.argtypes = [P, C.c_int64, P, P, P]
     lib.slu_solve_refine_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P,
                                              C.c_int64, P, C.POINTER(SolveInfo)]
     lib.slu_plan_destroy.argtypes = [P]
@@ -300,6 +301,15 @@ class Factor:
         return {"launches": st.launches,
                 "calls": dict(zip(KERNEL_CLASSES, list(st.calls))),
                 "ms": dict(zip(KERNEL_CLASSES, list(st.ms)))}
+
+    def trace(self):
+        """(classes, ms) of every launch profiled so far, in launch order."""
+        n = np.zeros(1, np.int64)
+        _check(lib.slu_handle_trace(self._h, 0, None, None, _np(n)))
+        cls = np.empty(n[0], np.int32)
+        ms = np.empty(n[0], np.float32)
+        _check(lib.slu_handle_trace(self._h, n[0], _np(cls), _np(ms), _np(n)))
+        return cls, ms
 
     def export_factors(self, stream=None):
         """Factor values (FP64) in the order of ``plan.export()``'s pattern."""
