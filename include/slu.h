@@ -147,6 +147,21 @@ void slu_opts_default(slu_opts *opts);
 slu_status slu_analyze(int64_t n, const int64_t *colptr, const int32_t *rowidx,
                        const slu_opts *opts, slu_plan **out);
 
+/* Batch analysis: `count` independent square matrices (member q: order
+ * n[q], CSC colptr[q] / rowidx[q], host) analysed as one block-diagonal
+ * system of order sum n[q].  Each member is blocked on its own (its own
+ * diagonal block pointer, samples and Algorithm 3), and the level lists of
+ * all members are merged, so one launch per level and kernel class walks
+ * every member's tasks of that level.  Values, right-hand sides and
+ * solutions of the batch plan are the members' concatenated in order
+ * (values: member 0's CSC values, then member 1's, ...; rows likewise).
+ * Refinement measures the backward error of every member separately and
+ * stops when the largest is <= refine_tol. */
+slu_status slu_analyze_batch(int32_t count, const int64_t *n,
+                             const int64_t *const *colptr,
+                             const int32_t *const *rowidx,
+                             const slu_opts *opts, slu_plan **out);
+
 slu_status slu_plan_query(const slu_plan *plan, slu_plan_info *info);
 
 /* Copies of the plan's host arrays, for bit-exact checks.  Every output is
@@ -195,6 +210,13 @@ slu_status slu_factor(const slu_plan *plan, const double *values,
 slu_status slu_refactor(slu_handle *h, const double *values, void *stream,
                         slu_factor_info *info);
 
+/* Graph mode: when enabled, slu_refactor records its launch sequence into
+ * a CUDA graph on its first call (and again whenever `values` differs from
+ * the recorded pointer) and replays the graph afterwards.  The stream given
+ * to slu_refactor must then be a created stream, not the legacy NULL
+ * stream, and profiling is ignored while recording. */
+slu_status slu_set_graph(slu_handle *h, int32_t enable);
+
 /* X = A^{-1} B.  B, X: device, float64, column-major n x nrhs with leading
  * dimensions ldb, ldx >= n, 1 <= nrhs <= 64; X may alias B.  With
  * refinement (FP32 factors by default, or refine_max_iter > 0) the call
@@ -213,6 +235,16 @@ slu_status slu_solve(const slu_handle *h, const double *B, int64_t ldb,
 slu_status slu_solve_transpose(const slu_handle *h, const double *G,
                                int64_t ldg, int32_t nrhs, double *Lam,
                                int64_t ldl, void *stream);
+
+/* Gradient of a loss l(x), x = A^{-1} B, with respect to the stored values
+ * of A, given Lam = A^{-T} (dl/dx) (slu_solve_transpose) and X:
+ *   grad[p] = - sum_c Lam(row_p, c) X(col_p, c)
+ * over the entries p of A's pattern in the CSC order given to slu_analyze
+ * (dA = -Lam X^T restricted to the pattern).  Lam, X: device, column-major
+ * n x nrhs; grad: device float64[nnz_a]. */
+slu_status slu_grad_values(const slu_handle *h, const double *Lam, int64_t ldl,
+                           const double *X, int64_t ldx, int32_t nrhs,
+                           double *grad, void *stream);
 
 /* Factor values in the order of the plan's filled pattern (slu_plan_export
  * colptr/rowidx): rows < col hold U, the diagonal holds U's, rows > col hold

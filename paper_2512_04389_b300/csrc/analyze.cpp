@@ -578,9 +578,13 @@ static void build_levels_and_tasks(slu_plan &P) {
     }
 }
 
-extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,
-                                  const int32_t *rowidx, const slu_opts *opts,
-                                  slu_plan **out) {
+// Analysis of one pattern; `seg` (row offsets, size nseg + 1) splits it
+// into independent diagonal segments (a batch of matrices laid out block-
+// diagonally), each blocked on its own.
+static slu_status analyze_impl(int64_t n, const int64_t *colptr,
+                               const int32_t *rowidx, const slu_opts *opts,
+                               const std::vector<int64_t> &seg,
+                               slu_plan **out) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!out) return fail(SLU_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -628,6 +632,9 @@ extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,
         P->nnz_a = nnz;
         P->a_colptr.assign(colptr, colptr + n + 1);
         P->a_rowidx.assign(rowidx, rowidx + nnz);
+        P->a_ci.resize(nnz);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) P->a_ci[q] = (int32_t)j;
         // CSR view of A for the residual
         P->a_rowptr.assign(n + 1, 0);
         for (int64_t q = 0; q < nnz; ++q) P->a_rowptr[rowidx[q] + 1]++;
@@ -685,22 +692,38 @@ extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,
         P->blockptr.assign(n + 1, 0);
         diagonal_block_pointer(n, P->f_colptr.data(), P->f_rowidx.data(),
                                P->blockptr.data());
-        if (n == 0) {
-            P->ptr.assign(1, 0);
-            P->samples = 0;
-        } else if (o.blocking == SLU_BLOCKING_IRREGULAR) {
-            int64_t S_ = std::min<int64_t>(o.sample_points, n / o.b_min);
-            if (S_ < 1) S_ = 1;
-            P->samples = (int32_t)S_;
-            irregular_blocking(n, P->blockptr.data(), (int32_t)S_, o.step,
-                               o.max_num, o.stride, P->ptr);
-        } else {
-            P->ptr.clear();
-            for (int64_t r = 0; r < n; r += o.regular_block) P->ptr.push_back(r);
-            P->ptr.push_back(n);
-            P->samples = 0;
+        // blocking, segment by segment: for a block-diagonal pattern the
+        // diagonal block pointer of segment [s0, s1) is bp[s0 + k] - bp[s0]
+        P->seg = seg;
+        P->ptr.assign(1, 0);
+        P->samples = 0;
+        std::vector<int64_t> bps, ps;
+        for (size_t q = 0; q + 1 < seg.size(); ++q) {
+            const int64_t s0 = seg[q], N = seg[q + 1] - seg[q];
+            if (N == 0) continue;
+            if (o.blocking == SLU_BLOCKING_IRREGULAR) {
+                bps.resize(N + 1);
+                for (int64_t k = 0; k <= N; ++k)
+                    bps[k] = P->blockptr[s0 + k] - P->blockptr[s0];
+                int64_t S_ = std::min<int64_t>(o.sample_points, N / o.b_min);
+                if (S_ < 1) S_ = 1;
+                P->samples = std::max<int32_t>(P->samples, (int32_t)S_);
+                irregular_blocking(N, bps.data(), (int32_t)S_, o.step,
+                                   o.max_num, o.stride, ps);
+            } else {
+                ps.clear();
+                for (int64_t r = 0; r < N; r += o.regular_block) ps.push_back(r);
+                ps.push_back(N);
+            }
+            for (size_t t = 1; t < ps.size(); ++t) P->ptr.push_back(s0 + ps[t]);
         }
         P->p = (int32_t)P->ptr.size() - 1;
+        P->row_seg.clear();
+        if (seg.size() > 2) {
+            P->row_seg.resize(n);
+            for (size_t q = 0; q + 1 < seg.size(); ++q)
+                for (int64_t r = seg[q]; r < seg[q + 1]; ++r) P->row_seg[r] = (int32_t)q;
+        }
         const slu_status st = build_blocks(*P);
         if (st != SLU_OK) {
             delete P;
@@ -738,6 +761,48 @@ extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,
                         std::chrono::steady_clock::now() - t0).count();
     *out = P;
     return SLU_OK;
+}
+
+extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,
+                                  const int32_t *rowidx, const slu_opts *opts,
+                                  slu_plan **out) {
+    return analyze_impl(n, colptr, rowidx, opts,
+                        std::vector<int64_t>{0, std::max<int64_t>(n, 0)}, out);
+}
+
+extern "C" slu_status slu_analyze_batch(int32_t count, const int64_t *n,
+                                        const int64_t *const *colptr,
+                                        const int32_t *const *rowidx,
+                                        const slu_opts *opts, slu_plan **out) {
+    if (!out) return fail(SLU_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !n || !colptr || !rowidx)
+        return fail(SLU_ERR_INVALID_ARG, "bad batch arguments");
+    std::vector<int64_t> seg(1, 0);
+    int64_t nnz = 0;
+    for (int32_t q = 0; q < count; ++q) {
+        if (n[q] < 0 || !colptr[q] || (n[q] > 0 && !rowidx[q]))
+            return fail(SLU_ERR_INVALID_ARG, "bad batch member");
+        seg.push_back(seg.back() + n[q]);
+        nnz += colptr[q][n[q]];
+    }
+    const int64_t N = seg.back();
+    if (N > INT32_MAX - 1) return fail(SLU_ERR_INVALID_ARG, "batch too large");
+    std::vector<int64_t> cp(N + 1, 0);
+    std::vector<int32_t> ri;
+    ri.reserve(nnz);
+    for (int32_t q = 0; q < count; ++q) {
+        for (int64_t j = 0; j < n[q]; ++j) {
+            for (int64_t e = colptr[q][j]; e < colptr[q][j + 1]; ++e) {
+                const int32_t r = rowidx[q][e];
+                if (r < 0 || r >= n[q])
+                    return fail(SLU_ERR_INVALID_ARG, "row index out of range");
+                ri.push_back((int32_t)(seg[q] + r));
+            }
+            cp[seg[q] + j + 1] = (int64_t)ri.size();
+        }
+    }
+    return analyze_impl(N, cp.data(), ri.data(), opts, seg, out);
 }
 
 extern "C" slu_status slu_plan_query(const slu_plan *P, slu_plan_info *info) {

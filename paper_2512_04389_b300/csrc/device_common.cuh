@@ -26,6 +26,8 @@ struct DevPlan {
     int64_t *a2s = nullptr, *f2s = nullptr;
     int64_t *a_rowptr = nullptr, *a_vpos = nullptr;
     int32_t *a_colidx = nullptr;
+    int32_t *a_ri = nullptr, *a_ci = nullptr;   // A's entries: row, column
+    int32_t *row_seg = nullptr;                  // batch member of each row
     int32_t *sp_pairs[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t *sp_poff[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t *sd_pair0[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -194,6 +196,12 @@ struct slu_handle {
     int64_t work_elems = 0;
     double *red = nullptr;               // reduction scratch for refinement
     double *part = nullptr;              // solve partial sums (factor time)
+    double *anorm_seg = nullptr;         // batch: ||A_q||_inf per member
+    // graph mode
+    bool use_graph = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    const double *graph_values = nullptr;
+    bool capturing = false;
     // launch accounting and optional per-launch event timing
     int64_t launches = 0;
     bool profiling = false;
@@ -214,7 +222,7 @@ struct LaunchScope {
     LaunchScope(const slu_handle *hc, int c, cudaStream_t s)
         : h(const_cast<slu_handle *>(hc)), cls(c), st(s) {
         h->launches++;
-        if (h->profiling) {
+        if (h->profiling && !h->capturing) {
             cudaEventCreate(&a);
             cudaEventCreate(&b);
             cudaEventRecord(a, st);

@@ -53,6 +53,19 @@ __global__ void k_anorm(int64_t n, const int64_t *__restrict__ rp,
         atomicMax(out, (unsigned long long)__double_as_longlong(s));
 }
 
+// Batch: ||A_q||_inf per member q (row sums of the member's rows).
+__global__ void k_anorm_seg(int64_t n, const int64_t *__restrict__ rp,
+                            const int64_t *__restrict__ vpos,
+                            const double *__restrict__ v,
+                            const int32_t *__restrict__ row_seg,
+                            unsigned long long *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) s += fabs(v[vpos[q]]);
+    if (s > 0.0) atomicMax(&out[row_seg[i]], (unsigned long long)__double_as_longlong(s));
+}
+
 template <typename T>
 __global__ void k_scatter(int64_t n, const int64_t *__restrict__ a2s,
                           const double *__restrict__ v, T *__restrict__ val) {
@@ -637,6 +650,7 @@ void free_dev_plan(slu_plan *P) {
                     D->getrf, D->gessm, D->tstrf, D->tgt, D->src, D->srcoff,
                     D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
+                    D->a_ri, D->a_ci, D->row_seg,
                     D->lrow_off, D->urow_off, D->ucol_off, D->lcol_off,
                     D->lrow_blk, D->urow_blk, D->ucol_blk, D->lcol_blk};
     for (void *p : ptrs)
@@ -673,6 +687,8 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->a2s, &D->a2s) && upload(P->f2s, &D->f2s) &&
         upload(P->a_rowptr, &D->a_rowptr) && upload(P->a_vpos, &D->a_vpos) &&
         upload(P->a_colidx, &D->a_colidx) &&
+        upload(P->a_rowidx, &D->a_ri) && upload(P->a_ci, &D->a_ci) &&
+        upload(P->row_seg, &D->row_seg) &&
         upload(P->lrow_off, &D->lrow_off) && upload(P->urow_off, &D->urow_off) &&
         upload(P->ucol_off, &D->ucol_off) && upload(P->lcol_off, &D->lcol_off) &&
         upload(P->lrow_blk, &D->lrow_blk) && upload(P->urow_blk, &D->urow_blk) &&
@@ -736,6 +752,16 @@ static slu_status run_factor(slu_handle *h, const double *values,
                 P->n, D->a_rowptr, D->a_vpos, values,
                 reinterpret_cast<unsigned long long *>(h->scal + 1));
         }
+        if (h->anorm_seg) {
+            const int nseg = (int)P->seg.size() - 1;
+            if (!cuda_ok(cudaMemsetAsync(h->anorm_seg, 0, nseg * sizeof(double), st),
+                         "cudaMemsetAsync"))
+                return SLU_ERR_CUDA;
+            LaunchScope ls_(h, SLU_KC_PREP, st);
+            k_anorm_seg<<<(int)((P->n + 255) / 256), 256, 0, st>>>(
+                P->n, D->a_rowptr, D->a_vpos, values, D->row_seg,
+                reinterpret_cast<unsigned long long *>(h->anorm_seg));
+        }
         if (!cuda_ok(cudaMemcpyAsync(h->a_vals, values, P->nnz_a * sizeof(double),
                                      cudaMemcpyDeviceToDevice, st),
                      "cudaMemcpyAsync(A)"))
@@ -748,8 +774,6 @@ static slu_status run_factor(slu_handle *h, const double *values,
     }
     const size_t smem_f = (size_t)kWarps * P->maxb * sizeof(double);
     const size_t smem_a = (size_t)kWarps * P->maxb * sizeof(Acc);
-    if (set_smem_limits<T, Acc>(std::max(smem_f, smem_a)) != SLU_OK)
-        return SLU_ERR_CUDA;
     const size_t smem_big = std::max(kStageSmem, std::max(smem_f, smem_a));
     for (int lv = 0; lv < P->nlevels; ++lv) {
         const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
@@ -800,6 +824,16 @@ static slu_status finish_info(slu_handle *h, cudaStream_t st,
     return SLU_OK;
 }
 
+// Kernel attributes (dynamic shared memory limits), set once per handle
+// before any launch so that graph recording captures stream work only.
+slu_status init_solve_attrs(const slu_handle *h);
+static slu_status init_factor_attrs(const slu_handle *h) {
+    const slu_plan *P = h->plan;
+    const size_t g = (size_t)kWarps * P->maxb * sizeof(double);
+    return h->prec == SLU_PREC_FP64 ? set_smem_limits<double, double>(g)
+                                    : set_smem_limits<float, float>(g);
+}
+
 slu_status factor_into(slu_handle *h, const double *values, cudaStream_t st) {
     return h->prec == SLU_PREC_FP64 ? run_factor<double>(h, values, st)
                                     : run_factor<float>(h, values, st);
@@ -818,8 +852,9 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red,
-                    h->part};
+                    h->part, h->anorm_seg};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (cur >= 0) cudaSetDevice(cur);
@@ -855,13 +890,18 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
                 "cudaMalloc(A)") &&
         cuda_ok(cudaMalloc(&h->part, std::max<int64_t>(1, P->part_elems) * 4 *
                                          sizeof(double)),
-                "cudaMalloc(solve partials)");
+                "cudaMalloc(solve partials)") &&
+        (P->seg.size() <= 2 ||
+         cuda_ok(cudaMalloc(&h->anorm_seg, (P->seg.size() - 1) * sizeof(double)),
+                 "cudaMalloc(anorm_seg)"));
     if (!ok) {
         slu_handle_destroy(h);
         return SLU_ERR_OUT_OF_MEMORY;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    st = factor_into(h, values, s);
+    st = init_factor_attrs(h);
+    if (st == SLU_OK) st = init_solve_attrs(h);
+    if (st == SLU_OK) st = factor_into(h, values, s);
     if (st == SLU_OK) st = finish_info(h, s, info);
     if (st != SLU_OK && st != SLU_ERR_SINGULAR) {
         slu_handle_destroy(h);
@@ -877,9 +917,50 @@ extern "C" slu_status slu_refactor(slu_handle *h, const double *values,
     if (h->plan->nnz_a > 0 && !values)
         return fail(SLU_ERR_INVALID_ARG, "values is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const slu_status st = factor_into(h, values, s);
-    if (st != SLU_OK) return st;
+    slu_status st = SLU_OK;
+    if (h->use_graph) {
+        if (s == nullptr)
+            return fail(SLU_ERR_INVALID_ARG, "graph mode needs a created stream");
+        if (!h->graph_exec || h->graph_values != values) {
+            if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+            cudaGraph_t g = nullptr;
+            if (!cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal),
+                         "cudaStreamBeginCapture"))
+                return SLU_ERR_CUDA;
+            h->capturing = true;
+            st = factor_into(h, values, s);
+            h->capturing = false;
+            const cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (st != SLU_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (!cuda_ok(e, "cudaStreamEndCapture")) return SLU_ERR_CUDA;
+            const bool ok = cuda_ok(cudaGraphInstantiate(&h->graph_exec, g, 0),
+                                    "cudaGraphInstantiate");
+            cudaGraphDestroy(g);
+            if (!ok) return SLU_ERR_CUDA;
+            h->graph_values = values;
+        }
+        if (!cuda_ok(cudaGraphLaunch(h->graph_exec, s), "cudaGraphLaunch"))
+            return SLU_ERR_CUDA;
+    } else {
+        st = factor_into(h, values, s);
+        if (st != SLU_OK) return st;
+    }
     if (info) return finish_info(h, s, info);
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_set_graph(slu_handle *h, int32_t enable) {
+    if (!h) return fail(SLU_ERR_INVALID_ARG, "NULL handle");
+    h->use_graph = enable != 0;
+    if (!h->use_graph && h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        h->graph_values = nullptr;
+    }
     return SLU_OK;
 }
 

@@ -54,6 +54,7 @@ struct slu_plan {
     std::vector<int64_t> a_rowptr;       // CSR of A
     std::vector<int32_t> a_colidx;
     std::vector<int64_t> a_vpos;         // CSR entry -> position in values
+    std::vector<int32_t> a_ci;           // column of each CSC entry of A
     // filled, structurally symmetric L+U pattern (rows sorted)
     std::vector<int64_t> f_colptr;
     std::vector<int32_t> f_rowidx;
@@ -63,6 +64,8 @@ struct slu_plan {
     std::vector<int64_t> blockptr;       // Algorithm 2, n+1
     std::vector<int64_t> ptr;            // boundaries, p+1
     int32_t p = 0, samples = 0, maxb = 0;
+    std::vector<int64_t> seg;            // batch: row offsets of the members
+    std::vector<int32_t> row_seg;        // batch: member of each row
     std::vector<int32_t> rowblk;         // row -> block index
     // blocks, sorted by (J, I)
     std::vector<slu::BlockDesc> blocks;

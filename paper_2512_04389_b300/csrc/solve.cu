@@ -399,6 +399,57 @@ __global__ void k_norms(int64_t n, int nrhs, const double *__restrict__ R,
     }
 }
 
+// grad[p] = -sum_c Lam(row_p, c) X(col_p, c) over A's entries.
+__global__ void k_grad_values(int64_t nnz, const int32_t *__restrict__ ri,
+                              const int32_t *__restrict__ ci, int nrhs,
+                              const double *__restrict__ Lam, int64_t ldl,
+                              const double *__restrict__ X, int64_t ldx,
+                              double *__restrict__ grad) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nrhs; ++c)
+            s += Lam[ri[p] + (int64_t)c * ldl] * X[ci[p] + (int64_t)c * ldx];
+        grad[p] = -s;
+    }
+}
+
+// Batch: red[(q * nrhs + c) * 3 + {0,1,2}] = max |R|, |X|, |B| over the
+// rows of member q; warps whose 32 rows share a member reduce first.
+__global__ void k_norms_seg(int64_t n, int nrhs, const double *__restrict__ R,
+                            int64_t ldr, const double *__restrict__ X,
+                            int64_t ldx, const double *__restrict__ B,
+                            int64_t ldb, const int32_t *__restrict__ row_seg,
+                            unsigned long long *__restrict__ red) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool in = i < n;
+    const int q = in ? row_seg[i] : -1;
+    const int q0 = __shfl_sync(~0u, q, 0);
+    const bool same = __all_sync(~0u, q == q0 || !in);
+    for (int c = 0; c < nrhs; ++c) {
+        double v[3] = {0.0, 0.0, 0.0};
+        if (in) {
+            v[0] = fabs(R[i + c * ldr]);
+            v[1] = fabs(X[i + c * ldx]);
+            v[2] = fabs(B[i + c * ldb]);
+        }
+        if (same) {
+            for (int o = 16; o > 0; o >>= 1)
+                for (int k = 0; k < 3; ++k) v[k] = fmax(v[k], __shfl_xor_sync(~0u, v[k], o));
+            if ((threadIdx.x & 31) == 0 && q0 >= 0)
+                for (int k = 0; k < 3; ++k)
+                    if (v[k] > 0)
+                        atomicMax(&red[((int64_t)q0 * nrhs + c) * 3 + k],
+                                  (unsigned long long)__double_as_longlong(v[k]));
+        } else if (in) {
+            for (int k = 0; k < 3; ++k)
+                if (v[k] > 0)
+                    atomicMax(&red[((int64_t)q * nrhs + c) * 3 + k],
+                              (unsigned long long)__double_as_longlong(v[k]));
+        }
+    }
+}
+
 __global__ void k_add_cols(int64_t n, int nrhs, const double *__restrict__ D,
                            int64_t ldd, double *__restrict__ X, int64_t ldx) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -420,15 +471,9 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
     const DevPlan *D = P->dev;
     const T *val = static_cast<const T *>(h->storage);
     const BlockArgs a = block_args(P);
-    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     const size_t pull_smem = (size_t)kWarps * P->maxb * RC * sizeof(double);
     if (pull_smem > kStageSmem)
         return fail(SLU_ERR_NOT_SUPPORTED, "block too large for the solve");
-    if (!cuda_ok(cudaFuncSetAttribute(k_diag<T, MODE>, attr, (int)kStageSmem),
-                 "cudaFuncSetAttribute") ||
-        !cuda_ok(cudaFuncSetAttribute(k_pull_scatter<T>, attr, (int)kStageSmem),
-                 "cudaFuncSetAttribute"))
-        return SLU_ERR_CUDA;
     const int64_t *boff = MODE == FWD ? D->lrow_off : MODE == BWD ? D->urow_off
                         : MODE == FWD_T ? D->ucol_off : D->lcol_off;
     const bool up = (MODE == FWD || MODE == FWD_T);
@@ -462,6 +507,17 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
 }
 
 template <typename T>
+static bool solve_attrs_t() {
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const int b = (int)kStageSmem;
+    return cuda_ok(cudaFuncSetAttribute(k_diag<T, FWD>, attr, b), "attr") &&
+           cuda_ok(cudaFuncSetAttribute(k_diag<T, BWD>, attr, b), "attr") &&
+           cuda_ok(cudaFuncSetAttribute(k_diag<T, FWD_T>, attr, b), "attr") &&
+           cuda_ok(cudaFuncSetAttribute(k_diag<T, BWD_T>, attr, b), "attr") &&
+           cuda_ok(cudaFuncSetAttribute(k_pull_scatter<T>, attr, b), "attr");
+}
+
+template <typename T>
 static slu_status sweep(const slu_handle *h, Sweep sw, double *X, int64_t ldx,
                         int nrhs, cudaStream_t st) {
     switch (sw) {
@@ -470,6 +526,12 @@ static slu_status sweep(const slu_handle *h, Sweep sw, double *X, int64_t ldx,
         case FWD_T: return sweep_t<T, FWD_T>(h, X, ldx, nrhs, st);
         default: return sweep_t<T, BWD_T>(h, X, ldx, nrhs, st);
     }
+}
+
+slu_status init_solve_attrs(const slu_handle *h) {
+    const bool ok = h->prec == SLU_PREC_FP64 ? solve_attrs_t<double>()
+                                             : solve_attrs_t<float>();
+    return ok ? SLU_OK : SLU_ERR_CUDA;
 }
 
 static slu_status solve_inplace(const slu_handle *h, double *X, int64_t ldx,
@@ -494,8 +556,9 @@ static slu_status ensure_work(slu_handle *h, int64_t elems) {
             return SLU_ERR_OUT_OF_MEMORY;
         h->work_elems = elems;
     }
+    const size_t nseg = h->anorm_seg ? h->plan->seg.size() - 1 : 1;
     if (!h->red &&
-        !cuda_ok(cudaMalloc(&h->red, 3 * 64 * sizeof(double)), "cudaMalloc(red)"))
+        !cuda_ok(cudaMalloc(&h->red, 3 * 64 * nseg * sizeof(double)), "cudaMalloc(red)"))
         return SLU_ERR_OUT_OF_MEMORY;
     return SLU_OK;
 }
@@ -511,41 +574,50 @@ static slu_status copy_cols(double *dst, int64_t ldd, const double *src,
                : SLU_ERR_CUDA;
 }
 
-// Residual R = B - A X and the normwise backward error (max over columns).
+// Residual R = B - A X and the normwise backward error (max over columns,
+// and over the members of a batch plan).
 static slu_status backward_error(slu_handle *h, const double *B, int64_t ldb,
                                  const double *X, int64_t ldx, int nrhs,
                                  double *R, cudaStream_t st, double *be) {
     const slu_plan *P = h->plan;
     const DevPlan *D = P->dev;
     const int64_t n = P->n;
+    const int nseg = h->anorm_seg ? (int)P->seg.size() - 1 : 1;
     {
         LaunchScope ls_(h, SLU_KC_RESID, st);
         k_residual<<<(int)((n * 32 + 255) / 256), 256, 0, st>>>(
-        n, nrhs, D->a_rowptr, D->a_colidx, D->a_vpos, h->a_vals, B, ldb, X, ldx,
-        R, n);
+            n, nrhs, D->a_rowptr, D->a_colidx, D->a_vpos, h->a_vals, B, ldb, X,
+            ldx, R, n);
     }
-    if (!cuda_ok(cudaMemsetAsync(h->red, 0, 3 * nrhs * sizeof(double), st),
+    if (!cuda_ok(cudaMemsetAsync(h->red, 0, 3 * (size_t)nseg * nrhs * sizeof(double), st),
                  "cudaMemsetAsync"))
         return SLU_ERR_CUDA;
     {
         LaunchScope ls_(h, SLU_KC_RESID, st);
-        k_norms<<<148 * 2, 256, 0, st>>>(
-            n, nrhs, R, n, X, ldx, B, ldb,
-            reinterpret_cast<unsigned long long *>(h->red));
+        if (nseg > 1)
+            k_norms_seg<<<(int)((n + 255) / 256), 256, 0, st>>>(
+                n, nrhs, R, n, X, ldx, B, ldb, D->row_seg,
+                reinterpret_cast<unsigned long long *>(h->red));
+        else
+            k_norms<<<148 * 2, 256, 0, st>>>(
+                n, nrhs, R, n, X, ldx, B, ldb,
+                reinterpret_cast<unsigned long long *>(h->red));
     }
-    double hr[3 * 64 + 1];
-    if (!cuda_ok(cudaMemcpyAsync(hr, h->red, 3 * nrhs * sizeof(double),
+    std::vector<double> hr(3 * (size_t)nseg * nrhs), an(nseg);
+    if (!cuda_ok(cudaMemcpyAsync(hr.data(), h->red, hr.size() * sizeof(double),
                                  cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
-        !cuda_ok(cudaMemcpyAsync(hr + 3 * 64, h->scal + 1, sizeof(double),
-                                 cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
+        !cuda_ok(cudaMemcpyAsync(an.data(), nseg > 1 ? h->anorm_seg : h->scal + 1,
+                                 nseg * sizeof(double), cudaMemcpyDeviceToHost, st),
+                 "cudaMemcpyAsync") ||
         !cuda_ok(cudaStreamSynchronize(st), "residual"))
         return SLU_ERR_CUDA;
-    const double anorm = hr[3 * 64];
     double worst = 0.0;
-    for (int c = 0; c < nrhs; ++c) {
-        const double den = anorm * hr[3 * c + 1] + hr[3 * c + 2];
-        worst = std::max(worst, den > 0 ? hr[3 * c] / den : 0.0);
-    }
+    for (int q = 0; q < nseg; ++q)
+        for (int c = 0; c < nrhs; ++c) {
+            const double *r = &hr[((size_t)q * nrhs + c) * 3];
+            const double den = an[q] * r[1] + r[2];
+            worst = std::max(worst, den > 0 ? r[0] / den : 0.0);
+        }
     *be = worst;
     return SLU_OK;
 }
@@ -616,6 +688,26 @@ extern "C" slu_status slu_solve(const slu_handle *ch, const double *B,
     if (maxit > 0 && !(be <= P->opts.refine_tol))
         return fail(SLU_ERR_NOT_CONVERGED, "refinement did not reach refine_tol");
     return SLU_OK;
+}
+
+extern "C" slu_status slu_grad_values(const slu_handle *h, const double *Lam,
+                                      int64_t ldl, const double *X,
+                                      int64_t ldx, int32_t nrhs, double *grad,
+                                      void *stream) {
+    if (!h || !Lam || !X || !grad) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
+    const slu_plan *P = h->plan;
+    if (nrhs < 1 || ldl < P->n || ldx < P->n)
+        return fail(SLU_ERR_INVALID_ARG, "bad nrhs or leading dimension");
+    if (P->nnz_a == 0) return SLU_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    {
+        LaunchScope ls_(h, SLU_KC_RESID, st);
+        const int64_t g = std::min<int64_t>((P->nnz_a + 255) / 256, 148 * 32);
+        k_grad_values<<<(int)g, 256, 0, st>>>(P->nnz_a, P->dev->a_ri,
+                                              P->dev->a_ci, nrhs, Lam, ldl, X,
+                                              ldx, grad);
+    }
+    return cuda_ok(cudaGetLastError(), "grad launch") ? SLU_OK : SLU_ERR_CUDA;
 }
 
 extern "C" slu_status slu_solve_transpose(const slu_handle *h, const double *G,

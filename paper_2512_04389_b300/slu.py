@@ -66,11 +66,12 @@ class Stats(C.Structure):
 
 
 # every entry point declared in include/slu.h
-EXPORTS = ["slu_opts_default", "slu_analyze", "slu_plan_query",
+EXPORTS = ["slu_opts_default", "slu_analyze", "slu_analyze_batch",
+           "slu_plan_query",
            "slu_plan_export", "slu_plan_export_blocks", "slu_plan_export_tasks",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
-           "slu_export_factors", "slu_set_profiling", "slu_handle_stats",
-           "slu_plan_flops", "slu_handle_trace", "slu_solve_refine_noalloc", "slu_plan_destroy",
+           "slu_export_factors", "slu_grad_values", "slu_set_profiling", "slu_handle_stats",
+           "slu_plan_flops", "slu_handle_trace", "slu_set_graph", "slu_solve_refine_noalloc", "slu_plan_destroy",
            "slu_handle_destroy", "slu_last_error"]
 
 
@@ -84,6 +85,8 @@ def _load():
     lib.slu_opts_default.argtypes = [C.POINTER(Opts)]
     lib.slu_opts_default.restype = None
     lib.slu_analyze.argtypes = [C.c_int64, P, P, C.POINTER(Opts), C.POINTER(P)]
+    lib.slu_analyze_batch.argtypes = [C.c_int32, P, P, P, C.POINTER(Opts),
+                                      C.POINTER(P)]
     lib.slu_plan_query.argtypes = [P, C.POINTER(PlanInfo)]
     lib.slu_plan_export.argtypes = [P, P, P, P, P]
     lib.slu_plan_export_blocks.argtypes = [P, P, P, P, P, P]
@@ -95,10 +98,13 @@ def _load():
     lib.slu_solve_transpose.argtypes = [P, P, C.c_int64, C.c_int32, P,
                                         C.c_int64, P]
     lib.slu_export_factors.argtypes = [P, P, P]
+    lib.slu_grad_values.argtypes = [P, P, C.c_int64, P, C.c_int64, C.c_int32,
+                                    P, P]
     lib.slu_set_profiling.argtypes = [P, C.c_int32]
     lib.slu_handle_stats.argtypes = [P, C.POINTER(Stats)]
     lib.slu_plan_flops.argtypes = [P, P]
     lib.slu_handle_trace.argtypes = [P, C.c_int64, P, P, P]
+    lib.slu_set_graph.argtypes = [P, C.c_int32]
     lib.slu_solve_refine_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P,
                                              C.c_int64, P, C.POINTER(SolveInfo)]
     lib.slu_plan_destroy.argtypes = [P]
@@ -179,6 +185,8 @@ class Plan:
 
     def __init__(self, n, colptr, rowidx, **opts):
         self._h = C.c_void_p()
+        if isinstance(n, (list, tuple)):          # batch of matrices
+            return self._init_batch(n, colptr, rowidx, opts)
         self.n = int(n)
         self.colptr = np.ascontiguousarray(colptr, dtype=np.int64)
         self.rowidx = np.ascontiguousarray(rowidx, dtype=np.int32)
@@ -188,6 +196,22 @@ class Plan:
         i = PlanInfo()
         _check(lib.slu_plan_query(self._h, C.byref(i)))
         self.info = {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+
+    def _init_batch(self, ns, colptrs, rowidxs, opts):
+        k = len(ns)
+        self.members = [int(x) for x in ns]
+        self._cps = [np.ascontiguousarray(c, dtype=np.int64) for c in colptrs]
+        self._ris = [np.ascontiguousarray(r, dtype=np.int32) for r in rowidxs]
+        na = np.asarray(self.members, dtype=np.int64)
+        cpa = (C.c_void_p * k)(*[c.ctypes.data for c in self._cps])
+        ria = (C.c_void_p * k)(*[r.ctypes.data for r in self._ris])
+        self.opts = default_opts(**opts)
+        _check(lib.slu_analyze_batch(k, _np(na), cpa, ria, C.byref(self.opts),
+                                     C.byref(self._h)))
+        self.n = int(na.sum())
+        i = PlanInfo()
+        _check(lib.slu_plan_query(self._h, C.byref(i)))
+        self.info = {kk: getattr(i, kk) for kk, _ in PlanInfo._fields_}
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -290,6 +314,23 @@ class Factor:
         _check(lib.slu_solve_transpose(self._h, _dev_ptr(Gc), ldg, k,
                                        _dev_ptr(L), ldl, _stream_ptr(stream)))
         return L.reshape(-1) if vec else L
+
+    def grad_values(self, Lam, X, stream=None):
+        """-sum_c Lam(row_p, c) X(col_p, c) over A's pattern (CSC order)."""
+        import torch
+        Lc, ldl, k, _ = _colmajor(Lam)
+        Xc, ldx, k2, _ = _colmajor(X)
+        assert k == k2
+        out = torch.empty(self.plan.info["nnz_a"], dtype=torch.float64,
+                          device=Lc.device)
+        _check(lib.slu_grad_values(self._h, _dev_ptr(Lc), ldl, _dev_ptr(Xc),
+                                   ldx, k, _dev_ptr(out), _stream_ptr(stream)))
+        return out
+
+    def set_graph(self, enable=True):
+        """Replay refactor() from a recorded CUDA graph (needs a created
+        stream, e.g. inside ``torch.cuda.stream(torch.cuda.Stream())``)."""
+        _check(lib.slu_set_graph(self._h, 1 if enable else 0))
 
     def set_profiling(self, enable=True):
         _check(lib.slu_set_profiling(self._h, 1 if enable else 0))

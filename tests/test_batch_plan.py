@@ -1,0 +1,43 @@
+"""Batch analysis: a batch plan is the members' own plans laid out
+block-diagonally (each member blocked by its own Algorithm 2/3 curve), with
+levels merged by index."""
+import numpy as np
+import pytest
+
+import workloads
+
+S = pytest.importorskip("paper_2512_04389_b300.slu")
+
+
+def _members():
+    return [workloads.grid5(k, seed=3 + k) for k in (16, 23, 9, 31)]
+
+
+@pytest.mark.parametrize("opts", [{}, dict(blocking="regular", regular_block=40),
+                                  dict(b_min=8, stride=2)])
+def test_batch_plan_is_concatenation_of_member_plans(opts):
+    ms = _members()
+    PB = S.Plan([m.n for m in ms], [m.colptr for m in ms],
+                [m.rowidx for m in ms], **opts)
+    eb = PB.export()
+    bb = PB.export_blocks()
+    off = 0
+    ptrs, levels, blocks = [0], [], []
+    nb_off = 0
+    for m in ms:
+        P = S.Plan(m.n, m.colptr, m.rowidx, **opts)
+        e = P.export()
+        b = P.export_blocks()
+        ptrs += (e["ptr"][1:] + off).tolist()
+        levels += b["level"].tolist()
+        blocks.append(b["blocks"] + nb_off)
+        off += m.n
+        nb_off += P.info["nblocks_1d"]
+    assert eb["ptr"].tolist() == ptrs
+    assert bb["level"].tolist() == levels
+    got = {tuple(x) for x in bb["blocks"].tolist()}
+    exp = {tuple(x) for x in np.concatenate(blocks).tolist()}
+    assert got == exp
+    assert PB.info["nlevels"] == max(levels) + 1
+    assert PB.info["flops"] == sum(S.Plan(m.n, m.colptr, m.rowidx, **opts).info["flops"]
+                                   for m in ms)

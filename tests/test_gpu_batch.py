@@ -1,0 +1,84 @@
+"""Batching form: many independent matrices factored level by level in the
+same launches (block-diagonal batch plan), optionally replayed from a CUDA
+graph; results must equal the per-matrix launch loop's."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import lu as OL
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+S = pytest.importorskip("paper_2512_04389_b300.slu")
+
+
+def _dev(x):
+    return torch.as_tensor(np.asarray(x), dtype=torch.float64, device="cuda")
+
+
+def _batch(count=12, seed=5):
+    return workloads.batch_grid5(count=count, seed=seed, k_lo=16, k_hi=40)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_factors_equal_member_factors(prec):
+    ms = _batch()
+    PB = S.Plan([m.n for m in ms], [m.colptr for m in ms],
+                [m.rowidx for m in ms], precision=prec)
+    vals = np.concatenate([m.values for m in ms])
+    FB = S.Factor(PB, _dev(vals))
+    gb = FB.export_factors().cpu().numpy()
+    eb = PB.export()
+    pos = 0
+    for m in ms:
+        P = S.Plan(m.n, m.colptr, m.rowidx, precision=prec)
+        F = S.Factor(P, _dev(m.values))
+        g = F.export_factors().cpu().numpy()
+        assert np.array_equal(gb[pos:pos + g.size], g)
+        if prec == "fp64":
+            Fo = OL.lu(m.n, m.colptr, m.rowidx, m.values)
+            _, _, pv = OL.lu_pattern(Fo)
+            assert np.abs(g - pv).max() <= 1e-10 * np.abs(pv).max()
+        pos += g.size
+    assert pos == gb.size == eb["rowidx"].size
+
+
+def test_batch_fp32_refinement_per_member():
+    ms = _batch(count=16, seed=9)
+    PB = S.Plan([m.n for m in ms], [m.colptr for m in ms],
+                [m.rowidx for m in ms], precision="fp32")
+    FB = S.Factor(PB, _dev(np.concatenate([m.values for m in ms])))
+    B = np.concatenate([m.rhs[:, 0] for m in ms])
+    X, info = FB.solve(_dev(B), info=True)
+    assert info["converged"] and info["backward_error"] <= 1e-14
+    Xh = X.cpu().numpy()
+    pos = 0
+    for m in ms:
+        be = OL.backward_error(m.n, m.colptr, m.rowidx, m.values,
+                               Xh[pos:pos + m.n], m.rhs[:, 0])
+        assert be <= 1e-14
+        pos += m.n
+
+
+def test_graph_replay_matches_plain_refactor():
+    ms = _batch(count=8, seed=2)
+    PB = S.Plan([m.n for m in ms], [m.colptr for m in ms],
+                [m.rowidx for m in ms])
+    v = _dev(np.concatenate([m.values for m in ms]))
+    F = S.Factor(PB, v)
+    ref = F.export_factors().clone()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        F.set_graph(True)
+        v2 = v * 1.25
+        F.refactor(v2)          # records
+        F.refactor(v2)          # replays
+        torch.cuda.current_stream().synchronize()
+        F.set_graph(False)
+    F2 = S.Factor(PB, v2)
+    assert torch.equal(F.export_factors(), F2.export_factors())
+    F.refactor(v)
+    assert torch.equal(F.export_factors(), ref)
