@@ -307,9 +307,10 @@ def main():
     st = F.stats()
     F.set_profiling(False)
     fcls = plan.flops_by_class()
+    fcls["inv"] = fcls["getrf"]
     cls_ms = {k: v / args.steps for k, v in st["ms"].items()}
     peak = fp64_peak_tflops(torch)
-    dom = max(("getrf", "panel", "ssssm"), key=lambda k: cls_ms[k])
+    dom = max(("getrf", "panel", "ssssm", "inv"), key=lambda k: cls_ms[k])
     ach = fcls[dom] / (cls_ms[dom] * 1e-3) / 1e12
     out["roofline"] = {
         "kernel": f"k_{dom}", "bound": "alu", "achieved": ach, "peak": peak,

@@ -121,9 +121,11 @@ enum {
     SLU_KC_GETRF = 1,
     SLU_KC_PANEL = 2,            /* GESSM + TSTRF                           */
     SLU_KC_SSSSM = 3,
-    SLU_KC_SOLVE = 4,            /* triangular sweeps                       */
+    SLU_KC_SOLVE = 4,            /* solve: pull of solved blocks            */
     SLU_KC_RESID = 5,            /* residual, norms, update                 */
-    SLU_KC_COUNT = 6
+    SLU_KC_INV = 6,              /* inverses of dense diagonal factors      */
+    SLU_KC_DIAG = 7,             /* solve: diagonal-block step              */
+    SLU_KC_COUNT = 8
 };
 
 typedef struct {

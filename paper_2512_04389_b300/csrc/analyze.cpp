@@ -548,6 +548,70 @@ static void build_levels_and_tasks(slu_plan &P) {
     flat(upper_row, P.urow_off, P.urow_blk);
     flat(upper_col, P.ucol_off, P.ucol_blk);
     flat(lower_col, P.lcol_off, P.lcol_blk);
+    // inverses of dense diagonal blocks and the panel split
+    constexpr int32_t kChunk = 64;
+    const int64_t esz = P.opts.precision == SLU_PREC_FP64 ? 8 : 4;
+    // a 64-wide chunk of the largest block must fit the kernels' shared memory
+    auto inv_ok = [&](const BlockDesc &d) {
+        return d.dense && d.rows <= 384 &&
+               ((int64_t)d.rows * 64 + 16 * 64) * esz <= 220 * 1024;
+    };
+    P.woff.assign(p, -1);
+    P.wsize = 0;
+    for (int32_t I = 0; I < p; ++I) {
+        const BlockDesc &d = P.blocks[P.diagblk[I]];
+        if (inv_ok(d)) {
+            P.woff[I] = P.wsize;
+            P.wsize += 2 * (int64_t)d.rows * d.rows;
+        }
+    }
+    P.inv_off.assign(L + 1, 0);
+    P.pd_off.assign(L + 1, 0);
+    P.pg_goff.assign(L + 1, 0);
+    P.pg_toff.assign(L + 1, 0);
+    P.inv_task.clear();
+    P.pd_task.clear();
+    P.pg_gessm.clear();
+    P.pg_tstrf.clear();
+    for (int32_t lv = 0; lv < L; ++lv) {
+        for (int64_t g = P.getrf_off[lv]; g < P.getrf_off[lv + 1]; ++g) {
+            const BlockDesc &d = P.blocks[P.getrf[g]];
+            if (!inv_ok(d)) continue;
+            for (int32_t which = 0; which < 2; ++which)
+                for (int32_t j0 = 0; j0 < d.rows; j0 += 8) {
+                    const int32_t t3[3] = {P.getrf[g], which, j0};
+                    P.inv_task.insert(P.inv_task.end(), t3, t3 + 3);
+                }
+        }
+        for (int64_t e = P.gessm_off[lv]; e < P.gessm_off[lv + 1]; ++e) {
+            const int32_t tb = P.gessm[2 * e], db = P.gessm[2 * e + 1];
+            if (P.blocks[tb].dense && inv_ok(P.blocks[db])) {
+                for (int32_t c0 = 0; c0 < P.blocks[tb].cols; c0 += kChunk) {
+                    const int32_t t4[4] = {0, tb, db, c0};
+                    P.pd_task.insert(P.pd_task.end(), t4, t4 + 4);
+                }
+            } else {
+                P.pg_gessm.push_back(tb);
+                P.pg_gessm.push_back(db);
+            }
+        }
+        for (int64_t e = P.tstrf_off[lv]; e < P.tstrf_off[lv + 1]; ++e) {
+            const int32_t tb = P.tstrf[2 * e], db = P.tstrf[2 * e + 1];
+            if (P.blocks[tb].dense && inv_ok(P.blocks[db])) {
+                for (int32_t r0 = 0; r0 < P.blocks[tb].rows; r0 += kChunk) {
+                    const int32_t t4[4] = {1, tb, db, r0};
+                    P.pd_task.insert(P.pd_task.end(), t4, t4 + 4);
+                }
+            } else {
+                P.pg_tstrf.push_back(tb);
+                P.pg_tstrf.push_back(db);
+            }
+        }
+        P.inv_off[lv + 1] = (int64_t)P.inv_task.size() / 3;
+        P.pd_off[lv + 1] = (int64_t)P.pd_task.size() / 4;
+        P.pg_goff[lv + 1] = (int64_t)P.pg_gessm.size() / 2;
+        P.pg_toff[lv + 1] = (int64_t)P.pg_tstrf.size() / 2;
+    }
     // solve pull pairs per sweep and level
     P.part_elems = 0;
     for (int sw = 0; sw < 4; ++sw) {

@@ -28,6 +28,9 @@ struct DevPlan {
     int32_t *a_colidx = nullptr;
     int32_t *a_ri = nullptr, *a_ci = nullptr;   // A's entries: row, column
     int32_t *row_seg = nullptr;                  // batch member of each row
+    int64_t *woff = nullptr;
+    int32_t *inv_task = nullptr, *pd_task = nullptr, *pg_gessm = nullptr,
+            *pg_tstrf = nullptr;
     int32_t *sp_pairs[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t *sp_poff[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t *sd_pair0[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -197,6 +200,7 @@ struct slu_handle {
     double *red = nullptr;               // reduction scratch for refinement
     double *part = nullptr;              // solve partial sums (factor time)
     double *anorm_seg = nullptr;         // batch: ||A_q||_inf per member
+    void *winv = nullptr;                // T[plan->wsize]: diagonal inverses
     // graph mode
     bool use_graph = false;
     cudaGraphExec_t graph_exec = nullptr;

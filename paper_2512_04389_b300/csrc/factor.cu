@@ -132,60 +132,54 @@ __device__ __forceinline__ void axpy_rows(T *vj, const uint16_t *rj, int cj,
 template <typename M>
 __device__ void getrf_dense_core(M *A, int b, int ld, double tau,
                                  unsigned long long *cnt) {
+    // Each thread owns rows r = tid, tid + nt, ...; step k only needs row k
+    // (updated by its owner in step k - 1) to be final, so one barrier per
+    // step suffices.  Every thread forms the same (perturbed) pivot; the
+    // owner of row k stores and counts it.
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int k = 0; k < b; ++k) {
-        if (tid == 0) {
-            double piv = (double)A[(int64_t)k * ld + k];
-            if (tau > 0.0 && fabs(piv) < tau) {
-                piv = (piv >= 0.0) ? tau : -tau;
-                atomicAdd(&cnt[0], 1ull);
-            } else if (piv == 0.0) {
-                atomicOr(&cnt[1], 1ull);
-            }
+        double piv = (double)A[(int64_t)k * ld + k];
+        const bool small = tau > 0.0 && fabs(piv) < tau;
+        if (small) piv = (piv >= 0.0) ? tau : -tau;
+        if (k % nt == tid) {
+            if (small) atomicAdd(&cnt[0], 1ull);
+            else if (piv == 0.0) atomicOr(&cnt[1], 1ull);
             A[(int64_t)k * ld + k] = (M)piv;
         }
-        __syncthreads();
-        const double piv = (double)A[(int64_t)k * ld + k];
-        M *colk = A + (int64_t)k * ld;
-        for (int r = k + 1 + tid; r < b; r += nt) colk[r] = (M)((double)colk[r] / piv);
-        __syncthreads();
-        const int m = b - k - 1;
-        for (int e = tid; e < m * m; e += nt) {
-            const int r = k + 1 + e % m, c = k + 1 + e / m;
-            const M u = A[(int64_t)c * ld + k];
-            if (u != M(0)) A[(int64_t)c * ld + r] -= colk[r] * u;
+        for (int r = k + 1 + ((tid - k - 1) % nt + nt) % nt; r < b; r += nt) {
+            const M l = (M)((double)A[(int64_t)k * ld + r] / piv);
+            A[(int64_t)k * ld + r] = l;
+            if (l == M(0)) continue;
+            for (int c = k + 1; c < b; ++c) {
+                const M u = A[(int64_t)c * ld + k];
+                A[(int64_t)c * ld + r] -= l * u;
+            }
         }
         __syncthreads();
     }
 }
 
-
-
 // Right-looking LU of a tall m x w panel held column-major in shared
 // memory (leading dimension m); pivots on the first w rows.
-__device__ void getrf_panel_tall(double *P, int m, int w, double tau,
+template <typename M>
+__device__ void getrf_panel_tall(M *P, int m, int w, double tau,
                                  unsigned long long *cnt) {
+    // Row ownership as in getrf_dense_core, on an m x w panel (ld m).
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int k = 0; k < w; ++k) {
-        if (tid == 0) {
-            double piv = P[k * m + k];
-            if (tau > 0.0 && fabs(piv) < tau) {
-                piv = (piv >= 0.0) ? tau : -tau;
-                atomicAdd(&cnt[0], 1ull);
-            } else if (piv == 0.0) {
-                atomicOr(&cnt[1], 1ull);
-            }
-            P[k * m + k] = piv;
+        double piv = (double)P[k * m + k];
+        const bool small = tau > 0.0 && fabs(piv) < tau;
+        if (small) piv = (piv >= 0.0) ? tau : -tau;
+        if (k % nt == tid) {
+            if (small) atomicAdd(&cnt[0], 1ull);
+            else if (piv == 0.0) atomicOr(&cnt[1], 1ull);
+            P[k * m + k] = (M)piv;
         }
-        __syncthreads();
-        const double piv = P[k * m + k];
-        for (int r = k + 1 + tid; r < m; r += nt) P[k * m + r] /= piv;
-        __syncthreads();
-        const int mr = m - k - 1, nc = w - k - 1;
-        for (int e = tid; e < mr * nc; e += nt) {
-            const int r = k + 1 + e % mr, c = k + 1 + e / mr;
-            const double u = P[c * m + k];
-            if (u != 0.0) P[c * m + r] -= P[k * m + r] * u;
+        for (int r = k + 1 + ((tid - k - 1) % nt + nt) % nt; r < m; r += nt) {
+            const M l = (M)((double)P[k * m + r] / piv);
+            P[k * m + r] = l;
+            if (l == M(0)) continue;
+            for (int c = k + 1; c < w; ++c) P[c * m + r] -= l * P[c * m + k];
         }
         __syncthreads();
     }
@@ -202,48 +196,75 @@ __device__ void getrf_dense_panels(T *A, int b, int ld, double tau,
                                    unsigned char *smem, size_t cap) {
     constexpr int W = 32;
     const int tid = threadIdx.x, nt = blockDim.x;
-    double *Pn = reinterpret_cast<double *>(smem);          // (b - p0) x W
-    double *U = Pn + (size_t)b * W;                          // W x (b - p0 - w)
+    const int tx = tid & 15, ty = tid >> 4;
+    T *Pn = reinterpret_cast<T *>(smem);          // panel, (b - p0) x W, ld m
+    T *U = Pn + (size_t)b * W;                    // U12 as U[k * b + c]
     (void)cap;
     for (int p0 = 0; p0 < b; p0 += W) {
         const int w = min(W, b - p0), m = b - p0, n2 = b - p0 - w;
         for (int e = tid; e < m * w; e += nt) {
             const int r = e % m, c = e / m;
-            Pn[c * m + r] = (double)A[(int64_t)(p0 + c) * ld + p0 + r];
+            Pn[c * m + r] = A[(int64_t)(p0 + c) * ld + p0 + r];
         }
         for (int e = tid; e < w * n2; e += nt) {
-            const int r = e % w, c = e / w;
-            U[c * w + r] = (double)A[(int64_t)(p0 + w + c) * ld + p0 + r];
+            const int k = e % w, c = e / w;
+            U[k * b + c] = A[(int64_t)(p0 + w + c) * ld + p0 + k];
         }
         __syncthreads();
-        getrf_panel_tall(Pn, m, w, tau, cnt);
+        getrf_panel_tall<T>(Pn, m, w, tau, cnt);
         // U12 = L11^{-1} A12: one thread per column
         for (int c = tid; c < n2; c += nt) {
-            double *u = U + c * w;
             for (int k = 0; k < w; ++k) {
-                const double x = u[k];
-                if (x == 0.0) continue;
-                for (int r = k + 1; r < w; ++r) u[r] -= Pn[k * m + r] * x;
+                const T x = U[k * b + c];
+                if (x == T(0)) continue;
+                for (int r = k + 1; r < w; ++r) U[r * b + c] -= Pn[k * m + r] * x;
             }
         }
         __syncthreads();
         for (int e = tid; e < m * w; e += nt) {
             const int r = e % m, c = e / m;
-            A[(int64_t)(p0 + c) * ld + p0 + r] = (T)Pn[c * m + r];
+            A[(int64_t)(p0 + c) * ld + p0 + r] = Pn[c * m + r];
         }
         for (int e = tid; e < w * n2; e += nt) {
-            const int r = e % w, c = e / w;
-            A[(int64_t)(p0 + w + c) * ld + p0 + r] = (T)U[c * w + r];
+            const int k = e % w, c = e / w;
+            A[(int64_t)(p0 + w + c) * ld + p0 + k] = U[k * b + c];
         }
-        // A22 -= L21 U12
-        for (int e = tid; e < n2 * n2; e += nt) {
-            const int r = e % n2, c = e / n2;
-            double acc = 0.0;
-#pragma unroll 8
-            for (int k = 0; k < w; ++k) acc += Pn[k * m + w + r] * U[c * w + k];
-            T *q = A + (int64_t)(p0 + w + c) * ld + p0 + w + r;
-            *q = (T)((double)*q - acc);
-        }
+        // A22 -= L21 U12 in 64 x 64 tiles, 4 x 4 per thread
+        for (int tr = 0; tr < n2; tr += 64)
+            for (int tc = 0; tc < n2; tc += 64) {
+                T acc[4][4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+                for (int k = 0; k < w; ++k) {
+                    T av[4], bv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = tr + ty * 4 + i;
+                        av[i] = r < n2 ? Pn[k * m + w + r] : T(0);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int c = tc + tx * 4 + j;
+                        bv[j] = c < n2 ? U[k * b + c] : T(0);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = tc + tx * 4 + j;
+                    if (c >= n2) continue;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = tr + ty * 4 + i;
+                        if (r < n2) A[(int64_t)(p0 + w + c) * ld + p0 + w + r] -= acc[i][j];
+                    }
+                }
+            }
         __syncthreads();
     }
 }
@@ -264,13 +285,13 @@ k_getrf(const int32_t *__restrict__ ids, BlockArgs a, T *__restrict__ val,
     if (d.dense) {
         const int b = d.rows;
         T *g = val + d.voff;
-        if ((size_t)b * b * sizeof(double) <= kStageSmem) {
-            double *M = reinterpret_cast<double *>(smem);
-            for (int e = threadIdx.x; e < b * b; e += blockDim.x) M[e] = (double)g[e];
+        if ((size_t)b * b * sizeof(T) <= kStageSmem) {
+            T *M = reinterpret_cast<T *>(smem);
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x) M[e] = g[e];
             __syncthreads();
-            getrf_dense_core<double>(M, b, b, tau, cnt);
-            for (int e = threadIdx.x; e < b * b; e += blockDim.x) g[e] = (T)M[e];
-        } else if ((size_t)b * 64 * sizeof(double) <= kStageSmem) {
+            getrf_dense_core<T>(M, b, b, tau, cnt);
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x) g[e] = M[e];
+        } else if ((size_t)b * 64 * sizeof(T) + 64 <= kStageSmem) {
             getrf_dense_panels<T>(g, b, d.ld, tau, cnt, smem, kStageSmem);
         } else {
             getrf_dense_core<T>(g, b, d.ld, tau, cnt);
@@ -502,6 +523,162 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
     if (staged_b) unstage_block<T>(d, a, Bv, val);
 }
 
+
+// Explicit inverses of a dense diagonal block's factors.  One warp per
+// column j of L^{-1} (forward solve of L x = e_j) or U^{-1} (backward solve
+// of U x = e_j); lane l holds rows l, l + 32, ... of x in registers, the
+// factor's column mm is read coalesced, and x(mm) is broadcast by a shuffle
+// at each step.  Task (diag block, 0: L^{-1} / 1: U^{-1}, first column j0);
+// a CTA's 8 warps take columns j0 .. j0 + 7.
+constexpr int kInvCols = 8;
+constexpr int kInvRows = 12;      // rows per lane: blocks up to 384
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
+      const T *__restrict__ val, T *__restrict__ winv,
+      const int64_t *__restrict__ woff) {
+    const int32_t *tk = task + 3 * (int64_t)blockIdx.x;
+    const BlockDesc d = bd[tk[0]];
+    const int which = tk[1], b = d.rows;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = tk[2] + warp;
+    if (j >= b) return;
+    const T *__restrict__ F = val + d.voff;           // dense LU, ld = b
+    T x[kInvRows];
+#pragma unroll
+    for (int q = 0; q < kInvRows; ++q) x[q] = (q * 32 + lane == j) ? T(1) : T(0);
+    if (which == 0) {
+        for (int mm = j; mm < b; ++mm) {
+            const T xm = __shfl_sync(~0u, x[(mm >> 5) % kInvRows], mm & 31);
+            if (xm == T(0)) continue;
+            const T *Lc = F + (int64_t)mm * b;
+#pragma unroll
+            for (int q = 0; q < kInvRows; ++q) {
+                const int r = q * 32 + lane;
+                if (r > mm && r < b) x[q] -= Lc[r] * xm;
+            }
+        }
+    } else {
+        for (int mm = j; mm >= 0; --mm) {
+            const T *Uc = F + (int64_t)mm * b;
+            const T own = __shfl_sync(~0u, x[(mm >> 5) % kInvRows], mm & 31);
+            const T xm = own / Uc[mm];
+#pragma unroll
+            for (int q = 0; q < kInvRows; ++q)
+                if (q * 32 + lane == mm) x[q] = xm;
+            if (xm == T(0)) continue;
+#pragma unroll
+            for (int q = 0; q < kInvRows; ++q) {
+                const int r = q * 32 + lane;
+                if (r < mm) x[q] -= Uc[r] * xm;
+            }
+        }
+    }
+    T *out = winv + woff[d.I] + (which ? (int64_t)b * b : 0) + (int64_t)j * b;
+#pragma unroll
+    for (int q = 0; q < kInvRows; ++q) {
+        const int r = q * 32 + lane;
+        if (r < b) out[r] = x[q];
+    }
+}
+
+// Dense GESSM / TSTRF through the inverses, one CTA per 64-wide chunk:
+//   GESSM: U_IJ(:, c0:c0+64) = L_II^{-1} B_IJ(:, c0:c0+64)
+//   TSTRF: L_JI(r0:r0+64, :) = B_JI(r0:r0+64, :) U_II^{-1}
+// The chunk of B is staged in shared memory (so the result can be written
+// in place), the triangular inverse is streamed in 16-deep k-slices, and a
+// 64 x 64 output tile is accumulated in registers (4 x 4 per thread) over
+// the nonzero triangle of the inverse only.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
+            T *__restrict__ val, const T *__restrict__ winv,
+            const int64_t *__restrict__ woff) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int KT = 16;
+    const int32_t *tk = task + 4 * (int64_t)blockIdx.x;
+    const int type = tk[0];
+    const BlockDesc d = bd[tk[1]];
+    const BlockDesc dd = bd[tk[2]];
+    const int c0 = tk[3], m = dd.rows, tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    T *X = reinterpret_cast<T *>(smem);                 // m x 64 chunk, X[k * 64 + c]
+    T *Ts = X + (size_t)m * 64;                          // 16 x 64 inverse slice
+    const int64_t ld = d.ld;
+    T *Bg = val + d.voff;
+    const T *Inv = winv + woff[dd.I] + (type == 0 ? 0 : (int64_t)m * m);
+    const int nv = min(64, (type == 0 ? d.cols : d.rows) - c0);
+    // stage the chunk: GESSM columns c0.. (X[k][c] = B(k, c0 + c));
+    // TSTRF rows c0.. (X[k][r] = B(c0 + r, k))
+    for (int e = tid; e < m * 64; e += 256) {
+        const int k = e / 64, c = e % 64;
+        T v = T(0);
+        if (c < nv)
+            v = type == 0 ? Bg[(int64_t)(c0 + c) * ld + k] : Bg[(int64_t)k * ld + c0 + c];
+        X[e] = v;
+    }
+    __syncthreads();
+    for (int ob = 0; ob < m; ob += 64) {       // output chunk along m
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jx = 0; jx < 4; ++jx) acc[i][jx] = T(0);
+        // GESSM: out(i, c) = sum_{k <= i} Linv(i, k) X(k, c), i in [ob, ob+64)
+        // TSTRF: out(r, i) = sum_{k <= i} X(r, k) Uinv(k, i), i in [ob, ob+64)
+        const int kend = min(m, ob + 64);
+        for (int k0 = 0; k0 < kend; k0 += KT) {
+            for (int e = tid; e < KT * 64; e += 256) {
+                int kk, ii;
+                T v = T(0);
+                if (type == 0) {               // Ts[kk][ii] = Linv(ob + ii, k0 + kk)
+                    ii = e % 64; kk = e / 64;
+                    const int gi = ob + ii, gk = k0 + kk;
+                    if (gi < m && gk < m) v = Inv[(int64_t)gk * m + gi];
+                } else {                       // Ts[kk][ii] = Uinv(k0 + kk, ob + ii)
+                    kk = e % KT; ii = e / KT;
+                    const int gi = ob + ii, gk = k0 + kk;
+                    if (gi < m && gk < m) v = Inv[(int64_t)gi * m + gk];
+                }
+                Ts[kk * 64 + ii] = v;
+            }
+            __syncthreads();
+            const int kn = min(KT, m - k0);
+            for (int kk = 0; kk < kn; ++kk) {
+                T a[4], bv[4];
+                if (type == 0) {               // rows of out = ob + ty*4+i, cols = tx*4+jx
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] = Ts[kk * 64 + ty * 4 + i];
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx) bv[jx] = X[(k0 + kk) * 64 + tx * 4 + jx];
+                } else {                       // rows = chunk rows ty*4+i, cols = ob + tx*4+jx
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] = X[(k0 + kk) * 64 + ty * 4 + i];
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx) bv[jx] = Ts[kk * 64 + tx * 4 + jx];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx) acc[i][jx] += a[i] * bv[jx];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jx = 0; jx < 4; ++jx) {
+                if (type == 0) {
+                    const int gi = ob + ty * 4 + i, c = tx * 4 + jx;
+                    if (gi < m && c < nv) Bg[(int64_t)(c0 + c) * ld + gi] = acc[i][jx];
+                } else {
+                    const int r = ty * 4 + i, gi = ob + tx * 4 + jx;
+                    if (r < nv && gi < m) Bg[(int64_t)gi * ld + c0 + r] = acc[i][jx];
+                }
+            }
+    }
+}
+
 // SSSSM: target B_KJ -= sum over the level's sources I of L_KI U_IJ.
 // One warp per target column jj: for each source, for each stored U_IJ(i,jj)
 // (fetched 32 at a time and broadcast by shuffles),
@@ -650,7 +827,8 @@ void free_dev_plan(slu_plan *P) {
                     D->getrf, D->gessm, D->tstrf, D->tgt, D->src, D->srcoff,
                     D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
-                    D->a_ri, D->a_ci, D->row_seg,
+                    D->a_ri, D->a_ci, D->row_seg, D->woff, D->inv_task,
+                    D->pd_task, D->pg_gessm, D->pg_tstrf,
                     D->lrow_off, D->urow_off, D->ucol_off, D->lcol_off,
                     D->lrow_blk, D->urow_blk, D->ucol_blk, D->lcol_blk};
     for (void *p : ptrs)
@@ -688,7 +866,9 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->a_rowptr, &D->a_rowptr) && upload(P->a_vpos, &D->a_vpos) &&
         upload(P->a_colidx, &D->a_colidx) &&
         upload(P->a_rowidx, &D->a_ri) && upload(P->a_ci, &D->a_ci) &&
-        upload(P->row_seg, &D->row_seg) &&
+        upload(P->row_seg, &D->row_seg) && upload(P->woff, &D->woff) &&
+        upload(P->inv_task, &D->inv_task) && upload(P->pd_task, &D->pd_task) &&
+        upload(P->pg_gessm, &D->pg_gessm) && upload(P->pg_tstrf, &D->pg_tstrf) &&
         upload(P->lrow_off, &D->lrow_off) && upload(P->urow_off, &D->urow_off) &&
         upload(P->ucol_off, &D->ucol_off) && upload(P->lcol_off, &D->lcol_off) &&
         upload(P->lrow_blk, &D->lrow_blk) && upload(P->urow_blk, &D->urow_blk) &&
@@ -719,7 +899,8 @@ static slu_status set_smem_limits(size_t generic) {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     const int big = (int)std::max(generic, kStageSmem);
     bool ok = cuda_ok(cudaFuncSetAttribute(k_getrf<T>, attr, big), "smem") &&
-              cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem");
+              cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_panel_inv<T>, attr, (int)kStageSmem), "smem");
     if (ok && generic > 48 * 1024)
         ok = cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, (int)generic), "smem");
     return ok ? SLU_OK : SLU_ERR_CUDA;
@@ -782,13 +963,27 @@ static slu_status run_factor(slu_handle *h, const double *values,
                 k_getrf<T><<<(int)(g1 - g0), kThreads, smem_big, st>>>(
                     D->getrf + g0, a, val, h->scal, h->tau_rel, h->cnt);
             }
-        const int64_t e0 = P->gessm_off[lv], e1 = P->gessm_off[lv + 1];
-        const int64_t t0 = P->tstrf_off[lv], t1 = P->tstrf_off[lv + 1];
+        const int64_t i0 = P->inv_off[lv], i1 = P->inv_off[lv + 1];
+        if (i1 > i0) {
+            LaunchScope ls_(h, SLU_KC_INV, st);
+            k_inv<T><<<(int)(i1 - i0), 256, 0, st>>>(
+                D->inv_task + 3 * i0, D->bd, val, static_cast<T *>(h->winv), D->woff);
+        }
+        const int64_t d0 = P->pd_off[lv], d1 = P->pd_off[lv + 1];
+        if (d1 > d0) {
+            LaunchScope ls_(h, SLU_KC_PANEL, st);
+            k_panel_inv<T><<<(int)(d1 - d0), 256,
+                             ((size_t)P->maxb * 64 + 16 * 64) * sizeof(T), st>>>(
+                D->pd_task + 4 * d0, D->bd, val, static_cast<const T *>(h->winv),
+                D->woff);
+        }
+        const int64_t e0 = P->pg_goff[lv], e1 = P->pg_goff[lv + 1];
+        const int64_t t0 = P->pg_toff[lv], t1 = P->pg_toff[lv + 1];
         if (e1 - e0 + t1 - t0 > 0) {
-                LaunchScope ls_(h, SLU_KC_PANEL, st);
-                k_panel<T, Acc><<<(int)(e1 - e0 + t1 - t0), kThreads, smem_big, st>>>(
-                    D->gessm + 2 * e0, (int)(e1 - e0), D->tstrf + 2 * t0, a, val);
-            }
+            LaunchScope ls_(h, SLU_KC_PANEL, st);
+            k_panel<T, Acc><<<(int)(e1 - e0 + t1 - t0), kThreads, smem_big, st>>>(
+                D->pg_gessm + 2 * e0, (int)(e1 - e0), D->pg_tstrf + 2 * t0, a, val);
+        }
         const int64_t m0 = P->gm_off[lv], m1 = P->gm_off[lv + 1];
         if (m1 > m0) {
             LaunchScope ls_(h, SLU_KC_SSSSM, st);
@@ -854,7 +1049,7 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
     }
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red,
-                    h->part, h->anorm_seg};
+                    h->part, h->anorm_seg, h->winv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (cur >= 0) cudaSetDevice(cur);
@@ -891,6 +1086,8 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
         cuda_ok(cudaMalloc(&h->part, std::max<int64_t>(1, P->part_elems) * 4 *
                                          sizeof(double)),
                 "cudaMalloc(solve partials)") &&
+        cuda_ok(cudaMalloc(&h->winv, std::max<int64_t>(1, P->wsize) * esz),
+                "cudaMalloc(inverses)") &&
         (P->seg.size() <= 2 ||
          cuda_ok(cudaMalloc(&h->anorm_seg, (P->seg.size() - 1) * sizeof(double)),
                  "cudaMalloc(anorm_seg)"));

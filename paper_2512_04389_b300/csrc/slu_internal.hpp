@@ -95,6 +95,20 @@ struct slu_plan {
     std::vector<int32_t> gg_tgt;
     std::vector<int64_t> gg_srcoff;
     std::vector<int32_t> gg_src;
+    // dense diagonal blocks: explicit inverses of L_II and U_II live in a
+    // per-handle workspace at woff[I] (L^-1 then U^-1, b x b column-major
+    // each); -1 for sparse diagonal blocks
+    std::vector<int64_t> woff;
+    int64_t wsize = 0;
+    std::vector<int64_t> inv_off;        // per level, into inv_task
+    std::vector<int32_t> inv_task;       // 3 per task: diag blk, L(0)/U(1), j0
+    // panel split: dense pairs as 64-wide chunks of inverse GEMMs, the
+    // rest for the generic kernel
+    std::vector<int64_t> pd_off;         // per level, into pd_task
+    std::vector<int32_t> pd_task;        // 4 per task: 0 GESSM / 1 TSTRF, blk, diag, c0
+    std::vector<int64_t> pg_off;         // per level: GESSM count prefix
+    std::vector<int32_t> pg_gessm, pg_tstrf;
+    std::vector<int64_t> pg_goff, pg_toff;
     // solve pull pairs, per sweep (0 L fwd, 1 U bwd, 2 U^T fwd, 3 L^T bwd):
     // per level the (source block, diagonal block) pairs, each with the
     // offset (doubles, per right-hand side chunk) of its partial vector,

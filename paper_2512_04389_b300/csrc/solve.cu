@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -40,6 +41,62 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
     const BlockDesc db = a.bd[pairs[2 * blockIdx.x]];
     const int m = db.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double *pw = reinterpret_cast<double *>(smem);
+    constexpr int VW = 16 / sizeof(T);                  // rows per vector load
+    if (db.dense && db.ld % VW == 0 && m <= 64 * VW * 4) {
+        // dense GEMV: thread (row group, column group) accumulates VW rows
+        // over its columns with 16-byte loads, 8 in flight; the 4 column
+        // groups are reduced in a fixed order.
+        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        double *xs = pw;                                 // n x RC
+        double *red = pw + (size_t)db.cols * RC;         // 4 x m x RC
+        for (int t = threadIdx.x; t < db.cols * RC; t += kThreads) {
+            const int k = t / RC, c = t % RC;
+            xs[t] = c < nc ? X[(int64_t)c * ldx + db.c0 + k] : 0.0;
+        }
+        __syncthreads();
+        const int nrg = (m + VW - 1) / VW;
+        const int cg = threadIdx.x / 64, rg0 = threadIdx.x % 64;
+        for (int rg = rg0; rg < nrg; rg += 64) {
+            double acc[VW][RC];
+#pragma unroll
+            for (int i = 0; i < VW; ++i)
+#pragma unroll
+                for (int c = 0; c < RC; ++c) acc[i][c] = 0.0;
+            const T *base = val + db.voff + (int64_t)rg * VW;
+            for (int kb = cg; kb < db.cols; kb += 4 * 8) {
+                V v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = kb + 4 * u;
+                    if (k < db.cols)
+                        v[u] = *reinterpret_cast<const V *>(base + (int64_t)k * db.ld);
+                    else
+                        v[u] = V{};
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = min(kb + 4 * u, db.cols - 1);
+                    const T *vv = reinterpret_cast<const T *>(&v[u]);
+#pragma unroll
+                    for (int i = 0; i < VW; ++i)
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) acc[i][c] += (double)vv[i] * xs[k * RC + c];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < VW; ++i) {
+                const int r = rg * VW + i;
+                if (r < m)
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) red[((size_t)cg * RC + c) * m + r] = acc[i][c];
+            }
+        }
+        __syncthreads();
+        double *out = part + poff[blockIdx.x] * RC;
+        for (int t = threadIdx.x; t < m * RC; t += kThreads)
+            out[t] = (red[t] + red[m * RC + t]) + (red[2 * m * RC + t] + red[3 * m * RC + t]);
+        return;
+    }
     for (int t = threadIdx.x; t < kWarps * m * RC; t += kThreads) pw[t] = 0.0;
     __syncthreads();
     double *mine = pw + warp * m * RC;
@@ -58,9 +115,9 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
             colview(db, jj, a, vb, cn, rows);
             for (int e = lane; e < cn; e += 32) {
                 const double l = (double)val[vb + e];
-                double *q = mine + rowat(rows, e) * RC;
+                double *q = mine + rowat(rows, e);     // rhs-major: c * m + row
 #pragma unroll
-                for (int c = 0; c < RC; ++c) q[c] += l * xv[c];
+                for (int c = 0; c < RC; ++c) q[c * m] += l * xv[c];
             }
         }
         __syncwarp();
@@ -70,7 +127,7 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
     for (int t = threadIdx.x; t < m * RC; t += kThreads) {
         double sum = 0.0;
         for (int w = 0; w < kWarps; ++w) sum += pw[w * m * RC + t];
-        out[t] = sum;
+        out[t] = sum;                                   // index c * m + row
     }
 }
 
@@ -85,6 +142,53 @@ k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
     const BlockDesc db = a.bd[pairs[2 * blockIdx.x]];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double *out = part + poff[blockIdx.x] * RC;
+    constexpr int VW = 16 / sizeof(T);
+    if (db.dense && db.ld % VW == 0) {
+        // dense: thread per column, streaming its contiguous column with
+        // 16-byte loads, 8 in flight; x rows staged in shared memory
+        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        __shared__ double xs[kThreads * RC];
+        for (int ii0 = 0; ii0 < db.cols; ii0 += kThreads) {
+            const int ii = ii0 + threadIdx.x;
+            double acc[RC] = {0.0, 0.0, 0.0, 0.0};
+            for (int r0 = 0; r0 < db.rows; r0 += kThreads) {
+                const int nr = min(kThreads, db.rows - r0);
+                __syncthreads();
+                for (int t = threadIdx.x; t < nr * RC; t += kThreads) {
+                    const int r = t / RC, c = t % RC;
+                    xs[t] = c < nc ? X[(int64_t)c * ldx + db.r0 + r0 + r] : 0.0;
+                }
+                __syncthreads();
+                if (ii < db.cols) {
+                    const T *col = val + db.voff + (int64_t)ii * db.ld + r0;
+                    for (int rb = 0; rb < nr; rb += 8 * VW) {
+                        V v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int r = rb + u * VW;
+                            if (r < nr) v[u] = *reinterpret_cast<const V *>(col + r);
+                            else v[u] = V{};
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const T *vv = reinterpret_cast<const T *>(&v[u]);
+#pragma unroll
+                            for (int i = 0; i < VW; ++i) {
+                                const int r = min(rb + u * VW + i, nr - 1);
+#pragma unroll
+                                for (int c = 0; c < RC; ++c)
+                                    acc[c] += (double)vv[i] * xs[r * RC + c];
+                            }
+                        }
+                    }
+                }
+            }
+            if (ii < db.cols)
+#pragma unroll
+                for (int c = 0; c < RC; ++c) out[c * db.cols + ii] = acc[c];
+        }
+        return;
+    }
     for (int ii = warp; ii < db.cols; ii += kWarps) {
         int64_t vb;
         int cn;
@@ -100,7 +204,7 @@ k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
         }
 #pragma unroll
         for (int c = 0; c < RC; ++c) sv[c] = warp_sum(sv[c]);
-        if (lane < RC) out[ii * RC + lane] = sv[lane];
+        if (lane < RC) out[lane * db.cols + ii] = sv[lane];   // c * m + ii
     }
 }
 
@@ -238,7 +342,8 @@ __global__ void __launch_bounds__(kThreads)
 k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
        const int64_t *__restrict__ boff, const int64_t *__restrict__ poff,
        BlockArgs a, const T *__restrict__ val, double *__restrict__ X,
-       int64_t ldx, int nc, const double *__restrict__ part) {
+       int64_t ldx, int nc, const double *__restrict__ part,
+       const T *__restrict__ winv, const int64_t *__restrict__ woff) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int W = 16;
     const BlockDesc dd = a.bd[ids[blockIdx.x]];
@@ -246,12 +351,102 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
     double *y = reinterpret_cast<double *>(smem);
     const size_t ybytes = align16((size_t)m * RC * sizeof(double));
     const int64_t p0 = pair0[blockIdx.x];
-    const int64_t np = boff[dd.I + 1] - boff[dd.I];
+    const int np = (int)(boff[dd.I + 1] - boff[dd.I]);
+    // partial offsets of this block's sources, staged once (the partials
+    // themselves are then independent loads)
+    __shared__ int64_t s_po[256];
     for (int t = threadIdx.x; t < m * RC; t += kThreads) {
         const int r = t / RC, c = t % RC;
-        double v = c < nc ? X[(int64_t)c * ldx + dd.r0 + r] : 0.0;
-        for (int64_t q = 0; q < np; ++q) v -= part[poff[p0 + q] * RC + t];
-        y[t] = v;
+        y[t] = c < nc ? X[(int64_t)c * ldx + dd.r0 + r] : 0.0;
+    }
+    for (int q0 = 0; q0 < np; q0 += 256) {
+        const int nq = min(256, np - q0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nq; q += kThreads) s_po[q] = poff[p0 + q0 + q] * RC;
+        __syncthreads();
+        for (int t0 = 0; t0 < m * RC; t0 += 4 * kThreads) {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int q = 0; q < nq; q += 4) {
+                double v[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int t = t0 + w * kThreads + threadIdx.x;
+                        v[u][w] = (q + u < nq && t < m * RC) ? part[s_po[q + u] + t] : 0.0;
+                    }
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    acc[w] += (v[0][w] + v[1][w]) + (v[2][w] + v[3][w]);
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int t = t0 + w * kThreads + threadIdx.x;
+                if (t < m * RC) {
+                    const int r = t % m, c = t / m;     // partials are c * m + row
+                    y[r * RC + c] -= acc[w];
+                }
+            }
+        }
+    }
+    if (woff[dd.I] >= 0) {
+        // dense diagonal block with explicit inverses: one mat-vec
+        //   L y -> L^{-1} y, U y -> U^{-1} y, U^T -> U^{-T}, L^T -> L^{-T}
+        const bool useL = (MODE == FWD || MODE == BWD_T);
+        const T *M = winv + woff[dd.I] + (useL ? 0 : (int64_t)m * m);
+        double *o = y + m * RC;
+        __syncthreads();
+        if (MODE == FWD || MODE == BWD) {
+            // out(r) = sum_k M(r, k) y(k): thread per row, coalesced over r;
+            // loads issued 8 at a time ahead of their FMAs
+            for (int r = threadIdx.x; r < m; r += kThreads) {
+                double acc[RC] = {0.0, 0.0, 0.0, 0.0};
+                const int k0 = MODE == FWD ? 0 : r, k1 = MODE == FWD ? r + 1 : m;
+                for (int kb = k0; kb < k1; kb += 8) {
+                    double mv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        mv[u] = kb + u < k1 ? (double)M[(int64_t)(kb + u) * m + r] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = min(kb + u, m - 1);
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < RC; ++c) o[r * RC + c] = acc[c];
+            }
+        } else {
+            // out(r) = sum_k M(k, r) y(k): warp per row, lanes over k
+            for (int r = warp; r < m; r += kWarps) {
+                double acc[RC] = {0.0, 0.0, 0.0, 0.0};
+                const int k0 = MODE == FWD_T ? 0 : r, k1 = MODE == FWD_T ? r + 1 : m;
+                for (int kb = k0; kb < k1; kb += 128) {
+                    double mv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = kb + u * 32 + lane;
+                        mv[u] = k < k1 ? (double)M[(int64_t)r * m + k] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = min(kb + u * 32 + lane, m - 1);
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < RC; ++c) acc[c] = warp_sum(acc[c]);
+                if (lane < RC) o[r * RC + lane] = acc[lane];
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+            const int r = t / RC, c = t % RC;
+            if (c < nc) X[(int64_t)c * ldx + dd.r0 + r] = o[t];
+        }
+        return;
     }
     // values as double: full copy if it fits, else panel buffers
     const int64_t nnz = dd.dense ? (int64_t)dd.ld * dd.cols
@@ -496,10 +691,11 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
             }
             const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
             if (g1 > g0) {
-                LaunchScope ls_(h, SLU_KC_SOLVE, st);
+                LaunchScope ls_(h, SLU_KC_DIAG, st);
                 k_diag<T, MODE><<<(int)(g1 - g0), kThreads, kStageSmem, st>>>(
                     D->getrf + g0, D->sd_pair0[MODE] + g0, boff, D->sp_poff[MODE], a,
-                    val, Xc, ldx, nc, h->part);
+                    val, Xc, ldx, nc, h->part, static_cast<const T *>(h->winv),
+                    D->woff);
             }
         }
     }

@@ -57,12 +57,13 @@ class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("backward_error", C.c_double)]
 
 
-KERNEL_CLASSES = ["prep", "getrf", "panel", "ssssm", "solve", "resid"]
+KERNEL_CLASSES = ["prep", "getrf", "panel", "ssssm", "solve_pull", "resid",
+                  "inv", "solve_diag"]
 
 
 class Stats(C.Structure):
-    _fields_ = [("launches", C.c_int64), ("calls", C.c_int64 * 6),
-                ("ms", C.c_double * 6)]
+    _fields_ = [("launches", C.c_int64), ("calls", C.c_int64 * 8),
+                ("ms", C.c_double * 8)]
 
 
 # every entry point declared in include/slu.h
