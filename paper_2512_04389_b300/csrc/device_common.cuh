@@ -211,6 +211,8 @@ struct slu_handle {
     bool profiling = false;
     struct Rec { int cls; cudaEvent_t a, b; };
     std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;       // profiling events, reused
+    size_t pool_next = 0;
     int64_t calls[SLU_KC_COUNT] = {0};
     double ms[SLU_KC_COUNT] = {0};
 };
@@ -227,8 +229,13 @@ struct LaunchScope {
         : h(const_cast<slu_handle *>(hc)), cls(c), st(s) {
         h->launches++;
         if (h->profiling && !h->capturing) {
-            cudaEventCreate(&a);
-            cudaEventCreate(&b);
+            while (h->pool.size() < h->pool_next + 2) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                h->pool.push_back(e);
+            }
+            a = h->pool[h->pool_next++];
+            b = h->pool[h->pool_next++];
             cudaEventRecord(a, st);
         }
     }

@@ -106,16 +106,16 @@ __device__ __forceinline__ int find_row(const uint16_t *rows, int cnt, int r) {
 // so several global round trips are in flight at once.
 template <typename T>
 __device__ __forceinline__ void axpy_rows(T *vj, const uint16_t *rj, int cj,
-                                          const uint16_t *rs, const double *ls,
-                                          int n, double u, int lane) {
+                                          const uint16_t *rs, const T *ls,
+                                          int n, T u, int lane) {
     for (int t0 = 0; t0 < n; t0 += 128) {
         int pr[4];
-        double bv[4];
+        T bv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int t = t0 + q * 32 + lane;
             pr[q] = t < n ? find_row(rj, cj, rs[t]) : -1;
-            bv[q] = pr[q] >= 0 ? (double)vj[pr[q]] : 0.0;
+            bv[q] = pr[q] >= 0 ? vj[pr[q]] : T(0);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -129,60 +129,66 @@ __device__ __forceinline__ void axpy_rows(T *vj, const uint16_t *rj, int cj,
 // the pivot (FP64, perturbation as in the sparse path), scales L(k+1:, k)
 // and applies the rank-1 update to the trailing block.  Entries outside the
 // symbolic pattern are exact zeros and stay zero.
+// Pivot of step k: the FP64 test |piv| < tau and the +-tau replacement
+// (sign of zero taken as +), counted once; returns the value to store.
+__device__ __forceinline__ double fix_pivot(double piv, double tau,
+                                           unsigned long long *cnt) {
+    if (tau > 0.0 && fabs(piv) < tau) {
+        atomicAdd(&cnt[0], 1ull);
+        return (piv >= 0.0) ? tau : -tau;
+    }
+    if (piv == 0.0) atomicOr(&cnt[1], 1ull);
+    return piv;
+}
+
+// Dense LU of an m x w column-major block (leading dimension ld, w <= m,
+// pivots on the first w rows), right-looking with the whole CTA.  Step k:
+// scale L(k+1:, k) by the published reciprocal pivot; barrier; rank-1
+// update with warps over columns and lanes over rows; thread 0 updates
+// entry (k+1, k+1) first, so it then fixes pivot k+1 (FP64 test and
+// perturbation) and publishes its reciprocal; barrier.
 template <typename M>
-__device__ void getrf_dense_core(M *A, int b, int ld, double tau,
-                                 unsigned long long *cnt) {
-    // Each thread owns rows r = tid, tid + nt, ...; step k only needs row k
-    // (updated by its owner in step k - 1) to be final, so one barrier per
-    // step suffices.  Every thread forms the same (perturbed) pivot; the
-    // owner of row k stores and counts it.
+__device__ void lu_dense(M *A, int m, int w, int ld, double tau,
+                         unsigned long long *cnt) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = 0; k < b; ++k) {
-        double piv = (double)A[(int64_t)k * ld + k];
-        const bool small = tau > 0.0 && fabs(piv) < tau;
-        if (small) piv = (piv >= 0.0) ? tau : -tau;
-        if (k % nt == tid) {
-            if (small) atomicAdd(&cnt[0], 1ull);
-            else if (piv == 0.0) atomicOr(&cnt[1], 1ull);
-            A[(int64_t)k * ld + k] = (M)piv;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    __shared__ M s_pinv;
+    if (tid == 0 && w > 0) {
+        const double piv = fix_pivot((double)A[0], tau, cnt);
+        A[0] = (M)piv;
+        s_pinv = (M)(1.0 / piv);
+    }
+    __syncthreads();
+    for (int k = 0; k < w; ++k) {
+        const M pinv = s_pinv;
+        M *colk = A + (int64_t)k * ld;
+        for (int r = k + 1 + tid; r < m; r += nt) colk[r] *= pinv;
+        __syncthreads();
+        for (int c = k + 1 + warp; c < w; c += nw) {
+            M *colc = A + (int64_t)c * ld;
+            const M u = colc[k];
+            if (u != M(0))
+                for (int r = k + 1 + lane; r < m; r += 32) colc[r] -= colk[r] * u;
         }
-        for (int r = k + 1 + ((tid - k - 1) % nt + nt) % nt; r < b; r += nt) {
-            const M l = (M)((double)A[(int64_t)k * ld + r] / piv);
-            A[(int64_t)k * ld + r] = l;
-            if (l == M(0)) continue;
-            for (int c = k + 1; c < b; ++c) {
-                const M u = A[(int64_t)c * ld + k];
-                A[(int64_t)c * ld + r] -= l * u;
-            }
+        if (tid == 0 && k + 1 < w) {
+            const double piv = fix_pivot((double)A[(int64_t)(k + 1) * ld + k + 1], tau, cnt);
+            A[(int64_t)(k + 1) * ld + k + 1] = (M)piv;
+            s_pinv = (M)(1.0 / piv);
         }
         __syncthreads();
     }
 }
 
-// Right-looking LU of a tall m x w panel held column-major in shared
-// memory (leading dimension m); pivots on the first w rows.
+template <typename M>
+__device__ void getrf_dense_core(M *A, int b, int ld, double tau,
+                                 unsigned long long *cnt) {
+    lu_dense<M>(A, b, b, ld, tau, cnt);
+}
+
 template <typename M>
 __device__ void getrf_panel_tall(M *P, int m, int w, double tau,
                                  unsigned long long *cnt) {
-    // Row ownership as in getrf_dense_core, on an m x w panel (ld m).
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = 0; k < w; ++k) {
-        double piv = (double)P[k * m + k];
-        const bool small = tau > 0.0 && fabs(piv) < tau;
-        if (small) piv = (piv >= 0.0) ? tau : -tau;
-        if (k % nt == tid) {
-            if (small) atomicAdd(&cnt[0], 1ull);
-            else if (piv == 0.0) atomicOr(&cnt[1], 1ull);
-            P[k * m + k] = (M)piv;
-        }
-        for (int r = k + 1 + ((tid - k - 1) % nt + nt) % nt; r < m; r += nt) {
-            const M l = (M)((double)P[k * m + r] / piv);
-            P[k * m + r] = l;
-            if (l == M(0)) continue;
-            for (int c = k + 1; c < w; ++c) P[c * m + r] -= l * P[c * m + k];
-        }
-        __syncthreads();
-    }
+    lu_dense<M>(P, m, w, m, tau, cnt);
 }
 
 // Dense diagonal block too large for a shared-memory tile: right-looking LU
@@ -194,13 +200,15 @@ template <typename T>
 __device__ void getrf_dense_panels(T *A, int b, int ld, double tau,
                                    unsigned long long *cnt,
                                    unsigned char *smem, size_t cap) {
+    // Right-looking by 32-wide column panels only while the trailing block
+    // does not fit in shared memory; the rest is factored in shared memory.
     constexpr int W = 32;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int tx = tid & 15, ty = tid >> 4;
-    T *Pn = reinterpret_cast<T *>(smem);          // panel, (b - p0) x W, ld m
-    T *U = Pn + (size_t)b * W;                    // U12 as U[k * b + c]
-    (void)cap;
-    for (int p0 = 0; p0 < b; p0 += W) {
+    int p0 = 0;
+    while (p0 < b && (size_t)(b - p0) * (b - p0) * sizeof(T) > cap) {
+        T *Pn = reinterpret_cast<T *>(smem);      // panel, (b - p0) x W, ld m
+        T *U = Pn + (size_t)b * W;                // U12 as U[k * b + c]
         const int w = min(W, b - p0), m = b - p0, n2 = b - p0 - w;
         for (int e = tid; e < m * w; e += nt) {
             const int r = e % m, c = e / m;
@@ -212,8 +220,7 @@ __device__ void getrf_dense_panels(T *A, int b, int ld, double tau,
         }
         __syncthreads();
         getrf_panel_tall<T>(Pn, m, w, tau, cnt);
-        // U12 = L11^{-1} A12: one thread per column
-        for (int c = tid; c < n2; c += nt) {
+        for (int c = tid; c < n2; c += nt) {     // U12 = L11^{-1} A12
             for (int k = 0; k < w; ++k) {
                 const T x = U[k * b + c];
                 if (x == T(0)) continue;
@@ -229,14 +236,20 @@ __device__ void getrf_dense_panels(T *A, int b, int ld, double tau,
             const int k = e % w, c = e / w;
             A[(int64_t)(p0 + w + c) * ld + p0 + k] = U[k * b + c];
         }
-        // A22 -= L21 U12 in 64 x 64 tiles, 4 x 4 per thread
+        // A22 -= L21 U12 in 64 x 64 tiles, 4 x 4 per thread; the C tile is
+        // loaded before the k-loop so its latency overlaps the products
         for (int tr = 0; tr < n2; tr += 64)
             for (int tc = 0; tc < n2; tc += 64) {
                 T acc[4][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = tr + ty * 4 + i, c = tc + tx * 4 + j;
+                        acc[i][j] = (r < n2 && c < n2)
+                                        ? A[(int64_t)(p0 + w + c) * ld + p0 + w + r]
+                                        : T(0);
+                    }
                 for (int k = 0; k < w; ++k) {
                     T av[4], bv[4];
 #pragma unroll
@@ -252,7 +265,7 @@ __device__ void getrf_dense_panels(T *A, int b, int ld, double tau,
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+                        for (int j = 0; j < 4; ++j) acc[i][j] -= av[i] * bv[j];
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -261,12 +274,28 @@ __device__ void getrf_dense_panels(T *A, int b, int ld, double tau,
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int r = tr + ty * 4 + i;
-                        if (r < n2) A[(int64_t)(p0 + w + c) * ld + p0 + w + r] -= acc[i][j];
+                        if (r < n2) A[(int64_t)(p0 + w + c) * ld + p0 + w + r] = acc[i][j];
                     }
                 }
             }
         __syncthreads();
+        p0 += w;
     }
+    if (p0 >= b) return;
+    // the trailing block fits: factor it in shared memory
+    const int mt = b - p0;
+    T *M = reinterpret_cast<T *>(smem);
+    for (int e = tid; e < mt * mt; e += nt) {
+        const int r = e % mt, c = e / mt;
+        M[e] = A[(int64_t)(p0 + c) * ld + p0 + r];
+    }
+    __syncthreads();
+    getrf_dense_core<T>(M, mt, mt, tau, cnt);
+    for (int e = tid; e < mt * mt; e += nt) {
+        const int r = e % mt, c = e / mt;
+        A[(int64_t)(p0 + c) * ld + p0 + r] = M[e];
+    }
+    __syncthreads();
 }
 
 // GETRF on diagonal blocks.  Columns run in height groups of the block's
@@ -306,9 +335,9 @@ k_getrf(const int32_t *__restrict__ ids, BlockArgs a, T *__restrict__ val,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ double s_piv;
     // source column buffer (values, rows), then the staged block
-    double *sv = reinterpret_cast<double *>(smem);
+    T *sv = reinterpret_cast<T *>(smem);
     uint16_t *sr = reinterpret_cast<uint16_t *>(sv + d.rows);
-    const size_t sbytes = align16((size_t)d.rows * 10);
+    const size_t sbytes = align16((size_t)d.rows * (sizeof(T) + 2));
     bool staged;
     size_t used;
     const BlockView<T> B = stage_block<T>(d, a, val, smem + sbytes,
@@ -321,23 +350,17 @@ k_getrf(const int32_t *__restrict__ ids, BlockArgs a, T *__restrict__ val,
         const int dk = B.dp[k];
         const int nL = ck - dk - 1;
         if (threadIdx.x == 0) {
-            double piv = (double)B.v[ok + dk];
-            if (tau > 0.0 && fabs(piv) < tau) {
-                piv = (piv >= 0.0) ? tau : -tau;
-                atomicAdd(&cnt[0], 1ull);
-            } else if (piv == 0.0) {
-                atomicOr(&cnt[1], 1ull);
-            }
+            const double piv = fix_pivot((double)B.v[ok + dk], tau, cnt);
             B.v[ok + dk] = (T)piv;
-            s_piv = piv;
+            s_piv = 1.0 / piv;
         }
         __syncthreads();
         if (nL == 0) continue;
-        const double piv = s_piv;
+        const T pinv = (T)s_piv;
         for (int e = threadIdx.x; e < nL; e += blockDim.x) {
-            const T l = (T)((double)B.v[ok + dk + 1 + e] / piv);
+            const T l = B.v[ok + dk + 1 + e] * pinv;
             B.v[ok + dk + 1 + e] = l;
-            sv[e] = (double)l;
+            sv[e] = l;
             sr[e] = (uint16_t)rowat(rk, dk + 1 + e);
         }
         __syncthreads();
@@ -347,8 +370,8 @@ k_getrf(const int32_t *__restrict__ ids, BlockArgs a, T *__restrict__ val,
             const uint16_t *rj;
             B.col(j, oj, cj, rj);
             const int pu = find_row(rj, B.dp[j], k);
-            const double u = pu >= 0 ? (double)B.v[oj + pu] : 0.0;
-            if (u == 0.0) continue;
+            const T u = pu >= 0 ? B.v[oj + pu] : T(0);
+            if (u == T(0)) continue;
             axpy_rows<T>(B.v + oj, rj, cj, sr, sv, nL, u, lane);
         }
         __syncthreads();
@@ -438,9 +461,9 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
     // per step.  Shared memory: a source-column buffer, then the diagonal
     // factor (read at every step), then the panel block if it also fits.
     const int mb = max(d.rows, dd.rows);
-    double *sv = reinterpret_cast<double *>(smem);
+    T *sv = reinterpret_cast<T *>(smem);
     uint16_t *sr = reinterpret_cast<uint16_t *>(sv + mb);
-    const size_t sbytes = align16((size_t)mb * 10);
+    const size_t sbytes = align16((size_t)mb * (sizeof(T) + 2));
     bool staged_f, staged_b;
     size_t used_f, used_b;
     const BlockView<T> F = stage_block<T>(dd, a, val, smem + sbytes,
@@ -462,7 +485,7 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
             // row k in one column; the warp then walks the hits.
             if (nL == 0) continue;
             for (int e = threadIdx.x; e < nL; e += blockDim.x) {
-                sv[e] = (double)F.v[fk + dk + 1 + e];
+                sv[e] = F.v[fk + dk + 1 + e];
                 sr[e] = (uint16_t)rowat(frk, dk + 1 + e);
             }
             __syncthreads();
@@ -470,18 +493,18 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
                 const int c = cb + lane;
                 int oc = 0, cc = 0, pk = -1;
                 const uint16_t *rc = nullptr;
-                double x = 0.0;
+                T x = T(0);
                 if (c < d.cols) {
                     Bv.col(c, oc, cc, rc);
                     pk = find_row(rc, cc, k);
-                    if (pk >= 0) x = (double)Bv.v[oc + pk];
+                    if (pk >= 0) x = Bv.v[oc + pk];
                 }
-                unsigned hits = __ballot_sync(~0u, pk >= 0 && x != 0.0);
+                unsigned hits = __ballot_sync(~0u, pk >= 0 && x != T(0));
                 while (hits) {
                     const int src = __ffs(hits) - 1;
                     hits &= hits - 1;
                     const int c2 = cb + src;
-                    const double x2 = __shfl_sync(~0u, x, src);
+                    const T x2 = __shfl_sync(~0u, x, src);
                     int o2c, c2c;
                     const uint16_t *r2c;
                     Bv.col(c2, o2c, c2c, r2c);
@@ -496,11 +519,11 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
             const uint16_t *rk;
             Bv.col(k, ok, ck, rk);
             if (ck == 0) continue;
-            const double ukk = (double)F.v[fk + dk];
+            const T uinv = T(1) / F.v[fk + dk];
             for (int e = threadIdx.x; e < ck; e += blockDim.x) {
-                const T l = (T)((double)Bv.v[ok + e] / ukk);
+                const T l = Bv.v[ok + e] * uinv;
                 Bv.v[ok + e] = l;
-                sv[e] = (double)l;
+                sv[e] = l;
                 sr[e] = (uint16_t)rowat(rk, e);
             }
             __syncthreads();
@@ -510,8 +533,8 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
                 const uint16_t *frj;
                 F.col(j, fj, fcj, frj);
                 const int pu = find_row(frj, F.dp[j], k);
-                const double u = pu >= 0 ? (double)F.v[fj + pu] : 0.0;
-                if (u == 0.0) continue;
+                const T u = pu >= 0 ? F.v[fj + pu] : T(0);
+                if (u == T(0)) continue;
                 int oj, cj;
                 const uint16_t *rj;
                 Bv.col(j, oj, cj, rj);
@@ -530,7 +553,6 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
 // factor's column mm is read coalesced, and x(mm) is broadcast by a shuffle
 // at each step.  Task (diag block, 0: L^{-1} / 1: U^{-1}, first column j0);
 // a CTA's 8 warps take columns j0 .. j0 + 7.
-constexpr int kInvCols = 8;
 constexpr int kInvRows = 12;      // rows per lane: blocks up to 384
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -742,14 +764,16 @@ k_ssssm(const int32_t *__restrict__ tgt, const int64_t *__restrict__ srcoff,
 // SSSSM on dense tiles: a 64 x 64 tile of a dense target B_KJ minus the sum
 // over the level's dense sources of L_KI U_IJ, accumulated in registers
 // (4 x 4 per thread) over all sources and k-slices of 16, written once.
+// Slices are double-buffered: the next slice's global loads are in flight
+// (in registers) while the current one is multiplied from shared memory.
 // Sources run in ascending I, so the result is deterministic.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
              const BlockDesc *__restrict__ bd, T *__restrict__ val) {
     constexpr int TM = 64, TN = 64, KT = 16, PAD = 16 / sizeof(T);
-    __shared__ __align__(16) T As[KT][TM];
-    __shared__ __align__(16) T Bs[KT][TN + PAD];
+    __shared__ __align__(16) T As[2][KT][TM];
+    __shared__ __align__(16) T Bs[2][KT][TN + PAD];
     const int32_t *tk = task + 5 * (int64_t)blockIdx.x;
     const BlockDesc d = bd[tk[0]];
     const int s0 = tk[1], s1 = tk[2], r0 = tk[3], c0 = tk[4];
@@ -759,38 +783,76 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    for (int s = s0; s < s1; ++s) {
-        const BlockDesc dl = bd[src[2 * s]];
-        const BlockDesc du = bd[src[2 * s + 1]];
-        const T *__restrict__ A = val + dl.voff;
-        const T *__restrict__ B = val + du.voff;
-        const int K = dl.cols;
-        for (int k0 = 0; k0 < K; k0 += KT) {
-            for (int e = tid; e < KT * TM; e += 256) {
-                const int r = e % TM, k = e / TM;
-                const int gr = r0 + r, gk = k0 + k;
-                As[k][r] = (gr < d.rows && gk < K) ? A[(int64_t)gk * dl.ld + gr] : T(0);
-            }
-            for (int e = tid; e < KT * TN; e += 256) {
-                const int k = e % KT, c = e / KT;
-                const int gk = k0 + k, gc = c0 + c;
-                Bs[k][c] = (gk < K && gc < d.cols) ? B[(int64_t)gc * du.ld + gk] : T(0);
-            }
-            __syncthreads();
+    if (s0 >= s1) return;
+    // slice state: source s, k offset k0 within it
+    int s = s0, k0 = 0;
+    BlockDesc dl = bd[src[2 * s]], du = bd[src[2 * s + 1]];
+    T ra[4], rb[4];
+    auto load = [&](const BlockDesc &L, const BlockDesc &U, int kk0) {
+        const T *__restrict__ A = val + L.voff;
+        const T *__restrict__ B = val + U.voff;
+        const int K = L.cols;
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                T a[4], b[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
-            }
-            __syncthreads();
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int r = e % TM, k = e / TM;
+            const int gr = r0 + r, gk = kk0 + k;
+            ra[q] = (gr < d.rows && gk < K) ? A[(int64_t)gk * L.ld + gr] : T(0);
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int k = e % KT, c = e / KT;
+            const int gk = kk0 + k, gc = c0 + c;
+            rb[q] = (gk < K && gc < d.cols) ? B[(int64_t)gc * U.ld + gk] : T(0);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            As[buf][e / TM][e % TM] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            Bs[buf][e % KT][e / KT] = rb[q];
+        }
+    };
+    load(dl, du, 0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (;;) {
+        // advance to the next slice
+        int ns = s, nk0 = k0 + KT;
+        if (nk0 >= dl.cols) { ++ns; nk0 = 0; }
+        const bool more = ns < s1;
+        BlockDesc nl = dl, nu = du;
+        if (more) {
+            if (ns != s) { nl = bd[src[2 * ns]]; nu = bd[src[2 * ns + 1]]; }
+            load(nl, nu, nk0);
+        }
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[buf][k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        if (!more) break;
+        store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+        s = ns;
+        k0 = nk0;
+        dl = nl;
+        du = nu;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1043,10 +1105,7 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (h->device >= 0) cudaSetDevice(h->device);
-    for (auto &r : h->recs) {
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
-    }
+    for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red,
                     h->part, h->anorm_seg, h->winv};
@@ -1163,11 +1222,8 @@ extern "C" slu_status slu_set_graph(slu_handle *h, int32_t enable) {
 
 extern "C" slu_status slu_set_profiling(slu_handle *h, int32_t enable) {
     if (!h) return fail(SLU_ERR_INVALID_ARG, "NULL handle");
-    for (auto &r : h->recs) {
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
-    }
     h->recs.clear();
+    h->pool_next = 0;
     for (int c = 0; c < SLU_KC_COUNT; ++c) {
         h->calls[c] = 0;
         h->ms[c] = 0.0;
@@ -1187,10 +1243,9 @@ extern "C" slu_status slu_handle_stats(slu_handle *h, slu_stats *out) {
             return SLU_ERR_CUDA;
         h->calls[r.cls]++;
         h->ms[r.cls] += t;
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
     }
     h->recs.clear();
+    h->pool_next = 0;
     out->launches = h->launches;
     for (int c = 0; c < SLU_KC_COUNT; ++c) {
         out->calls[c] = h->calls[c];

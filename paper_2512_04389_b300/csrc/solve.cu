@@ -20,7 +20,8 @@
 
 namespace slu {
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename C>
+__device__ __forceinline__ C warp_sum(C v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
     return v;
 }
@@ -36,19 +37,21 @@ __global__ void __launch_bounds__(kThreads)
 k_pull_scatter(const int32_t *__restrict__ pairs,
                const int64_t *__restrict__ poff, BlockArgs a,
                const T *__restrict__ val, const double *__restrict__ X,
-               int64_t ldx, int nc, double *__restrict__ part) {
+               int64_t ldx, int nc, double *__restrict__ part_d) {
+    using C = T;
+    C *part = reinterpret_cast<C *>(part_d);
     extern __shared__ __align__(16) unsigned char smem[];
     const BlockDesc db = a.bd[pairs[2 * blockIdx.x]];
     const int m = db.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *pw = reinterpret_cast<double *>(smem);
+    C *pw = reinterpret_cast<C *>(smem);
     constexpr int VW = 16 / sizeof(T);                  // rows per vector load
     if (db.dense && db.ld % VW == 0 && m <= 64 * VW * 4) {
         // dense GEMV: thread (row group, column group) accumulates VW rows
         // over its columns with 16-byte loads, 8 in flight; the 4 column
         // groups are reduced in a fixed order.
         using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-        double *xs = pw;                                 // n x RC
-        double *red = pw + (size_t)db.cols * RC;         // 4 x m x RC
+        C *xs = pw;                                 // n x RC
+        C *red = pw + (size_t)db.cols * RC;         // 4 x m x RC
         for (int t = threadIdx.x; t < db.cols * RC; t += kThreads) {
             const int k = t / RC, c = t % RC;
             xs[t] = c < nc ? X[(int64_t)c * ldx + db.c0 + k] : 0.0;
@@ -57,7 +60,7 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
         const int nrg = (m + VW - 1) / VW;
         const int cg = threadIdx.x / 64, rg0 = threadIdx.x % 64;
         for (int rg = rg0; rg < nrg; rg += 64) {
-            double acc[VW][RC];
+            C acc[VW][RC];
 #pragma unroll
             for (int i = 0; i < VW; ++i)
 #pragma unroll
@@ -80,7 +83,7 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
 #pragma unroll
                     for (int i = 0; i < VW; ++i)
 #pragma unroll
-                        for (int c = 0; c < RC; ++c) acc[i][c] += (double)vv[i] * xs[k * RC + c];
+                        for (int c = 0; c < RC; ++c) acc[i][c] += (C)vv[i] * xs[k * RC + c];
                 }
             }
 #pragma unroll
@@ -92,16 +95,16 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
             }
         }
         __syncthreads();
-        double *out = part + poff[blockIdx.x] * RC;
+        C *out = part + poff[blockIdx.x] * RC;
         for (int t = threadIdx.x; t < m * RC; t += kThreads)
             out[t] = (red[t] + red[m * RC + t]) + (red[2 * m * RC + t] + red[3 * m * RC + t]);
         return;
     }
     for (int t = threadIdx.x; t < kWarps * m * RC; t += kThreads) pw[t] = 0.0;
     __syncthreads();
-    double *mine = pw + warp * m * RC;
+    C *mine = pw + warp * m * RC;
     for (int jj = warp; jj < db.cols; jj += kWarps) {
-        double xv[RC];
+        C xv[RC];
         bool any = false;
 #pragma unroll
         for (int c = 0; c < RC; ++c) {
@@ -114,8 +117,8 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
             const uint16_t *rows;
             colview(db, jj, a, vb, cn, rows);
             for (int e = lane; e < cn; e += 32) {
-                const double l = (double)val[vb + e];
-                double *q = mine + rowat(rows, e);     // rhs-major: c * m + row
+                const C l = (C)val[vb + e];
+                C *q = mine + rowat(rows, e);     // rhs-major: c * m + row
 #pragma unroll
                 for (int c = 0; c < RC; ++c) q[c * m] += l * xv[c];
             }
@@ -123,9 +126,9 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
         __syncwarp();
     }
     __syncthreads();
-    double *out = part + poff[blockIdx.x] * RC;
+    C *out = part + poff[blockIdx.x] * RC;
     for (int t = threadIdx.x; t < m * RC; t += kThreads) {
-        double sum = 0.0;
+        C sum = 0.0;
         for (int w = 0; w < kWarps; ++w) sum += pw[w * m * RC + t];
         out[t] = sum;                                   // index c * m + row
     }
@@ -138,19 +141,21 @@ __global__ void __launch_bounds__(kThreads)
 k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
            BlockArgs a, const T *__restrict__ val,
            const double *__restrict__ X, int64_t ldx, int nc,
-           double *__restrict__ part) {
+           double *__restrict__ part_d) {
+    using C = T;
+    C *part = reinterpret_cast<C *>(part_d);
     const BlockDesc db = a.bd[pairs[2 * blockIdx.x]];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *out = part + poff[blockIdx.x] * RC;
+    C *out = part + poff[blockIdx.x] * RC;
     constexpr int VW = 16 / sizeof(T);
     if (db.dense && db.ld % VW == 0) {
         // dense: thread per column, streaming its contiguous column with
         // 16-byte loads, 8 in flight; x rows staged in shared memory
         using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-        __shared__ double xs[kThreads * RC];
+        __shared__ C xs[kThreads * RC];
         for (int ii0 = 0; ii0 < db.cols; ii0 += kThreads) {
             const int ii = ii0 + threadIdx.x;
-            double acc[RC] = {0.0, 0.0, 0.0, 0.0};
+            C acc[RC] = {0.0, 0.0, 0.0, 0.0};
             for (int r0 = 0; r0 < db.rows; r0 += kThreads) {
                 const int nr = min(kThreads, db.rows - r0);
                 __syncthreads();
@@ -177,7 +182,7 @@ k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
                                 const int r = min(rb + u * VW + i, nr - 1);
 #pragma unroll
                                 for (int c = 0; c < RC; ++c)
-                                    acc[c] += (double)vv[i] * xs[r * RC + c];
+                                    acc[c] += (C)vv[i] * xs[r * RC + c];
                             }
                         }
                     }
@@ -194,9 +199,9 @@ k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
         int cn;
         const uint16_t *rows;
         colview(db, ii, a, vb, cn, rows);
-        double sv[RC] = {0.0, 0.0, 0.0, 0.0};
+        C sv[RC] = {0.0, 0.0, 0.0, 0.0};
         for (int e = lane; e < cn; e += 32) {
-            const double l = (double)val[vb + e];
+            const C l = (C)val[vb + e];
             const int64_t r = db.r0 + rowat(rows, e);
 #pragma unroll
             for (int c = 0; c < RC; ++c)
@@ -210,47 +215,47 @@ k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
 
 // One column step of a diagonal-block sweep; cv[e] is entry e of column jj
 // (rows rows[e], diagonal at slot dp), y the m x RC right-hand sides.
-template <int MODE>
-__device__ __forceinline__ void chain_step(int jj, const double *cv,
+template <typename C, int MODE>
+__device__ __forceinline__ void chain_step(int jj, const C *cv,
                                            const uint16_t *rows, int cn,
-                                           int dp, double *y, int lane) {
+                                           int dp, C *y, int lane) {
     if (MODE == FWD) {                 // unit lower, scatter below
-        double xv[RC];
+        C xv[RC];
         bool any = false;
 #pragma unroll
         for (int c = 0; c < RC; ++c) { xv[c] = y[jj * RC + c]; any |= xv[c] != 0.0; }
         if (any)
             for (int e = dp + 1 + lane; e < cn; e += 32) {
-                double *q = y + rowat(rows, e) * RC;
+                C *q = y + rowat(rows, e) * RC;
 #pragma unroll
                 for (int c = 0; c < RC; ++c) q[c] -= cv[e] * xv[c];
             }
     } else if (MODE == BWD) {          // upper, divide then scatter above
-        double xv[RC];
+        C xv[RC];
         bool any = false;
-        const double piv = cv[dp];
+        const C piv = cv[dp];
 #pragma unroll
         for (int c = 0; c < RC; ++c) { xv[c] = y[jj * RC + c] / piv; any |= xv[c] != 0.0; }
         __syncwarp();
         if (lane < RC) y[jj * RC + lane] = xv[lane];
         if (any)
             for (int e = lane; e < dp; e += 32) {
-                double *q = y + rowat(rows, e) * RC;
+                C *q = y + rowat(rows, e) * RC;
 #pragma unroll
                 for (int c = 0; c < RC; ++c) q[c] -= cv[e] * xv[c];
             }
     } else {                           // transposed: gather dot
-        double sv[RC] = {0.0, 0.0, 0.0, 0.0};
+        C sv[RC] = {0.0, 0.0, 0.0, 0.0};
         const int e0 = MODE == FWD_T ? lane : dp + 1 + lane;
         const int e1 = MODE == FWD_T ? dp : cn;
         for (int e = e0; e < e1; e += 32) {
-            const double *q = y + rowat(rows, e) * RC;
+            const C *q = y + rowat(rows, e) * RC;
 #pragma unroll
             for (int c = 0; c < RC; ++c) sv[c] += cv[e] * q[c];
         }
 #pragma unroll
         for (int c = 0; c < RC; ++c) sv[c] = warp_sum(sv[c]);
-        double zi = 0.0;
+        C zi = 0.0;
         if (lane < RC) {
             zi = y[jj * RC + lane] - sv[lane];
             if (MODE == FWD_T) zi /= cv[dp];
@@ -265,50 +270,50 @@ __device__ __forceinline__ void chain_step(int jj, const double *cv,
 template <typename T, int MODE>
 __device__ __forceinline__ void chain_step_t(int jj, const T *cv,
                                              const uint16_t *rows, int cn,
-                                             int dp, double *y, int lane) {
+                                             int dp, T *y, int lane) {
     if (MODE == FWD) {
-        double xv[RC];
+        T xv[RC];
         bool any = false;
 #pragma unroll
         for (int c = 0; c < RC; ++c) { xv[c] = y[jj * RC + c]; any |= xv[c] != 0.0; }
         if (any)
             for (int e = dp + 1 + lane; e < cn; e += 32) {
-                double *q = y + rowat(rows, e) * RC;
-                const double l = (double)cv[e];
+                T *q = y + rowat(rows, e) * RC;
+                const T l = (T)cv[e];
 #pragma unroll
                 for (int c = 0; c < RC; ++c) q[c] -= l * xv[c];
             }
     } else if (MODE == BWD) {
-        double xv[RC];
+        T xv[RC];
         bool any = false;
-        const double piv = (double)cv[dp];
+        const T piv = (T)cv[dp];
 #pragma unroll
         for (int c = 0; c < RC; ++c) { xv[c] = y[jj * RC + c] / piv; any |= xv[c] != 0.0; }
         __syncwarp();
         if (lane < RC) y[jj * RC + lane] = xv[lane];
         if (any)
             for (int e = lane; e < dp; e += 32) {
-                double *q = y + rowat(rows, e) * RC;
-                const double u = (double)cv[e];
+                T *q = y + rowat(rows, e) * RC;
+                const T u = (T)cv[e];
 #pragma unroll
                 for (int c = 0; c < RC; ++c) q[c] -= u * xv[c];
             }
     } else {
-        double sv[RC] = {0.0, 0.0, 0.0, 0.0};
+        T sv[RC] = {0.0, 0.0, 0.0, 0.0};
         const int e0 = MODE == FWD_T ? lane : dp + 1 + lane;
         const int e1 = MODE == FWD_T ? dp : cn;
         for (int e = e0; e < e1; e += 32) {
-            const double *q = y + rowat(rows, e) * RC;
-            const double l = (double)cv[e];
+            const T *q = y + rowat(rows, e) * RC;
+            const T l = (T)cv[e];
 #pragma unroll
             for (int c = 0; c < RC; ++c) sv[c] += l * q[c];
         }
 #pragma unroll
         for (int c = 0; c < RC; ++c) sv[c] = warp_sum(sv[c]);
-        double zi = 0.0;
+        T zi = 0.0;
         if (lane < RC) {
             zi = y[jj * RC + lane] - sv[lane];
-            if (MODE == FWD_T) zi /= (double)cv[dp];
+            if (MODE == FWD_T) zi /= (T)cv[dp];
         }
         __syncwarp();
         if (lane < RC) y[jj * RC + lane] = zi;
@@ -328,7 +333,7 @@ __device__ bool panels_fit(const BlockView<T> &F, int m, int W, size_t cap) {
         F.col(j1 - 1, o1, c1, r1);
         maxp = max(maxp, (int64_t)(o1 + c1 - o0));
     }
-    return (size_t)(2 * maxp) * sizeof(double) <= cap;
+    return (size_t)(2 * maxp) * sizeof(T) <= cap;
 }
 
 // Diagonal part of a sweep: one CTA per diagonal block of the level.
@@ -342,14 +347,16 @@ __global__ void __launch_bounds__(kThreads)
 k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
        const int64_t *__restrict__ boff, const int64_t *__restrict__ poff,
        BlockArgs a, const T *__restrict__ val, double *__restrict__ X,
-       int64_t ldx, int nc, const double *__restrict__ part,
+       int64_t ldx, int nc, const double *__restrict__ part_d,
        const T *__restrict__ winv, const int64_t *__restrict__ woff) {
+    using C = T;
+    const C *part = reinterpret_cast<const C *>(part_d);
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int W = 16;
     const BlockDesc dd = a.bd[ids[blockIdx.x]];
     const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *y = reinterpret_cast<double *>(smem);
-    const size_t ybytes = align16((size_t)m * RC * sizeof(double));
+    C *y = reinterpret_cast<C *>(smem);
+    const size_t ybytes = align16((size_t)m * RC * sizeof(C));
     const int64_t p0 = pair0[blockIdx.x];
     const int np = (int)(boff[dd.I + 1] - boff[dd.I]);
     // partial offsets of this block's sources, staged once (the partials
@@ -365,9 +372,9 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
         for (int q = threadIdx.x; q < nq; q += kThreads) s_po[q] = poff[p0 + q0 + q] * RC;
         __syncthreads();
         for (int t0 = 0; t0 < m * RC; t0 += 4 * kThreads) {
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            C acc[4] = {0.0, 0.0, 0.0, 0.0};
             for (int q = 0; q < nq; q += 4) {
-                double v[4][4];
+                C v[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -394,19 +401,19 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
         //   L y -> L^{-1} y, U y -> U^{-1} y, U^T -> U^{-T}, L^T -> L^{-T}
         const bool useL = (MODE == FWD || MODE == BWD_T);
         const T *M = winv + woff[dd.I] + (useL ? 0 : (int64_t)m * m);
-        double *o = y + m * RC;
+        C *o = y + m * RC;
         __syncthreads();
         if (MODE == FWD || MODE == BWD) {
             // out(r) = sum_k M(r, k) y(k): thread per row, coalesced over r;
             // loads issued 8 at a time ahead of their FMAs
             for (int r = threadIdx.x; r < m; r += kThreads) {
-                double acc[RC] = {0.0, 0.0, 0.0, 0.0};
+                C acc[RC] = {0.0, 0.0, 0.0, 0.0};
                 const int k0 = MODE == FWD ? 0 : r, k1 = MODE == FWD ? r + 1 : m;
                 for (int kb = k0; kb < k1; kb += 8) {
-                    double mv[8];
+                    C mv[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
-                        mv[u] = kb + u < k1 ? (double)M[(int64_t)(kb + u) * m + r] : 0.0;
+                        mv[u] = kb + u < k1 ? (C)M[(int64_t)(kb + u) * m + r] : 0.0;
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int k = min(kb + u, m - 1);
@@ -420,14 +427,14 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
         } else {
             // out(r) = sum_k M(k, r) y(k): warp per row, lanes over k
             for (int r = warp; r < m; r += kWarps) {
-                double acc[RC] = {0.0, 0.0, 0.0, 0.0};
+                C acc[RC] = {0.0, 0.0, 0.0, 0.0};
                 const int k0 = MODE == FWD_T ? 0 : r, k1 = MODE == FWD_T ? r + 1 : m;
                 for (int kb = k0; kb < k1; kb += 128) {
-                    double mv[4];
+                    C mv[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int k = kb + u * 32 + lane;
-                        mv[u] = k < k1 ? (double)M[(int64_t)r * m + k] : 0.0;
+                        mv[u] = k < k1 ? (C)M[(int64_t)r * m + k] : 0.0;
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -448,25 +455,25 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
         }
         return;
     }
-    // values as double: full copy if it fits, else panel buffers
+    // values as C: full copy if it fits, else panel buffers
     const int64_t nnz = dd.dense ? (int64_t)dd.ld * dd.cols
                                  : (int64_t)a.lcolptr[dd.coff + dd.cols];
     bool staged;
     size_t used;
-    const size_t full = align16(nnz * sizeof(double));
+    const size_t full = align16(nnz * sizeof(C));
     const BlockView<T> F = stage_block<T>(dd, a, const_cast<T *>(val),
                                           smem + ybytes, kStageSmem - ybytes,
                                           true, &staged, &used);
-    // F.v is T; copy values into a double buffer for the chain
+    // F.v is T; copy values into a C buffer for the chain
     unsigned char *vbuf = smem + ybytes + used;
     const size_t vcap = kStageSmem - ybytes - used;
     const bool whole = staged ? false : full <= vcap;
     const bool up = (MODE == FWD || MODE == FWD_T);
     if (staged || whole) {
         const T *src = F.v;
-        double *vd = reinterpret_cast<double *>(vbuf);
+        C *vd = reinterpret_cast<C *>(vbuf);
         if (whole)
-            for (int64_t e = threadIdx.x; e < nnz; e += kThreads) vd[e] = (double)src[e];
+            for (int64_t e = threadIdx.x; e < nnz; e += kThreads) vd[e] = (C)src[e];
         __syncthreads();
         if (warp == 0)
             for (int k = 0; k < m; ++k) {
@@ -475,7 +482,7 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
                 const uint16_t *rows;
                 F.col(jj, off, cn, rows);
                 if (whole)
-                    chain_step<MODE>(jj, vd + off, rows, cn, F.dp[jj], y, lane);
+                    chain_step<C, MODE>(jj, vd + off, rows, cn, F.dp[jj], y, lane);
                 else {
                     // staged T values: convert on the fly through registers
                     chain_step_t<T, MODE>(jj, F.v + off, rows, cn, F.dp[jj], y, lane);
@@ -504,17 +511,17 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
             F.col(j1 - 1, o1, c1, r1);
             maxp = max(maxp, (int64_t)(o1 + c1 - o0));
         }
-        double *buf[2] = {reinterpret_cast<double *>(vbuf),
-                          reinterpret_cast<double *>(vbuf) + maxp};
+        C *buf[2] = {reinterpret_cast<C *>(vbuf),
+                          reinterpret_cast<C *>(vbuf) + maxp};
         auto panel_of = [&](int q) { return up ? q : npan - 1 - q; };
-        auto load = [&](int pn, double *dst, int t0, int nt) {
+        auto load = [&](int pn, C *dst, int t0, int nt) {
             const int j0 = pn * W, j1 = min(m, j0 + W);
             int o0, c0, o1, c1;
             const uint16_t *r0, *r1;
             F.col(j0, o0, c0, r0);
             F.col(j1 - 1, o1, c1, r1);
             for (int64_t e = t0; e < (int64_t)(o1 + c1 - o0); e += nt)
-                dst[e] = (double)F.v[o0 + e];
+                dst[e] = (C)F.v[o0 + e];
         };
         load(panel_of(0), buf[0], threadIdx.x, kThreads);
         __syncthreads();
@@ -530,7 +537,7 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
                     int off, cn;
                     const uint16_t *rows;
                     F.col(jj, off, cn, rows);
-                    chain_step<MODE>(jj, buf[q & 1] + (off - ob), rows, cn,
+                    chain_step<C, MODE>(jj, buf[q & 1] + (off - ob), rows, cn,
                                      F.dp[jj], y, lane);
                 }
             } else if (q + 1 < npan) {
