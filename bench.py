@@ -172,7 +172,7 @@ def batch_leg(torch, S, dev, args):
     against a loop of per-matrix factor + solve calls."""
     ms = workloads.batch_grid5(count=256, seed=0)
     PB = S.Plan([m.n for m in ms], [m.colptr for m in ms],
-                [m.rowidx for m in ms], precision="fp32")
+                [m.rowidx for m in ms], precision="fp32", dense_threshold=0.0)
     vb = dev(np.concatenate([m.values for m in ms]))
     bb = dev(np.concatenate([m.rhs[:, 0] for m in ms]))
     FB = S.Factor(PB, vb)
@@ -186,7 +186,8 @@ def batch_leg(torch, S, dev, args):
         msb = timed(torch, step_b, args.steps, 2)
         _, ib = FB.solve(bb, info=True)
         FB.set_graph(False)
-    plans = [S.Plan(m.n, m.colptr, m.rowidx, precision="fp32") for m in ms]
+    plans = [S.Plan(m.n, m.colptr, m.rowidx, precision="fp32",
+                    dense_threshold=0.0) for m in ms]
     vs = [dev(m.values) for m in ms]
     rs = [dev(m.rhs[:, 0]) for m in ms]
     fs = [S.Factor(p, v) for p, v in zip(plans, vs)]
@@ -252,12 +253,15 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         barrier = dist.barrier
     from paper_2512_04389_b300 import slu as S
+    from paper_2512_04389_b300.tune import tune
 
     s = workloads.grid7_cd(40)
     dev = lambda a: torch.as_tensor(np.asarray(a), dtype=torch.float64,
                                     device="cuda")
     vals_d, rhs_d = dev(s.values), dev(s.rhs)
-    plan = S.Plan(s.n, s.colptr, s.rowidx)
+    # sparse/dense switch picked by the autotuner (cached per pattern)
+    thr64, tun64 = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d, precision="fp64")
+    plan = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=thr64)
     fl = step_flops(plan, s.nrhs)
     F = S.Factor(plan, vals_d)
 
@@ -294,6 +298,7 @@ def main():
                       "blocks_1d": plan.info["nblocks_1d"],
                       "levels": plan.info["nlevels"],
                       "analyze_ms": plan.info["analyze_ms"],
+                      "dense_threshold": thr64, "tuning_ms": tun64,
                       "backward_error": sinfo["backward_error"],
                       "l2": "no flush: factors (340 MB) exceed L2",
                       "parallelism": f"replicas x{world}"},
@@ -323,7 +328,10 @@ def main():
     if not args.no_extras:
         extras = {}
         # FP32 factors + FP64 refinement
-        p32 = S.Plan(s.n, s.colptr, s.rowidx, precision="fp32")
+        thr32, tun32 = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
+                            precision="fp32")
+        p32 = S.Plan(s.n, s.colptr, s.rowidx, precision="fp32",
+                     dense_threshold=thr32)
         F32 = S.Factor(p32, vals_d)
 
         def step32():
@@ -331,21 +339,23 @@ def main():
             F32.solve(rhs_d)
         ms32 = timed(torch, step32, args.steps, 2)
         _, i32 = F32.solve(rhs_d, info=True)
-        extras["fp32_ir"] = {"ms_per_step": ms32,
+        extras["fp32_ir"] = {"ms_per_step": ms32, "dense_threshold": thr32,
                              "gflops": fl / (ms32 * 1e-3) / 1e9,
                              "backward_error": i32["backward_error"],
                              "ir_iterations": i32["iterations"]}
         del F32
         # regular blocking, same code
+        thrr, _ = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
+                       precision="fp64", blocking="regular", regular_block=128)
         preg = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular",
-                      regular_block=128)
+                      regular_block=128, dense_threshold=thrr)
         Freg = S.Factor(preg, vals_d)
 
         def stepreg():
             Freg.refactor(vals_d)
             Freg.solve(rhs_d)
         msr = timed(torch, stepreg, args.steps, 2)
-        extras["regular128_fp64"] = {"ms_per_step": msr,
+        extras["regular128_fp64"] = {"ms_per_step": msr, "dense_threshold": thrr,
                                      "gflops": fl / (msr * 1e-3) / 1e9,
                                      "levels": preg.info["nlevels"]}
         del Freg

@@ -558,9 +558,11 @@ static void build_levels_and_tasks(slu_plan &P) {
     };
     P.woff.assign(p, -1);
     P.wsize = 0;
+    P.inv_maxb = 0;
     for (int32_t I = 0; I < p; ++I) {
         const BlockDesc &d = P.blocks[P.diagblk[I]];
         if (inv_ok(d)) {
+            P.inv_maxb = std::max(P.inv_maxb, d.rows);
             P.woff[I] = P.wsize;
             P.wsize += 2 * (int64_t)d.rows * d.rows;
         }

@@ -631,13 +631,18 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
     const T *Inv = winv + woff[dd.I] + (type == 0 ? 0 : (int64_t)m * m);
     const int nv = min(64, (type == 0 ? d.cols : d.rows) - c0);
     // stage the chunk: GESSM columns c0.. (X[k][c] = B(k, c0 + c));
-    // TSTRF rows c0.. (X[k][r] = B(c0 + r, k))
+    // TSTRF rows c0.. (X[k][r] = B(c0 + r, k)); flag the 16-deep k-slices
+    // of the chunk that hold a nonzero (all-zero slices contribute nothing)
+    int *zflag = reinterpret_cast<int *>(Ts + KT * 64);
+    for (int e = tid; e < (m + KT - 1) / KT; e += 256) zflag[e] = 0;
+    __syncthreads();
     for (int e = tid; e < m * 64; e += 256) {
         const int k = e / 64, c = e % 64;
         T v = T(0);
         if (c < nv)
             v = type == 0 ? Bg[(int64_t)(c0 + c) * ld + k] : Bg[(int64_t)k * ld + c0 + c];
         X[e] = v;
+        if (v != T(0)) zflag[k / KT] = 1;
     }
     __syncthreads();
     for (int ob = 0; ob < m; ob += 64) {       // output chunk along m
@@ -650,6 +655,7 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
         // TSTRF: out(r, i) = sum_{k <= i} X(r, k) Uinv(k, i), i in [ob, ob+64)
         const int kend = min(m, ob + 64);
         for (int k0 = 0; k0 < kend; k0 += KT) {
+            if (!zflag[k0 / KT]) continue;             // uniform across the CTA
             for (int e = tid; e < KT * 64; e += 256) {
                 int kk, ii;
                 T v = T(0);
@@ -821,7 +827,18 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
     };
     load(dl, du, 0);
     store(0);
-    __syncthreads();
+    // a slice is skipped when its L or U part is entirely zero (dense
+    // storage of a sparse-ish block); the flag rides on the barrier
+    auto nonzero = [&]() {
+        bool a = false, b = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a |= ra[q] != T(0);
+            b |= rb[q] != T(0);
+        }
+        return (int)a | ((int)b << 1);
+    };
+    int live = __syncthreads_or(nonzero() & 1) && __syncthreads_or(nonzero() & 2);
     int buf = 0;
     for (;;) {
         // advance to the next slice
@@ -833,21 +850,24 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
             if (ns != s) { nl = bd[src[2 * ns]]; nu = bd[src[2 * ns + 1]]; }
             load(nl, nu, nk0);
         }
+        if (live) {
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            T a[4], b[4];
+            for (int k = 0; k < KT; ++k) {
+                T a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[buf][k][ty * 4 + i];
+                for (int i = 0; i < 4; ++i) a[i] = As[buf][k][ty * 4 + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[buf][k][tx * 4 + j];
+                for (int j = 0; j < 4; ++j) b[j] = Bs[buf][k][tx * 4 + j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+            }
         }
         if (!more) break;
         store(buf ^ 1);
-        __syncthreads();
+        const int nzf = nonzero();
+        live = __syncthreads_or(nzf & 1) && __syncthreads_or(nzf & 2);
         buf ^= 1;
         s = ns;
         k0 = nk0;
@@ -1035,7 +1055,7 @@ static slu_status run_factor(slu_handle *h, const double *values,
         if (d1 > d0) {
             LaunchScope ls_(h, SLU_KC_PANEL, st);
             k_panel_inv<T><<<(int)(d1 - d0), 256,
-                             ((size_t)P->maxb * 64 + 16 * 64) * sizeof(T), st>>>(
+                             ((size_t)P->inv_maxb * 64 + 16 * 64) * sizeof(T) + 256, st>>>(
                 D->pd_task + 4 * d0, D->bd, val, static_cast<const T *>(h->winv),
                 D->woff);
         }

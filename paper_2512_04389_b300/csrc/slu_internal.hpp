@@ -100,6 +100,7 @@ struct slu_plan {
     // each); -1 for sparse diagonal blocks
     std::vector<int64_t> woff;
     int64_t wsize = 0;
+    int32_t inv_maxb = 0;                // largest block on the inverse path
     std::vector<int64_t> inv_off;        // per level, into inv_task
     std::vector<int32_t> inv_task;       // 3 per task: diag blk, L(0)/U(1), j0
     // panel split: dense pairs as 64-wide chunks of inverse GEMMs, the

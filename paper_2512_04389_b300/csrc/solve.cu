@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(kThreads)
 k_pull_scatter(const int32_t *__restrict__ pairs,
                const int64_t *__restrict__ poff, BlockArgs a,
                const T *__restrict__ val, const double *__restrict__ X,
-               int64_t ldx, int nc, double *__restrict__ part_d) {
+               int64_t ldx, int nc, double *__restrict__ part_d,
+               int rows_per_chunk) {
     using C = T;
     C *part = reinterpret_cast<C *>(part_d);
     extern __shared__ __align__(16) unsigned char smem[];
@@ -45,7 +46,8 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
     const int m = db.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     C *pw = reinterpret_cast<C *>(smem);
     constexpr int VW = 16 / sizeof(T);                  // rows per vector load
-    if (db.dense && db.ld % VW == 0 && m <= 64 * VW * 4) {
+    if (db.dense && db.ld % VW == 0) {
+        if (blockIdx.y > 0) return;                      // row chunks: sparse only
         // dense GEMV: thread (row group, column group) accumulates VW rows
         // over its columns with 16-byte loads, 8 in flight; the 4 column
         // groups are reduced in a fixed order.
@@ -100,9 +102,13 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
             out[t] = (red[t] + red[m * RC + t]) + (red[2 * m * RC + t] + red[3 * m * RC + t]);
         return;
     }
-    for (int t = threadIdx.x; t < kWarps * m * RC; t += kThreads) pw[t] = 0.0;
+    // rows [rc0, rc0 + mc) of the partial (one chunk per blockIdx.y)
+    const int mc = min(m, rows_per_chunk), rc0 = blockIdx.y * rows_per_chunk;
+    if (rc0 >= m) return;
+    const int mr = min(mc, m - rc0);
+    for (int t = threadIdx.x; t < kWarps * mc * RC; t += kThreads) pw[t] = 0.0;
     __syncthreads();
-    C *mine = pw + warp * m * RC;
+    C *mine = pw + warp * mc * RC;
     for (int jj = warp; jj < db.cols; jj += kWarps) {
         C xv[RC];
         bool any = false;
@@ -117,20 +123,23 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
             const uint16_t *rows;
             colview(db, jj, a, vb, cn, rows);
             for (int e = lane; e < cn; e += 32) {
+                const int r = rowat(rows, e) - rc0;
+                if (r < 0 || r >= mr) continue;
                 const C l = (C)val[vb + e];
-                C *q = mine + rowat(rows, e);     // rhs-major: c * m + row
+                C *q = mine + r;                        // rhs-major: c * mc + r
 #pragma unroll
-                for (int c = 0; c < RC; ++c) q[c * m] += l * xv[c];
+                for (int c = 0; c < RC; ++c) q[c * mc] += l * xv[c];
             }
         }
         __syncwarp();
     }
     __syncthreads();
     C *out = part + poff[blockIdx.x] * RC;
-    for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+    for (int t = threadIdx.x; t < mr * RC; t += kThreads) {
+        const int r = t % mr, c = t / mr;
         C sum = 0.0;
-        for (int w = 0; w < kWarps; ++w) sum += pw[w * m * RC + t];
-        out[t] = sum;                                   // index c * m + row
+        for (int w = 0; w < kWarps; ++w) sum += pw[w * mc * RC + c * mc + r];
+        out[c * m + rc0 + r] = sum;                     // index c * m + row
     }
 }
 
@@ -673,7 +682,15 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
     const DevPlan *D = P->dev;
     const T *val = static_cast<const T *>(h->storage);
     const BlockArgs a = block_args(P);
-    const size_t pull_smem = (size_t)kWarps * P->maxb * RC * sizeof(double);
+    // sparse sources keep kWarps partials of (rows x RC); split the rows
+    // into chunks when a whole block's partials do not fit
+    const int rpc = (int)std::min<int64_t>(
+        P->maxb, kStageSmem / ((size_t)kWarps * RC * sizeof(double)));
+    const int nch = (P->maxb + rpc - 1) / rpc;
+    // dense sources: x (cols x RC) + 4 partials (rows x RC)
+    const size_t pull_smem = std::max<size_t>(
+        (size_t)kWarps * rpc * RC * sizeof(double),
+        (size_t)5 * P->maxb * RC * sizeof(double));
     if (pull_smem > kStageSmem)
         return fail(SLU_ERR_NOT_SUPPORTED, "block too large for the solve");
     const int64_t *boff = MODE == FWD ? D->lrow_off : MODE == BWD ? D->urow_off
@@ -688,9 +705,10 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
             if (q1 > q0) {
                 LaunchScope ls_(h, SLU_KC_SOLVE, st);
                 if (MODE == FWD || MODE == BWD)
-                    k_pull_scatter<T><<<(int)(q1 - q0), kThreads, pull_smem, st>>>(
+                    k_pull_scatter<T><<<dim3((unsigned)(q1 - q0), (unsigned)nch),
+                                        kThreads, pull_smem, st>>>(
                         D->sp_pairs[MODE] + 2 * q0, D->sp_poff[MODE] + q0, a, val,
-                        Xc, ldx, nc, h->part);
+                        Xc, ldx, nc, h->part, rpc);
                 else
                     k_pull_dot<T><<<(int)(q1 - q0), kThreads, 0, st>>>(
                         D->sp_pairs[MODE] + 2 * q0, D->sp_poff[MODE] + q0, a, val,

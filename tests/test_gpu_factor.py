@@ -83,8 +83,15 @@ def test_fp64_factor_and_solve_parity(name, mk, opts):
     assert np.abs(Lam - Lo).max() / np.abs(Lo).max() <= 1e-10
 
 
-@pytest.mark.parametrize("name,mk,opts", CASES[:1] + CASES[5:8],
-                         ids=[c[0] for c in CASES[:1] + CASES[5:8]])
+FP32_CASES = CASES[:1] + CASES[5:8] + [
+    ("circuit_20k", lambda: workloads.circuit_bbd(n=20_000, border=400),
+     dict(dense_threshold=0.0)),
+    ("grid7cd_14 all dense", lambda: workloads.grid7_cd(14, nrhs=4),
+     dict(b_min=16, dense_threshold=0.0))]
+
+
+@pytest.mark.parametrize("name,mk,opts", FP32_CASES,
+                         ids=[c[0] for c in FP32_CASES])
 def test_fp32_factor_with_fp64_refinement(name, mk, opts):
     s = mk()
     P, F = gpu_factor(s, precision="fp32", **opts)
@@ -156,14 +163,19 @@ def test_empty_rhs_and_vector_rhs():
     assert np.abs(x.cpu().numpy() - xo).max() <= 1e-12 * np.abs(xo).max()
 
 
-@pytest.mark.parametrize("name,mk", [
-    ("grid5_48 (2304)", lambda: workloads.grid5(48)),
-    ("grid7theta_32 (32768)", lambda: workloads.grid7_theta(32)),
+@pytest.mark.parametrize("name,mk,thr", [
+    ("grid5_48 (2304)", lambda: workloads.grid5(48), 0.6),
+    ("grid7theta_32 (32768)", lambda: workloads.grid7_theta(32), 0.6),
+    ("grid7theta_32 all dense", lambda: workloads.grid7_theta(32), 0.0),
+    ("circuit_20k (400 border)", lambda: workloads.circuit_bbd(
+        n=20_000, border=400), 0.6),
+    ("circuit_20k all dense", lambda: workloads.circuit_bbd(
+        n=20_000, border=400), 0.0),
 ])
-def test_full_size_parity(name, mk):
-    """Full-size configurations the oracle factors in seconds: element-wise."""
+def test_full_size_parity(name, mk, thr):
+    """Configurations the oracle factors in seconds: element-wise."""
     s = mk()
-    P, F = gpu_factor(s)
+    P, F = gpu_factor(s, dense_threshold=thr)
     _, _, _, pv = oracle_factor(s)
     assert factor_error(P, F, pv) <= FP64_TOL
     X, info = F.solve(_dev(s.rhs), info=True)

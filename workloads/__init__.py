@@ -83,12 +83,10 @@ def coo_to_csc(n, rows, cols, vals, sum_duplicates=True):
         first = np.ones(key.size, dtype=bool)
         first[1:] = key[1:] != key[:-1]
         idx = np.cumsum(first) - 1
-        v2 = np.zeros(int(first.sum()))
-        np.add.at(v2, idx, vals)
+        v2 = np.bincount(idx, weights=vals, minlength=int(first.sum()))
         rows, cols, vals = rows[first], cols[first], v2
     colptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(colptr, cols + 1, 1)
-    colptr = np.cumsum(colptr)
+    colptr[1:] = np.cumsum(np.bincount(cols, minlength=n))
     return colptr, rows.astype(np.int32), vals
 
 
@@ -282,6 +280,8 @@ def circuit_bbd(n=200_000, border=4_000, seed=0, nrhs=8, block_lo=32,
     Draw order: block sizes; per block: Zipf draws, pair coin flips; border
     targets, one border node at a time; magnitudes, signs (both for the
     directed entries in sorted (col, row) order); diagonal factors; RHS.
+    Border coin flips are drawn for 64 border nodes at a time, each a
+    64 x n block of U(0, 1) in row-major order.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     nb = n - border
@@ -307,27 +307,28 @@ def circuit_bbd(n=200_000, border=4_000, seed=0, nrhs=8, block_lo=32,
         E_i.append(base + pos[iu[keep]])
         E_j.append(base + pos[ju[keep]])
         base += s
-    k = int(round(border_frac * n))
-    for t in range(border):
-        node = nb + t
-        tg = rng.choice(n - 1, size=k, replace=False)
-        tg = np.where(tg >= node, tg + 1, tg)      # skip self
-        E_i.append(np.full(k, node, dtype=np.int64))
-        E_j.append(tg.astype(np.int64))
+    for t0 in range(0, border, 64):
+        t1 = min(border, t0 + 64)
+        hit = rng.random((t1 - t0, n)) < border_frac
+        rr, cc = np.nonzero(hit)
+        node = nb + t0 + rr
+        keep = cc != node                           # no self links
+        E_i.append(node[keep].astype(np.int64))
+        E_j.append(cc[keep].astype(np.int64))
     ei = np.concatenate(E_i)
     ej = np.concatenate(E_j)
     # symmetric pattern, duplicates removed
     r = np.concatenate([ei, ej])
     c = np.concatenate([ej, ei])
-    key = np.unique(c * n + r)
+    key = np.sort(c * n + r)                       # sort + dedupe
+    key = key[np.r_[True, key[1:] != key[:-1]]] if key.size else key
     cols = key // n
     rows = key % n
     m = rows.size
     mag = 10.0 ** rng.uniform(-3.0, 0.0, size=m)
     sgn = np.where(rng.random(m) < 0.5, -1.0, 1.0)
     off = mag * sgn
-    rowsum = np.zeros(n)
-    np.add.at(rowsum, rows, np.abs(off))
+    rowsum = np.bincount(rows, weights=np.abs(off), minlength=n)
     diag = rowsum * rng.uniform(1.05, 2.0, size=n)
     diag[diag == 0.0] = 1.0                      # isolated node
     colptr, rowidx, values = coo_to_csc(
