@@ -202,7 +202,12 @@ slu_status slu_plan_export_tasks(const slu_plan *plan, int64_t *getrf_off,
  * (device memory on the current device) and enqueues the factorization on
  * `stream`.  The call synchronizes the stream before returning (it reads
  * the perturbation count), so *info is final.  *out receives a new handle;
- * with SLU_ERR_SINGULAR a handle is still returned (factors not usable). */
+ * with SLU_ERR_SINGULAR a handle is still returned (factors not usable).
+ * The handle owns a second, non-blocking stream: each level's Schur updates
+ * whose target lies outside the next level's block rows and columns run
+ * there, forked from `stream` after the level's panels and joined back
+ * before the next level's updates, so every launch stays ordered after
+ * earlier work on `stream` and completes before later work on it. */
 slu_status slu_factor(const slu_plan *plan, const double *values,
                       void *stream, slu_handle **out, slu_factor_info *info);
 
@@ -255,18 +260,22 @@ slu_status slu_export_factors(const slu_handle *h, double *out, void *stream);
 
 /* Profiling: while enabled, every kernel launch of the handle is bracketed
  * by a pair of CUDA events on its stream, and slu_handle_stats sums their
- * durations per kernel class (it synchronizes on the last event).  Enabling
+ * durations per kernel class (it synchronizes on every recorded event).  Enabling
  * clears the accumulated figures; the launch counter runs always. */
 slu_status slu_set_profiling(slu_handle *h, int32_t enable);
 slu_status slu_handle_stats(slu_handle *h, slu_stats *out);
 
 /* Per-launch record of the launches profiled since the last
- * slu_set_profiling / slu_handle_stats call, in launch order: kernel class
- * and CUDA-event duration (ms).  Copies min(cap, count) records into the
- * host arrays cls and ms and the count into *count; synchronizes on the
- * last event; does not consume the records. */
+ * slu_set_profiling / slu_handle_stats call, in launch order: kernel class,
+ * CUDA-event duration (ms), factorization level (-1 outside the level loop)
+ * and grid size in CTAs (negative for the generic sparse GESSM/TSTRF and
+ * SSSSM kernels, 0 where not recorded).  Copies min(cap, count) records
+ * into whichever of the host arrays cls, ms, level, ctas are non-NULL and
+ * the count into *count; synchronizes on every recorded event; does not consume
+ * the records. */
 slu_status slu_handle_trace(slu_handle *h, int64_t cap, int32_t *cls,
-                            float *ms, int64_t *count);
+                            float *ms, int32_t *level, int32_t *ctas,
+                            int64_t *count);
 
 /* Algorithmic flops of the factorization by kernel class, from the filled
  * pattern: with l_k the entries of L(:,k) inside k's diagonal block and

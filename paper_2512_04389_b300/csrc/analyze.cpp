@@ -468,6 +468,10 @@ static void build_levels_and_tasks(slu_plan &P) {
     P.tstrf_off.assign(L + 1, 0);
     P.tgt_off.assign(L + 1, 0);
     P.getrf.clear();
+    P.gd_off.assign(L + 1, 0);
+    P.gs_off.assign(L + 1, 0);
+    P.gd.clear();
+    P.gs.clear();
     P.gessm.clear();
     P.tstrf.clear();
     P.tgt.clear();
@@ -487,6 +491,9 @@ static void build_levels_and_tasks(slu_plan &P) {
             P.srcoff.push_back((int64_t)P.src.size() / 2);
         }
         P.getrf_off[lv + 1] = (int64_t)P.getrf.size();
+        for (int32_t db : lv_getrf[lv]) (P.blocks[db].dense ? P.gd : P.gs).push_back(db);
+        P.gd_off[lv + 1] = (int64_t)P.gd.size();
+        P.gs_off[lv + 1] = (int64_t)P.gs.size();
         P.gessm_off[lv + 1] = (int64_t)P.gessm.size() / 2;
         P.tstrf_off[lv + 1] = (int64_t)P.tstrf.size() / 2;
         P.tgt_off[lv + 1] = (int64_t)P.tgt.size();
@@ -501,10 +508,22 @@ static void build_levels_and_tasks(slu_plan &P) {
     P.gg_src.clear();
     P.gg_srcoff.assign(1, 0);
     constexpr int32_t kTile = 64;
+    P.gm_mid.assign(L, 0);
+    P.gg_mid.assign(L, 0);
     for (int32_t lv = 0; lv < L; ++lv) {
+      // pass 0: targets in a block row or column of the next level (needed
+      // by its GETRF / GESSM / TSTRF); pass 1: the rest, which touch no
+      // block of the next level
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            P.gm_mid[lv] = (int64_t)P.gm_task.size() / 5;
+            P.gg_mid[lv] = (int64_t)P.gg_tgt.size();
+        }
         for (int64_t k = P.tgt_off[lv]; k < P.tgt_off[lv + 1]; ++k) {
             const int32_t tb = P.tgt[k];
             const BlockDesc &td = P.blocks[tb];
+            const bool next = P.level[std::min(td.I, td.J)] == lv + 1;
+            if (next != (pass == 0)) continue;
             std::vector<int32_t> dense_pairs, other;
             for (int64_t q = P.srcoff[k]; q < P.srcoff[k + 1]; ++q) {
                 const int32_t lb = P.src[2 * q], ub = P.src[2 * q + 1];
@@ -532,6 +551,7 @@ static void build_levels_and_tasks(slu_plan &P) {
                 P.gg_srcoff.push_back((int64_t)P.gg_src.size() / 2);
             }
         }
+      }
         P.gm_off[lv + 1] = (int64_t)P.gm_task.size() / 5;
         P.gg_off[lv + 1] = (int64_t)P.gg_tgt.size();
     }

@@ -18,6 +18,7 @@ struct DevPlan {
     uint16_t *lrow = nullptr;
     int32_t *dpos = nullptr, *sched = nullptr, *sgrp = nullptr;
     int32_t *getrf = nullptr, *gessm = nullptr, *tstrf = nullptr;
+    int32_t *gd = nullptr, *gs = nullptr;
     int32_t *tgt = nullptr, *src = nullptr;
     int64_t *srcoff = nullptr;
     int32_t *gm_task = nullptr, *gm_src = nullptr, *gg_tgt = nullptr,
@@ -201,6 +202,9 @@ struct slu_handle {
     double *part = nullptr;              // solve partial sums (factor time)
     double *anorm_seg = nullptr;         // batch: ||A_q||_inf per member
     void *winv = nullptr;                // T[plan->wsize]: diagonal inverses
+    // second stream for the deferred Schur updates, fork / join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // graph mode
     bool use_graph = false;
     cudaGraphExec_t graph_exec = nullptr;
@@ -209,7 +213,8 @@ struct slu_handle {
     // launch accounting and optional per-launch event timing
     int64_t launches = 0;
     bool profiling = false;
-    struct Rec { int cls; cudaEvent_t a, b; };
+    struct Rec { int cls; cudaEvent_t a, b; int level, ctas; };
+    int cur_level = -1;                  // factor level being launched, else -1
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;       // profiling events, reused
     size_t pool_next = 0;
@@ -225,8 +230,9 @@ struct LaunchScope {
     int cls;
     cudaStream_t st;
     cudaEvent_t a = nullptr, b = nullptr;
-    LaunchScope(const slu_handle *hc, int c, cudaStream_t s)
-        : h(const_cast<slu_handle *>(hc)), cls(c), st(s) {
+    int ctas;
+    LaunchScope(const slu_handle *hc, int c, cudaStream_t s, int nctas = 0)
+        : h(const_cast<slu_handle *>(hc)), cls(c), st(s), ctas(nctas) {
         h->launches++;
         if (h->profiling && !h->capturing) {
             while (h->pool.size() < h->pool_next + 2) {
@@ -242,7 +248,7 @@ struct LaunchScope {
     ~LaunchScope() {
         if (a) {
             cudaEventRecord(b, st);
-            h->recs.push_back({cls, a, b});
+            h->recs.push_back({cls, a, b, h->cur_level, ctas});
         }
     }
 };

@@ -141,161 +141,202 @@ __device__ __forceinline__ double fix_pivot(double piv, double tau,
     return piv;
 }
 
-// Dense LU of an m x w column-major block (leading dimension ld, w <= m,
-// pivots on the first w rows), right-looking with the whole CTA.  Step k:
-// scale L(k+1:, k) by the published reciprocal pivot; barrier; rank-1
-// update with warps over columns and lanes over rows; thread 0 updates
-// entry (k+1, k+1) first, so it then fixes pivot k+1 (FP64 test and
-// perturbation) and publishes its reciprocal; barrier.
-template <typename M>
-__device__ void lu_dense(M *A, int m, int w, int ld, double tau,
-                         unsigned long long *cnt) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    __shared__ M s_pinv;
-    if (tid == 0 && w > 0) {
-        const double piv = fix_pivot((double)A[0], tau, cnt);
-        A[0] = (M)piv;
-        s_pinv = (M)(1.0 / piv);
+// Dense-stored diagonal block, right-looking LU that skips exact zeros.
+// Storage is split: entry (r, c) with r, c >= p0 lives in shared memory S
+// (column-major, leading dimension ls), the rest in the block's global
+// storage G (leading dimension ld, L2-resident).  Step k, two barriers:
+//   1. warp 0 scales L(k+1:, k) by the published reciprocal pivot and
+//      compacts its nonzeros by ballot into a (row, value) list; warp 1
+//      compacts the nonzeros of U(k, k+1:) into a (column, value) list;
+//   2. all threads apply B(r, c) -= L(r, k) U(k, c) over the list product
+//      (lane groups per column, four updates in flight per thread); thread
+//      0 owns the product's first entry, (k+1, k+1) when that is updated,
+//      and then fixes pivot k+1 (FP64 test and perturbation) and publishes
+//      its reciprocal.
+// The terms left out are exact zeros, so the result is that of the dense
+// right-looking LU; a blocked tile skip would keep most of them, because
+// the fill of a coarse block is scattered along its elimination tree.
+#ifdef SLU_SELFCHECK
+// checked builds only: bit 0 entry index, bit 1 list index, bit 2 update
+__device__ unsigned long long g_selfcheck;
+__device__ double g_selfcheck_sink[4];
+extern "C" unsigned long long slu_selfcheck_read() {
+    unsigned long long v = 0;
+    cudaMemcpyFromSymbol(&v, g_selfcheck, sizeof(v));
+    return v;
+}
+#define SLU_CHECK(cond, bit) \
+    do { if (!(cond)) atomicOr(&g_selfcheck, 1ull << (bit)); } while (0)
+#else
+#define SLU_CHECK(cond, bit) do { } while (0)
+#endif
+
+template <typename T>
+struct SplitBlock {
+    T *G;
+    int64_t ld;
+    T *S;
+    int ls, p0, n;
+    __device__ __forceinline__ T &at(int r, int c) const {
+#ifdef SLU_SELFCHECK
+        if (r < 0 || c < 0 || r >= n || c >= n) {
+            atomicOr(&g_selfcheck, 1ull);
+            return reinterpret_cast<T *>(g_selfcheck_sink)[0];
+        }
+#endif
+        return (r >= p0 && c >= p0) ? S[(int64_t)(c - p0) * ls + (r - p0)]
+                                    : G[(int64_t)c * ld + r];
+    }
+};
+
+// Shared-memory bytes of the step lists for a b-row block.
+__host__ __device__ constexpr size_t lu_list_bytes(int b, size_t esz) {
+    return 2 * (size_t)b * (esz + 2) + 64;
+}
+
+// One warp: compact the nonzeros of entries k+1..b-1 of a column (col =
+// true: (r, k), scaled by rcp and stored back) or of a row ((k, c)).
+template <typename T>
+__device__ __forceinline__ int lu_compact(const SplitBlock<T> &B, int b, int k,
+                                          bool col, T rcp, T *X, uint16_t *I) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int n = 0;
+    for (int i0 = k + 1; i0 < b; i0 += 128) {
+        T v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + 32 * q + lane;
+            v[q] = i < b ? (col ? B.at(i, k) : B.at(k, i)) : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + 32 * q + lane;
+            // only entries inside the block are scaled and listed (with a
+            // zero pivot and no perturbation rcp is inf, and 0 * inf would
+            // list a NaN for a lane past the end)
+            const bool in = i < b;
+            if (col && in) {
+                v[q] *= rcp;
+                B.at(i, k) = v[q];
+            }
+            const bool nz = in && v[q] != T(0);
+            const unsigned m = __ballot_sync(0xffffffffu, nz);
+            if (nz) {
+                const int p = n + __popc(m & lt);
+                SLU_CHECK(p < b && i < b, 1);
+                I[p] = (uint16_t)i;
+                X[p] = v[q];
+            }
+            n += __popc(m);
+        }
+    }
+    return n;
+}
+
+template <typename T>
+__device__ void lu_skip(const SplitBlock<T> &B, int b, unsigned char *lists,
+                        double tau, unsigned long long *cnt) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const int warp = tid >> 5, nw = nt >> 5;
+    T *Lv = reinterpret_cast<T *>(lists), *Uv = Lv + b;
+    uint16_t *R = reinterpret_cast<uint16_t *>(Uv + b), *C = R + b;
+    __shared__ T s_pinv;
+    __shared__ int s_nR, s_nC;
+    if (tid == 0 && b > 0) {
+        const T pv = (T)fix_pivot((double)B.at(0, 0), tau, cnt);
+        B.at(0, 0) = pv;
+        s_pinv = T(1) / pv;
     }
     __syncthreads();
-    for (int k = 0; k < w; ++k) {
-        const M pinv = s_pinv;
-        M *colk = A + (int64_t)k * ld;
-        for (int r = k + 1 + tid; r < m; r += nt) colk[r] *= pinv;
-        __syncthreads();
-        for (int c = k + 1 + warp; c < w; c += nw) {
-            M *colc = A + (int64_t)c * ld;
-            const M u = colc[k];
-            if (u != M(0))
-                for (int r = k + 1 + lane; r < m; r += 32) colc[r] -= colk[r] * u;
-        }
-        if (tid == 0 && k + 1 < w) {
-            const double piv = fix_pivot((double)A[(int64_t)(k + 1) * ld + k + 1], tau, cnt);
-            A[(int64_t)(k + 1) * ld + k + 1] = (M)piv;
-            s_pinv = (M)(1.0 / piv);
+    for (int k = 0; k + 1 < b; ++k) {
+        if (warp == 0) {
+            const int n = lu_compact<T>(B, b, k, true, s_pinv, Lv, R);
+            if (lane == 0) s_nR = n;
+        } else if (warp == 1) {
+            const int n = lu_compact<T>(B, b, k, false, T(0), Uv, C);
+            if (lane == 0) s_nC = n;
         }
         __syncthreads();
-    }
-}
-
-template <typename M>
-__device__ void getrf_dense_core(M *A, int b, int ld, double tau,
-                                 unsigned long long *cnt) {
-    lu_dense<M>(A, b, b, ld, tau, cnt);
-}
-
-template <typename M>
-__device__ void getrf_panel_tall(M *P, int m, int w, double tau,
-                                 unsigned long long *cnt) {
-    lu_dense<M>(P, m, w, m, tau, cnt);
-}
-
-// Dense diagonal block too large for a shared-memory tile: right-looking LU
-// by column panels of width W.  Per panel: factor the tall panel in shared
-// memory (FP64), form U12 = L11^{-1} A12 in shared memory, then update the
-// trailing block A22 -= L21 U12 in place (each element read and written
-// once per panel).
-template <typename T>
-__device__ void getrf_dense_panels(T *A, int b, int ld, double tau,
-                                   unsigned long long *cnt,
-                                   unsigned char *smem, size_t cap) {
-    // Right-looking by 32-wide column panels only while the trailing block
-    // does not fit in shared memory; the rest is factored in shared memory.
-    constexpr int W = 32;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int tx = tid & 15, ty = tid >> 4;
-    int p0 = 0;
-    while (p0 < b && (size_t)(b - p0) * (b - p0) * sizeof(T) > cap) {
-        T *Pn = reinterpret_cast<T *>(smem);      // panel, (b - p0) x W, ld m
-        T *U = Pn + (size_t)b * W;                // U12 as U[k * b + c]
-        const int w = min(W, b - p0), m = b - p0, n2 = b - p0 - w;
-        for (int e = tid; e < m * w; e += nt) {
-            const int r = e % m, c = e / m;
-            Pn[c * m + r] = A[(int64_t)(p0 + c) * ld + p0 + r];
-        }
-        for (int e = tid; e < w * n2; e += nt) {
-            const int k = e % w, c = e / w;
-            U[k * b + c] = A[(int64_t)(p0 + w + c) * ld + p0 + k];
-        }
-        __syncthreads();
-        getrf_panel_tall<T>(Pn, m, w, tau, cnt);
-        for (int c = tid; c < n2; c += nt) {     // U12 = L11^{-1} A12
-            for (int k = 0; k < w; ++k) {
-                const T x = U[k * b + c];
-                if (x == T(0)) continue;
-                for (int r = k + 1; r < w; ++r) U[r * b + c] -= Pn[k * m + r] * x;
-            }
-        }
-        __syncthreads();
-        for (int e = tid; e < m * w; e += nt) {
-            const int r = e % m, c = e / m;
-            A[(int64_t)(p0 + c) * ld + p0 + r] = Pn[c * m + r];
-        }
-        for (int e = tid; e < w * n2; e += nt) {
-            const int k = e % w, c = e / w;
-            A[(int64_t)(p0 + w + c) * ld + p0 + k] = U[k * b + c];
-        }
-        // A22 -= L21 U12 in 64 x 64 tiles, 4 x 4 per thread; the C tile is
-        // loaded before the k-loop so its latency overlaps the products
-        for (int tr = 0; tr < n2; tr += 64)
-            for (int tc = 0; tc < n2; tc += 64) {
-                T acc[4][4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = tr + ty * 4 + i, c = tc + tx * 4 + j;
-                        acc[i][j] = (r < n2 && c < n2)
-                                        ? A[(int64_t)(p0 + w + c) * ld + p0 + w + r]
-                                        : T(0);
-                    }
-                for (int k = 0; k < w; ++k) {
-                    T av[4], bv[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = tr + ty * 4 + i;
-                        av[i] = r < n2 ? Pn[k * m + w + r] : T(0);
-                    }
+        const int nR = s_nR, nC = s_nC;
+        if (nR > 0) {
+            const int g = nR > 16 ? 32 : nR > 8 ? 16 : nR > 4 ? 8 : nR > 2 ? 4 : nR > 1 ? 2 : 1;
+            const int cpw = 32 / g, sub = lane / g, li = lane & (g - 1);
+            for (int ci = warp * cpw + sub; ci < nC; ci += nw * cpw) {
+                const int c = C[ci];
+                const T u = Uv[ci];
+                const bool cs = c >= B.p0;
+                T *colG = B.G + (int64_t)c * B.ld;
+                T *colS = cs ? B.S + (int64_t)(c - B.p0) * B.ls - B.p0 : B.S;
+                for (int r0 = li; r0 < nR; r0 += 4 * g) {
+                    T *q[4];
+                    T x[4], l[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const int c = tc + tx * 4 + j;
-                        bv[j] = c < n2 ? U[k * b + c] : T(0);
+                        const int ri = r0 + j * g;
+                        if (ri < nR) {
+                            const int r = R[ri];
+                            SLU_CHECK(r > k && r < b && c > k && c < b && ri < b && ci < b, 2);
+                            q[j] = (cs && r >= B.p0) ? colS + r : colG + r;
+                            x[j] = *q[j];
+                            l[j] = Lv[ri];
+                        }
                     }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[i][j] -= av[i] * bv[j];
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = tc + tx * 4 + j;
-                    if (c >= n2) continue;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = tr + ty * 4 + i;
-                        if (r < n2) A[(int64_t)(p0 + w + c) * ld + p0 + w + r] = acc[i][j];
-                    }
+                    for (int j = 0; j < 4; ++j)
+                        if (r0 + j * g < nR) *q[j] = x[j] - l[j] * u;
                 }
             }
+        }
+        if (tid == 0) {
+            T &p = B.at(k + 1, k + 1);
+            const T pv = (T)fix_pivot((double)p, tau, cnt);
+            p = pv;
+            s_pinv = T(1) / pv;
+        }
         __syncthreads();
-        p0 += w;
     }
-    if (p0 >= b) return;
-    // the trailing block fits: factor it in shared memory
-    const int mt = b - p0;
-    T *M = reinterpret_cast<T *>(smem);
-    for (int e = tid; e < mt * mt; e += nt) {
-        const int r = e % mt, c = e / mt;
-        M[e] = A[(int64_t)(p0 + c) * ld + p0 + r];
+}
+
+// Dense diagonal block b x b at g (leading dimension ld): stage the largest
+// trailing square that fits next to the step lists, factor, write back.
+template <typename T>
+__device__ void getrf_dense(T *g, int b, int64_t ld, double tau,
+                            unsigned long long *cnt, unsigned char *smem,
+                            size_t cap) {
+    const size_t lb = align16(lu_list_bytes(b, sizeof(T)));
+    int ms = 0;
+    if (cap > lb) {
+        ms = (int)sqrt((double)((cap - lb) / sizeof(T)));
+        while (ms > 0 && (size_t)ms * (ms | 1) * sizeof(T) > cap - lb) --ms;
+        ms = min(ms, b);
+    }
+    const int p0 = b - ms, ls = ms | 1;
+    T *S = reinterpret_cast<T *>(smem + lb);
+    for (int e = threadIdx.x; e < ms * ms; e += blockDim.x) {
+        const int r = e % ms, c = e / ms;
+        S[c * ls + r] = g[(int64_t)(p0 + c) * ld + p0 + r];
     }
     __syncthreads();
-    getrf_dense_core<T>(M, mt, mt, tau, cnt);
-    for (int e = tid; e < mt * mt; e += nt) {
-        const int r = e % mt, c = e / mt;
-        A[(int64_t)(p0 + c) * ld + p0 + r] = M[e];
+    const SplitBlock<T> B{g, ld, S, ls, p0, b};
+    lu_skip<T>(B, b, smem, tau, cnt);
+    for (int e = threadIdx.x; e < ms * ms; e += blockDim.x) {
+        const int r = e % ms, c = e / ms;
+        g[(int64_t)(p0 + c) * ld + p0 + r] = S[c * ls + r];
     }
-    __syncthreads();
+}
+
+// GETRF on dense-stored diagonal blocks, one CTA of kDenseLuThreads per block.
+constexpr int kDenseLuThreads = 512;
+template <typename T>
+__global__ void __launch_bounds__(kDenseLuThreads, 1)
+k_getrf_dense(const int32_t *__restrict__ ids, const BlockDesc *__restrict__ bd,
+              T *__restrict__ val, const double *__restrict__ scal,
+              double tau_rel, unsigned long long *__restrict__ cnt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const BlockDesc d = bd[ids[blockIdx.x]];
+    getrf_dense<T>(val + d.voff, d.rows, d.ld, tau_rel * scal[0], cnt, smem,
+                   kStageSmem);
 }
 
 // GETRF on diagonal blocks.  Columns run in height groups of the block's
@@ -311,22 +352,6 @@ k_getrf(const int32_t *__restrict__ ids, BlockArgs a, T *__restrict__ val,
     const BlockDesc d = a.bd[ids[blockIdx.x]];
     extern __shared__ __align__(16) unsigned char smem[];
     const double tau = tau_rel * scal[0];
-    if (d.dense) {
-        const int b = d.rows;
-        T *g = val + d.voff;
-        if ((size_t)b * b * sizeof(T) <= kStageSmem) {
-            T *M = reinterpret_cast<T *>(smem);
-            for (int e = threadIdx.x; e < b * b; e += blockDim.x) M[e] = g[e];
-            __syncthreads();
-            getrf_dense_core<T>(M, b, b, tau, cnt);
-            for (int e = threadIdx.x; e < b * b; e += blockDim.x) g[e] = M[e];
-        } else if ((size_t)b * 64 * sizeof(T) + 64 <= kStageSmem) {
-            getrf_dense_panels<T>(g, b, d.ld, tau, cnt, smem, kStageSmem);
-        } else {
-            getrf_dense_core<T>(g, b, d.ld, tau, cnt);
-        }
-        return;
-    }
     // Sparse diagonal block, right-looking with the whole CTA: step k fixes
     // the pivot, scales L(k+1:, k), and applies the rank-1 update
     // B(r, j) -= L(r, k) U(k, j) for r, j in the rows of L(:, k) below the
@@ -907,6 +932,7 @@ void free_dev_plan(slu_plan *P) {
     if (D->device >= 0) cudaSetDevice(D->device);
     void *ptrs[] = {D->bd, D->lcolptr, D->lrow, D->dpos, D->sched, D->sgrp,
                     D->getrf, D->gessm, D->tstrf, D->tgt, D->src, D->srcoff,
+                    D->gd, D->gs,
                     D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
                     D->a_ri, D->a_ci, D->row_seg, D->woff, D->inv_task,
@@ -939,6 +965,7 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->lrow, &D->lrow) && upload(P->dpos, &D->dpos) &&
         upload(P->sched, &D->sched) && upload(P->sgrp, &D->sgrp) &&
         upload(P->getrf, &D->getrf) && upload(P->gessm, &D->gessm) &&
+        upload(P->gd, &D->gd) && upload(P->gs, &D->gs) &&
         upload(P->tstrf, &D->tstrf) && upload(P->tgt, &D->tgt) &&
         upload(P->src, &D->src) && upload(P->srcoff, &D->srcoff) &&
         upload(P->gm_task, &D->gm_task) && upload(P->gm_src, &D->gm_src) &&
@@ -981,6 +1008,7 @@ static slu_status set_smem_limits(size_t generic) {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     const int big = (int)std::max(generic, kStageSmem);
     bool ok = cuda_ok(cudaFuncSetAttribute(k_getrf<T>, attr, big), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_getrf_dense<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_inv<T>, attr, (int)kStageSmem), "smem");
     if (ok && generic > 48 * 1024)
@@ -1038,22 +1066,30 @@ static slu_status run_factor(slu_handle *h, const double *values,
     const size_t smem_f = (size_t)kWarps * P->maxb * sizeof(double);
     const size_t smem_a = (size_t)kWarps * P->maxb * sizeof(Acc);
     const size_t smem_big = std::max(kStageSmem, std::max(smem_f, smem_a));
+    bool deferred = false;
     for (int lv = 0; lv < P->nlevels; ++lv) {
-        const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
+        h->cur_level = lv;
+        const int64_t g0 = P->gd_off[lv], g1 = P->gd_off[lv + 1];
         if (g1 > g0) {
-                LaunchScope ls_(h, SLU_KC_GETRF, st);
-                k_getrf<T><<<(int)(g1 - g0), kThreads, smem_big, st>>>(
-                    D->getrf + g0, a, val, h->scal, h->tau_rel, h->cnt);
-            }
+            LaunchScope ls_(h, SLU_KC_GETRF, st, (int)(g1 - g0));
+            k_getrf_dense<T><<<(int)(g1 - g0), kDenseLuThreads, kStageSmem, st>>>(
+                D->gd + g0, D->bd, val, h->scal, h->tau_rel, h->cnt);
+        }
+        const int64_t q0 = P->gs_off[lv], q1 = P->gs_off[lv + 1];
+        if (q1 > q0) {
+            LaunchScope ls_(h, SLU_KC_GETRF, st, -(int)(q1 - q0));
+            k_getrf<T><<<(int)(q1 - q0), kThreads, smem_big, st>>>(
+                D->gs + q0, a, val, h->scal, h->tau_rel, h->cnt);
+        }
         const int64_t i0 = P->inv_off[lv], i1 = P->inv_off[lv + 1];
         if (i1 > i0) {
-            LaunchScope ls_(h, SLU_KC_INV, st);
+            LaunchScope ls_(h, SLU_KC_INV, st, (int)(i1 - i0));
             k_inv<T><<<(int)(i1 - i0), 256, 0, st>>>(
                 D->inv_task + 3 * i0, D->bd, val, static_cast<T *>(h->winv), D->woff);
         }
         const int64_t d0 = P->pd_off[lv], d1 = P->pd_off[lv + 1];
         if (d1 > d0) {
-            LaunchScope ls_(h, SLU_KC_PANEL, st);
+            LaunchScope ls_(h, SLU_KC_PANEL, st, (int)(d1 - d0));
             k_panel_inv<T><<<(int)(d1 - d0), 256,
                              ((size_t)P->inv_maxb * 64 + 16 * 64) * sizeof(T) + 256, st>>>(
                 D->pd_task + 4 * d0, D->bd, val, static_cast<const T *>(h->winv),
@@ -1062,23 +1098,49 @@ static slu_status run_factor(slu_handle *h, const double *values,
         const int64_t e0 = P->pg_goff[lv], e1 = P->pg_goff[lv + 1];
         const int64_t t0 = P->pg_toff[lv], t1 = P->pg_toff[lv + 1];
         if (e1 - e0 + t1 - t0 > 0) {
-            LaunchScope ls_(h, SLU_KC_PANEL, st);
+            LaunchScope ls_(h, SLU_KC_PANEL, st, -(int)(e1 - e0 + t1 - t0));
             k_panel<T, Acc><<<(int)(e1 - e0 + t1 - t0), kThreads, smem_big, st>>>(
                 D->pg_gessm + 2 * e0, (int)(e1 - e0), D->pg_tstrf + 2 * t0, a, val);
         }
-        const int64_t m0 = P->gm_off[lv], m1 = P->gm_off[lv + 1];
-        if (m1 > m0) {
-            LaunchScope ls_(h, SLU_KC_SSSSM, st);
-            k_ssssm_gemm<T><<<(int)(m1 - m0), 256, 0, st>>>(
-                D->gm_task + 5 * m0, D->gm_src, D->bd, val);
+        // Schur updates: the part the next level reads runs on the main
+        // stream; the deferred part runs on the side stream, overlapping
+        // the next level's GETRF and panels, and is joined before the next
+        // level's updates (a target gets its updates in level order)
+        if (deferred) {
+            if (!cuda_ok(cudaStreamWaitEvent(st, h->ev_join, 0), "cudaStreamWaitEvent"))
+                return SLU_ERR_CUDA;
+            deferred = false;
         }
-        const int64_t s0 = P->gg_off[lv], s1 = P->gg_off[lv + 1];
-        if (s1 > s0) {
-            LaunchScope ls_(h, SLU_KC_SSSSM, st);
-            k_ssssm<T, Acc><<<(int)(s1 - s0), kThreads, smem_a, st>>>(
-                D->gg_tgt + s0, D->gg_srcoff + s0, D->gg_src, a, val);
+        const int64_t m0 = P->gm_off[lv], mm = P->gm_mid[lv], m1 = P->gm_off[lv + 1];
+        const int64_t s0 = P->gg_off[lv], sm = P->gg_mid[lv], s1 = P->gg_off[lv + 1];
+        auto updates = [&](int64_t ma, int64_t mb, int64_t sa, int64_t sb,
+                           cudaStream_t ss) {
+            if (mb > ma) {
+                LaunchScope ls_(h, SLU_KC_SSSSM, ss, (int)(mb - ma));
+                k_ssssm_gemm<T><<<(int)(mb - ma), 256, 0, ss>>>(
+                    D->gm_task + 5 * ma, D->gm_src, D->bd, val);
+            }
+            if (sb > sa) {
+                LaunchScope ls_(h, SLU_KC_SSSSM, ss, -(int)(sb - sa));
+                k_ssssm<T, Acc><<<(int)(sb - sa), kThreads, smem_a, ss>>>(
+                    D->gg_tgt + sa, D->gg_srcoff + sa, D->gg_src, a, val);
+            }
+        };
+        updates(m0, mm, s0, sm, st);
+        if (m1 > mm || s1 > sm) {
+            if (!cuda_ok(cudaEventRecord(h->ev_fork, st), "cudaEventRecord") ||
+                !cuda_ok(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "cudaStreamWaitEvent"))
+                return SLU_ERR_CUDA;
+            updates(mm, m1, sm, s1, h->side);
+            if (!cuda_ok(cudaEventRecord(h->ev_join, h->side), "cudaEventRecord"))
+                return SLU_ERR_CUDA;
+            deferred = true;
         }
     }
+    if (deferred &&
+        !cuda_ok(cudaStreamWaitEvent(st, h->ev_join, 0), "cudaStreamWaitEvent"))
+        return SLU_ERR_CUDA;
+    h->cur_level = -1;
     if (!cuda_ok(cudaGetLastError(), "factor launch")) return SLU_ERR_CUDA;
     return SLU_OK;
 }
@@ -1126,6 +1188,9 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
     cudaGetDevice(&cur);
     if (h->device >= 0) cudaSetDevice(h->device);
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red,
                     h->part, h->anorm_seg, h->winv};
@@ -1173,6 +1238,15 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
     if (!ok) {
         slu_handle_destroy(h);
         return SLU_ERR_OUT_OF_MEMORY;
+    }
+    if (!cuda_ok(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking),
+                 "cudaStreamCreate") ||
+        !cuda_ok(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming),
+                 "cudaEventCreate") ||
+        !cuda_ok(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming),
+                 "cudaEventCreate")) {
+        slu_handle_destroy(h);
+        return SLU_ERR_CUDA;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     st = init_factor_attrs(h);
@@ -1254,9 +1328,9 @@ extern "C" slu_status slu_set_profiling(slu_handle *h, int32_t enable) {
 
 extern "C" slu_status slu_handle_stats(slu_handle *h, slu_stats *out) {
     if (!h || !out) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
-    if (!h->recs.empty() &&
-        !cuda_ok(cudaEventSynchronize(h->recs.back().b), "cudaEventSynchronize"))
-        return SLU_ERR_CUDA;
+    for (auto &r : h->recs)      // launches may sit on either stream
+        if (!cuda_ok(cudaEventSynchronize(r.b), "cudaEventSynchronize"))
+            return SLU_ERR_CUDA;
     for (auto &r : h->recs) {
         float t = 0.f;
         if (!cuda_ok(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime"))
@@ -1275,12 +1349,12 @@ extern "C" slu_status slu_handle_stats(slu_handle *h, slu_stats *out) {
 }
 
 extern "C" slu_status slu_handle_trace(slu_handle *h, int64_t cap,
-                                       int32_t *cls, float *ms,
-                                       int64_t *count) {
+                                       int32_t *cls, float *ms, int32_t *level,
+                                       int32_t *ctas, int64_t *count) {
     if (!h || !count) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
-    if (!h->recs.empty() &&
-        !cuda_ok(cudaEventSynchronize(h->recs.back().b), "cudaEventSynchronize"))
-        return SLU_ERR_CUDA;
+    for (auto &r : h->recs)
+        if (!cuda_ok(cudaEventSynchronize(r.b), "cudaEventSynchronize"))
+            return SLU_ERR_CUDA;
     *count = (int64_t)h->recs.size();
     for (int64_t i = 0; i < std::min<int64_t>(cap, *count); ++i) {
         float t = 0.f;
@@ -1289,6 +1363,8 @@ extern "C" slu_status slu_handle_trace(slu_handle *h, int64_t cap,
             return SLU_ERR_CUDA;
         if (cls) cls[i] = h->recs[i].cls;
         if (ms) ms[i] = t;
+        if (level) level[i] = h->recs[i].level;
+        if (ctas) ctas[i] = h->recs[i].ctas;
     }
     return SLU_OK;
 }

@@ -81,6 +81,10 @@ struct slu_plan {
     int32_t nlevels = 0;
     std::vector<int64_t> getrf_off, gessm_off, tstrf_off, tgt_off;
     std::vector<int32_t> getrf;          // diag block ids
+    // execution split of each level's GETRF list: dense-stored diagonal
+    // blocks [gd_off[lv], gd_off[lv+1]) of gd, sparse ones likewise in gs
+    std::vector<int64_t> gd_off, gs_off;
+    std::vector<int32_t> gd, gs;
     std::vector<int32_t> gessm;          // pairs (blk(I,J), blk(I,I))
     std::vector<int32_t> tstrf;          // pairs (blk(J,I), blk(I,I))
     std::vector<int32_t> tgt;            // target block ids
@@ -95,6 +99,10 @@ struct slu_plan {
     std::vector<int32_t> gg_tgt;
     std::vector<int64_t> gg_srcoff;
     std::vector<int32_t> gg_src;
+    // per level, the first gm / gg entry of the deferred part: targets whose
+    // block row and column both lie beyond the next level (they may run
+    // while the next level factors its diagonal blocks and panels)
+    std::vector<int64_t> gm_mid, gg_mid;
     // dense diagonal blocks: explicit inverses of L_II and U_II live in a
     // per-handle workspace at woff[I] (L^-1 then U^-1, b x b column-major
     // each); -1 for sparse diagonal blocks

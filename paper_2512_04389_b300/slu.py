@@ -104,7 +104,7 @@ def _load():
     lib.slu_set_profiling.argtypes = [P, C.c_int32]
     lib.slu_handle_stats.argtypes = [P, C.POINTER(Stats)]
     lib.slu_plan_flops.argtypes = [P, P]
-    lib.slu_handle_trace.argtypes = [P, C.c_int64, P, P, P]
+    lib.slu_handle_trace.argtypes = [P, C.c_int64, P, P, P, P, P]
     lib.slu_set_graph.argtypes = [P, C.c_int32]
     lib.slu_solve_refine_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P,
                                              C.c_int64, P, C.POINTER(SolveInfo)]
@@ -344,14 +344,20 @@ class Factor:
                 "calls": dict(zip(KERNEL_CLASSES, list(st.calls))),
                 "ms": dict(zip(KERNEL_CLASSES, list(st.ms)))}
 
-    def trace(self):
-        """(classes, ms) of every launch profiled so far, in launch order."""
+    def trace(self, detail=False):
+        """(classes, ms) of every launch profiled so far, in launch order;
+        with ``detail`` also (levels, ctas): the factorization level of each
+        launch (-1 outside the level loop) and its grid size (negative for
+        the generic sparse kernels)."""
         n = np.zeros(1, np.int64)
-        _check(lib.slu_handle_trace(self._h, 0, None, None, _np(n)))
+        _check(lib.slu_handle_trace(self._h, 0, None, None, None, None, _np(n)))
         cls = np.empty(n[0], np.int32)
         ms = np.empty(n[0], np.float32)
-        _check(lib.slu_handle_trace(self._h, n[0], _np(cls), _np(ms), _np(n)))
-        return cls, ms
+        lv = np.empty(n[0], np.int32)
+        ct = np.empty(n[0], np.int32)
+        _check(lib.slu_handle_trace(self._h, n[0], _np(cls), _np(ms), _np(lv),
+                                    _np(ct), _np(n)))
+        return (cls, ms, lv, ct) if detail else (cls, ms)
 
     def export_factors(self, stream=None):
         """Factor values (FP64) in the order of ``plan.export()``'s pattern."""
