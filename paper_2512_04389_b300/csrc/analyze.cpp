@@ -574,7 +574,7 @@ static void build_levels_and_tasks(slu_plan &P) {
     // a 64-wide chunk of the largest block must fit the kernels' shared memory
     auto inv_ok = [&](const BlockDesc &d) {
         return d.dense && d.rows <= 384 &&
-               ((int64_t)d.rows * 64 + 16 * 64) * esz <= 220 * 1024;
+               ((int64_t)d.rows * 64 + 16 * 64) * esz + 8 * d.rows + 256 <= 220 * 1024;
     };
     P.woff.assign(p, -1);
     P.wsize = 0;

@@ -658,8 +658,11 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
     // stage the chunk: GESSM columns c0.. (X[k][c] = B(k, c0 + c));
     // TSTRF rows c0.. (X[k][r] = B(c0 + r, k)); flag the 16-deep k-slices
     // of the chunk that hold a nonzero (all-zero slices contribute nothing)
-    int *zflag = reinterpret_cast<int *>(Ts + KT * 64);
-    for (int e = tid; e < (m + KT - 1) / KT; e += 256) zflag[e] = 0;
+    // and, per k, whether row k of the chunk holds one (the warps staging a
+    // row ballot; m * 64 is a whole number of warps)
+    int *zrow = reinterpret_cast<int *>(Ts + KT * 64);
+    int *zflag = zrow + m;
+    for (int e = tid; e < m + (m + KT - 1) / KT; e += 256) zrow[e] = 0;
     __syncthreads();
     for (int e = tid; e < m * 64; e += 256) {
         const int k = e / 64, c = e % 64;
@@ -667,7 +670,10 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
         if (c < nv)
             v = type == 0 ? Bg[(int64_t)(c0 + c) * ld + k] : Bg[(int64_t)k * ld + c0 + c];
         X[e] = v;
-        if (v != T(0)) zflag[k / KT] = 1;
+        if (sizeof(T) == 8 && __ballot_sync(0xffffffffu, v != T(0)) && (tid & 31) == 0) {
+            atomicOr(&zrow[k], 1);
+            atomicOr(&zflag[k / KT], 1);
+        }
     }
     __syncthreads();
     for (int ob = 0; ob < m; ob += 64) {       // output chunk along m
@@ -680,7 +686,7 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
         // TSTRF: out(r, i) = sum_{k <= i} X(r, k) Uinv(k, i), i in [ob, ob+64)
         const int kend = min(m, ob + 64);
         for (int k0 = 0; k0 < kend; k0 += KT) {
-            if (!zflag[k0 / KT]) continue;             // uniform across the CTA
+            if (sizeof(T) == 8 && !zflag[k0 / KT]) continue;  // uniform across the CTA
             for (int e = tid; e < KT * 64; e += 256) {
                 int kk, ii;
                 T v = T(0);
@@ -698,6 +704,7 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
             __syncthreads();
             const int kn = min(KT, m - k0);
             for (int kk = 0; kk < kn; ++kk) {
+                if (sizeof(T) == 8 && !zrow[k0 + kk]) continue;
                 T a[4], bv[4];
                 if (type == 0) {               // rows of out = ob + ty*4+i, cols = tx*4+jx
 #pragma unroll
@@ -838,32 +845,48 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
             rb[q] = (gk < K && gc < d.cols) ? B[(int64_t)gc * U.ld + gk] : T(0);
         }
     };
+    // Per-k liveness of a slice: column k of the A slice and row k of the
+    // B slice both nonzero.  Warp w stages A rows 32 (w % 2) .. + 31 of
+    // columns k = w / 2 + 4 q, and B rows k = lane % 16 of two columns per
+    // q, so one ballot per q gives the warp's share; lane 0 records it and
+    // the consumers OR the eight records after the barrier.
+    __shared__ unsigned sA[2][8], sB[2][8];
+    const int warp = tid >> 5, lane = tid & 31;
     auto store = [&](int buf) {
+        unsigned fa = 0, fb = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = tid + 256 * q;
             As[buf][e / TM][e % TM] = ra[q];
+            fa |= (__ballot_sync(0xffffffffu, ra[q] != T(0)) ? 1u : 0u) << q;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = tid + 256 * q;
             Bs[buf][e % KT][e / KT] = rb[q];
+            const unsigned m = __ballot_sync(0xffffffffu, rb[q] != T(0));
+            fb |= (m | (m >> 16)) & 0xffffu;
         }
+        if (lane == 0) {
+            sA[buf][warp] = fa;
+            sB[buf][warp] = fb;
+        }
+    };
+    auto live_mask = [&](int buf) {
+        unsigned ma = 0, mb = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const unsigned fa = sA[buf][w];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((fa >> q) & 1u) ma |= 1u << (w / 2 + 4 * q);
+            mb |= sB[buf][w];
+        }
+        return ma & mb;
     };
     load(dl, du, 0);
     store(0);
-    // a slice is skipped when its L or U part is entirely zero (dense
-    // storage of a sparse-ish block); the flag rides on the barrier
-    auto nonzero = [&]() {
-        bool a = false, b = false;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            a |= ra[q] != T(0);
-            b |= rb[q] != T(0);
-        }
-        return (int)a | ((int)b << 1);
-    };
-    int live = __syncthreads_or(nonzero() & 1) && __syncthreads_or(nonzero() & 2);
+    __syncthreads();
     int buf = 0;
     for (;;) {
         // advance to the next slice
@@ -875,9 +898,13 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
             if (ns != s) { nl = bd[src[2 * ns]]; nu = bd[src[2 * ns + 1]]; }
             load(nl, nu, nk0);
         }
+        // FP64 is bound by the FP64 pipe, so zero columns are skipped; FP32
+        // is bound by latency, and the mask would only lengthen the chain
+        const unsigned live = sizeof(T) == 8 ? live_mask(buf) : 0xffffu;
         if (live) {
 #pragma unroll
             for (int k = 0; k < KT; ++k) {
+                if (!((live >> k) & 1u)) continue;     // uniform across the CTA
                 T a[4], b[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = As[buf][k][ty * 4 + i];
@@ -891,8 +918,7 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
         }
         if (!more) break;
         store(buf ^ 1);
-        const int nzf = nonzero();
-        live = __syncthreads_or(nzf & 1) && __syncthreads_or(nzf & 2);
+        __syncthreads();
         buf ^= 1;
         s = ns;
         k0 = nk0;
@@ -1091,7 +1117,8 @@ static slu_status run_factor(slu_handle *h, const double *values,
         if (d1 > d0) {
             LaunchScope ls_(h, SLU_KC_PANEL, st, (int)(d1 - d0));
             k_panel_inv<T><<<(int)(d1 - d0), 256,
-                             ((size_t)P->inv_maxb * 64 + 16 * 64) * sizeof(T) + 256, st>>>(
+                             ((size_t)P->inv_maxb * 64 + 16 * 64) * sizeof(T) +
+                                 8 * (size_t)P->inv_maxb + 256, st>>>(
                 D->pd_task + 4 * d0, D->bd, val, static_cast<const T *>(h->winv),
                 D->woff);
         }
