@@ -587,6 +587,17 @@ static void build_levels_and_tasks(slu_plan &P) {
             P.wsize += 2 * (int64_t)d.rows * d.rows;
         }
     }
+    P.dv_off.assign(L + 1, 0);
+    P.dn_off.assign(L + 1, 0);
+    P.dv_pos.clear();
+    P.dn_pos.clear();
+    for (int32_t lv = 0; lv < L; ++lv) {
+        for (int64_t g = P.getrf_off[lv]; g < P.getrf_off[lv + 1]; ++g)
+            (P.woff[P.blocks[P.getrf[g]].I] >= 0 ? P.dv_pos : P.dn_pos)
+                .push_back((int32_t)g);
+        P.dv_off[lv + 1] = (int64_t)P.dv_pos.size();
+        P.dn_off[lv + 1] = (int64_t)P.dn_pos.size();
+    }
     P.inv_off.assign(L + 1, 0);
     P.pd_off.assign(L + 1, 0);
     P.pg_goff.assign(L + 1, 0);

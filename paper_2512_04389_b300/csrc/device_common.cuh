@@ -19,6 +19,7 @@ struct DevPlan {
     int32_t *dpos = nullptr, *sched = nullptr, *sgrp = nullptr;
     int32_t *getrf = nullptr, *gessm = nullptr, *tstrf = nullptr;
     int32_t *gd = nullptr, *gs = nullptr;
+    int32_t *dv_pos = nullptr, *dn_pos = nullptr;
     int32_t *tgt = nullptr, *src = nullptr;
     int64_t *srcoff = nullptr;
     int32_t *gm_task = nullptr, *gm_src = nullptr, *gg_tgt = nullptr,

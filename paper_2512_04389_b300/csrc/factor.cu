@@ -958,7 +958,7 @@ void free_dev_plan(slu_plan *P) {
     if (D->device >= 0) cudaSetDevice(D->device);
     void *ptrs[] = {D->bd, D->lcolptr, D->lrow, D->dpos, D->sched, D->sgrp,
                     D->getrf, D->gessm, D->tstrf, D->tgt, D->src, D->srcoff,
-                    D->gd, D->gs,
+                    D->gd, D->gs, D->dv_pos, D->dn_pos,
                     D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
                     D->a_ri, D->a_ci, D->row_seg, D->woff, D->inv_task,
@@ -992,6 +992,7 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->sched, &D->sched) && upload(P->sgrp, &D->sgrp) &&
         upload(P->getrf, &D->getrf) && upload(P->gessm, &D->gessm) &&
         upload(P->gd, &D->gd) && upload(P->gs, &D->gs) &&
+        upload(P->dv_pos, &D->dv_pos) && upload(P->dn_pos, &D->dn_pos) &&
         upload(P->tstrf, &D->tstrf) && upload(P->tgt, &D->tgt) &&
         upload(P->src, &D->src) && upload(P->srcoff, &D->srcoff) &&
         upload(P->gm_task, &D->gm_task) && upload(P->gm_src, &D->gm_src) &&

@@ -85,6 +85,10 @@ struct slu_plan {
     // blocks [gd_off[lv], gd_off[lv+1]) of gd, sparse ones likewise in gs
     std::vector<int64_t> gd_off, gs_off;
     std::vector<int32_t> gd, gs;
+    // solve split of each level's diagonal blocks, as positions in the
+    // GETRF list: with explicit inverses (dv) and without (dn)
+    std::vector<int64_t> dv_off, dn_off;
+    std::vector<int32_t> dv_pos, dn_pos;
     std::vector<int32_t> gessm;          // pairs (blk(I,J), blk(I,I))
     std::vector<int32_t> tstrf;          // pairs (blk(J,I), blk(I,I))
     std::vector<int32_t> tgt;            // target block ids

@@ -27,6 +27,7 @@ __device__ __forceinline__ C warp_sum(C v) {
 }
 
 constexpr int RC = 4;   // right-hand sides processed together
+constexpr int kDenseRows = 64;   // rows of a dense source per pull CTA
 enum Sweep { FWD = 0, BWD = 1, FWD_T = 2, BWD_T = 3 };
 
 // Pull, scatter form (L y = b and U x = y): one CTA per source block B of
@@ -47,32 +48,37 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
     C *pw = reinterpret_cast<C *>(smem);
     constexpr int VW = 16 / sizeof(T);                  // rows per vector load
     if (db.dense && db.ld % VW == 0) {
-        if (blockIdx.y > 0) return;                      // row chunks: sparse only
-        // dense GEMV: thread (row group, column group) accumulates VW rows
-        // over its columns with 16-byte loads, 8 in flight; the 4 column
-        // groups are reduced in a fixed order.
+        // dense GEMV over the row chunk [y * kDenseRows, +kDenseRows): thread
+        // (row group, column slice) accumulates VW rows over its columns
+        // with 16-byte loads, 8 in flight; the column slices are reduced in
+        // a fixed order.  Several CTAs share a block, so one large source
+        // no longer runs at the bandwidth of a single SM.
         using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-        C *xs = pw;                                 // n x RC
-        C *red = pw + (size_t)db.cols * RC;         // 4 x m x RC
+        constexpr int NRG = kDenseRows / VW;            // row groups per chunk
+        constexpr int NCG = kThreads / NRG;             // column slices
+        const int rbase = blockIdx.y * kDenseRows;
+        if (rbase >= m) return;
+        C *xs = pw;                                     // cols x RC
+        C *red = pw + (size_t)db.cols * RC;             // NCG x kDenseRows x RC
         for (int t = threadIdx.x; t < db.cols * RC; t += kThreads) {
             const int k = t / RC, c = t % RC;
             xs[t] = c < nc ? X[(int64_t)c * ldx + db.c0 + k] : 0.0;
         }
         __syncthreads();
-        const int nrg = (m + VW - 1) / VW;
-        const int cg = threadIdx.x / 64, rg0 = threadIdx.x % 64;
-        for (int rg = rg0; rg < nrg; rg += 64) {
-            C acc[VW][RC];
+        const int rg = threadIdx.x % NRG, cg = threadIdx.x / NRG;
+        const int r0 = rbase + rg * VW;
+        C acc[VW][RC];
 #pragma unroll
-            for (int i = 0; i < VW; ++i)
+        for (int i = 0; i < VW; ++i)
 #pragma unroll
-                for (int c = 0; c < RC; ++c) acc[i][c] = 0.0;
-            const T *base = val + db.voff + (int64_t)rg * VW;
-            for (int kb = cg; kb < db.cols; kb += 4 * 8) {
+            for (int c = 0; c < RC; ++c) acc[i][c] = 0.0;
+        if (r0 < m) {
+            const T *base = val + db.voff + r0;
+            for (int kb = cg; kb < db.cols; kb += NCG * 8) {
                 V v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int k = kb + 4 * u;
+                    const int k = kb + NCG * u;
                     if (k < db.cols)
                         v[u] = *reinterpret_cast<const V *>(base + (int64_t)k * db.ld);
                     else
@@ -80,7 +86,7 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int k = min(kb + 4 * u, db.cols - 1);
+                    const int k = min(kb + NCG * u, db.cols - 1);
                     const T *vv = reinterpret_cast<const T *>(&v[u]);
 #pragma unroll
                     for (int i = 0; i < VW; ++i)
@@ -88,18 +94,21 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
                         for (int c = 0; c < RC; ++c) acc[i][c] += (C)vv[i] * xs[k * RC + c];
                 }
             }
-#pragma unroll
-            for (int i = 0; i < VW; ++i) {
-                const int r = rg * VW + i;
-                if (r < m)
-#pragma unroll
-                    for (int c = 0; c < RC; ++c) red[((size_t)cg * RC + c) * m + r] = acc[i][c];
-            }
         }
+#pragma unroll
+        for (int i = 0; i < VW; ++i)
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                red[((size_t)cg * RC + c) * kDenseRows + rg * VW + i] = acc[i][c];
         __syncthreads();
         C *out = part + poff[blockIdx.x] * RC;
-        for (int t = threadIdx.x; t < m * RC; t += kThreads)
-            out[t] = (red[t] + red[m * RC + t]) + (red[2 * m * RC + t] + red[3 * m * RC + t]);
+        const int mr = min(kDenseRows, m - rbase);
+        for (int t = threadIdx.x; t < mr * RC; t += kThreads) {
+            const int r = t % mr, c = t / mr;
+            C sum = 0.0;
+            for (int g = 0; g < NCG; ++g) sum += red[((size_t)g * RC + c) * kDenseRows + r];
+            out[c * m + rbase + r] = sum;                // index c * m + row
+        }
         return;
     }
     // rows [rc0, rc0 + mc) of the partial (one chunk per blockIdx.y)
@@ -345,6 +354,139 @@ __device__ bool panels_fit(const BlockView<T> &F, int m, int W, size_t cap) {
     return (size_t)(2 * maxp) * sizeof(T) <= cap;
 }
 
+// Diagonal part of a sweep for a dense diagonal block with explicit
+// inverses: one cluster of kInvCluster CTAs per block.  CTA q of the
+// cluster owns rows [q h, q h + h), h = ceil(m / kInvCluster):
+//   1. y(rows) = x(rows) minus the level's partials (fixed source order);
+//   2. cluster barrier; every CTA copies the whole y from its peers'
+//      shared memory (DSMEM); cluster barrier (no CTA leaves, or reuses
+//      its buffer, while a peer may still read it);
+//   3. out(rows) = M(rows, :) y with M = L^{-1}, U^{-1} (or the transposes
+//      for the transposed sweeps), written to x.
+constexpr int kInvCluster = 8;
+template <typename T, int MODE>
+__global__ void __cluster_dims__(kInvCluster, 1, 1) __launch_bounds__(kThreads)
+k_diag_inv(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
+           const int64_t *__restrict__ pair0, const int64_t *__restrict__ boff,
+           const int64_t *__restrict__ poff, const BlockDesc *__restrict__ bd,
+           double *__restrict__ X, int64_t ldx, int nc,
+           const double *__restrict__ part_d, const T *__restrict__ winv,
+           const int64_t *__restrict__ woff) {
+    using C = T;
+    const C *part = reinterpret_cast<const C *>(part_d);
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned q;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(q));
+    const int g = pos[blockIdx.x / kInvCluster];
+    const BlockDesc dd = bd[ids[g]];
+    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int h = (m + kInvCluster - 1) / kInvCluster;
+    const int ra = min(m, (int)q * h), rb = min(m, ra + h), mh = rb - ra;
+    C *yo = reinterpret_cast<C *>(smem);                 // own rows, h x RC
+    C *y = yo + (size_t)h * RC;                          // all rows, m x RC
+    C *red = y + (size_t)m * RC;                         // kWarps x h x RC
+    const int64_t p0 = pair0[g];
+    const int np = (int)(boff[dd.I + 1] - boff[dd.I]);
+    // 1. own rows: x minus the partials (partials are c * m + row)
+    for (int t = threadIdx.x; t < mh * RC; t += kThreads) {
+        const int r = t % mh, c = t / mh;
+        C acc = 0.0;
+        for (int s = 0; s < np; ++s) acc += part[poff[p0 + s] * RC + (int64_t)c * m + ra + r];
+        const C xv = c < nc ? (C)X[(int64_t)c * ldx + dd.r0 + ra + r] : C(0);
+        yo[r * RC + c] = xv - acc;
+    }
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    // 2. gather y from the cluster
+    {
+        const uint32_t local = (uint32_t)__cvta_generic_to_shared(yo);
+        for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+            const int r = t / RC, c = t % RC;
+            const unsigned owner = (unsigned)(r / h);
+            const uint32_t off = (uint32_t)(((r - (int)owner * h) * RC + c) * sizeof(C));
+            uint32_t remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                         : "=r"(remote) : "r"(local + off), "r"(owner));
+            C v;
+            if (sizeof(C) == 8) {
+                double dv;
+                asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(dv) : "r"(remote));
+                v = (C)dv;
+            } else {
+                float fv;
+                asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(fv) : "r"(remote));
+                v = (C)fv;
+            }
+            y[t] = v;
+        }
+    }
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    if (mh <= 0) return;
+    const bool useL = (MODE == FWD || MODE == BWD_T);
+    const T *M = winv + woff[dd.I] + (useL ? 0 : (int64_t)m * m);
+    // 3. own rows of M y
+    if (MODE == FWD || MODE == BWD) {
+        // M column-major: lanes over rows (coalesced), warps over k; the k
+        // range is the chunk's (the stored inverses hold exact zeros in the
+        // other triangle), so a warp's lanes read one column together
+        const int k0 = MODE == FWD ? 0 : ra, k1 = MODE == FWD ? rb : m;
+        for (int rr = lane; rr < ((mh + 31) & ~31); rr += 32) {
+            const int r = ra + rr;
+            C acc[RC] = {0.0, 0.0, 0.0, 0.0};
+            if (rr < mh) {
+                for (int kb = k0 + warp; kb < k1; kb += kWarps * 4) {
+                    C mv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = kb + kWarps * u;
+                        mv[u] = k < k1 ? (C)M[(int64_t)k * m + r] : C(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = min(kb + kWarps * u, m - 1);
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < RC; ++c) red[((size_t)warp * h + rr) * RC + c] = acc[c];
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < mh * RC; t += kThreads) {
+            const int rr = t / RC, c = t % RC;
+            C sum = 0.0;
+            for (int w = 0; w < kWarps; ++w) sum += red[((size_t)w * h + rr) * RC + c];
+            if (c < nc) X[(int64_t)c * ldx + dd.r0 + ra + rr] = sum;
+        }
+    } else {
+        // transposed: out(r) = sum_k M(k, r) y(k), row r of M^T contiguous
+        for (int rr = warp; rr < mh; rr += kWarps) {
+            const int r = ra + rr;
+            C acc[RC] = {0.0, 0.0, 0.0, 0.0};
+            const int k0 = MODE == FWD_T ? 0 : r, k1 = MODE == FWD_T ? r + 1 : m;
+            for (int kb = k0; kb < k1; kb += 128) {
+                C mv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = kb + u * 32 + lane;
+                    mv[u] = k < k1 ? (C)M[(int64_t)r * m + k] : C(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = min(kb + u * 32 + lane, m - 1);
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < RC; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane < nc) X[(int64_t)lane * ldx + dd.r0 + r] = acc[lane];
+        }
+    }
+}
+
 // Diagonal part of a sweep: one CTA per diagonal block of the level.
 // y = x(block rows) minus the level's partials (fixed order), then the
 // chain over the block's columns by warp 0.  The block's index data is
@@ -353,7 +495,8 @@ __device__ bool panels_fit(const BlockView<T> &F, int m, int W, size_t cap) {
 // panel while warp 0 works on the current one.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads)
-k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
+k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
+       const int64_t *__restrict__ pair0,
        const int64_t *__restrict__ boff, const int64_t *__restrict__ poff,
        BlockArgs a, const T *__restrict__ val, double *__restrict__ X,
        int64_t ldx, int nc, const double *__restrict__ part_d,
@@ -362,11 +505,12 @@ k_diag(const int32_t *__restrict__ ids, const int64_t *__restrict__ pair0,
     const C *part = reinterpret_cast<const C *>(part_d);
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int W = 16;
-    const BlockDesc dd = a.bd[ids[blockIdx.x]];
+    const int gpos = pos[blockIdx.x];
+    const BlockDesc dd = a.bd[ids[gpos]];
     const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     C *y = reinterpret_cast<C *>(smem);
     const size_t ybytes = align16((size_t)m * RC * sizeof(C));
-    const int64_t p0 = pair0[blockIdx.x];
+    const int64_t p0 = pair0[gpos];
     const int np = (int)(boff[dd.I + 1] - boff[dd.I]);
     // partial offsets of this block's sources, staged once (the partials
     // themselves are then independent loads)
@@ -686,11 +830,14 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
     // into chunks when a whole block's partials do not fit
     const int rpc = (int)std::min<int64_t>(
         P->maxb, kStageSmem / ((size_t)kWarps * RC * sizeof(double)));
-    const int nch = (P->maxb + rpc - 1) / rpc;
-    // dense sources: x (cols x RC) + 4 partials (rows x RC)
+    const int nch = std::max((P->maxb + rpc - 1) / rpc,
+                             (P->maxb + kDenseRows - 1) / kDenseRows);
+    // dense sources: x (cols x RC) + one row chunk of partials per column
+    // slice (kThreads / (kDenseRows / VW) slices, VW = 16 / sizeof(T))
+    constexpr size_t kSlices = kThreads / (kDenseRows / (16 / sizeof(T)));
     const size_t pull_smem = std::max<size_t>(
         (size_t)kWarps * rpc * RC * sizeof(double),
-        (size_t)5 * P->maxb * RC * sizeof(double));
+        ((size_t)P->maxb + kSlices * kDenseRows) * RC * sizeof(T));
     if (pull_smem > kStageSmem)
         return fail(SLU_ERR_NOT_SUPPORTED, "block too large for the solve");
     const int64_t *boff = MODE == FWD ? D->lrow_off : MODE == BWD ? D->urow_off
@@ -714,13 +861,25 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
                         D->sp_pairs[MODE] + 2 * q0, D->sp_poff[MODE] + q0, a, val,
                         Xc, ldx, nc, h->part);
             }
-            const int64_t g0 = P->getrf_off[lv], g1 = P->getrf_off[lv + 1];
-            if (g1 > g0) {
-                LaunchScope ls_(h, SLU_KC_DIAG, st);
-                k_diag<T, MODE><<<(int)(g1 - g0), kThreads, kStageSmem, st>>>(
-                    D->getrf + g0, D->sd_pair0[MODE] + g0, boff, D->sp_poff[MODE], a,
-                    val, Xc, ldx, nc, h->part, static_cast<const T *>(h->winv),
-                    D->woff);
+            // diagonal blocks with explicit inverses: a cluster each; the
+            // rest: one CTA each
+            const int64_t v0 = P->dv_off[lv], v1 = P->dv_off[lv + 1];
+            if (v1 > v0) {
+                LaunchScope ls_(h, SLU_KC_DIAG, st, (int)(v1 - v0));
+                const int hh = (P->inv_maxb + kInvCluster - 1) / kInvCluster;
+                const size_t sm = (size_t)(hh + P->inv_maxb + kWarps * hh) * RC * sizeof(T);
+                k_diag_inv<T, MODE><<<(int)(v1 - v0) * kInvCluster, kThreads, sm, st>>>(
+                    D->dv_pos + v0, D->getrf, D->sd_pair0[MODE], boff,
+                    D->sp_poff[MODE], D->bd, Xc, ldx, nc, h->part,
+                    static_cast<const T *>(h->winv), D->woff);
+            }
+            const int64_t n0 = P->dn_off[lv], n1 = P->dn_off[lv + 1];
+            if (n1 > n0) {
+                LaunchScope ls_(h, SLU_KC_DIAG, st, -(int)(n1 - n0));
+                k_diag<T, MODE><<<(int)(n1 - n0), kThreads, kStageSmem, st>>>(
+                    D->dn_pos + n0, D->getrf, D->sd_pair0[MODE], boff,
+                    D->sp_poff[MODE], a, val, Xc, ldx, nc, h->part,
+                    static_cast<const T *>(h->winv), D->woff);
             }
         }
     }
