@@ -3,7 +3,8 @@
 
 Workload: 3-D 7-point nonsymmetric convection-diffusion operator on a 40^3
 grid (n = 64,000) in nested-dissection order, 4 right-hand sides, FP64,
-irregular blocking (Algorithm 3, S = 1000, step 2, max_num 3), seeded
+irregular blocking (Algorithm 3, S = 1000, step 2; the block-size bound
+max_num and the sparse/dense threshold picked by the autotuner), seeded
 synthetic data.  One step = value scatter + numerical factorization
 (GETRF / GESSM / TSTRF / SSSSM per level) + forward/backward solve of the 4
 right-hand sides.  The factors (42.6 M values, 340 MB) exceed the 126 MB L2,
@@ -290,8 +291,8 @@ def main():
                                     device="cuda")
     vals_d, rhs_d = dev(s.values), dev(s.rhs)
     # sparse/dense switch picked by the autotuner (cached per pattern)
-    thr64, tun64 = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d, precision="fp64")
-    plan = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=thr64)
+    best64, tun64 = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d, precision="fp64")
+    plan = S.Plan(s.n, s.colptr, s.rowidx, **best64)
     fl = step_flops(plan, s.nrhs)
     F = S.Factor(plan, vals_d)
 
@@ -328,7 +329,7 @@ def main():
                       "blocks_1d": plan.info["nblocks_1d"],
                       "levels": plan.info["nlevels"],
                       "analyze_ms": plan.info["analyze_ms"],
-                      "dense_threshold": thr64, "tuning_ms": tun64,
+                      "tuned": best64, "tuning_ms": tun64,
                       "backward_error": sinfo["backward_error"],
                       "l2": "no flush: factors (340 MB) exceed L2",
                       "parallelism": f"replicas x{world}"},
@@ -366,10 +367,9 @@ def main():
     if not args.no_extras:
         extras = {}
         # FP32 factors + FP64 refinement
-        thr32, tun32 = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
-                            precision="fp32")
-        p32 = S.Plan(s.n, s.colptr, s.rowidx, precision="fp32",
-                     dense_threshold=thr32)
+        best32, tun32 = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
+                             precision="fp32")
+        p32 = S.Plan(s.n, s.colptr, s.rowidx, precision="fp32", **best32)
         F32 = S.Factor(p32, vals_d)
 
         def step32():
@@ -377,26 +377,39 @@ def main():
             F32.solve(rhs_d)
         ms32 = timed(torch, step32, args.steps, 2)
         _, i32 = F32.solve(rhs_d, info=True)
-        extras["fp32_ir"] = {"ms_per_step": ms32, "dense_threshold": thr32,
+        extras["fp32_ir"] = {"ms_per_step": ms32, "tuned": best32,
                              "gflops": fl / (ms32 * 1e-3) / 1e9,
                              "backward_error": i32["backward_error"],
                              "ir_iterations": i32["iterations"]}
         del F32
         # regular blocking, same code
-        thrr, _ = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
-                       precision="fp64", blocking="regular", regular_block=128)
+        bestr, _ = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
+                        precision="fp64", blocking="regular", regular_block=128)
         preg = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular",
-                      regular_block=128, dense_threshold=thrr)
+                      regular_block=128, **bestr)
         Freg = S.Factor(preg, vals_d)
 
         def stepreg():
             Freg.refactor(vals_d)
             Freg.solve(rhs_d)
         msr = timed(torch, stepreg, args.steps, 2)
-        extras["regular128_fp64"] = {"ms_per_step": msr, "dense_threshold": thrr,
+        extras["regular128_fp64"] = {"ms_per_step": msr, "tuned": bestr,
                                      "gflops": fl / (msr * 1e-3) / 1e9,
                                      "levels": preg.info["nlevels"]}
         del Freg
+        bestr32, _ = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
+                          precision="fp32", blocking="regular", regular_block=128)
+        preg32 = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular",
+                        regular_block=128, precision="fp32", **bestr32)
+        Freg32 = S.Factor(preg32, vals_d)
+
+        def stepreg32():
+            Freg32.refactor(vals_d)
+            Freg32.solve(rhs_d)
+        msr32 = timed(torch, stepreg32, args.steps, 2)
+        extras["regular128_fp32_ir"] = {"ms_per_step": msr32, "tuned": bestr32,
+                                        "gflops": fl / (msr32 * 1e-3) / 1e9}
+        del Freg32
         extras["batch_256_grid5"] = batch_leg(torch, S, dev, args)
         out["extras"] = extras
         # end to end through the public API with host buffers

@@ -206,6 +206,14 @@ struct slu_handle {
     // second stream for the deferred Schur updates, fork / join events
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // solve graphs: the level sweeps of one solve, recorded once per
+    // (right-hand side count, transposed) on a private stream over the
+    // handle's vector buffer and replayed on the caller's stream
+    struct SolveGraph { int nrhs; bool tr; cudaGraphExec_t exec; int64_t launches; };
+    std::vector<SolveGraph> sgraphs;
+    double *xbuf = nullptr;
+    int64_t xbuf_cols = 0;
+    cudaStream_t cap = nullptr;
     // graph mode
     bool use_graph = false;
     cudaGraphExec_t graph_exec = nullptr;

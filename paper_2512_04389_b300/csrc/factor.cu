@@ -1216,6 +1216,9 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
     cudaGetDevice(&cur);
     if (h->device >= 0) cudaSetDevice(h->device);
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+    for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.exec);
+    if (h->xbuf) cudaFree(h->xbuf);
+    if (h->cap) cudaStreamDestroy(h->cap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->side) cudaStreamDestroy(h->side);

@@ -927,6 +927,64 @@ static slu_status solve_inplace(const slu_handle *h, double *X, int64_t ldx,
     return s;
 }
 
+static slu_status copy_cols(double *dst, int64_t ldd, const double *src,
+                            int64_t lds, int64_t n, int nrhs, cudaStream_t st);
+
+// The sweeps of one solve as a replayed CUDA graph: X is copied into the
+// handle's buffer, the graph recorded for (nrhs, transposed) runs on `st`,
+// and the result is copied back.  Profiling (per-launch events) and an
+// enclosing capture take the direct path.
+static slu_status solve_graphed(slu_handle *h, double *X, int64_t ldx, int nrhs,
+                                bool tr, cudaStream_t st) {
+    if (h->profiling || h->capturing) return solve_inplace(h, X, ldx, nrhs, tr, st);
+    const int64_t n = h->plan->n;
+    if (nrhs > h->xbuf_cols) {
+        for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.exec);
+        h->sgraphs.clear();
+        if (h->xbuf) cudaFree(h->xbuf);
+        h->xbuf = nullptr;
+        h->xbuf_cols = 0;
+        if (!cuda_ok(cudaMalloc(&h->xbuf, (size_t)n * nrhs * sizeof(double)),
+                     "cudaMalloc(solve buffer)"))
+            return SLU_ERR_OUT_OF_MEMORY;
+        h->xbuf_cols = nrhs;
+    }
+    const slu_handle::SolveGraph *g = nullptr;
+    for (const auto &e : h->sgraphs)
+        if (e.nrhs == nrhs && e.tr == tr) g = &e;
+    if (!g) {
+        if (!h->cap && !cuda_ok(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking),
+                                "cudaStreamCreate"))
+            return SLU_ERR_CUDA;
+        if (!cuda_ok(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal),
+                     "cudaStreamBeginCapture"))
+            return SLU_ERR_CUDA;
+        const int64_t l0 = h->launches;
+        h->capturing = true;
+        slu_status s = solve_inplace(h, h->xbuf, n, nrhs, tr, h->cap);
+        h->capturing = false;
+        const int64_t nl = h->launches - l0;
+        h->launches = l0;
+        cudaGraph_t graph = nullptr;
+        const bool ended = cuda_ok(cudaStreamEndCapture(h->cap, &graph), "cudaStreamEndCapture");
+        if (s != SLU_OK || !ended) {
+            if (graph) cudaGraphDestroy(graph);
+            return s != SLU_OK ? s : SLU_ERR_CUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        const bool ok = cuda_ok(cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate");
+        cudaGraphDestroy(graph);
+        if (!ok) return SLU_ERR_CUDA;
+        h->sgraphs.push_back({nrhs, tr, exec, nl});
+        g = &h->sgraphs.back();
+    }
+    slu_status s = copy_cols(h->xbuf, n, X, ldx, n, nrhs, st);
+    if (s != SLU_OK) return s;
+    if (!cuda_ok(cudaGraphLaunch(g->exec, st), "cudaGraphLaunch")) return SLU_ERR_CUDA;
+    h->launches += g->launches;
+    return copy_cols(X, ldx, h->xbuf, n, n, nrhs, st);
+}
+
 static slu_status ensure_work(slu_handle *h, int64_t elems) {
     if (h->work_elems < elems) {
         if (h->work) cudaFree(h->work);
@@ -1027,7 +1085,7 @@ extern "C" slu_status slu_solve(const slu_handle *ch, const double *B,
     slu_status s;
     if (maxit == 0 && !info) {
         s = copy_cols(X, ldx, B, ldb, n, nrhs, st);
-        if (s == SLU_OK) s = solve_inplace(h, X, ldx, nrhs, false, st);
+        if (s == SLU_OK) s = solve_graphed(h, X, ldx, nrhs, false, st);
         return s;
     }
     // B must survive for the residual: keep a copy when X aliases it.
@@ -1045,7 +1103,7 @@ extern "C" slu_status slu_solve(const slu_handle *ch, const double *B,
         ldbk = n;
     }
     s = copy_cols(X, ldx, Bk, ldbk, n, nrhs, st);
-    if (s == SLU_OK) s = solve_inplace(h, X, ldx, nrhs, false, st);
+    if (s == SLU_OK) s = solve_graphed(h, X, ldx, nrhs, false, st);
     if (s != SLU_OK) return s;
     double be = 0.0;
     int it = 0;
@@ -1053,7 +1111,7 @@ extern "C" slu_status slu_solve(const slu_handle *ch, const double *B,
         s = backward_error(h, Bk, ldbk, X, ldx, nrhs, R, st, &be);
         if (s != SLU_OK) return s;
         if (be <= P->opts.refine_tol || it >= maxit) break;
-        s = solve_inplace(h, R, n, nrhs, false, st);
+        s = solve_graphed(h, R, n, nrhs, false, st);
         if (s != SLU_OK) return s;
         {
             LaunchScope ls_(h, SLU_KC_RESID, st);
@@ -1100,7 +1158,7 @@ extern "C" slu_status slu_solve_transpose(const slu_handle *h, const double *G,
     if (nrhs == 0 || n == 0) return SLU_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     slu_status s = copy_cols(Lam, ldl, G, ldg, n, nrhs, st);
-    if (s == SLU_OK) s = solve_inplace(h, Lam, ldl, nrhs, true, st);
+    if (s == SLU_OK) s = solve_graphed(const_cast<slu_handle *>(h), Lam, ldl, nrhs, true, st);
     return s;
 }
 

@@ -1,13 +1,16 @@
-"""Autotuner for the per-block sparse/dense switch.
+"""Autotuner for the block shapes and the per-block sparse/dense switch.
 
 The paper runs each block with a sparse kernel or a dense routine chosen by
-the block's density (Section 1); the density threshold that pays off
-depends on the precision and the GPU.  ``tune`` factors and solves the given
-system once per candidate threshold and keeps the fastest, timing with CUDA
-events on the current stream.  Results are cached in a JSON file (path from
-the ``SLU_TUNE_CACHE`` environment variable, default
-``~/.cache/slu_b300_tune.json``) under a key made of the pattern's hash, the
-precision and the blocking options, so a pattern is tuned once.
+the block's density (Section 1), and Algorithm 3 sizes the irregular blocks
+from sampling parameters (the number of sample steps merged into one block
+is bounded by ``max_num``).  Which density threshold and which block-size
+bound pay off depends on the precision, the pattern and the GPU, so
+``tune`` factors and solves the given system once per candidate and keeps
+the fastest, timing with CUDA events on the current stream.  Results are
+cached in a JSON file (path from the ``SLU_TUNE_CACHE`` environment
+variable, default ``~/.cache/slu_b300_tune.json``) under a key made of the
+pattern's hash, the precision and the other plan options, so a pattern is
+tuned once.
 """
 from __future__ import annotations
 
@@ -19,7 +22,17 @@ import numpy as np
 
 from . import slu as S
 
-CANDIDATES = (0.0, 0.05, 0.3, 0.6)
+THRESHOLDS = (0.0, 0.3)
+MAX_NUM = (3, 2, 1)
+
+
+def candidates(blocking="irregular"):
+    """Plan options tried by default: thresholds x Algorithm 3 block-size
+    bounds for irregular blocking, thresholds alone for regular blocking."""
+    if blocking == "regular":
+        return [{"dense_threshold": t} for t in THRESHOLDS]
+    return [{"dense_threshold": t, "max_num": m} for m in MAX_NUM
+            for t in THRESHOLDS]
 
 
 def _key(n, colptr, rowidx, opts):
@@ -53,20 +66,26 @@ def _save(cache):
     os.replace(tmp, p)
 
 
-def tune(n, colptr, rowidx, values, rhs, candidates=CANDIDATES, reps=2,
-         use_cache=True, **opts):
-    """Return ``(best_threshold, timings)``; ``values`` and ``rhs`` are CUDA
-    float64 tensors, ``opts`` the other plan options (precision, blocking,
-    ...).  Timings map each candidate to its factor + solve milliseconds."""
+def tune(n, colptr, rowidx, values, rhs, cands=None, reps=2, use_cache=True,
+         **opts):
+    """Return ``(best, timings)``: ``best`` is the dict of tuned plan options
+    (``dense_threshold`` and, for irregular blocking, ``max_num``) to pass to
+    ``Plan`` together with ``opts``; ``timings`` maps each candidate (as
+    JSON) to its factor + solve milliseconds.  ``values`` and ``rhs`` are
+    CUDA float64 tensors, ``opts`` the fixed plan options (precision,
+    blocking, ...)."""
     import torch
-    key = _key(n, colptr, rowidx, opts)
+    if cands is None:
+        cands = candidates(opts.get("blocking", "irregular"))
+    key = _key(n, colptr, rowidx, dict(opts, cands=cands))
     cache = _load() if use_cache else {}
     if key in cache:
         e = cache[key]
-        return e["threshold"], e["timings"]
+        return e["best"], e["timings"]
     timings = {}
-    for thr in candidates:
-        P = S.Plan(n, colptr, rowidx, dense_threshold=thr, **opts)
+    best, best_ms = None, float("inf")
+    for c in cands:
+        P = S.Plan(n, colptr, rowidx, **opts, **c)
         F = S.Factor(P, values)
         F.solve(rhs)
         torch.cuda.synchronize()
@@ -78,10 +97,12 @@ def tune(n, colptr, rowidx, values, rhs, candidates=CANDIDATES, reps=2,
             F.solve(rhs)
         e1.record()
         torch.cuda.synchronize()
-        timings[str(thr)] = e0.elapsed_time(e1) / reps
+        ms = e0.elapsed_time(e1) / reps
+        timings[json.dumps(c, sort_keys=True)] = ms
+        if ms < best_ms:
+            best, best_ms = dict(c), ms
         del F, P
-    best = float(min(timings, key=timings.get))
     if use_cache:
-        cache[key] = {"threshold": best, "timings": timings}
+        cache[key] = {"best": best, "timings": timings}
         _save(cache)
     return best, timings

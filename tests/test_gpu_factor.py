@@ -220,3 +220,37 @@ def test_full_size_grid7cd_40_properties():
                 acc += lik * u[k]
         worst = max(worst, abs(acc - s.values[q]) / scale)
     assert worst <= 1e-12
+
+
+def test_solve_graph_replay_matches_direct_launches():
+    """Solves replay a recorded graph of the level sweeps; with profiling on
+    the same sweeps run as direct launches.  Both give identical results,
+    for several right-hand-side counts and the transposed solve."""
+    s = workloads.grid7_cd(14, nrhs=6)
+    P, F = gpu_factor(s, b_min=16, dense_threshold=0.0)
+    B = _dev(s.rhs)
+    for k in (1, 4, 6):
+        x1 = F.solve(B[:, :k].contiguous())
+        x2 = F.solve(B[:, :k].contiguous())          # replay
+        F.set_profiling(True)
+        x3 = F.solve(B[:, :k].contiguous())          # direct launches
+        F.set_profiling(False)
+        assert torch.equal(x1, x2) and torch.equal(x1, x3)
+    t1 = F.solve_transpose(B)
+    F.set_profiling(True)
+    t2 = F.solve_transpose(B)
+    F.set_profiling(False)
+    assert torch.equal(t1, t2)
+
+
+def test_autotuner_picks_a_candidate_and_caches(tmp_path, monkeypatch):
+    from paper_2512_04389_b300 import tune as T
+    monkeypatch.setenv("SLU_TUNE_CACHE", str(tmp_path / "tune.json"))
+    s = workloads.grid5(32)
+    best, timings = T.tune(s.n, s.colptr, s.rowidx, _dev(s.values),
+                           _dev(s.rhs), precision="fp32")
+    assert best in T.candidates("irregular")
+    assert len(timings) == len(T.candidates("irregular"))
+    again, t2 = T.tune(s.n, s.colptr, s.rowidx, _dev(s.values), _dev(s.rhs),
+                       precision="fp32")
+    assert again == best and t2 == timings          # served from the cache
