@@ -374,6 +374,52 @@ static slu_status build_blocks(slu_plan &P) {
         }
         P.sgrp.push_back(m);
     }
+    // non-empty columns of the sparse blocks
+    P.ne_off.assign(nb + 1, 0);
+    P.ne_col.clear();
+    for (int64_t b = 0; b < nb; ++b) {
+        const BlockDesc &d = P.blocks[b];
+        if (!d.dense)
+            for (int32_t jj = 0; jj < d.cols; ++jj)
+                if (P.lcolptr[d.coff + jj + 1] > P.lcolptr[d.coff + jj])
+                    P.ne_col.push_back((uint16_t)jj);
+        P.ne_off[b + 1] = (int64_t)P.ne_col.size();
+    }
+    // rows of the strict lower part of the sparse diagonal blocks
+    P.lr_ptr.assign(ndiag_slots + p + 1, 0);
+    P.lr_col.clear();
+    P.lr_pos.clear();
+    {
+        std::vector<int32_t> cnt;
+        std::vector<int64_t> at;
+        for (int32_t I = 0; I < p; ++I) {
+            const BlockDesc &d = P.blocks[P.diagblk[I]];
+            const int64_t base = d.doff + I;
+            const int32_t m = d.rows;
+            cnt.assign(m, 0);
+            if (!d.dense)
+                for (int32_t jj = 0; jj < m; ++jj)
+                    for (int32_t t = P.lcolptr[d.coff + jj]; t < P.lcolptr[d.coff + jj + 1]; ++t)
+                        if (P.lrow[d.roff + t] > jj) cnt[P.lrow[d.roff + t]]++;
+            const int32_t start = (int32_t)P.lr_col.size();
+            at.assign(m + 1, 0);
+            for (int32_t r = 0; r < m; ++r) at[r + 1] = at[r] + cnt[r];
+            for (int32_t r = 0; r <= m; ++r) P.lr_ptr[base + r] = start + (int32_t)at[r];
+            P.lr_col.resize(start + at[m]);
+            P.lr_pos.resize(start + at[m]);
+            if (!d.dense)
+                for (int32_t jj = 0; jj < m; ++jj)
+                    for (int32_t t = P.lcolptr[d.coff + jj]; t < P.lcolptr[d.coff + jj + 1]; ++t) {
+                        const int32_t r = P.lrow[d.roff + t];
+                        if (r <= jj) continue;
+                        const int64_t q = start + at[r]++;
+                        P.lr_col[q] = (uint16_t)jj;
+                        P.lr_pos[q] = t;
+                    }
+        }
+        if (P.lr_col.size() > (size_t)INT32_MAX)
+            return fail(SLU_ERR_NOT_SUPPORTED, "sparse diagonal blocks too large");
+    }
     return SLU_OK;
 }
 
@@ -606,6 +652,8 @@ static void build_levels_and_tasks(slu_plan &P) {
     P.pd_task.clear();
     P.pg_gessm.clear();
     P.pg_tstrf.clear();
+    P.ps_off.assign(L + 1, 0);
+    P.ps_task.clear();
     for (int32_t lv = 0; lv < L; ++lv) {
         for (int64_t g = P.getrf_off[lv]; g < P.getrf_off[lv + 1]; ++g) {
             const BlockDesc &d = P.blocks[P.getrf[g]];
@@ -618,11 +666,14 @@ static void build_levels_and_tasks(slu_plan &P) {
         }
         for (int64_t e = P.gessm_off[lv]; e < P.gessm_off[lv + 1]; ++e) {
             const int32_t tb = P.gessm[2 * e], db = P.gessm[2 * e + 1];
-            if (P.blocks[tb].dense && inv_ok(P.blocks[db])) {
+            if (inv_ok(P.blocks[db])) {
                 for (int32_t c0 = 0; c0 < P.blocks[tb].cols; c0 += kChunk) {
                     const int32_t t4[4] = {0, tb, db, c0};
                     P.pd_task.insert(P.pd_task.end(), t4, t4 + 4);
                 }
+            } else if (!P.blocks[db].dense) {
+                const int32_t t3[3] = {0, tb, db};
+                P.ps_task.insert(P.ps_task.end(), t3, t3 + 3);
             } else {
                 P.pg_gessm.push_back(tb);
                 P.pg_gessm.push_back(db);
@@ -630,11 +681,14 @@ static void build_levels_and_tasks(slu_plan &P) {
         }
         for (int64_t e = P.tstrf_off[lv]; e < P.tstrf_off[lv + 1]; ++e) {
             const int32_t tb = P.tstrf[2 * e], db = P.tstrf[2 * e + 1];
-            if (P.blocks[tb].dense && inv_ok(P.blocks[db])) {
+            if (inv_ok(P.blocks[db])) {
                 for (int32_t r0 = 0; r0 < P.blocks[tb].rows; r0 += kChunk) {
                     const int32_t t4[4] = {1, tb, db, r0};
                     P.pd_task.insert(P.pd_task.end(), t4, t4 + 4);
                 }
+            } else if (!P.blocks[db].dense) {
+                const int32_t t3[3] = {1, tb, db};
+                P.ps_task.insert(P.ps_task.end(), t3, t3 + 3);
             } else {
                 P.pg_tstrf.push_back(tb);
                 P.pg_tstrf.push_back(db);
@@ -644,6 +698,7 @@ static void build_levels_and_tasks(slu_plan &P) {
         P.pd_off[lv + 1] = (int64_t)P.pd_task.size() / 4;
         P.pg_goff[lv + 1] = (int64_t)P.pg_gessm.size() / 2;
         P.pg_toff[lv + 1] = (int64_t)P.pg_tstrf.size() / 2;
+        P.ps_off[lv + 1] = (int64_t)P.ps_task.size() / 3;
     }
     // solve pull pairs per sweep and level
     P.part_elems = 0;

@@ -326,6 +326,66 @@ __device__ void getrf_dense(T *g, int b, int64_t ld, double tau,
     }
 }
 
+// Sparse-stored diagonal block with few height groups: left-looking by
+// columns, the columns of one height in parallel (one warp each), a CTA
+// barrier between heights.  Column jj: x = B(:, jj) in a per-warp dense
+// vector; for each m < jj with U(m, jj) stored, ascending, x(m) is final and
+// x(rows of L(:, m)) -= L(:, m) x(m) (column m has a smaller height, so it
+// is finished); then U(:, jj) = x(<= jj), pivot x(jj) fixed in FP64 and
+// L(:, jj) = x(> jj) / pivot.
+template <typename T>
+__device__ void getrf_sparse_groups(const BlockDesc &d, const BlockArgs &a,
+                                    T *val, unsigned char *smem, double tau,
+                                    unsigned long long *cnt) {
+    const int m = d.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    T *x = reinterpret_cast<T *>(smem) + (size_t)warp * m;
+    const size_t xbytes = align16((size_t)nw * m * sizeof(T));
+    bool staged;
+    size_t used;
+    const BlockView<T> B = stage_block<T>(d, a, val, smem + xbytes,
+                                          kStageSmem - xbytes, true, &staged, &used);
+    for (int i = lane; i < m; i += 32) x[i] = T(0);
+    __syncwarp();
+    const int32_t *sched = a.sched + d.doff;
+    const int32_t *grp = a.sgrp + d.goff;
+    for (int g = 0; g < d.ngroups; ++g) {
+        for (int t = grp[g] + warp; t < grp[g + 1]; t += nw) {
+            const int jj = sched[t];
+            int oj, cj;
+            const uint16_t *rj;
+            B.col(jj, oj, cj, rj);
+            const int dj = B.dp[jj];
+            for (int e = lane; e < cj; e += 32) x[rj[e]] = B.v[oj + e];
+            __syncwarp();
+            for (int e = 0; e < dj; ++e) {
+                const int mm = rj[e];
+                const T xm = x[mm];
+                if (xm == T(0)) continue;
+                int om, cm;
+                const uint16_t *rm;
+                B.col(mm, om, cm, rm);
+                const int dm = B.dp[mm];
+                for (int q = dm + 1 + lane; q < cm; q += 32) x[rm[q]] -= B.v[om + q] * xm;
+                __syncwarp();
+            }
+            T piv = T(0);
+            if (lane == 0) piv = (T)fix_pivot((double)x[jj], tau, cnt);
+            piv = __shfl_sync(0xffffffffu, piv, 0);
+            const T rcp = T(1) / piv;
+            for (int e = lane; e < cj; e += 32) {
+                const int r = rj[e];
+                const T v = r < jj ? x[r] : r == jj ? piv : x[r] * rcp;
+                B.v[oj + e] = v;
+                x[r] = T(0);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    if (staged) unstage_block<T>(d, a, B, val);
+}
+
 // GETRF on dense-stored diagonal blocks, one CTA of kDenseLuThreads per block.
 constexpr int kDenseLuThreads = 512;
 template <typename T>
@@ -352,6 +412,10 @@ k_getrf(const int32_t *__restrict__ ids, BlockArgs a, T *__restrict__ val,
     const BlockDesc d = a.bd[ids[blockIdx.x]];
     extern __shared__ __align__(16) unsigned char smem[];
     const double tau = tau_rel * scal[0];
+    if (4 * d.ngroups <= d.rows) {
+        getrf_sparse_groups<T>(d, a, val, smem, tau, cnt);
+        return;
+    }
     // Sparse diagonal block, right-looking with the whole CTA: step k fixes
     // the pivot, scales L(k+1:, k), and applies the rank-1 update
     // B(r, j) -= L(r, k) U(k, j) for r, j in the rows of L(:, k) below the
@@ -461,6 +525,138 @@ __device__ void panel_dense(bool gessm, const BlockDesc &d,
             else       B[(int64_t)i * ldb + v0 + t] = v;
         }
         __syncthreads();
+    }
+}
+
+// GESSM / TSTRF against a sparse-stored diagonal block I, using the height
+// groups of its column DAG (columns of one height do not depend on each
+// other; there are far fewer heights than columns in a sparse block):
+//   TSTRF  L_JI = B_JI U_II^{-1}, left-looking per column k:
+//          L(:, k) = (B(:, k) - sum_{m < k, U(m,k) != 0} L(:, m) U(m, k)) / U(k, k);
+//          one warp per column of the current height group, a CTA barrier
+//          between groups (the columns m read are of smaller height);
+//   GESSM  U_IJ = L_II^{-1} B_IJ, columns independent: one warp per column
+//          j, x = B(:, j) in shared memory, then group by group each lane
+//          takes rows r of the group: x(r) -= sum_{m < r} L(r, m) x(m)
+//          over row r of L (kept by rows in lr_*), all m of smaller height.
+// Fixed summation orders: deterministic.  The panel block may be dense or
+// sparse (then a per-warp dense accumulator maps its pattern).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_panel_grp(const int32_t *__restrict__ task, BlockArgs a,
+            const int32_t *__restrict__ lr_ptr, const uint16_t *__restrict__ lr_col,
+            const int32_t *__restrict__ lr_pos, T *__restrict__ val) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int32_t *tk = task + 3 * (int64_t)blockIdx.x;
+    const int type = tk[0];
+    const BlockDesc d = a.bd[tk[1]];
+    const BlockDesc dd = a.bd[tk[2]];
+    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per-warp vectors at the front, the diagonal block staged behind them
+    const int vlen = type == 0 ? m : d.rows;
+    T *vec = reinterpret_cast<T *>(smem) + (size_t)warp * vlen;
+    const size_t vbytes = align16((size_t)kWarps * vlen * sizeof(T));
+    bool staged;
+    size_t used;
+    const BlockView<T> F = stage_block<T>(dd, a, val, smem + vbytes,
+                                          kStageSmem - vbytes, true, &staged, &used);
+    const int32_t *sched = a.sched + dd.doff;
+    const int32_t *grp = a.sgrp + dd.goff;
+    const int ng = dd.ngroups;
+    if (type == 1) {                                   // TSTRF
+        if (!d.dense)
+            for (int i = lane; i < d.rows; i += 32) vec[i] = T(0);
+        __syncwarp();
+        for (int g = 0; g < ng; ++g) {
+            for (int t = grp[g] + warp; t < grp[g + 1]; t += kWarps) {
+                const int k = sched[t];
+                int fo, fc;
+                const uint16_t *fr;
+                F.col(k, fo, fc, fr);
+                const int dp = F.dp[k];
+                const T rcp = T(1) / F.v[fo + dp];
+                if (d.dense) {
+                    T *ck = val + d.voff + (int64_t)k * d.ld;
+                    for (int r = lane; r < d.rows; r += 32) {
+                        T acc = ck[r];
+                        for (int e = 0; e < dp; ++e) {
+                            const T u = F.v[fo + e];
+                            if (u != T(0))
+                                acc -= val[d.voff + (int64_t)rowat(fr, e) * d.ld + r] * u;
+                        }
+                        ck[r] = acc * rcp;
+                    }
+                } else {
+                    int64_t kb;
+                    int kc;
+                    const uint16_t *kr;
+                    colview(d, k, a, kb, kc, kr);
+                    for (int e = lane; e < kc; e += 32) vec[kr[e]] = val[kb + e];
+                    __syncwarp();
+                    for (int e = 0; e < dp; ++e) {
+                        const T u = F.v[fo + e];
+                        if (u == T(0)) continue;
+                        int64_t mb;
+                        int mc;
+                        const uint16_t *mr;
+                        colview(d, rowat(fr, e), a, mb, mc, mr);
+                        for (int q = lane; q < mc; q += 32) vec[mr[q]] -= val[mb + q] * u;
+                        __syncwarp();
+                    }
+                    for (int e = lane; e < kc; e += 32) {
+                        val[kb + e] = vec[kr[e]] * rcp;
+                        vec[kr[e]] = T(0);
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
+    } else {                                           // GESSM
+        const int32_t *rp = lr_ptr + dd.doff + dd.I;
+        if (!d.dense)
+            for (int i = lane; i < m; i += 32) vec[i] = T(0);
+        __syncwarp();
+        for (int j = warp; j < d.cols; j += kWarps) {
+            int64_t jb;
+            int jc;
+            const uint16_t *jr;
+            colview(d, j, a, jb, jc, jr);
+            if (jc == 0) continue;                     // empty column: stays empty
+            for (int e = lane; e < jc; e += 32) vec[rowat(jr, e)] = val[jb + e];
+            __syncwarp();
+            if (!d.dense && jc <= 2 * ng) {
+                // short column: push form over its own rows, ascending (its
+                // pattern is closed under the solve)
+                for (int e = 0; e < jc; ++e) {
+                    const int k = jr[e];
+                    const T xk = vec[k];
+                    if (xk == T(0)) continue;
+                    int fo, fc;
+                    const uint16_t *fr;
+                    F.col(k, fo, fc, fr);
+                    for (int q = F.dp[k] + 1 + lane; q < fc; q += 32)
+                        vec[fr[q]] -= F.v[fo + q] * xk;
+                    __syncwarp();
+                }
+            } else {
+                for (int g = 0; g < ng; ++g) {
+                    for (int t = grp[g] + lane; t < grp[g + 1]; t += 32) {
+                        const int r = sched[t];
+                        T x = vec[r];
+                        for (int q = rp[r]; q < rp[r + 1]; ++q) x -= F.v[lr_pos[q]] * vec[lr_col[q]];
+                        vec[r] = x;
+                    }
+                    __syncwarp();
+                }
+            }
+            for (int e = lane; e < jc; e += 32) {
+                const int r = rowat(jr, e);
+                val[jb + e] = vec[r];
+                if (!d.dense) vec[r] = T(0);
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -640,7 +836,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
             T *__restrict__ val, const T *__restrict__ winv,
-            const int64_t *__restrict__ woff) {
+            const int64_t *__restrict__ woff, BlockArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int KT = 16;
     const int32_t *tk = task + 4 * (int64_t)blockIdx.x;
@@ -662,17 +858,46 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
     // row ballot; m * 64 is a whole number of warps)
     int *zrow = reinterpret_cast<int *>(Ts + KT * 64);
     int *zflag = zrow + m;
-    for (int e = tid; e < m + (m + KT - 1) / KT; e += 256) zrow[e] = 0;
-    __syncthreads();
-    for (int e = tid; e < m * 64; e += 256) {
-        const int k = e / 64, c = e % 64;
-        T v = T(0);
-        if (c < nv)
-            v = type == 0 ? Bg[(int64_t)(c0 + c) * ld + k] : Bg[(int64_t)k * ld + c0 + c];
-        X[e] = v;
-        if (sizeof(T) == 8 && __ballot_sync(0xffffffffu, v != T(0)) && (tid & 31) == 0) {
-            atomicOr(&zrow[k], 1);
-            atomicOr(&zflag[k / KT], 1);
+    const int lane = tid & 31, warp = tid >> 5;
+    if (d.dense) {
+        for (int e = tid; e < m + (m + KT - 1) / KT; e += 256) zrow[e] = 0;
+        __syncthreads();
+        for (int e = tid; e < m * 64; e += 256) {
+            const int k = e / 64, c = e % 64;
+            T v = T(0);
+            if (c < nv)
+                v = type == 0 ? Bg[(int64_t)(c0 + c) * ld + k] : Bg[(int64_t)k * ld + c0 + c];
+            X[e] = v;
+            if (sizeof(T) == 8 && __ballot_sync(0xffffffffu, v != T(0)) && lane == 0) {
+                atomicOr(&zrow[k], 1);
+                atomicOr(&zflag[k / KT], 1);
+            }
+        }
+    } else {
+        // sparse panel block: scatter its pattern into the zeroed chunk (no
+        // zero-row skipping: every row is flagged)
+        for (int e = tid; e < m + (m + KT - 1) / KT; e += 256) zrow[e] = 1;
+        for (int e = tid; e < m * 64; e += 256) X[e] = T(0);
+        __syncthreads();
+        if (type == 0) {                 // columns c0 + c of B_IJ, rows k
+            for (int c = warp; c < nv; c += 8) {
+                int64_t vb;
+                int cn;
+                const uint16_t *rw;
+                colview(d, c0 + c, a, vb, cn, rw);
+                for (int e = lane; e < cn; e += 32) X[rw[e] * 64 + c] = val[vb + e];
+            }
+        } else {                         // rows c0 .. c0 + nv of B_JI, columns k
+            for (int k = warp; k < m; k += 8) {
+                int64_t vb;
+                int cn;
+                const uint16_t *rw;
+                colview(d, k, a, vb, cn, rw);
+                for (int e = lane; e < cn; e += 32) {
+                    const int r = rw[e] - c0;
+                    if (r >= 0 && r < nv) X[k * 64 + r] = val[vb + e];
+                }
+            }
         }
     }
     __syncthreads();
@@ -728,12 +953,23 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int jx = 0; jx < 4; ++jx) {
-                if (type == 0) {
-                    const int gi = ob + ty * 4 + i, c = tx * 4 + jx;
-                    if (gi < m && c < nv) Bg[(int64_t)(c0 + c) * ld + gi] = acc[i][jx];
+                // (row, column) of the panel block; a sparse block keeps only
+                // its pattern (the result is zero elsewhere)
+                int br, bc;
+                if (type == 0) { br = ob + ty * 4 + i; bc = c0 + tx * 4 + jx; }
+                else           { br = c0 + ty * 4 + i; bc = ob + tx * 4 + jx; }
+                const bool in = type == 0 ? (br < m && bc - c0 < nv)
+                                          : (br - c0 < nv && bc < m);
+                if (!in) continue;
+                if (d.dense) {
+                    Bg[(int64_t)bc * ld + br] = acc[i][jx];
                 } else {
-                    const int r = ty * 4 + i, gi = ob + tx * 4 + jx;
-                    if (r < nv && gi < m) Bg[(int64_t)gi * ld + c0 + r] = acc[i][jx];
+                    int64_t vb;
+                    int cn;
+                    const uint16_t *rw;
+                    colview(d, bc, a, vb, cn, rw);
+                    const int q = find_row(rw, cn, br);
+                    if (q >= 0) val[vb + q] = acc[i][jx];
                 }
             }
     }
@@ -746,45 +982,84 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(kThreads)
 k_ssssm(const int32_t *__restrict__ tgt, const int64_t *__restrict__ srcoff,
-        const int32_t *__restrict__ src, BlockArgs a, T *__restrict__ val) {
+        const int32_t *__restrict__ src, BlockArgs a, T *__restrict__ val,
+        const int64_t *__restrict__ ne_off, const uint16_t *__restrict__ ne_col,
+        size_t stage_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const BlockDesc d = a.bd[tgt[blockIdx.x]];
     const int64_t s0 = srcoff[blockIdx.x], s1 = srcoff[blockIdx.x + 1];
     Acc *acc = reinterpret_cast<Acc *>(smem) + warp * d.rows;
+    // a target with a single sparse L source stages that block once (its
+    // columns are then read from shared memory by every warp)
+    BlockView<T> LV{};
+    bool lview = false;
+    if (s1 - s0 == 1 && !a.bd[src[2 * s0]].dense) {
+        const size_t ab = align16((size_t)kWarps * d.rows * sizeof(Acc));
+        bool st;
+        size_t used;
+        LV = stage_block<T>(a.bd[src[2 * s0]], a, val, smem + ab,
+                            stage_cap > ab ? stage_cap - ab : 0, false, &st, &used);
+        lview = true;
+    }
     for (int t = lane; t < d.rows; t += 32) acc[t] = Acc(0);
     __syncwarp();
     for (int jj = warp; jj < d.cols; jj += kWarps) {
+        bool any = false;                 // warp-uniform: column received an update
         for (int64_t s = s0; s < s1; ++s) {
-            const BlockDesc dl = a.bd[src[2 * s]];
+            const int32_t lb = src[2 * s];
+            const BlockDesc dl = a.bd[lb];
             const BlockDesc du = a.bd[src[2 * s + 1]];
             int64_t vu;
             int cu;
             const uint16_t *ru;
             colview(du, jj, a, vu, cu, ru);
-            for (int c0 = 0; c0 < cu; c0 += 32) {
+            // walk U(:, jj)'s stored rows, or, when L_KI is sparse with fewer
+            // non-empty columns, those columns (U looked up); both ascending
+            const int64_t ne0 = dl.dense ? 0 : ne_off[lb];
+            const int nne = dl.dense ? 0 : (int)(ne_off[lb + 1] - ne0);
+            const bool by_l = !dl.dense && nne < cu;
+            const int nit = by_l ? nne : cu;
+            for (int c0 = 0; c0 < nit; c0 += 32) {
                 const int t = c0 + lane;
                 int il = 0;
                 Acc ul = Acc(0);
-                if (t < cu) {
-                    il = rowat(ru, t);
-                    ul = (Acc)val[vu + t];
+                if (t < nit) {
+                    if (by_l) {
+                        il = ne_col[ne0 + t];
+                        const int q = find_row(ru, cu, il);
+                        ul = q >= 0 ? (Acc)val[vu + q] : Acc(0);
+                    } else {
+                        il = rowat(ru, t);
+                        ul = (Acc)val[vu + t];
+                    }
                 }
-                const int nn = min(32, cu - c0);
+                const int nn = min(32, nit - c0);
                 for (int k = 0; k < nn; ++k) {
                     const Acc u = __shfl_sync(~0u, ul, k);
                     const int i = __shfl_sync(~0u, il, k);
                     if (u == Acc(0)) continue;
-                    int64_t vl;
-                    int cl;
-                    const uint16_t *rl;
-                    colview(dl, i, a, vl, cl, rl);
-                    for (int e = lane; e < cl; e += 32)
-                        acc[rowat(rl, e)] += (Acc)val[vl + e] * u;
+                    if (lview) {
+                        int ol, cl;
+                        const uint16_t *rl;
+                        LV.col(i, ol, cl, rl);
+                        any |= cl > 0;
+                        for (int e = lane; e < cl; e += 32)
+                            acc[rowat(rl, e)] += (Acc)LV.v[ol + e] * u;
+                    } else {
+                        int64_t vl;
+                        int cl;
+                        const uint16_t *rl;
+                        colview(dl, i, a, vl, cl, rl);
+                        any |= cl > 0;
+                        for (int e = lane; e < cl; e += 32)
+                            acc[rowat(rl, e)] += (Acc)val[vl + e] * u;
+                    }
                     __syncwarp();
                 }
             }
         }
+        if (!any) continue;               // nothing accumulated: column unchanged
         int64_t vb;
         int cn;
         const uint16_t *rows;
@@ -958,7 +1233,8 @@ void free_dev_plan(slu_plan *P) {
     if (D->device >= 0) cudaSetDevice(D->device);
     void *ptrs[] = {D->bd, D->lcolptr, D->lrow, D->dpos, D->sched, D->sgrp,
                     D->getrf, D->gessm, D->tstrf, D->tgt, D->src, D->srcoff,
-                    D->gd, D->gs, D->dv_pos, D->dn_pos,
+                    D->gd, D->gs, D->dv_pos, D->dn_pos, D->lr_ptr, D->lr_pos,
+                    D->ps_task, D->lr_col, D->ne_col, D->ne_off,
                     D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
                     D->a_ri, D->a_ci, D->row_seg, D->woff, D->inv_task,
@@ -993,6 +1269,9 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->getrf, &D->getrf) && upload(P->gessm, &D->gessm) &&
         upload(P->gd, &D->gd) && upload(P->gs, &D->gs) &&
         upload(P->dv_pos, &D->dv_pos) && upload(P->dn_pos, &D->dn_pos) &&
+        upload(P->lr_ptr, &D->lr_ptr) && upload(P->lr_pos, &D->lr_pos) &&
+        upload(P->lr_col, &D->lr_col) && upload(P->ps_task, &D->ps_task) &&
+        upload(P->ne_col, &D->ne_col) && upload(P->ne_off, &D->ne_off) &&
         upload(P->tstrf, &D->tstrf) && upload(P->tgt, &D->tgt) &&
         upload(P->src, &D->src) && upload(P->srcoff, &D->srcoff) &&
         upload(P->gm_task, &D->gm_task) && upload(P->gm_src, &D->gm_src) &&
@@ -1030,6 +1309,13 @@ static int grid_for(int64_t n, int threads) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 148 * 32));
 }
 
+// Dynamic shared memory of the generic SSSSM kernel: per-warp accumulators
+// of the largest block and up to 64 KB for a staged sparse source.
+static size_t ssssm_smem(const slu_plan *P, size_t acc_size) {
+    return std::min(kStageSmem,
+                    align16((size_t)kWarps * P->maxb * acc_size) + 64 * 1024);
+}
+
 template <typename T, typename Acc>
 static slu_status set_smem_limits(size_t generic) {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -1037,9 +1323,10 @@ static slu_status set_smem_limits(size_t generic) {
     bool ok = cuda_ok(cudaFuncSetAttribute(k_getrf<T>, attr, big), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_getrf_dense<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem") &&
-              cuda_ok(cudaFuncSetAttribute(k_panel_inv<T>, attr, (int)kStageSmem), "smem");
-    if (ok && generic > 48 * 1024)
-        ok = cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, (int)generic), "smem");
+              cuda_ok(cudaFuncSetAttribute(k_panel_inv<T>, attr, (int)kStageSmem), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_panel_grp<T>, attr, (int)kStageSmem), "smem");
+    if (ok)
+        ok = cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, (int)kStageSmem), "smem");
     return ok ? SLU_OK : SLU_ERR_CUDA;
 }
 
@@ -1093,6 +1380,8 @@ static slu_status run_factor(slu_handle *h, const double *values,
     const size_t smem_f = (size_t)kWarps * P->maxb * sizeof(double);
     const size_t smem_a = (size_t)kWarps * P->maxb * sizeof(Acc);
     const size_t smem_big = std::max(kStageSmem, std::max(smem_f, smem_a));
+    // generic SSSSM: per-warp accumulators plus room to stage a sparse source
+    const size_t smem_g = ssssm_smem(P, sizeof(Acc));
     bool deferred = false;
     for (int lv = 0; lv < P->nlevels; ++lv) {
         h->cur_level = lv;
@@ -1121,7 +1410,7 @@ static slu_status run_factor(slu_handle *h, const double *values,
                              ((size_t)P->inv_maxb * 64 + 16 * 64) * sizeof(T) +
                                  8 * (size_t)P->inv_maxb + 256, st>>>(
                 D->pd_task + 4 * d0, D->bd, val, static_cast<const T *>(h->winv),
-                D->woff);
+                D->woff, a);
         }
         const int64_t e0 = P->pg_goff[lv], e1 = P->pg_goff[lv + 1];
         const int64_t t0 = P->pg_toff[lv], t1 = P->pg_toff[lv + 1];
@@ -1139,6 +1428,12 @@ static slu_status run_factor(slu_handle *h, const double *values,
                 return SLU_ERR_CUDA;
             deferred = false;
         }
+        const int64_t u0 = P->ps_off[lv], u1 = P->ps_off[lv + 1];
+        if (u1 > u0) {
+            LaunchScope ls_(h, SLU_KC_PANEL, st, -(int)(u1 - u0));
+            k_panel_grp<T><<<(int)(u1 - u0), kThreads, kStageSmem, st>>>(
+                D->ps_task + 3 * u0, a, D->lr_ptr, D->lr_col, D->lr_pos, val);
+        }
         const int64_t m0 = P->gm_off[lv], mm = P->gm_mid[lv], m1 = P->gm_off[lv + 1];
         const int64_t s0 = P->gg_off[lv], sm = P->gg_mid[lv], s1 = P->gg_off[lv + 1];
         auto updates = [&](int64_t ma, int64_t mb, int64_t sa, int64_t sb,
@@ -1150,8 +1445,9 @@ static slu_status run_factor(slu_handle *h, const double *values,
             }
             if (sb > sa) {
                 LaunchScope ls_(h, SLU_KC_SSSSM, ss, -(int)(sb - sa));
-                k_ssssm<T, Acc><<<(int)(sb - sa), kThreads, smem_a, ss>>>(
-                    D->gg_tgt + sa, D->gg_srcoff + sa, D->gg_src, a, val);
+                k_ssssm<T, Acc><<<(int)(sb - sa), kThreads, smem_g, ss>>>(
+                    D->gg_tgt + sa, D->gg_srcoff + sa, D->gg_src, a, val,
+                    D->ne_off, D->ne_col, smem_g);
             }
         };
         updates(m0, mm, s0, sm, st);

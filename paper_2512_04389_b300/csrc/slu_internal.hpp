@@ -74,6 +74,15 @@ struct slu_plan {
     std::vector<int32_t> lcolptr;
     std::vector<uint16_t> lrow;
     std::vector<int32_t> dpos, sched, sgrp;
+    // strict lower part of each sparse diagonal block by rows: row r of
+    // diagonal block I spans [lr_ptr[doff + I + r], lr_ptr[doff + I + r + 1])
+    // of lr_col (local column, ascending) and lr_pos (slot in the block's
+    // values); dense diagonal blocks have empty rows
+    std::vector<int32_t> lr_ptr, lr_pos;
+    std::vector<uint16_t> lr_col;
+    // non-empty columns of each sparse block b: ne_col[ne_off[b] .. ne_off[b+1])
+    std::vector<int64_t> ne_off;
+    std::vector<uint16_t> ne_col;
     int64_t storage = 0;
     int64_t ndense = 0;
     // levels and tasks (block ids; the export calls translate to (I, J))
@@ -107,6 +116,10 @@ struct slu_plan {
     // block row and column both lie beyond the next level (they may run
     // while the next level factors its diagonal blocks and panels)
     std::vector<int64_t> gm_mid, gg_mid;
+    // GESSM / TSTRF tasks whose diagonal block is stored sparse, per level:
+    // 3 ints (0 GESSM / 1 TSTRF, panel block, diagonal block)
+    std::vector<int64_t> ps_off;
+    std::vector<int32_t> ps_task;
     // dense diagonal blocks: explicit inverses of L_II and U_II live in a
     // per-handle workspace at woff[I] (L^-1 then U^-1, b x b column-major
     // each); -1 for sparse diagonal blocks

@@ -87,7 +87,9 @@ FP32_CASES = CASES[:1] + CASES[5:8] + [
     ("circuit_20k", lambda: workloads.circuit_bbd(n=20_000, border=400),
      dict(dense_threshold=0.0)),
     ("grid7cd_14 all dense", lambda: workloads.grid7_cd(14, nrhs=4),
-     dict(b_min=16, dense_threshold=0.0))]
+     dict(b_min=16, dense_threshold=0.0)),
+    ("circuit_20k dense border", lambda: workloads.circuit_bbd(n=20_000, border=400),
+     dict(dense_threshold=0.1))]
 
 
 @pytest.mark.parametrize("name,mk,opts", FP32_CASES,
@@ -171,6 +173,8 @@ def test_empty_rhs_and_vector_rhs():
         n=20_000, border=400), 0.6),
     ("circuit_20k all dense", lambda: workloads.circuit_bbd(
         n=20_000, border=400), 0.0),
+    ("circuit_20k dense border, sparse body", lambda: workloads.circuit_bbd(
+        n=20_000, border=400), 0.1),
 ])
 def test_full_size_parity(name, mk, thr):
     """Configurations the oracle factors in seconds: element-wise."""
