@@ -13,8 +13,12 @@ so no flush is needed between steps.
 Metric: GFLOP/s of factor + solve, with the algorithmic flop count
 sum_k (l_k + 2 l_k u_k) of the filled pattern plus 2 nnz(L+U) per
 right-hand side for the solve; higher is better.  Extra legs in the same
-run: FP32 factors + FP64 refinement to backward error <= 1e-14, and the same
-code with regular 128-row blocking.
+run: FP32 factors + FP64 refinement to backward error <= 1e-14, the same
+code with regular 128-row blocking (FP64 and FP32), 256 batched grids
+replayed from a CUDA graph against a per-matrix loop, the 48 x 48 grid
+(irregular against regular 64), autograd forward + backward on the 32^3
+parameterised operator, and the n = 200,000 bordered circuit matrix (FP32 +
+refinement against FP64; --no-circuit skips it).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -49,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP32+IR / regular / e2e / CPU legs")
+    ap.add_argument("--no-circuit", action="store_true",
+                    help="skip the n = 200,000 circuit leg (about 2 minutes)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["grid7cd_40", "grid7cd_32", "grid7cd_24"],
                     help="40^3 is the benchmark; the smaller grids of the same "
@@ -236,6 +242,80 @@ def batch_leg(torch, S, dev, args):
             "n_total": PB.info["n"]}
 
 
+def small_grid_leg(torch, S, dev, args):
+    """48 x 48 5-point grid (n = 2304), FP64, irregular blocking against
+    regular 64 x 64 blocking in the same code, 1 RHS."""
+    from paper_2512_04389_b300.tune import tune
+    s = workloads.grid5(48)
+    v, r = dev(s.values), dev(s.rhs)
+    out = {}
+    for name, opts in (("irregular", {}),
+                       ("regular64", dict(blocking="regular", regular_block=64))):
+        best, _ = tune(s.n, s.colptr, s.rowidx, v, r, precision="fp64", **opts)
+        P = S.Plan(s.n, s.colptr, s.rowidx, **opts, **best)
+        F = S.Factor(P, v)
+
+        def step():
+            F.refactor(v)
+            F.solve(r)
+        ms = timed(torch, step, args.steps, 3)
+        out[name] = {"ms_per_step": ms, "tuned": best,
+                     "blocks_1d": P.info["nblocks_1d"], "levels": P.info["nlevels"],
+                     "gflops": step_flops(P, s.nrhs) / (ms * 1e-3) / 1e9}
+    return out
+
+
+def circuit_leg(torch, S, dev, args):
+    """Bordered circuit matrix, n = 200,000 (4,000 border rows), 8 RHS:
+    FP32 factors + FP64 refinement to backward error <= 1e-14 against the
+    plain FP64 factorization, both irregular blocking with the sparse/dense
+    threshold 0.1 (the best of {0.3, 0.1, 0.05, 0.02} for FP32 in a sweep;
+    tuning it here would repeat the 20 s host analysis per candidate).
+    One timed factor + solve each (the factor alone is seconds)."""
+    s = workloads.circuit_bbd()
+    v, r = dev(s.values), dev(s.rhs)
+    out = {"n": s.n, "nnz_a": s.nnz}
+    for prec in ("fp32", "fp64"):
+        t0 = time.perf_counter()
+        P = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=0.1)
+        ana = time.perf_counter() - t0
+        F = S.Factor(P, v)
+
+        def step():
+            F.refactor(v)
+            F.solve(r)
+        ms = timed(torch, step, 1, 1)
+        _, info = F.solve(r, info=True)
+        out[prec] = {"ms_per_step": ms, "analyze_s": ana,
+                     "gflops": step_flops(P, s.nrhs) / (ms * 1e-3) / 1e9,
+                     "backward_error": info["backward_error"],
+                     "ir_iterations": info["iterations"],
+                     "nnz_lu": P.info["nnz_lu"], "flops_factor": P.info["flops"],
+                     "levels": P.info["nlevels"]}
+        del F, P
+        torch.cuda.empty_cache()
+    return out
+
+
+def autograd_leg(torch, S, dev, args):
+    """x = A(theta)^{-1} b on the parameterised 32^3 operator (n = 32,768),
+    FP64: forward solve plus backward (transposed solve through the stored
+    factors and the gradient gather), loss 1/2 ||x||^2."""
+    from paper_2512_04389_b300.autograd import lu_solve
+    s = workloads.grid7_theta(32)
+    P = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=0.0)
+    v0, b0 = dev(s.values), dev(s.rhs[:, 0])
+
+    def step():
+        vv = v0.clone().requires_grad_(True)
+        bb = b0.clone().requires_grad_(True)
+        x = lu_solve(vv, bb, P)
+        (0.5 * (x * x).sum()).backward()
+    ms = timed(torch, step, args.steps, 2)
+    return {"ms_per_step": ms, "n": s.n, "nnz_a": s.nnz,
+            "what": "factor + solve forward, transposed solve + gradient gather backward"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -411,6 +491,10 @@ def main():
                                         "gflops": fl / (msr32 * 1e-3) / 1e9}
         del Freg32
         extras["batch_256_grid5"] = batch_leg(torch, S, dev, args)
+        extras["grid5_48"] = small_grid_leg(torch, S, dev, args)
+        extras["autograd_theta_32"] = autograd_leg(torch, S, dev, args)
+        if not args.no_circuit:
+            extras["circuit_200k"] = circuit_leg(torch, S, dev, args)
         out["extras"] = extras
         # end to end through the public API with host buffers
         vals_h = torch.from_numpy(np.ascontiguousarray(s.values)).pin_memory()

@@ -298,6 +298,51 @@ __device__ void lu_skip(const SplitBlock<T> &B, int b, unsigned char *lists,
     }
 }
 
+// Dense LU of a block held whole in shared memory, one CTA barrier per
+// step (FP32 storage, where the step chain, not arithmetic, is the bound).
+// Step k: every thread reads the pivot A(k, k) (final after step k-1),
+// applies the FP64 small-pivot test itself (thread 0 counts it) and forms
+// the reciprocal; warps over columns c > k with U(k, c) != 0, lanes over
+// rows: A(r, c) -= A(r, k) (U(k, c) / pivot).  Column k is read unscaled in
+// step k; its scaling by the reciprocal (L(:, k)) and the write of the fixed
+// pivot are deferred to step k+1, when nothing reads column k.
+template <typename T>
+__device__ void lu_dense_smem(T *S, int b, int ls, double tau,
+                              unsigned long long *cnt) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    T prev_rcp = T(0), prev_piv = T(0);
+    for (int k = 0; k < b; ++k) {
+        const T p = S[(int64_t)k * ls + k];
+        const double pd = (double)p;
+        double fd = pd;
+        if (tau > 0.0 && fabs(pd) < tau) fd = pd >= 0.0 ? tau : -tau;
+        const T piv = (T)fd;
+        const T rcp = T(1) / piv;
+        if (tid == 0) {
+            if (fd != pd) atomicAdd(&cnt[0], 1ull);
+            else if (pd == 0.0) atomicOr(&cnt[1], 1ull);
+        }
+        if (k > 0 && warp == ((k - 1) % nw)) {      // deferred: column k-1
+            T *c = S + (int64_t)(k - 1) * ls;
+            for (int r = k + lane; r < b; r += 32) c[r] *= prev_rcp;
+            if (lane == 0) c[k - 1] = prev_piv;
+        }
+        const T *ck = S + (int64_t)k * ls;
+        for (int c = k + 1 + warp; c < b; c += nw) {
+            T *cc = S + (int64_t)c * ls;
+            const T u = cc[k] * rcp;
+            if (u == T(0)) continue;                    // uniform across the warp
+            for (int r = k + 1 + lane; r < b; r += 32) cc[r] -= ck[r] * u;
+        }
+        prev_rcp = rcp;
+        prev_piv = piv;
+        __syncthreads();
+    }
+    if (b > 0 && warp == ((b - 1) % nw) && lane == 0) S[(int64_t)(b - 1) * ls + b - 1] = prev_piv;
+    __syncthreads();
+}
+
 // Dense diagonal block b x b at g (leading dimension ld): stage the largest
 // trailing square that fits next to the step lists, factor, write back.
 template <typename T>
@@ -310,6 +355,17 @@ __device__ void getrf_dense(T *g, int b, int64_t ld, double tau,
         ms = (int)sqrt((double)((cap - lb) / sizeof(T)));
         while (ms > 0 && (size_t)ms * (ms | 1) * sizeof(T) > cap - lb) --ms;
         ms = min(ms, b);
+    }
+    if (sizeof(T) == 4 && (size_t)b * b * sizeof(T) <= cap) {
+        // FP32 block that fits whole: dense steps with one barrier each
+        T *S = reinterpret_cast<T *>(smem);
+        for (int e = threadIdx.x; e < b * b; e += blockDim.x)
+            S[e] = g[(int64_t)(e / b) * ld + e % b];
+        __syncthreads();
+        lu_dense_smem<T>(S, b, b, tau, cnt);
+        for (int e = threadIdx.x; e < b * b; e += blockDim.x)
+            g[(int64_t)(e / b) * ld + e % b] = S[e];
+        return;
     }
     const int p0 = b - ms, ls = ms | 1;
     T *S = reinterpret_cast<T *>(smem + lb);
