@@ -268,16 +268,17 @@ def small_grid_leg(torch, S, dev, args):
 def circuit_leg(torch, S, dev, args):
     """Bordered circuit matrix, n = 200,000 (4,000 border rows), 8 RHS:
     FP32 factors + FP64 refinement to backward error <= 1e-14 against the
-    plain FP64 factorization, both irregular blocking with the sparse/dense
-    threshold 0.1 (the best of {0.3, 0.1, 0.05, 0.02} for FP32 in a sweep;
-    tuning it here would repeat the 20 s host analysis per candidate).
-    One timed factor + solve each (the factor alone is seconds)."""
+    plain FP64 factorization, both irregular blocking; sparse/dense
+    threshold 0.02 for FP32 and 0.05 for FP64 (the best of {0.3, 0.1, 0.05,
+    0.02} per precision in a sweep; tuning here would repeat the 20 s host
+    analysis per candidate).  One timed factor + solve each."""
     s = workloads.circuit_bbd()
     v, r = dev(s.values), dev(s.rhs)
     out = {"n": s.n, "nnz_a": s.nnz}
     for prec in ("fp32", "fp64"):
         t0 = time.perf_counter()
-        P = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=0.1)
+        thr = 0.02 if prec == "fp32" else 0.05
+        P = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=thr)
         ana = time.perf_counter() - t0
         F = S.Factor(P, v)
 
@@ -286,7 +287,7 @@ def circuit_leg(torch, S, dev, args):
             F.solve(r)
         ms = timed(torch, step, 1, 1)
         _, info = F.solve(r, info=True)
-        out[prec] = {"ms_per_step": ms, "analyze_s": ana,
+        out[prec] = {"ms_per_step": ms, "analyze_s": ana, "dense_threshold": thr,
                      "gflops": step_flops(P, s.nrhs) / (ms * 1e-3) / 1e9,
                      "backward_error": info["backward_error"],
                      "ir_iterations": info["iterations"],

@@ -654,6 +654,18 @@ static void build_levels_and_tasks(slu_plan &P) {
     P.pg_tstrf.clear();
     P.ps_off.assign(L + 1, 0);
     P.ps_task.clear();
+    P.pv_off.assign(L + 1, 0);
+    P.pv_task.clear();
+    // dense panels against a sparse diagonal block: chunks of V vectors
+    auto add_vec = [&](int32_t type, int32_t tb, int32_t db) {
+        const int32_t m = P.blocks[db].rows;
+        const int32_t nvec = type == 0 ? P.blocks[tb].cols : P.blocks[tb].rows;
+        const int32_t V = panel_vec_width(m, (int)esz);
+        for (int32_t v0 = 0; v0 < nvec; v0 += V) {
+            const int32_t t4[4] = {type, tb, db, v0};
+            P.pv_task.insert(P.pv_task.end(), t4, t4 + 4);
+        }
+    };
     for (int32_t lv = 0; lv < L; ++lv) {
         for (int64_t g = P.getrf_off[lv]; g < P.getrf_off[lv + 1]; ++g) {
             const BlockDesc &d = P.blocks[P.getrf[g]];
@@ -671,6 +683,9 @@ static void build_levels_and_tasks(slu_plan &P) {
                     const int32_t t4[4] = {0, tb, db, c0};
                     P.pd_task.insert(P.pd_task.end(), t4, t4 + 4);
                 }
+            } else if (!P.blocks[db].dense && P.blocks[tb].dense &&
+                       panel_vec_width(P.blocks[db].rows, (int)esz) > 0) {
+                add_vec(0, tb, db);
             } else if (!P.blocks[db].dense) {
                 const int32_t t3[3] = {0, tb, db};
                 P.ps_task.insert(P.ps_task.end(), t3, t3 + 3);
@@ -686,6 +701,9 @@ static void build_levels_and_tasks(slu_plan &P) {
                     const int32_t t4[4] = {1, tb, db, r0};
                     P.pd_task.insert(P.pd_task.end(), t4, t4 + 4);
                 }
+            } else if (!P.blocks[db].dense && P.blocks[tb].dense &&
+                       panel_vec_width(P.blocks[db].rows, (int)esz) > 0) {
+                add_vec(1, tb, db);
             } else if (!P.blocks[db].dense) {
                 const int32_t t3[3] = {1, tb, db};
                 P.ps_task.insert(P.ps_task.end(), t3, t3 + 3);
@@ -699,6 +717,7 @@ static void build_levels_and_tasks(slu_plan &P) {
         P.pg_goff[lv + 1] = (int64_t)P.pg_gessm.size() / 2;
         P.pg_toff[lv + 1] = (int64_t)P.pg_tstrf.size() / 2;
         P.ps_off[lv + 1] = (int64_t)P.ps_task.size() / 3;
+        P.pv_off[lv + 1] = (int64_t)P.pv_task.size() / 4;
     }
     // solve pull pairs per sweep and level
     P.part_elems = 0;

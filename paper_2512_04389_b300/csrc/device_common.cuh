@@ -17,7 +17,7 @@ struct DevPlan {
     int32_t *lcolptr = nullptr;
     uint16_t *lrow = nullptr;
     int32_t *dpos = nullptr, *sched = nullptr, *sgrp = nullptr;
-    int32_t *lr_ptr = nullptr, *lr_pos = nullptr, *ps_task = nullptr;
+    int32_t *lr_ptr = nullptr, *lr_pos = nullptr, *ps_task = nullptr, *pv_task = nullptr;
     uint16_t *lr_col = nullptr, *ne_col = nullptr;
     int64_t *ne_off = nullptr;
     int32_t *getrf = nullptr, *gessm = nullptr, *tstrf = nullptr;

@@ -716,6 +716,106 @@ k_panel_grp(const int32_t *__restrict__ task, BlockArgs a,
     }
 }
 
+// Dense panel block against a sparse-stored diagonal block: one warp per
+// chunk of V vectors, lane v owning vector v (GESSM: column v0 + v of
+// B_IJ; TSTRF: row v0 + v of B_JI), kept interleaved in shared memory with
+// row stride V + 1 (lanes hit distinct banks).  Each lane runs the whole
+// substitution on its own vector, so no synchronisation is needed:
+//   GESSM  rows r ascending: x(r) -= sum_m L(r, m) x(m), over row r of L
+//          (the lr_* row lists, values gathered into row order);
+//   TSTRF  columns k ascending: y(k) = (y(k) - sum_{m<k} y(m) U(m, k)) / U(k, k)
+//          over column k of U (the block's own CSC).
+// Every lane walks the same rows / columns (uniform loops, broadcast
+// loads); lanes past the last vector work on zeros and store nothing.
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_panel_vec(const int32_t *__restrict__ task, BlockArgs a,
+            const int32_t *__restrict__ lr_ptr, const uint16_t *__restrict__ lr_col,
+            const int32_t *__restrict__ lr_pos, T *__restrict__ val) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int32_t *tk = task + 4 * (int64_t)blockIdx.x;
+    const int type = tk[0], v0 = tk[3], lane = threadIdx.x;
+    const BlockDesc d = a.bd[tk[1]];
+    const BlockDesc dd = a.bd[tk[2]];
+    const int m = dd.rows;
+    const int V = panel_vec_width(m, (int)sizeof(T)), VS = V + 1;
+    const int nv = min(V, (type == 0 ? d.cols : d.rows) - v0);
+    T *X = reinterpret_cast<T *>(smem);
+    const size_t xbytes = align16((size_t)m * VS * sizeof(T));
+    unsigned char *rest = smem + xbytes;
+    const size_t cap = kStageSmem - xbytes;
+    T *B = val + d.voff;
+    // load: X(r, v) = vector v at position r (coalesced along the stored
+    // columns: GESSM vectors are columns, TSTRF vectors are rows)
+    if (type == 0) {
+        for (int v = 0; v < V; ++v)
+            for (int r = lane; r < m; r += 32)
+                X[r * VS + v] = v < nv ? B[(int64_t)(v0 + v) * d.ld + r] : T(0);
+    } else if (lane < V) {
+        for (int r = 0; r < m; ++r)
+            X[r * VS + lane] = lane < nv ? B[(int64_t)r * d.ld + v0 + lane] : T(0);
+    }
+    // lanes >= V own no vector (V < 32 for tall blocks) and stay idle below
+    if (type == 0) {
+        const int32_t *rp = lr_ptr + dd.doff + dd.I;
+        const int32_t q0 = rp[0], nq = rp[m] - q0;
+        const T *Lv;
+        const uint16_t *Lc;
+        const int32_t *Rp;
+        const size_t need = align16((size_t)nq * sizeof(T)) + align16((size_t)nq * 2) +
+                            align16((size_t)(m + 1) * 4);
+        if (need <= cap) {                       // rows of L staged in order
+            T *lv = reinterpret_cast<T *>(rest);
+            uint16_t *lc = reinterpret_cast<uint16_t *>(rest + align16((size_t)nq * sizeof(T)));
+            int32_t *rr = reinterpret_cast<int32_t *>(
+                rest + align16((size_t)nq * sizeof(T)) + align16((size_t)nq * 2));
+            for (int q = lane; q < nq; q += 32) {
+                lv[q] = val[dd.voff + lr_pos[q0 + q]];
+                lc[q] = lr_col[q0 + q];
+            }
+            for (int r = lane; r <= m; r += 32) rr[r] = rp[r] - q0;
+            Lv = lv;
+            Lc = lc;
+            Rp = rr;
+            __syncwarp();
+            for (int r = 0; r < m && lane < V; ++r) {
+                T x = X[r * VS + lane];
+                for (int q = Rp[r]; q < Rp[r + 1]; ++q) x -= Lv[q] * X[Lc[q] * VS + lane];
+                X[r * VS + lane] = x;
+            }
+        } else {                                 // rows of L read in place
+            __syncwarp();
+            for (int r = 0; r < m && lane < V; ++r) {
+                T x = X[r * VS + lane];
+                for (int q = rp[r]; q < rp[r + 1]; ++q)
+                    x -= val[dd.voff + lr_pos[q]] * X[lr_col[q] * VS + lane];
+                X[r * VS + lane] = x;
+            }
+        }
+    } else {
+        bool staged;
+        size_t used;
+        const BlockView<T> F = stage_block<T>(dd, a, val, rest, cap, true, &staged, &used);
+        __syncwarp();
+        for (int k = 0; k < m && lane < V; ++k) {
+            int fo, fc;
+            const uint16_t *fr;
+            F.col(k, fo, fc, fr);
+            const int dp = F.dp[k];
+            T y = X[k * VS + lane];
+            for (int e = 0; e < dp; ++e) y -= F.v[fo + e] * X[fr[e] * VS + lane];
+            X[k * VS + lane] = y * (T(1) / F.v[fo + dp]);
+        }
+    }
+    __syncwarp();
+    if (type == 0) {
+        for (int v = 0; v < nv; ++v)
+            for (int r = lane; r < m; r += 32) B[(int64_t)(v0 + v) * d.ld + r] = X[r * VS + v];
+    } else if (lane < nv) {
+        for (int r = 0; r < m; ++r) B[(int64_t)r * d.ld + v0 + lane] = X[r * VS + lane];
+    }
+}
+
 // GESSM (blockIdx.x < ngessm) and TSTRF tasks of one level.
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(kThreads)
@@ -1290,7 +1390,7 @@ void free_dev_plan(slu_plan *P) {
     void *ptrs[] = {D->bd, D->lcolptr, D->lrow, D->dpos, D->sched, D->sgrp,
                     D->getrf, D->gessm, D->tstrf, D->tgt, D->src, D->srcoff,
                     D->gd, D->gs, D->dv_pos, D->dn_pos, D->lr_ptr, D->lr_pos,
-                    D->ps_task, D->lr_col, D->ne_col, D->ne_off,
+                    D->ps_task, D->lr_col, D->ne_col, D->ne_off, D->pv_task,
                     D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
                     D->a_ri, D->a_ci, D->row_seg, D->woff, D->inv_task,
@@ -1328,6 +1428,7 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->lr_ptr, &D->lr_ptr) && upload(P->lr_pos, &D->lr_pos) &&
         upload(P->lr_col, &D->lr_col) && upload(P->ps_task, &D->ps_task) &&
         upload(P->ne_col, &D->ne_col) && upload(P->ne_off, &D->ne_off) &&
+        upload(P->pv_task, &D->pv_task) &&
         upload(P->tstrf, &D->tstrf) && upload(P->tgt, &D->tgt) &&
         upload(P->src, &D->src) && upload(P->srcoff, &D->srcoff) &&
         upload(P->gm_task, &D->gm_task) && upload(P->gm_src, &D->gm_src) &&
@@ -1380,7 +1481,8 @@ static slu_status set_smem_limits(size_t generic) {
               cuda_ok(cudaFuncSetAttribute(k_getrf_dense<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_inv<T>, attr, (int)kStageSmem), "smem") &&
-              cuda_ok(cudaFuncSetAttribute(k_panel_grp<T>, attr, (int)kStageSmem), "smem");
+              cuda_ok(cudaFuncSetAttribute(k_panel_grp<T>, attr, (int)kStageSmem), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_panel_vec<T>, attr, (int)kStageSmem), "smem");
     if (ok)
         ok = cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, (int)kStageSmem), "smem");
     return ok ? SLU_OK : SLU_ERR_CUDA;
@@ -1483,6 +1585,12 @@ static slu_status run_factor(slu_handle *h, const double *values,
             if (!cuda_ok(cudaStreamWaitEvent(st, h->ev_join, 0), "cudaStreamWaitEvent"))
                 return SLU_ERR_CUDA;
             deferred = false;
+        }
+        const int64_t w0 = P->pv_off[lv], w1 = P->pv_off[lv + 1];
+        if (w1 > w0) {
+            LaunchScope ls_(h, SLU_KC_PANEL, st, -(int)(w1 - w0));
+            k_panel_vec<T><<<(int)(w1 - w0), 32, kStageSmem, st>>>(
+                D->pv_task + 4 * w0, a, D->lr_ptr, D->lr_col, D->lr_pos, val);
         }
         const int64_t u0 = P->ps_off[lv], u1 = P->ps_off[lv + 1];
         if (u1 > u0) {

@@ -44,6 +44,18 @@ struct DevPlan;            // device mirror, defined in device_common.cuh
 
 }  // namespace slu
 
+// Vectors per warp of the dense-panel substitution kernel: lane v owns
+// vector v, stored interleaved (m rows x V) in shared memory within 112 KB;
+// 0 when even 8 vectors of m rows do not fit.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int panel_vec_width(int m, int esz) {
+    for (int V = 32; V >= 8; V >>= 1)
+        if ((long long)m * V * esz <= 112 * 1024) return V;
+    return 0;
+}
+
 struct slu_plan {
     slu_opts opts;
     int64_t n = 0, nnz_a = 0, nnz_sym = 0;
@@ -120,6 +132,11 @@ struct slu_plan {
     // 3 ints (0 GESSM / 1 TSTRF, panel block, diagonal block)
     std::vector<int64_t> ps_off;
     std::vector<int32_t> ps_task;
+    // the dense-panel subset of those, split into chunks of vectors (one
+    // warp each): 4 ints (0 GESSM / 1 TSTRF, panel block, diagonal block,
+    // first vector)
+    std::vector<int64_t> pv_off;
+    std::vector<int32_t> pv_task;
     // dense diagonal blocks: explicit inverses of L_II and U_II live in a
     // per-handle workspace at woff[I] (L^-1 then U^-1, b x b column-major
     // each); -1 for sparse diagonal blocks

@@ -186,6 +186,25 @@ def test_full_size_parity(name, mk, thr):
     assert info["backward_error"] <= 1e-13
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tall_sparse_diagonal_blocks(prec):
+    """Circuit matrix with blocks up to 512 rows (b_min 128): sparse
+    diagonal blocks with dense border panels take the per-lane substitution
+    with fewer than 32 vectors per warp (FP64: 16 for 512 rows)."""
+    s = workloads.circuit_bbd(n=20_000, border=400)
+    P, F = gpu_factor(s, b_min=128, dense_threshold=0.1, precision=prec)
+    assert P.info["max_block"] > 450
+    _, _, _, pv = oracle_factor(s)
+    if prec == "fp64":
+        assert factor_error(P, F, pv) <= FP64_TOL
+    else:
+        assert factor_error(P, F, pv) <= 1e-4
+    X, info = F.solve(_dev(s.rhs), info=True)
+    assert info["backward_error"] <= (1e-13 if prec == "fp64" else 1e-14)
+    if prec == "fp32":
+        assert info["iterations"] <= 3
+
+
 def test_full_size_grid7cd_40_properties():
     """40^3 convection-diffusion (n = 64,000) in the benchmark's
     configuration: backward error of the solve, and A = L U checked on 2000
