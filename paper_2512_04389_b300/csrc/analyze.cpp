@@ -553,7 +553,9 @@ static void build_levels_and_tasks(slu_plan &P) {
     P.gg_tgt.clear();
     P.gg_src.clear();
     P.gg_srcoff.assign(1, 0);
-    constexpr int32_t kTile = 64;
+    // tile rows: 128 for FP32 (one tensor-core MMA tile), 64 for FP64;
+    // tile columns: 64
+    const int32_t kTile = P.opts.precision == SLU_PREC_FP32 ? 128 : 64;
     P.gm_mid.assign(L, 0);
     P.gg_mid.assign(L, 0);
     for (int32_t lv = 0; lv < L; ++lv) {
@@ -586,7 +588,7 @@ static void build_levels_and_tasks(slu_plan &P) {
                 P.gm_src.insert(P.gm_src.end(), dense_pairs.begin(), dense_pairs.end());
                 const int32_t s1 = (int32_t)(P.gm_src.size() / 2);
                 for (int32_t r0 = 0; r0 < td.rows; r0 += kTile)
-                    for (int32_t c0 = 0; c0 < td.cols; c0 += kTile) {
+                    for (int32_t c0 = 0; c0 < td.cols; c0 += 64) {
                         const int32_t t5[5] = {tb, s0, s1, r0, c0};
                         P.gm_task.insert(P.gm_task.end(), t5, t5 + 5);
                     }

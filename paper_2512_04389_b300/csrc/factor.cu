@@ -1230,6 +1230,205 @@ k_ssssm(const int32_t *__restrict__ tgt, const int64_t *__restrict__ srcoff,
 }
 
 
+// SSSSM on dense tiles, FP32 storage, on the 5th-generation tensor cores:
+// a 128 x 64 tile of a dense target B_KJ minus the sum over the level's
+// dense sources of L_KI U_IJ.  Split precision (3xTF32): each operand x is
+// split into hi = x with the 13 low mantissa bits cleared (exact in TF32)
+// and lo = x - hi, and the tile accumulates hi*hi + hi*lo + lo*hi in FP32 in
+// tensor memory (the dropped lo*lo term and the TF32 reading of lo are
+// below FP32 rounding of the products).  K runs over the sources' columns
+// in 32-deep chunks staged in shared memory (K-major core-matrix layout, no
+// swizzle), two stages: while the tensor core works on one chunk the CTA
+// stages the next.  One thread issues the MMAs and commits them to the
+// stage's mbarrier; every wait is bounded, and a wait that runs out sets
+// err (reported as a timeout) instead of hanging.
+namespace tc {
+constexpr int TM = 128, TN = 64, KC = 32;
+constexpr int LBO = 128;                         // next core matrix along K
+constexpr int SBO = (KC / 4) * 128;              // next 8-row group
+constexpr int A_BYTES = TM * KC * 4, B_BYTES = TN * KC * 4;
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi, lo of A and B
+constexpr size_t SMEM = 2 * STAGE_BYTES + 1024;
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t kmaj(int row, int k) {
+    return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4;
+}
+__device__ __forceinline__ uint64_t desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((LBO >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void split(float x, float &hi, float &lo) {
+    hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+    lo = x - hi;
+}
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+}  // namespace tc
+
+__global__ void __launch_bounds__(256)
+k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
+           const BlockDesc *__restrict__ bd, float *__restrict__ val,
+           unsigned long long *__restrict__ err) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_holder;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int32_t *tk = task + 5 * (int64_t)blockIdx.x;
+    const BlockDesc d = bd[tk[0]];
+    const int s0 = tk[1], s1 = tk[2], r0 = tk[3], c0 = tk[4];
+    if (s0 >= s1) return;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_holder)), "r"(TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                           ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+    // Register image of one chunk: warp w holds A columns k = w + 8 j
+    // (j < 4) at rows lane + 32 i (i < 4), and B columns n = w + 8 j (j < 8)
+    // at row k = lane; every global load is a coalesced 128-byte line.
+    float ra[4][4], rb[8];
+    auto load = [&](const BlockDesc &L, const BlockDesc &U, int kk0) {
+        const float *A = val + L.voff, *Bm = val + U.voff;
+        const int K = L.cols;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gk = kk0 + warp + 8 * j;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int gr = r0 + lane + 32 * i;
+                ra[j][i] = (gk < K && gr < d.rows) ? A[(int64_t)gk * L.ld + gr] : 0.f;
+            }
+        }
+        const int gk = kk0 + lane;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gc = c0 + warp + 8 * j;
+            rb[j] = (gk < K && gc < d.cols) ? Bm[(int64_t)gc * U.ld + gk] : 0.f;
+        }
+    };
+    auto store = [&](unsigned char *base) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float hi, lo;
+                split(ra[j][i], hi, lo);
+                const uint32_t o = kmaj(lane + 32 * i, warp + 8 * j);
+                *reinterpret_cast<float *>(base + o) = hi;
+                *reinterpret_cast<float *>(base + A_BYTES + o) = lo;
+            }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float hi, lo;
+            split(rb[j], hi, lo);
+            const uint32_t o = kmaj(warp + 8 * j, lane);
+            *reinterpret_cast<float *>(base + 2 * A_BYTES + o) = hi;
+            *reinterpret_cast<float *>(base + 2 * A_BYTES + B_BYTES + o) = lo;
+        }
+    };
+    int s = s0, k0 = 0;
+    BlockDesc dl = bd[src[2 * s]], du = bd[src[2 * s + 1]];
+    load(dl, du, 0);
+    int chunk = 0;
+    bool ok = true;
+    uint32_t phase[2] = {0, 0};
+    for (;;) {
+        const int st = chunk & 1;
+        unsigned char *base = smem + st * STAGE_BYTES;
+        if (chunk >= 2) {               // the MMAs of chunk - 2 read this stage
+            ok = ok && wait_phase(smem_u32(&mbar[st]), phase[st]);
+            phase[st] ^= 1;
+        }
+        store(base);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(base), a_lo = a_hi + A_BYTES;
+            const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < KC / 8; ++kk) {
+                const uint32_t off = kk * 2 * LBO;
+                const uint32_t pa[3] = {a_hi, a_hi, a_lo}, pb[3] = {b_hi, b_lo, b_hi};
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const uint32_t acc = (chunk > 0 || kk > 0 || t > 0) ? 1u : 0u;
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                 :: "r"(tmem), "l"(desc(pa[t] + off)), "l"(desc(pb[t] + off)),
+                                    "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&mbar[st])) : "memory");
+        }
+        ++chunk;
+        k0 += KC;
+        if (k0 >= dl.cols) {
+            ++s;
+            k0 = 0;
+            if (s >= s1) break;
+            dl = bd[src[2 * s]];
+            du = bd[src[2 * s + 1]];
+        }
+        load(dl, du, k0);               // in flight while the tensor core works
+    }
+    for (int c = max(0, chunk - 2); c < chunk; ++c) {
+        const int st = c & 1;
+        ok = ok && wait_phase(smem_u32(&mbar[st]), phase[st]);
+        phase[st] ^= 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // warp w reads TMEM lanes 32 (w % 4) .. (rows), columns 32 (w / 4) ..
+        const int row = 32 * (warp & 3) + lane, gr = r0 + row;
+        for (int cb = 32 * (warp >> 2); cb < 32 * (warp >> 2) + 32; cb += 16) {
+            uint32_t v[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]),
+                           "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]),
+                           "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                           "=r"(v[15])
+                         : "r"(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cb));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (gr < d.rows)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int gc = c0 + cb + j;
+                    if (gc < d.cols) val[d.voff + (int64_t)gc * d.ld + gr] -= __uint_as_float(v[j]);
+                }
+        }
+    } else if (tid == 0) {
+        atomicOr(&err[0], 1ull);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TN));
+}
+
 // SSSSM on dense tiles: a 64 x 64 tile of a dense target B_KJ minus the sum
 // over the level's dense sources of L_KI U_IJ, accumulated in registers
 // (4 x 4 per thread) over all sources and k-slices of 16, written once.
@@ -1482,7 +1681,8 @@ static slu_status set_smem_limits(size_t generic) {
               cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_inv<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_grp<T>, attr, (int)kStageSmem), "smem") &&
-              cuda_ok(cudaFuncSetAttribute(k_panel_vec<T>, attr, (int)kStageSmem), "smem");
+              cuda_ok(cudaFuncSetAttribute(k_panel_vec<T>, attr, (int)kStageSmem), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_ssssm_tc, attr, (int)tc::SMEM), "smem");
     if (ok)
         ok = cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, (int)kStageSmem), "smem");
     return ok ? SLU_OK : SLU_ERR_CUDA;
@@ -1500,7 +1700,7 @@ static slu_status run_factor(slu_handle *h, const double *values,
                  "cudaMemsetAsync(storage)") ||
         !cuda_ok(cudaMemsetAsync(h->scal, 0, 2 * sizeof(double), st),
                  "cudaMemsetAsync(scal)") ||
-        !cuda_ok(cudaMemsetAsync(h->cnt, 0, 2 * sizeof(unsigned long long), st),
+        !cuda_ok(cudaMemsetAsync(h->cnt, 0, 3 * sizeof(unsigned long long), st),
                  "cudaMemsetAsync(cnt)"))
         return SLU_ERR_CUDA;
     if (P->nnz_a > 0) {
@@ -1604,8 +1804,13 @@ static slu_status run_factor(slu_handle *h, const double *values,
                            cudaStream_t ss) {
             if (mb > ma) {
                 LaunchScope ls_(h, SLU_KC_SSSSM, ss, (int)(mb - ma));
-                k_ssssm_gemm<T><<<(int)(mb - ma), 256, 0, ss>>>(
-                    D->gm_task + 5 * ma, D->gm_src, D->bd, val);
+                if (sizeof(T) == 4)
+                    k_ssssm_tc<<<(int)(mb - ma), 256, tc::SMEM, ss>>>(
+                        D->gm_task + 5 * ma, D->gm_src, D->bd,
+                        reinterpret_cast<float *>(val), h->cnt + 2);
+                else
+                    k_ssssm_gemm<T><<<(int)(mb - ma), 256, 0, ss>>>(
+                        D->gm_task + 5 * ma, D->gm_src, D->bd, val);
             }
             if (sb > sa) {
                 LaunchScope ls_(h, SLU_KC_SSSSM, ss, -(int)(sb - sa));
@@ -1635,7 +1840,7 @@ static slu_status run_factor(slu_handle *h, const double *values,
 
 static slu_status finish_info(slu_handle *h, cudaStream_t st,
                               slu_factor_info *info) {
-    unsigned long long c[2];
+    unsigned long long c[3];
     double s[2];
     if (!cuda_ok(cudaMemcpyAsync(c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, st),
                  "cudaMemcpyAsync(info)") ||
@@ -1647,6 +1852,7 @@ static slu_status finish_info(slu_handle *h, cudaStream_t st,
         info->nperturb = (int64_t)c[0];
         info->tau = h->tau_rel * s[0];
     }
+    if (c[2]) return fail(SLU_ERR_TIMEOUT, "a tensor-core wait exceeded its bound");
     if (c[1]) return fail(SLU_ERR_SINGULAR, "zero pivot (perturbation off)");
     return SLU_OK;
 }
@@ -1715,7 +1921,7 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
         cuda_ok(cudaMalloc(&h->storage, std::max<int64_t>(1, P->storage) * esz),
                 "cudaMalloc(storage)") &&
         cuda_ok(cudaMalloc(&h->scal, 4 * sizeof(double)), "cudaMalloc") &&
-        cuda_ok(cudaMalloc(&h->cnt, 2 * sizeof(unsigned long long)), "cudaMalloc") &&
+        cuda_ok(cudaMalloc(&h->cnt, 3 * sizeof(unsigned long long)), "cudaMalloc") &&
         cuda_ok(cudaMalloc(&h->a_vals, std::max<int64_t>(1, P->nnz_a) * sizeof(double)),
                 "cudaMalloc(A)") &&
         cuda_ok(cudaMalloc(&h->part, std::max<int64_t>(1, P->part_elems) * 4 *
