@@ -389,7 +389,13 @@ static slu_status build_blocks(slu_plan &P) {
     P.lr_ptr.assign(ndiag_slots + p + 1, 0);
     P.lr_col.clear();
     P.lr_pos.clear();
-    {
+    P.ur_ptr.assign(ndiag_slots + p + 1, 0);
+    P.ur_col.clear();
+    P.ur_pos.clear();
+    for (int upper = 0; upper < 2; ++upper) {
+        std::vector<int32_t> &rptr = upper ? P.ur_ptr : P.lr_ptr;
+        std::vector<uint16_t> &rcol = upper ? P.ur_col : P.lr_col;
+        std::vector<int32_t> &rpos = upper ? P.ur_pos : P.lr_pos;
         std::vector<int32_t> cnt;
         std::vector<int64_t> at;
         for (int32_t I = 0; I < p; ++I) {
@@ -397,27 +403,28 @@ static slu_status build_blocks(slu_plan &P) {
             const int64_t base = d.doff + I;
             const int32_t m = d.rows;
             cnt.assign(m, 0);
+            auto keep = [&](int32_t r, int32_t jj) { return upper ? r < jj : r > jj; };
             if (!d.dense)
                 for (int32_t jj = 0; jj < m; ++jj)
                     for (int32_t t = P.lcolptr[d.coff + jj]; t < P.lcolptr[d.coff + jj + 1]; ++t)
-                        if (P.lrow[d.roff + t] > jj) cnt[P.lrow[d.roff + t]]++;
-            const int32_t start = (int32_t)P.lr_col.size();
+                        if (keep(P.lrow[d.roff + t], jj)) cnt[P.lrow[d.roff + t]]++;
+            const int32_t start = (int32_t)rcol.size();
             at.assign(m + 1, 0);
             for (int32_t r = 0; r < m; ++r) at[r + 1] = at[r] + cnt[r];
-            for (int32_t r = 0; r <= m; ++r) P.lr_ptr[base + r] = start + (int32_t)at[r];
-            P.lr_col.resize(start + at[m]);
-            P.lr_pos.resize(start + at[m]);
+            for (int32_t r = 0; r <= m; ++r) rptr[base + r] = start + (int32_t)at[r];
+            rcol.resize(start + at[m]);
+            rpos.resize(start + at[m]);
             if (!d.dense)
                 for (int32_t jj = 0; jj < m; ++jj)
                     for (int32_t t = P.lcolptr[d.coff + jj]; t < P.lcolptr[d.coff + jj + 1]; ++t) {
                         const int32_t r = P.lrow[d.roff + t];
-                        if (r <= jj) continue;
+                        if (!keep(r, jj)) continue;
                         const int64_t q = start + at[r]++;
-                        P.lr_col[q] = (uint16_t)jj;
-                        P.lr_pos[q] = t;
+                        rcol[q] = (uint16_t)jj;
+                        rpos[q] = t;
                     }
         }
-        if (P.lr_col.size() > (size_t)INT32_MAX)
+        if (rcol.size() > (size_t)INT32_MAX)
             return fail(SLU_ERR_NOT_SUPPORTED, "sparse diagonal blocks too large");
     }
     return SLU_OK;

@@ -18,7 +18,8 @@ struct DevPlan {
     uint16_t *lrow = nullptr;
     int32_t *dpos = nullptr, *sched = nullptr, *sgrp = nullptr;
     int32_t *lr_ptr = nullptr, *lr_pos = nullptr, *ps_task = nullptr, *pv_task = nullptr;
-    uint16_t *lr_col = nullptr, *ne_col = nullptr;
+    uint16_t *lr_col = nullptr, *ne_col = nullptr, *ur_col = nullptr;
+    int32_t *ur_ptr = nullptr, *ur_pos = nullptr;
     int64_t *ne_off = nullptr;
     int32_t *getrf = nullptr, *gessm = nullptr, *tstrf = nullptr;
     int32_t *gd = nullptr, *gs = nullptr;
@@ -43,6 +44,18 @@ struct DevPlan {
             *lcol_off = nullptr;
     int32_t *lrow_blk = nullptr, *urow_blk = nullptr, *ucol_blk = nullptr,
             *lcol_blk = nullptr;
+};
+
+// Row lists of the sparse diagonal blocks' strict lower (l*) and upper (u*)
+// parts: row r of diagonal block I spans [p[doff + I + r], p[doff + I + r + 1])
+// of the column (c) and value-slot (q) arrays.
+struct RowLists {
+    const int32_t *__restrict__ lp;
+    const uint16_t *__restrict__ lc;
+    const int32_t *__restrict__ lq;
+    const int32_t *__restrict__ up;
+    const uint16_t *__restrict__ uc;
+    const int32_t *__restrict__ uq;
 };
 
 // Everything a block kernel needs to address block storage.

@@ -1590,6 +1590,7 @@ void free_dev_plan(slu_plan *P) {
                     D->getrf, D->gessm, D->tstrf, D->tgt, D->src, D->srcoff,
                     D->gd, D->gs, D->dv_pos, D->dn_pos, D->lr_ptr, D->lr_pos,
                     D->ps_task, D->lr_col, D->ne_col, D->ne_off, D->pv_task,
+                    D->ur_ptr, D->ur_pos, D->ur_col,
                     D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
                     D->a_ri, D->a_ci, D->row_seg, D->woff, D->inv_task,
@@ -1628,6 +1629,8 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->lr_col, &D->lr_col) && upload(P->ps_task, &D->ps_task) &&
         upload(P->ne_col, &D->ne_col) && upload(P->ne_off, &D->ne_off) &&
         upload(P->pv_task, &D->pv_task) &&
+        upload(P->ur_ptr, &D->ur_ptr) && upload(P->ur_pos, &D->ur_pos) &&
+        upload(P->ur_col, &D->ur_col) &&
         upload(P->tstrf, &D->tstrf) && upload(P->tgt, &D->tgt) &&
         upload(P->src, &D->src) && upload(P->srcoff, &D->srcoff) &&
         upload(P->gm_task, &D->gm_task) && upload(P->gm_src, &D->gm_src) &&

@@ -92,6 +92,9 @@ struct slu_plan {
     // values); dense diagonal blocks have empty rows
     std::vector<int32_t> lr_ptr, lr_pos;
     std::vector<uint16_t> lr_col;
+    // the strict upper part likewise by rows (ur_*), same indexing
+    std::vector<int32_t> ur_ptr, ur_pos;
+    std::vector<uint16_t> ur_col;
     // non-empty columns of each sparse block b: ne_col[ne_off[b] .. ne_off[b+1])
     std::vector<int64_t> ne_off;
     std::vector<uint16_t> ne_col;

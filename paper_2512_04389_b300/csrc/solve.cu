@@ -500,7 +500,8 @@ k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
        const int64_t *__restrict__ boff, const int64_t *__restrict__ poff,
        BlockArgs a, const T *__restrict__ val, double *__restrict__ X,
        int64_t ldx, int nc, const double *__restrict__ part_d,
-       const T *__restrict__ winv, const int64_t *__restrict__ woff) {
+       const T *__restrict__ winv, const int64_t *__restrict__ woff,
+       RowLists rl) {
     using C = T;
     const C *part = reinterpret_cast<const C *>(part_d);
     extern __shared__ __align__(16) unsigned char smem[];
@@ -605,6 +606,72 @@ k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
         for (int t = threadIdx.x; t < m * RC; t += kThreads) {
             const int r = t / RC, c = t % RC;
             if (c < nc) X[(int64_t)c * ldx + dd.r0 + r] = o[t];
+        }
+        return;
+    }
+    if (!dd.dense && 4 * dd.ngroups <= m) {
+        // sparse block with few heights: rows of one height of the block's
+        // column DAG do not depend on each other, so each height is one
+        // parallel step (one thread per row, all right-hand sides), rows
+        // pulling from the rows they depend on (row lists of L or U, or the
+        // block's own columns for the transposed sweeps); ascending heights
+        // for the lower-triangular sweeps, descending for the upper ones
+        bool staged;
+        size_t used;
+        const BlockView<T> F = stage_block<T>(dd, a, const_cast<T *>(val),
+                                              smem + ybytes, kStageSmem - ybytes,
+                                              true, &staged, &used);
+        __syncthreads();
+        const int32_t *sched = a.sched + dd.doff, *grp = a.sgrp + dd.goff;
+        const int ng = dd.ngroups;
+        const int64_t rb = dd.doff + dd.I;
+        const bool asc = (MODE == FWD || MODE == FWD_T);
+        for (int gi = 0; gi < ng; ++gi) {
+            const int g = asc ? gi : ng - 1 - gi;
+            for (int t = grp[g] + threadIdx.x; t < grp[g + 1]; t += kThreads) {
+                const int r = sched[t];
+                C acc[RC];
+#pragma unroll
+                for (int c = 0; c < RC; ++c) acc[c] = y[r * RC + c];
+                if (MODE == FWD || MODE == BWD) {
+                    const int32_t *pp = MODE == FWD ? rl.lp : rl.up;
+                    const uint16_t *pc = MODE == FWD ? rl.lc : rl.uc;
+                    const int32_t *pq = MODE == FWD ? rl.lq : rl.uq;
+                    for (int q = pp[rb + r]; q < pp[rb + r + 1]; ++q) {
+                        const C v = (C)F.v[pq[q]];
+                        const int mm = pc[q];
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) acc[c] -= v * y[mm * RC + c];
+                    }
+                } else {
+                    int fo, fc;
+                    const uint16_t *fr;
+                    F.col(r, fo, fc, fr);
+                    const int dp = F.dp[r];
+                    const int e0 = MODE == FWD_T ? 0 : dp + 1, e1 = MODE == FWD_T ? dp : fc;
+                    for (int e = e0; e < e1; ++e) {
+                        const C v = (C)F.v[fo + e];
+                        const int mm = fr[e];
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) acc[c] -= v * y[mm * RC + c];
+                    }
+                }
+                if (MODE == BWD || MODE == FWD_T) {
+                    int fo, fc;
+                    const uint16_t *fr;
+                    F.col(r, fo, fc, fr);
+                    const C dg = (C)F.v[fo + F.dp[r]];
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) acc[c] /= dg;
+                }
+#pragma unroll
+                for (int c = 0; c < RC; ++c) y[r * RC + c] = acc[c];
+            }
+            __syncthreads();
+        }
+        for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+            const int r = t / RC, c = t % RC;
+            if (c < nc) X[(int64_t)c * ldx + dd.r0 + r] = y[t];
         }
         return;
     }
@@ -879,7 +946,9 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
                 k_diag<T, MODE><<<(int)(n1 - n0), kThreads, kStageSmem, st>>>(
                     D->dn_pos + n0, D->getrf, D->sd_pair0[MODE], boff,
                     D->sp_poff[MODE], a, val, Xc, ldx, nc, h->part,
-                    static_cast<const T *>(h->winv), D->woff);
+                    static_cast<const T *>(h->winv), D->woff,
+                    RowLists{D->lr_ptr, D->lr_col, D->lr_pos, D->ur_ptr, D->ur_col,
+                             D->ur_pos});
             }
         }
     }
