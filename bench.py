@@ -71,6 +71,25 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(ms, world, device="cpu"):
+    """Step time of the whole job: the maximum over ranks (all-reduce MAX on
+    the current process group; the value itself at world size 1)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(flops_per_rank, ms, world):
+    """Whole-job throughput: every rank factors its own replica (weak
+    scaling), so the job does world x flops_per_rank in the slowest rank's
+    time."""
+    return world * flops_per_rank / (ms * 1e-3) / 1e9
+
+
 def step_flops(plan, nrhs):
     return plan.info["flops"] + 2 * plan.info["nnz_lu"] * nrhs
 
@@ -402,12 +421,8 @@ def main():
     with Clocks(local) as clk:
         ms = timed(torch, step, args.steps, 0, barrier, nvtx="bench_step")
     launches = (F.stats()["launches"] - l0) // max(1, args.steps)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * fl / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(ms, world, device="cuda")
+    value = job_gflops(fl, ms, world)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
