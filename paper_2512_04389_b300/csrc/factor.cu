@@ -1304,45 +1304,47 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
     const uint32_t tmem = tmem_holder;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-    // Register image of one chunk: warp w holds A columns k = w + 8 j
-    // (j < 4) at rows lane + 32 i (i < 4), and B columns n = w + 8 j (j < 8)
-    // at row k = lane; every global load is a coalesced 128-byte line.
-    float ra[4][4], rb[8];
+    // Register image of one chunk, one core matrix (8 rows x 4 k, 128
+    // contiguous bytes in shared memory) per warp instruction: lane l holds
+    // row (l & 7) and k (l >> 3) of it, so each store fills 32 distinct
+    // banks and each global load reads 32-byte runs.  Warp w takes the A
+    // core matrices q = w + 8 j (j < 16: row group q % 16, k group q / 16)
+    // and the B core matrices q = w + 8 j (j < 8: column group q % 8, k
+    // group q / 8).
+    float ra[16], rb[8];
+    const int lr = lane & 7, lk = lane >> 3;
     auto load = [&](const BlockDesc &L, const BlockDesc &U, int kk0) {
         const float *A = val + L.voff, *Bm = val + U.voff;
         const int K = L.cols;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gk = kk0 + warp + 8 * j;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int gr = r0 + lane + 32 * i;
-                ra[j][i] = (gk < K && gr < d.rows) ? A[(int64_t)gk * L.ld + gr] : 0.f;
-            }
+        for (int j = 0; j < 16; ++j) {
+            const int q = warp + 8 * j;
+            const int gr = r0 + 8 * (q & 15) + lr, gk = kk0 + 4 * (q >> 4) + lk;
+            ra[j] = (gk < K && gr < d.rows) ? A[(int64_t)gk * L.ld + gr] : 0.f;
         }
-        const int gk = kk0 + lane;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int gc = c0 + warp + 8 * j;
+            const int q = warp + 8 * j;
+            const int gc = c0 + 8 * (q & 7) + lr, gk = kk0 + 4 * (q >> 3) + lk;
             rb[j] = (gk < K && gc < d.cols) ? Bm[(int64_t)gc * U.ld + gk] : 0.f;
         }
     };
     auto store = [&](unsigned char *base) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float hi, lo;
-                split(ra[j][i], hi, lo);
-                const uint32_t o = kmaj(lane + 32 * i, warp + 8 * j);
-                *reinterpret_cast<float *>(base + o) = hi;
-                *reinterpret_cast<float *>(base + A_BYTES + o) = lo;
-            }
+        for (int j = 0; j < 16; ++j) {
+            const int q = warp + 8 * j;
+            float hi, lo;
+            split(ra[j], hi, lo);
+            const uint32_t o = kmaj(8 * (q & 15) + lr, 4 * (q >> 4) + lk);
+            *reinterpret_cast<float *>(base + o) = hi;
+            *reinterpret_cast<float *>(base + A_BYTES + o) = lo;
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
+            const int q = warp + 8 * j;
             float hi, lo;
             split(rb[j], hi, lo);
-            const uint32_t o = kmaj(warp + 8 * j, lane);
+            const uint32_t o = kmaj(8 * (q & 7) + lr, 4 * (q >> 3) + lk);
             *reinterpret_cast<float *>(base + 2 * A_BYTES + o) = hi;
             *reinterpret_cast<float *>(base + 2 * A_BYTES + B_BYTES + o) = lo;
         }
