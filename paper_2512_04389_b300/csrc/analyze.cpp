@@ -692,7 +692,7 @@ static void build_levels_and_tasks(slu_plan &P) {
                     const int32_t t4[4] = {0, tb, db, c0};
                     P.pd_task.insert(P.pd_task.end(), t4, t4 + 4);
                 }
-            } else if (!P.blocks[db].dense && P.blocks[tb].dense &&
+            } else if (P.blocks[tb].dense &&
                        panel_vec_width(P.blocks[db].rows, (int)esz) > 0) {
                 add_vec(0, tb, db);
             } else if (!P.blocks[db].dense) {
@@ -710,7 +710,7 @@ static void build_levels_and_tasks(slu_plan &P) {
                     const int32_t t4[4] = {1, tb, db, r0};
                     P.pd_task.insert(P.pd_task.end(), t4, t4 + 4);
                 }
-            } else if (!P.blocks[db].dense && P.blocks[tb].dense &&
+            } else if (P.blocks[tb].dense &&
                        panel_vec_width(P.blocks[db].rows, (int)esz) > 0) {
                 add_vec(1, tb, db);
             } else if (!P.blocks[db].dense) {

@@ -756,7 +756,26 @@ k_panel_vec(const int32_t *__restrict__ task, BlockArgs a,
             X[r * VS + lane] = lane < nv ? B[(int64_t)r * d.ld + v0 + lane] : T(0);
     }
     // lanes >= V own no vector (V < 32 for tall blocks) and stay idle below
-    if (type == 0) {
+    if (dd.dense) {
+        // dense diagonal factor (no explicit inverse): read it in place,
+        // rows of L / columns of U by index
+        const T *Fv = val + dd.voff;
+        __syncwarp();
+        if (type == 0) {
+            for (int r = 0; r < m && lane < V; ++r) {
+                T x = X[r * VS + lane];
+                for (int mm = 0; mm < r; ++mm) x -= Fv[(int64_t)mm * dd.ld + r] * X[mm * VS + lane];
+                X[r * VS + lane] = x;
+            }
+        } else {
+            for (int k = 0; k < m && lane < V; ++k) {
+                const T *Uc = Fv + (int64_t)k * dd.ld;
+                T y = X[k * VS + lane];
+                for (int mm = 0; mm < k; ++mm) y -= Uc[mm] * X[mm * VS + lane];
+                X[k * VS + lane] = y * (T(1) / Uc[k]);
+            }
+        }
+    } else if (type == 0) {
         const int32_t *rp = lr_ptr + dd.doff + dd.I;
         const int32_t q0 = rp[0], nq = rp[m] - q0;
         const T *Lv;
@@ -780,7 +799,19 @@ k_panel_vec(const int32_t *__restrict__ task, BlockArgs a,
             __syncwarp();
             for (int r = 0; r < m && lane < V; ++r) {
                 T x = X[r * VS + lane];
-                for (int q = Rp[r]; q < Rp[r + 1]; ++q) x -= Lv[q] * X[Lc[q] * VS + lane];
+                int q = Rp[r];
+                const int qe = Rp[r + 1];
+                for (; q + 4 <= qe; q += 4) {         // loads first, then the chain
+                    T lv[4], xv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        lv[u] = Lv[q + u];
+                        xv[u] = X[Lc[q + u] * VS + lane];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) x -= lv[u] * xv[u];
+                }
+                for (; q < qe; ++q) x -= Lv[q] * X[Lc[q] * VS + lane];
                 X[r * VS + lane] = x;
             }
         } else {                                 // rows of L read in place
@@ -803,7 +834,18 @@ k_panel_vec(const int32_t *__restrict__ task, BlockArgs a,
             F.col(k, fo, fc, fr);
             const int dp = F.dp[k];
             T y = X[k * VS + lane];
-            for (int e = 0; e < dp; ++e) y -= F.v[fo + e] * X[fr[e] * VS + lane];
+            int e = 0;
+            for (; e + 4 <= dp; e += 4) {
+                T uv[4], xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    uv[u] = F.v[fo + e + u];
+                    xv[u] = X[fr[e + u] * VS + lane];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) y -= uv[u] * xv[u];
+            }
+            for (; e < dp; ++e) y -= F.v[fo + e] * X[fr[e] * VS + lane];
             X[k * VS + lane] = y * (T(1) / F.v[fo + dp]);
         }
     }

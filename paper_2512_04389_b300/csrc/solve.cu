@@ -621,11 +621,51 @@ k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
         const BlockView<T> F = stage_block<T>(dd, a, const_cast<T *>(val),
                                               smem + ybytes, kStageSmem - ybytes,
                                               true, &staged, &used);
-        __syncthreads();
-        const int32_t *sched = a.sched + dd.doff, *grp = a.sgrp + dd.goff;
         const int ng = dd.ngroups;
         const int64_t rb = dd.doff + dd.I;
         const bool asc = (MODE == FWD || MODE == FWD_T);
+        // the height schedule and (forward / backward) the row lists, staged
+        // behind the block when they fit; row pointers rebased to the slice
+        const int32_t *sched = a.sched + dd.doff, *grp = a.sgrp + dd.goff;
+        const int32_t *pp = MODE == FWD ? rl.lp : rl.up;
+        const uint16_t *pc = MODE == FWD ? rl.lc : rl.uc;
+        const int32_t *pq = MODE == FWD ? rl.lq : rl.uq;
+        int64_t pbase = rb;                      // pp index of row 0
+        {
+            unsigned char *lp = smem + ybytes + used;
+            const size_t lcap = kStageSmem - ybytes - used;
+            const bool rows = (MODE == FWD || MODE == BWD);
+            const int32_t q0 = rows ? pp[rb] : 0;
+            const int32_t nq = rows ? pp[rb + m] - q0 : 0;
+            const size_t need = align16((size_t)m * 4) + align16((size_t)(ng + 1) * 4) +
+                                (rows ? align16((size_t)(m + 1) * 4) + align16((size_t)nq * 2) +
+                                        align16((size_t)nq * 4) : 0);
+            if (need <= lcap) {
+                int32_t *ss = reinterpret_cast<int32_t *>(lp);
+                int32_t *sg = reinterpret_cast<int32_t *>(lp + align16((size_t)m * 4));
+                for (int t = threadIdx.x; t < m; t += kThreads) ss[t] = sched[t];
+                for (int t = threadIdx.x; t <= ng; t += kThreads) sg[t] = grp[t];
+                if (rows) {
+                    unsigned char *o = lp + align16((size_t)m * 4) + align16((size_t)(ng + 1) * 4);
+                    int32_t *sp = reinterpret_cast<int32_t *>(o);
+                    uint16_t *sc = reinterpret_cast<uint16_t *>(o + align16((size_t)(m + 1) * 4));
+                    int32_t *sq = reinterpret_cast<int32_t *>(o + align16((size_t)(m + 1) * 4) +
+                                                             align16((size_t)nq * 2));
+                    for (int t = threadIdx.x; t <= m; t += kThreads) sp[t] = pp[rb + t] - q0;
+                    for (int t = threadIdx.x; t < nq; t += kThreads) {
+                        sc[t] = pc[q0 + t];
+                        sq[t] = pq[q0 + t];
+                    }
+                    pp = sp;
+                    pc = sc;
+                    pq = sq;
+                    pbase = 0;
+                }
+                sched = ss;
+                grp = sg;
+            }
+        }
+        __syncthreads();
         for (int gi = 0; gi < ng; ++gi) {
             const int g = asc ? gi : ng - 1 - gi;
             for (int t = grp[g] + threadIdx.x; t < grp[g + 1]; t += kThreads) {
@@ -634,10 +674,7 @@ k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
 #pragma unroll
                 for (int c = 0; c < RC; ++c) acc[c] = y[r * RC + c];
                 if (MODE == FWD || MODE == BWD) {
-                    const int32_t *pp = MODE == FWD ? rl.lp : rl.up;
-                    const uint16_t *pc = MODE == FWD ? rl.lc : rl.uc;
-                    const int32_t *pq = MODE == FWD ? rl.lq : rl.uq;
-                    for (int q = pp[rb + r]; q < pp[rb + r + 1]; ++q) {
+                    for (int q = pp[pbase + r]; q < pp[pbase + r + 1]; ++q) {
                         const C v = (C)F.v[pq[q]];
                         const int mm = pc[q];
 #pragma unroll

@@ -58,6 +58,8 @@ CASES = [
     ("grid5_7 ragged", lambda: workloads.grid5(7), dict(b_min=3)),
     ("grid5_30 regular37", lambda: workloads.grid5(30),
      dict(blocking="regular", regular_block=37)),
+    ("grid5_48 regular400 all dense", lambda: workloads.grid5(48),
+     dict(blocking="regular", regular_block=400, dense_threshold=0.0)),
 ]
 
 
@@ -83,7 +85,7 @@ def test_fp64_factor_and_solve_parity(name, mk, opts):
     assert np.abs(Lam - Lo).max() / np.abs(Lo).max() <= 1e-10
 
 
-FP32_CASES = CASES[:1] + CASES[5:8] + [
+FP32_CASES = CASES[:1] + CASES[5:8] + CASES[-1:] + [
     ("circuit_20k", lambda: workloads.circuit_bbd(n=20_000, border=400),
      dict(dense_threshold=0.0)),
     ("grid7cd_14 all dense", lambda: workloads.grid7_cd(14, nrhs=4),
