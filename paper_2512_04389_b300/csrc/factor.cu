@@ -1,20 +1,25 @@
 // Numerical factorization on the GPU: the right-looking blocked LU of
 // Section 2.2 (Algorithm 1) over the plan's non-empty blocks, one level of
-// the block dependency DAG at a time.
-//
-// Per level three launches:
+// the block dependency DAG at a time.  Per level:
 //   GETRF  one CTA per diagonal block B_II -> L_II U_II (no row exchange;
-//          pivots in FP64; |pivot| < tau replaced by +-tau and counted);
-//   panel  one CTA per GESSM task  U_IJ = L_II^{-1} B_IJ
-//          and per TSTRF task      L_JI = B_JI U_II^{-1};
-//   SSSSM  one CTA per target block B_KJ, which gathers every source I of
-//          the level, B_KJ -= sum_I L_KI U_IJ, sources in ascending I, so the
-//          result is deterministic and needs no atomics.
-//
-// The kernels work column by column with one warp per column and a dense
-// per-warp accumulator in shared memory; a dense block is read as a block
-// whose every column holds all rows.  Closure of the pattern under fill
-// guarantees that every update lands on a stored slot.
+//          the pivot test in FP64; |pivot| < tau replaced by +-tau and
+//          counted): k_getrf_dense (dense storage, zero-skipping or
+//          one-barrier dense steps) or k_getrf (sparse storage);
+//   inverses of the dense diagonal factors (k_inv), used by the panels and
+//          by the solves;
+//   panels GESSM U_IJ = L_II^{-1} B_IJ and TSTRF L_JI = B_JI U_II^{-1}:
+//          products with the inverses (k_panel_inv), per-lane substitution
+//          for dense panels (k_panel_vec), height-group kernels for sparse
+//          panels of sparse diagonal blocks (k_panel_grp), a right-looking
+//          fallback (k_panel);
+//   SSSSM  B_KJ -= sum_I L_KI U_IJ over the level's sources in ascending I
+//          (deterministic, no atomics): dense tiles on the FP64 pipe
+//          (k_ssssm_gemm) or the tcgen05 tensor cores (k_ssssm_tc, FP32),
+//          the rest column by column (k_ssssm).  The updates the next level
+//          does not read run on a second stream, overlapping it.
+// Closure of the pattern under fill guarantees that every update lands on a
+// stored slot; entries outside the pattern of a dense block are exact zeros
+// and stay zero.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -455,11 +460,10 @@ k_getrf_dense(const int32_t *__restrict__ ids, const BlockDesc *__restrict__ bd,
                    kStageSmem);
 }
 
-// GETRF on diagonal blocks.  Columns run in height groups of the block's
-// own column DAG; inside a group one warp per column performs the
-// left-looking update x = B(:,jj); for m in struct U(:,jj) ascending:
-// x(rows of L(:,m)) -= L(:,m) x(m); then U(:,jj) = x(<= jj),
-// L(:,jj) = x(> jj) / pivot.  Accumulation is FP64 for every storage type.
+// GETRF on sparse-stored diagonal blocks, one CTA per block: by height
+// groups (getrf_sparse_groups) when the block's column DAG has on average
+// at least four columns per height, else right-looking step by step.
+// Arithmetic in the storage type; the pivot test and perturbation in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_getrf(const int32_t *__restrict__ ids, BlockArgs a, T *__restrict__ val,

@@ -5,11 +5,15 @@
 //
 // Every solve walks the levels of the block dependency DAG (the same levels
 // as the factorization): a level's diagonal blocks have no block coupling
-// among themselves, so one CTA per diagonal block of the level
-//   1. pulls the contributions of already solved blocks into its rows
-//      (per-warp partial sums reduced in a fixed order: deterministic), then
-//   2. solves with its diagonal block.
-// Arithmetic is FP64 whatever the storage type of the factors.
+// among themselves, so per level
+//   1. the contributions of already solved blocks are pulled into partial
+//      sums, one CTA per source block and row chunk (reduced later in a
+//      fixed order: deterministic), then
+//   2. each diagonal block is solved: a cluster of CTAs per dense block with
+//      explicit inverses, one CTA per sparse block (by height groups).
+// Sweep arithmetic is in the storage type of the factors; residuals, norms
+// and the refinement update are FP64.  The sweeps of one solve are
+// recorded once per right-hand-side count as a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
