@@ -61,7 +61,10 @@ typedef enum {
 typedef enum {
     SLU_PREC_FP64 = 0,           /* factors stored and computed in FP64     */
     SLU_PREC_FP32 = 1            /* factors in FP32 (diagonal-block pivots
-                                    in FP64), solves refined in FP64        */
+                                    tested in FP64; dense Schur tiles on the
+                                    tensor cores as split-precision 3xTF32
+                                    with FP32 accumulation), solves refined
+                                    in FP64                                 */
 } slu_precision;
 
 typedef struct {
@@ -82,7 +85,8 @@ typedef struct {
     double refine_tol;           /* stop when backward error <= this        */
     int32_t refine_max_iter;     /* < 0 never refine; 0 = default (none for
                                     FP64, 30 for FP32); > 0 that many       */
-    int64_t wait_budget_ms;      /* bound on any device-side wait           */
+    int64_t wait_budget_ms;      /* reserved: device-side waits are bounded
+                                    by a fixed poll count instead           */
 } slu_opts;
 
 typedef struct {
@@ -203,6 +207,8 @@ slu_status slu_plan_export_tasks(const slu_plan *plan, int64_t *getrf_off,
  * `stream`.  The call synchronizes the stream before returning (it reads
  * the perturbation count), so *info is final.  *out receives a new handle;
  * with SLU_ERR_SINGULAR a handle is still returned (factors not usable).
+ * SLU_ERR_TIMEOUT reports that a tensor-core tile's bounded wait for its own
+ * MMAs ran out (that tile's update was skipped; factors not usable).
  * The handle owns a second, non-blocking stream: each level's Schur updates
  * whose target lies outside the next level's block rows and columns run
  * there, forked from `stream` after the level's panels and joined back
@@ -232,7 +238,11 @@ slu_status slu_set_graph(slu_handle *h, int32_t enable);
  * holding the last iterate) if it stops at the iteration limit.  A non-NULL
  * info also makes an unrefined solve compute the backward error (one
  * residual, synchronizing).  Refinement and info use a workspace that the
- * handle allocates on first use. */
+ * handle allocates on first use.  The level sweeps run as a CUDA graph that
+ * the handle records (on a private stream, over a vector buffer it
+ * allocates) the first time a right-hand-side count is solved and replays
+ * on `stream` afterwards; with profiling enabled they are launched
+ * directly. */
 slu_status slu_solve(const slu_handle *h, const double *B, int64_t ldb,
                      int32_t nrhs, double *X, int64_t ldx, void *stream,
                      slu_solve_info *info);
