@@ -218,6 +218,20 @@ def recorded_traffic(kernel, workload, launches):
     return None
 
 
+def host_cpu():
+    """Model name and logical core count of the host."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def cpu_oracle_leg(m=32):
     """The oracle as it stands on a bounded sample of the same workload
     family (grid7_cd(m), same generator, seed 0, 4 RHS), one core."""
@@ -229,7 +243,7 @@ def cpu_oracle_leg(m=32):
     dt = time.perf_counter() - t
     fl = OL.flops(F) + 2 * (len(F["Li"]) + len(F["Ui"])) * s.nrhs
     return {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": 1,
-            "kind": "oracle",
+            "kind": "oracle", "host": host_cpu(),
             "sample": f"grid7cd_{m} (n={s.n}, same generator, 4 RHS): "
                       f"factor+solve {dt:.2f} s on 1 host core"}
 
@@ -378,7 +392,7 @@ def run_reference(args):
         "config": {"workload": f"grid7cd_{m} sample of {WORKLOAD}",
                    "host_cores": os.cpu_count()},
         "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1,
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": sample, "host": host_cpu()},
         "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
     return 0
@@ -429,6 +443,8 @@ def main():
         return 0
 
     X, sinfo = F.solve(rhs_d, info=True)
+    ms_factor = timed(torch, lambda: F.refactor(vals_d), args.steps, 1)
+    ms_solve = timed(torch, lambda: F.solve(rhs_d), args.steps, 1)
     metric = METRIC if args.precision == "fp64" else METRIC.replace(
         "FP64,", "FP32 factors + FP64 refinement,")
     out = {"metric": metric, "value": value, "unit": "GFLOP/s",
@@ -442,6 +458,7 @@ def main():
                       "blocks_1d": plan.info["nblocks_1d"],
                       "levels": plan.info["nlevels"],
                       "analyze_ms": plan.info["analyze_ms"],
+                      "factor_ms": ms_factor, "solve_ms": ms_solve,
                       "tuned": best64, "tuning_ms": tun64,
                       "backward_error": sinfo["backward_error"],
                       "l2": "no flush: factors (340 MB) exceed L2",
@@ -483,6 +500,8 @@ def main():
         "unit": "TFLOP/s", "frac": ach / peak,
         "traffic": recorded_traffic(names[dom], args.workload, calls[dom]),
         "peak_source": peak_src,
+        "frac_by_class": {k: fcls[k] / (cls_ms[k] * 1e-3) / 1e12 / peak
+                          for k in ("getrf", "panel", "ssssm") if cls_ms[k] > 0},
         "ms_per_step_by_class": cls_ms,
         "flops_per_step_by_class": fcls,
         "launches_per_step_by_class": calls}
@@ -520,6 +539,24 @@ def main():
                                      "gflops": fl / (msr * 1e-3) / 1e9,
                                      "levels": preg.info["nlevels"]}
         del Freg
+        # best regular size (threshold 0, the tuned choice above) against
+        # the tuned irregular blocking
+        sweep = {}
+        for rb in (64, 256, 512):
+            pr = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular",
+                        regular_block=rb, dense_threshold=0.0)
+            Fr = S.Factor(pr, vals_d)
+
+            def stepr():
+                Fr.refactor(vals_d)
+                Fr.solve(rhs_d)
+            sweep[str(rb)] = timed(torch, stepr, 2, 1)
+            del Fr, pr
+        sweep["128"] = msr
+        best_rb = min(sweep, key=sweep.get)
+        extras["regular_best_fp64"] = {"ms_per_step_by_block": sweep,
+                                       "best_block": int(best_rb),
+                                       "best_ms": sweep[best_rb]}
         bestr32, _ = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
                           precision="fp32", blocking="regular", regular_block=128)
         preg32 = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular",
