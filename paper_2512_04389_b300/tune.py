@@ -2,9 +2,11 @@
 
 The paper runs each block with a sparse kernel or a dense routine chosen by
 the block's density (Section 1), and Algorithm 3 sizes the irregular blocks
-from sampling parameters (the number of sample steps merged into one block
-is bounded by ``max_num``).  Which density threshold and which block-size
-bound pay off depends on the precision, the pattern and the GPU, so
+from sampling parameters: the number of samples S (``sample_points``,
+capped at n / ``b_min``) sets the finest block n / S, and ``max_num``
+bounds how many sample steps one block may merge.  Which density threshold
+and which block sizes pay off depends on the precision, the pattern and the
+GPU, so
 ``tune`` factors and solves the given system once per candidate and keeps
 the fastest, timing with CUDA events on the current stream.  Results are
 cached in a JSON file (path from the ``SLU_TUNE_CACHE`` environment
@@ -24,15 +26,31 @@ from . import slu as S
 
 THRESHOLDS = (0.0, 0.3)
 MAX_NUM = (3, 2, 1)
+SAMPLE_POINTS = (1000, 2000)
+B_MIN = (32, 8)
 
 
-def candidates(blocking="irregular"):
-    """Plan options tried by default: thresholds x Algorithm 3 block-size
-    bounds for irregular blocking, thresholds alone for regular blocking."""
+def candidates(blocking="irregular", n=None):
+    """Plan options tried by default.  Regular blocking: the thresholds.
+    Irregular blocking: threshold 0 with every (sample_points, b_min,
+    max_num), plus threshold 0.3 with the paper's defaults; candidates whose
+    effective sample count S = min(sample_points, n / b_min) coincides are
+    tried once (their plans are identical)."""
     if blocking == "regular":
         return [{"dense_threshold": t} for t in THRESHOLDS]
-    return [{"dense_threshold": t, "max_num": m} for m in MAX_NUM
-            for t in THRESHOLDS]
+    out, seen = [], set()
+    for sp in SAMPLE_POINTS:
+        for bm in B_MIN:
+            for m in MAX_NUM:
+                eff = min(sp, n // bm) if n else (sp, bm)
+                if (eff, m) in seen:
+                    continue
+                seen.add((eff, m))
+                out.append({"dense_threshold": 0.0, "sample_points": sp,
+                            "b_min": bm, "max_num": m})
+    out.append({"dense_threshold": 0.3, "sample_points": 1000, "b_min": 32,
+                "max_num": 3})
+    return out
 
 
 def _key(n, colptr, rowidx, opts):
@@ -76,7 +94,7 @@ def tune(n, colptr, rowidx, values, rhs, cands=None, reps=2, use_cache=True,
     blocking, ...)."""
     import torch
     if cands is None:
-        cands = candidates(opts.get("blocking", "irregular"))
+        cands = candidates(opts.get("blocking", "irregular"), n)
     key = _key(n, colptr, rowidx, dict(opts, cands=cands))
     cache = _load() if use_cache else {}
     if key in cache:

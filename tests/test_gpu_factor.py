@@ -274,8 +274,8 @@ def test_autotuner_picks_a_candidate_and_caches(tmp_path, monkeypatch):
     s = workloads.grid5(32)
     best, timings = T.tune(s.n, s.colptr, s.rowidx, _dev(s.values),
                            _dev(s.rhs), precision="fp32")
-    assert best in T.candidates("irregular")
-    assert len(timings) == len(T.candidates("irregular"))
+    assert best in T.candidates("irregular", s.n)
+    assert len(timings) == len(T.candidates("irregular", s.n))
     again, t2 = T.tune(s.n, s.colptr, s.rowidx, _dev(s.values), _dev(s.rhs),
                        precision="fp32")
     assert again == best and t2 == timings          # served from the cache
