@@ -272,16 +272,16 @@ def circuit_bbd(n=200_000, border=4_000, seed=0, nrhs=8, block_lo=32,
     expected degrees w ~ Zipf(zipf_a) rescaled to mean ``mean_deg`` and capped
     at size-1; each unordered pair (a, b) is an edge with probability
     min(1, w_a w_b / sum w) (Chung-Lu); the subcircuit is ordered by ascending
-    w (hubs last, stable).  Border: node t links to ``border_frac`` of all n
-    nodes (distinct, self excluded), symmetric.  Off-diagonal magnitudes are
+    w (hubs last, stable).  Border: node t links to each of the n nodes
+    independently with probability ``border_frac`` (about 5% of all nodes;
+    self excluded), symmetric.  Off-diagonal magnitudes are
     log-uniform on [1e-3, 1] with a random sign; diagonal = row sum of
     |off-diagonals| x U(1.05, 2).
 
     Draw order: block sizes; per block: Zipf draws, pair coin flips; border
-    targets, one border node at a time; magnitudes, signs (both for the
-    directed entries in sorted (col, row) order); diagonal factors; RHS.
-    Border coin flips are drawn for 64 border nodes at a time, each a
-    64 x n block of U(0, 1) in row-major order.
+    coin flips, 64 border nodes at a time, each a 64 x n block of U(0, 1) in
+    row-major order; magnitudes, signs (both for the stored off-diagonal
+    entries in sorted (col, row) order); diagonal factors; RHS.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     nb = n - border
