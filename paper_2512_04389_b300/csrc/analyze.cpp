@@ -39,34 +39,27 @@ struct Sym {                      // symmetric pattern with diagonal
     std::vector<int32_t> i;
 };
 
-void symmetrize(int64_t n, const int64_t *cp, const int32_t *ri, Sym &S) {
-    std::vector<int64_t> cnt(n + 1, 0);
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
-            const int32_t r = ri[q];
-            cnt[j + 1]++;                       // (r, j)
-            if (r != j) cnt[r + 1]++;           // (j, r)
-        }
-    for (int64_t j = 0; j < n; ++j) cnt[j + 1] += 1;   // diagonal
-    for (int64_t j = 0; j < n; ++j) cnt[j + 1] += cnt[j];
-    std::vector<int32_t> tmp(cnt[n]);
-    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
-    for (int64_t j = 0; j < n; ++j) {
-        for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
-            const int32_t r = ri[q];
-            tmp[fill[j]++] = r;
-            if (r != j) tmp[fill[r]++] = (int32_t)j;
-        }
-        tmp[fill[j]++] = (int32_t)j;
-    }
+// pattern(A + A^T) plus the full diagonal, every column sorted.  Inputs:
+// A's columns with rows ascending (ap, ai) and A's rows with columns
+// ascending (rp, rc, the CSR view); column j of the result is the union of
+// A(:, j), A(j, :) and {j}, merged without sorting.
+void symmetrize(int64_t n, const int64_t *ap, const int32_t *ai,
+                const int64_t *rp, const int32_t *rc, Sym &S) {
     S.p.assign(n + 1, 0);
     S.i.clear();
-    S.i.reserve(cnt[n]);
+    S.i.reserve((size_t)(2 * ap[n] + n));
+    std::vector<int32_t> t;
     for (int64_t j = 0; j < n; ++j) {
-        auto b = tmp.begin() + cnt[j], e = tmp.begin() + cnt[j + 1];
-        std::sort(b, e);
-        auto u = std::unique(b, e);
-        S.i.insert(S.i.end(), b, u);
+        const int32_t *a0 = ai + ap[j], *a1 = ai + ap[j + 1];
+        const int32_t *r0 = rc + rp[j], *r1 = rc + rp[j + 1];
+        t.resize((size_t)((a1 - a0) + (r1 - r0)));
+        auto e = std::set_union(a0, a1, r0, r1, t.begin());
+        t.resize((size_t)(e - t.begin()));
+        // insert the diagonal in order
+        auto d = std::lower_bound(t.begin(), t.end(), (int32_t)j);
+        S.i.insert(S.i.end(), t.begin(), d);
+        if (d == t.end() || *d != (int32_t)j) S.i.push_back((int32_t)j);
+        S.i.insert(S.i.end(), d, t.end());
         S.p[j + 1] = (int64_t)S.i.size();
     }
 }
@@ -94,7 +87,10 @@ void etree(int64_t n, const Sym &S, std::vector<int32_t> &parent) {
 }
 
 // struct L(:,j) (strictly lower, sorted), columns in increasing order so
-// that children (always < parent) are complete before their parent.
+// that children (always < parent) are complete before their parent:
+// struct L(:,j) = rows > j of S(:,j) united with struct L(:,c) minus {j} for
+// every child c.  Every list involved is sorted, so the union is built by
+// merging (linear in the sizes, no sort).
 void symbolic(int64_t n, const Sym &S, const std::vector<int32_t> &par,
               std::vector<int64_t> &Lp, std::vector<int32_t> &Li) {
     std::vector<int64_t> chp(n + 1, 0);
@@ -107,25 +103,26 @@ void symbolic(int64_t n, const Sym &S, const std::vector<int32_t> &par,
         for (int64_t j = 0; j < n; ++j)
             if (par[j] >= 0) ch[f[par[j]]++] = (int32_t)j;
     }
-    std::vector<int64_t> mark(n, -1);
     Lp.assign(n + 1, 0);
     Li.clear();
-    std::vector<int32_t> col;
+    std::vector<int32_t> col, tmp;
     for (int64_t j = 0; j < n; ++j) {
         col.clear();
-        mark[j] = j;
-        for (int64_t q = S.p[j]; q < S.p[j + 1]; ++q) {
-            const int32_t r = S.i[q];
-            if (r > j && mark[r] != j) { mark[r] = j; col.push_back(r); }
+        {
+            const int32_t *b = S.i.data() + S.p[j], *e = S.i.data() + S.p[j + 1];
+            b = std::upper_bound(b, e, (int32_t)j);      // rows sorted
+            col.assign(b, e);
         }
         for (int64_t c = chp[j]; c < chp[j + 1]; ++c) {
             const int32_t k = ch[c];
-            for (int64_t q = Lp[k]; q < Lp[k + 1]; ++q) {
-                const int32_t r = Li[q];
-                if (mark[r] != j) { mark[r] = j; col.push_back(r); }
-            }
+            const int32_t *b = Li.data() + Lp[k], *e = Li.data() + Lp[k + 1];
+            b = std::upper_bound(b, e, (int32_t)j);      // drop j itself
+            if (b == e) continue;
+            tmp.resize(col.size() + (size_t)(e - b));
+            auto end = std::set_union(col.begin(), col.end(), b, e, tmp.begin());
+            tmp.resize((size_t)(end - tmp.begin()));
+            col.swap(tmp);
         }
-        std::sort(col.begin(), col.end());
         Li.insert(Li.end(), col.begin(), col.end());
         Lp[j + 1] = (int64_t)Li.size();
     }
@@ -830,11 +827,28 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
                     P->a_vpos[at] = q;
                 }
         }
+        // A's columns with rows ascending and their input positions: the
+        // transpose of the CSR view, taken in row order
+        std::vector<int64_t> sp(n + 1, 0);
+        std::vector<int32_t> si(nnz);
+        std::vector<int64_t> sq(nnz);
+        {
+            for (int64_t q = 0; q < nnz; ++q) sp[P->a_colidx[q] + 1]++;
+            for (int64_t j = 0; j < n; ++j) sp[j + 1] += sp[j];
+            std::vector<int64_t> f(sp.begin(), sp.end() - 1);
+            for (int64_t r = 0; r < n; ++r)
+                for (int64_t t = P->a_rowptr[r]; t < P->a_rowptr[r + 1]; ++t) {
+                    const int64_t at = f[P->a_colidx[t]]++;
+                    si[at] = (int32_t)r;
+                    sq[at] = P->a_vpos[t];
+                }
+        }
         std::vector<int64_t> Lp;
         std::vector<int32_t> Li;
         {
             Sym S;
-            symmetrize(n, colptr, rowidx, S);
+            symmetrize(n, sp.data(), si.data(), P->a_rowptr.data(),
+                       P->a_colidx.data(), S);
             P->nnz_sym = S.p[n];
             std::vector<int32_t> parent;
             etree(n, S, parent);
@@ -923,14 +937,14 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
             P->flops_cls[1] += lout + 4 * lin * lout;
             P->flops_cls[2] += 2 * lout * lout;
         }
-        // A entry -> storage slot, through the filled pattern
+        // A entry -> storage slot, through the filled pattern: both columns
+        // are sorted by row, so one walk per column finds every position
         P->a2s.resize(nnz);
         for (int64_t j = 0; j < n; ++j) {
-            const int32_t *b = P->f_rowidx.data() + P->f_colptr[j];
-            const int32_t *e = P->f_rowidx.data() + P->f_colptr[j + 1];
-            for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
-                const int32_t *it = std::lower_bound(b, e, rowidx[q]);
-                P->a2s[q] = P->f2s[P->f_colptr[j] + (it - b)];
+            int64_t f = P->f_colptr[j];
+            for (int64_t t = sp[j]; t < sp[j + 1]; ++t) {
+                while (P->f_rowidx[f] < si[t]) ++f;
+                P->a2s[sq[t]] = P->f2s[f];
             }
         }
     } catch (const std::bad_alloc &) {
