@@ -18,6 +18,8 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <thread>
+#include <vector>
 
 #include "slu_internal.hpp"
 
@@ -33,6 +35,72 @@ slu_status fail(slu_status st, const std::string &msg) {
 }
 
 namespace {
+
+// Worker threads for the host passes over the pattern: up to the hardware
+// concurrency (16 at most), fewer when the per-thread count arrays of a
+// transpose (threads x destinations) would get large.
+int host_threads(int64_t ndst) {
+    int64_t t = std::max(1u, std::thread::hardware_concurrency());
+    t = std::min<int64_t>(t, 16);
+    t = std::min<int64_t>(t, std::max<int64_t>(1, ((int64_t)1 << 26) / std::max<int64_t>(ndst, 1)));
+    return (int)t;
+}
+
+// Runs f(t) for t in [0, nt) on nt threads (the calling thread takes t = 0).
+template <class F>
+void run_threads(int nt, F f) {
+    if (nt <= 1) {
+        f(0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(nt - 1);
+    for (int t = 1; t < nt; ++t) th.emplace_back(f, t);
+    f(0);
+    for (auto &x : th) x.join();
+}
+
+// Stable transpose of a compressed pattern: source columns c in [0, nsrc)
+// with entries e in [sp[c], sp[c+1]), each sent to destination dst(e) in
+// [0, ndst).  A destination receives its entries in source order (c
+// ascending, then e), exactly as a sequential counting sort would.
+// total(d) receives each destination's count; base(d), called afterwards,
+// must return the destination's first output slot; emit(slot, c, e) stores
+// an entry.  Threads take contiguous source ranges balanced by entries.
+template <class Dst, class Total, class Base, class Emit>
+void stable_transpose(int64_t nsrc, const int64_t *sp, int64_t ndst, Dst dst,
+                      Total total, Base base, Emit emit) {
+    const int nt = host_threads(ndst);
+    std::vector<int64_t> cut(nt + 1, nsrc);
+    cut[0] = 0;
+    for (int t = 1; t < nt; ++t)
+        cut[t] = std::upper_bound(sp, sp + nsrc + 1, sp[nsrc] * t / nt) - sp - 1;
+    for (int t = 1; t <= nt; ++t) cut[t] = std::max(cut[t], cut[t - 1]);
+    std::vector<std::vector<int64_t>> cnt(nt);
+    run_threads(nt, [&](int t) {
+        cnt[t].assign(ndst, 0);
+        for (int64_t c = cut[t]; c < cut[t + 1]; ++c)
+            for (int64_t e = sp[c]; e < sp[c + 1]; ++e) cnt[t][dst(e)]++;
+    });
+    for (int64_t d = 0; d < ndst; ++d) {
+        int64_t sum = 0;
+        for (int t = 0; t < nt; ++t) sum += cnt[t][d];
+        total(d, sum);
+    }
+    for (int64_t d = 0; d < ndst; ++d) {       // counts become start slots
+        int64_t at = base(d);
+        for (int t = 0; t < nt; ++t) {
+            const int64_t c = cnt[t][d];
+            cnt[t][d] = at;
+            at += c;
+        }
+    }
+    run_threads(nt, [&](int t) {
+        std::vector<int64_t> &f = cnt[t];
+        for (int64_t c = cut[t]; c < cut[t + 1]; ++c)
+            for (int64_t e = sp[c]; e < sp[c + 1]; ++e) emit(f[dst(e)]++, c, e);
+    });
+}
 
 struct Sym {                      // symmetric pattern with diagonal
     std::vector<int64_t> p;
@@ -812,37 +880,39 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         P->a_ci.resize(nnz);
         for (int64_t j = 0; j < n; ++j)
             for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) P->a_ci[q] = (int32_t)j;
-        // CSR view of A for the residual
+        // CSR view of A for the residual (columns ascending in every row)
         P->a_rowptr.assign(n + 1, 0);
-        for (int64_t q = 0; q < nnz; ++q) P->a_rowptr[rowidx[q] + 1]++;
-        for (int64_t i = 0; i < n; ++i) P->a_rowptr[i + 1] += P->a_rowptr[i];
         P->a_colidx.resize(nnz);
         P->a_vpos.resize(nnz);
-        {
-            std::vector<int64_t> f(P->a_rowptr.begin(), P->a_rowptr.end() - 1);
-            for (int64_t j = 0; j < n; ++j)
-                for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
-                    const int64_t at = f[rowidx[q]]++;
-                    P->a_colidx[at] = (int32_t)j;
-                    P->a_vpos[at] = q;
-                }
-        }
+        stable_transpose(
+            n, colptr, n, [&](int64_t q) { return rowidx[q]; },
+            [&](int64_t r, int64_t c) { P->a_rowptr[r + 1] = c; },
+            [&](int64_t r) {
+                if (r == 0)
+                    for (int64_t i = 0; i < n; ++i) P->a_rowptr[i + 1] += P->a_rowptr[i];
+                return P->a_rowptr[r];
+            },
+            [&](int64_t at, int64_t j, int64_t q) {
+                P->a_colidx[at] = (int32_t)j;
+                P->a_vpos[at] = q;
+            });
         // A's columns with rows ascending and their input positions: the
         // transpose of the CSR view, taken in row order
         std::vector<int64_t> sp(n + 1, 0);
         std::vector<int32_t> si(nnz);
         std::vector<int64_t> sq(nnz);
-        {
-            for (int64_t q = 0; q < nnz; ++q) sp[P->a_colidx[q] + 1]++;
-            for (int64_t j = 0; j < n; ++j) sp[j + 1] += sp[j];
-            std::vector<int64_t> f(sp.begin(), sp.end() - 1);
-            for (int64_t r = 0; r < n; ++r)
-                for (int64_t t = P->a_rowptr[r]; t < P->a_rowptr[r + 1]; ++t) {
-                    const int64_t at = f[P->a_colidx[t]]++;
-                    si[at] = (int32_t)r;
-                    sq[at] = P->a_vpos[t];
-                }
-        }
+        stable_transpose(
+            n, P->a_rowptr.data(), n, [&](int64_t t) { return P->a_colidx[t]; },
+            [&](int64_t j, int64_t c) { sp[j + 1] = c; },
+            [&](int64_t j) {
+                if (j == 0)
+                    for (int64_t i = 0; i < n; ++i) sp[i + 1] += sp[i];
+                return sp[j];
+            },
+            [&](int64_t at, int64_t r, int64_t t) {
+                si[at] = (int32_t)r;
+                sq[at] = P->a_vpos[t];
+            });
         std::vector<int64_t> Lp;
         std::vector<int32_t> Li;
         {
@@ -856,24 +926,28 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         }
         // filled L+U pattern: column j = U rows (k < j with j in L(:,k),
         // ascending), the diagonal j, then L rows (ascending)
-        std::vector<int64_t> ucnt(n + 1, 0);
-        for (int64_t q = 0; q < Lp[n]; ++q) ucnt[Li[q] + 1]++;
+        std::vector<int64_t> ucnt(n, 0);
         P->f_colptr.assign(n + 1, 0);
-        for (int64_t j = 0; j < n; ++j)
-            P->f_colptr[j + 1] =
-                P->f_colptr[j] + ucnt[j + 1] + 1 + (Lp[j + 1] - Lp[j]);
-        P->f_rowidx.resize(P->f_colptr[n]);
-        {
-            std::vector<int64_t> f(P->f_colptr.begin(), P->f_colptr.end() - 1);
-            for (int64_t k = 0; k < n; ++k)
-                for (int64_t q = Lp[k]; q < Lp[k + 1]; ++q)
-                    P->f_rowidx[f[Li[q]]++] = (int32_t)k;
-            for (int64_t j = 0; j < n; ++j) {
-                P->f_rowidx[f[j]++] = (int32_t)j;
-                for (int64_t q = Lp[j]; q < Lp[j + 1]; ++q)
-                    P->f_rowidx[f[j]++] = Li[q];
+        stable_transpose(
+            n, Lp.data(), n, [&](int64_t q) { return Li[q]; },
+            [&](int64_t j, int64_t c) { ucnt[j] = c; },
+            [&](int64_t j) {
+                if (j == 0) {
+                    for (int64_t i = 0; i < n; ++i)
+                        P->f_colptr[i + 1] = P->f_colptr[i] + ucnt[i] + 1 + (Lp[i + 1] - Lp[i]);
+                    P->f_rowidx.resize(P->f_colptr[n]);
+                }
+                return P->f_colptr[j];
+            },
+            [&](int64_t at, int64_t k, int64_t) { P->f_rowidx[at] = (int32_t)k; });
+        run_threads(host_threads(0), [&](int t) {
+            const int nt = host_threads(0);
+            for (int64_t j = t; j < n; j += nt) {
+                int64_t f = P->f_colptr[j] + ucnt[j];
+                P->f_rowidx[f++] = (int32_t)j;
+                for (int64_t q = Lp[j]; q < Lp[j + 1]; ++q) P->f_rowidx[f++] = Li[q];
             }
-        }
+        });
         // flops = sum_k (l_k + 2 l_k u_k); by symmetry u_k = l_k
         P->flops = 0;
         for (int64_t k = 0; k < n; ++k) {
