@@ -42,6 +42,49 @@ CASES = [
 @pytest.mark.parametrize("name,mk,opts", CASES, ids=[c[0] for c in CASES])
 def test_plan_bit_exact(name, mk, opts):
     s = mk()
+    _check_plan(s, opts)
+
+
+class _Sys:
+    def __init__(self, n, colptr, rowidx, values):
+        self.n, self.colptr, self.rowidx, self.values = n, colptr, rowidx, values
+
+
+def _random_system(n, density, seed):
+    """Random nonsymmetric pattern (each off-diagonal entry drawn on its
+    own), rows listed in random order inside every column, diagonally
+    dominant values."""
+    rng = np.random.default_rng(seed)
+    M = rng.random((n, n)) < density
+    np.fill_diagonal(M, True)
+    V = np.where(M, rng.uniform(-1, 1, (n, n)), 0.0)
+    np.fill_diagonal(V, np.abs(V).sum(1) + 1.0)
+    colptr = np.zeros(n + 1, np.int64)
+    rows, vals = [], []
+    for j in range(n):
+        r = np.nonzero(M[:, j])[0]
+        r = r[rng.permutation(r.size)]
+        rows.append(r)
+        vals.append(V[r, j])
+        colptr[j + 1] = colptr[j] + r.size
+    return _Sys(n, colptr, np.concatenate(rows).astype(np.int32),
+                np.concatenate(vals))
+
+
+@pytest.mark.parametrize("n,density,seed,opts", [
+    (60, 0.05, 1, dict(b_min=4)),
+    (150, 0.02, 2, dict(b_min=8, max_num=1)),
+    (150, 0.02, 3, dict(blocking="regular", regular_block=17)),
+    (300, 0.01, 4, dict(b_min=8, sample_points=100, step=1)),
+    (300, 0.01, 5, dict(b_min=16, dense_threshold=0.0)),
+])
+def test_plan_bit_exact_random_unsorted(n, density, seed, opts):
+    """Random nonsymmetric patterns with unsorted rows: the library's
+    symmetrisation, symbolic factorization and plan match the oracle's."""
+    _check_plan(_random_system(n, density, seed), opts)
+
+
+def _check_plan(s, opts):
     P = S.Plan(s.n, s.colptr, s.rowidx, **opts)
     o = S.default_opts(**opts)
     F = OL.lu(s.n, s.colptr, s.rowidx, s.values)
