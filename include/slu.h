@@ -149,7 +149,15 @@ void slu_opts_default(slu_opts *opts);
 
 /* Host-only analysis (Sections 4.2-4.3, Algorithms 2 and 3; Algorithm 1's
  * block task lists).  colptr/rowidx: host, CSC of A's pattern (n x n).
- * opts: host, NULL for defaults.  *out receives a new plan on success. */
+ * opts: host, NULL for defaults.  *out receives a new plan on success;
+ * the caller keeps ownership of the arrays, which the plan copies.
+ * Errors: SLU_ERR_INVALID_ARG for n outside [0, 2^31 - 2], a NULL array,
+ * colptr[0] != 0, a decreasing colptr, a row index outside [0, n), a
+ * repeated (row, column) entry or a bad option; SLU_ERR_NOT_SUPPORTED for
+ * a blocking the kernels cannot take (a block over 65535 rows, or sparse
+ * blocks whose column or row index lists pass 2^31 entries);
+ * SLU_ERR_OUT_OF_MEMORY when a host allocation fails.  *out is NULL on any
+ * error and slu_last_error() says which check failed. */
 slu_status slu_analyze(int64_t n, const int64_t *colptr, const int32_t *rowidx,
                        const slu_opts *opts, slu_plan **out);
 
@@ -162,7 +170,10 @@ slu_status slu_analyze(int64_t n, const int64_t *colptr, const int32_t *rowidx,
  * solutions of the batch plan are the members' concatenated in order
  * (values: member 0's CSC values, then member 1's, ...; rows likewise).
  * Refinement measures the backward error of every member separately and
- * stops when the largest is <= refine_tol. */
+ * stops when the largest is <= refine_tol.  Every member is checked as
+ * slu_analyze checks its pattern, and its colptr before any of its row
+ * indices is read; count < 1, a NULL n, colptr or rowidx array, or a total
+ * order above 2^31 - 2 is SLU_ERR_INVALID_ARG. */
 slu_status slu_analyze_batch(int32_t count, const int64_t *n,
                              const int64_t *const *colptr,
                              const int32_t *const *rowidx,

@@ -16,8 +16,10 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <numeric>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -46,18 +48,39 @@ int host_threads(int64_t ndst) {
     return (int)t;
 }
 
-// Runs f(t) for t in [0, nt) on nt threads (the calling thread takes t = 0).
+// Runs f(t) for t in [0, nt) on nt threads (the calling thread takes t = 0
+// and every t whose thread could not be started).  Each t works on its own
+// slice, so the result does not depend on which thread ran it.  An exception
+// thrown by f is rethrown here after every thread has joined.
 template <class F>
 void run_threads(int nt, F f) {
     if (nt <= 1) {
         f(0);
         return;
     }
+    std::vector<std::exception_ptr> err(nt);
+    auto body = [&](int t) {
+        try {
+            f(t);
+        } catch (...) {
+            err[t] = std::current_exception();
+        }
+    };
     std::vector<std::thread> th;
     th.reserve(nt - 1);
-    for (int t = 1; t < nt; ++t) th.emplace_back(f, t);
-    f(0);
+    int started = 1;
+    for (; started < nt; ++started) {
+        try {
+            th.emplace_back(body, started);
+        } catch (const std::system_error &) {
+            break;
+        }
+    }
+    for (int t = started; t < nt; ++t) body(t);
+    body(0);
     for (auto &x : th) x.join();
+    for (auto &e : err)
+        if (e) std::rethrow_exception(e);
 }
 
 // Stable transpose of a compressed pattern: source columns c in [0, nsrc)
@@ -857,7 +880,7 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         if (colptr[j + 1] < colptr[j])
             return fail(SLU_ERR_INVALID_ARG, "colptr not monotone");
     const int64_t nnz = colptr[n];
-    {
+    try {
         std::vector<int64_t> seen(n, -1);
         for (int64_t j = 0; j < n; ++j)
             for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
@@ -868,6 +891,8 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
                     return fail(SLU_ERR_INVALID_ARG, "duplicate entry");
                 seen[r] = j;
             }
+    } catch (const std::exception &) {
+        return fail(SLU_ERR_OUT_OF_MEMORY, "host allocation in analyze");
     }
     slu_plan *P = new (std::nothrow) slu_plan();
     if (!P) return fail(SLU_ERR_OUT_OF_MEMORY, "plan allocation");
@@ -1021,9 +1046,10 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
                 P->a2s[sq[t]] = P->f2s[f];
             }
         }
-    } catch (const std::bad_alloc &) {
+    } catch (const std::exception &e) {
         delete P;
-        return fail(SLU_ERR_OUT_OF_MEMORY, "host allocation in analyze");
+        return fail(SLU_ERR_OUT_OF_MEMORY,
+                    std::string("host allocation in analyze: ") + e.what());
     }
     P->analyze_ms = std::chrono::duration<double, std::milli>(
                         std::chrono::steady_clock::now() - t0).count();
@@ -1046,19 +1072,37 @@ extern "C" slu_status slu_analyze_batch(int32_t count, const int64_t *n,
     *out = nullptr;
     if (count < 1 || !n || !colptr || !rowidx)
         return fail(SLU_ERR_INVALID_ARG, "bad batch arguments");
-    std::vector<int64_t> seg(1, 0);
-    int64_t nnz = 0;
+    // every member's column pointers are checked before any of its row
+    // indices is read, so a malformed member cannot send the reads below
+    // outside the caller's arrays
+    int64_t N = 0, nnz = 0;
     for (int32_t q = 0; q < count; ++q) {
-        if (n[q] < 0 || !colptr[q] || (n[q] > 0 && !rowidx[q]))
+        const int64_t m = n[q];
+        const int64_t *cq = colptr[q];
+        if (m < 0 || !cq || (m > 0 && !rowidx[q]))
             return fail(SLU_ERR_INVALID_ARG, "bad batch member");
-        seg.push_back(seg.back() + n[q]);
-        nnz += colptr[q][n[q]];
+        if (m > INT32_MAX - 1 - N)
+            return fail(SLU_ERR_INVALID_ARG, "batch too large");
+        if (cq[0] != 0)
+            return fail(SLU_ERR_INVALID_ARG, "colptr[0] must be 0");
+        for (int64_t j = 0; j < m; ++j)
+            if (cq[j + 1] < cq[j])
+                return fail(SLU_ERR_INVALID_ARG, "colptr not monotone");
+        if (cq[m] > INT64_MAX - nnz)
+            return fail(SLU_ERR_INVALID_ARG, "batch too large");
+        N += m;
+        nnz += cq[m];
     }
-    const int64_t N = seg.back();
-    if (N > INT32_MAX - 1) return fail(SLU_ERR_INVALID_ARG, "batch too large");
-    std::vector<int64_t> cp(N + 1, 0);
+    std::vector<int64_t> seg, cp;
     std::vector<int32_t> ri;
-    ri.reserve(nnz);
+    try {
+        seg.assign(1, 0);
+        for (int32_t q = 0; q < count; ++q) seg.push_back(seg.back() + n[q]);
+        cp.assign(N + 1, 0);
+        ri.reserve(nnz);
+    } catch (const std::exception &) {
+        return fail(SLU_ERR_OUT_OF_MEMORY, "host allocation in analyze");
+    }
     for (int32_t q = 0; q < count; ++q) {
         for (int64_t j = 0; j < n[q]; ++j) {
             for (int64_t e = colptr[q][j]; e < colptr[q][j + 1]; ++e) {

@@ -41,3 +41,26 @@ def test_batch_plan_is_concatenation_of_member_plans(opts):
     assert PB.info["nlevels"] == max(levels) + 1
     assert PB.info["flops"] == sum(S.Plan(m.n, m.colptr, m.rowidx, **opts).info["flops"]
                                    for m in ms)
+
+
+@pytest.mark.parametrize("bad,msg", [("start", "colptr[0]"),
+                                     ("monotone", "monotone"),
+                                     ("negative_n", "bad batch member"),
+                                     ("range", "out of range")])
+def test_batch_rejects_malformed_member(bad, msg):
+    """A malformed member is rejected before its row indices are read."""
+    good = workloads.grid5(4)
+    cp = np.array([0, 2, 3], np.int64)
+    ri = np.array([0, 1, 1], np.int32)
+    n = 2
+    if bad == "start":
+        cp = np.array([1, 2, 3], np.int64)
+    elif bad == "monotone":
+        cp = np.array([0, 5, 3], np.int64)
+    elif bad == "negative_n":
+        n = -1
+    else:
+        ri = np.array([0, 1, 2], np.int32)
+    with pytest.raises(S.SluError) as e:
+        S.Plan([good.n, n], [good.colptr, cp], [good.rowidx, ri])
+    assert e.value.status == 1 and msg in str(e.value)
