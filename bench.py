@@ -316,7 +316,7 @@ def circuit_leg(torch, S, dev, args):
     FP32 factors + FP64 refinement to backward error <= 1e-14 against the
     plain FP64 factorization, both irregular blocking; sparse/dense
     threshold 0.02 for FP32 and 0.05 for FP64 (the best of {0.3, 0.1, 0.05,
-    0.02} per precision in a sweep; tuning here would repeat the 20 s host
+    0.02} per precision in a sweep; tuning here would repeat the 8-11 s host
     analysis per candidate).  One timed factor + solve each."""
     s = workloads.circuit_bbd()
     v, r = dev(s.values), dev(s.rhs)

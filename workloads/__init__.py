@@ -76,7 +76,9 @@ def coo_to_csc(n, rows, cols, vals, sum_duplicates=True):
     rows = np.asarray(rows, dtype=np.int64)
     cols = np.asarray(cols, dtype=np.int64)
     vals = np.asarray(vals, dtype=np.float64)
-    order = np.lexsort((rows, cols))
+    # one stable sort on the (column, row) key: the order of a two-key
+    # lexicographic sort, with equal entries kept in input order
+    order = np.argsort(cols * n + rows, kind="stable")
     rows, cols, vals = rows[order], cols[order], vals[order]
     if sum_duplicates and rows.size:
         key = cols * n + rows
