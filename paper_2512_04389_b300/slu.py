@@ -163,6 +163,22 @@ def _dev_ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _values_ptr(t, nnz):
+    """Device pointer of a value vector: float64, contiguous, exactly the
+    plan's nnz(A) entries (the kernels read that many from the pointer)."""
+    if t.dim() != 1 or t.shape[0] != nnz:
+        raise ValueError(f"expected {nnz} values (the pattern's entries), "
+                         f"got shape {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError("values must be contiguous")
+    return _dev_ptr(t)
+
+
+def _check_rows(t, n, what):
+    if t.dim() not in (1, 2) or t.shape[0] != n:
+        raise ValueError(f"{what} must have {n} rows, got shape {tuple(t.shape)}")
+
+
 def _colmajor(B):
     """(tensor, leading dimension, columns, was_vector) in column-major."""
     if B.dim() == 1:
@@ -272,7 +288,8 @@ class Factor:
         self.plan = plan
         self._h = C.c_void_p()
         info = FactorInfo()
-        st = lib.slu_factor(plan._h, _dev_ptr(values), _stream_ptr(stream),
+        st = lib.slu_factor(plan._h, _values_ptr(values, plan.info["nnz_a"]),
+                            _stream_ptr(stream),
                             C.byref(self._h), C.byref(info))
         _check(st, (0, 4) if allow_singular else (0,))
         self.singular = st == 4
@@ -287,7 +304,9 @@ class Factor:
 
     def refactor(self, values, stream=None, sync_info=False):
         info = FactorInfo() if sync_info else None
-        _check(lib.slu_refactor(self._h, _dev_ptr(values), _stream_ptr(stream),
+        _check(lib.slu_refactor(self._h,
+                                _values_ptr(values, self.plan.info["nnz_a"]),
+                                _stream_ptr(stream),
                                 C.byref(info) if info is not None else None))
         self.values = values
         if info is not None:
@@ -295,6 +314,7 @@ class Factor:
 
     def solve(self, B, stream=None, info=False, allow_not_converged=False):
         """X = A^{-1} B for a CUDA float64 tensor B of shape (n,) or (n, k)."""
+        _check_rows(B, self.plan.n, "B")
         Bc, ldb, k, vec = _colmajor(B)
         X, ldx = _colmajor_empty(Bc.shape[0], k, Bc.device)
         si = SolveInfo()
@@ -310,6 +330,7 @@ class Factor:
 
     def solve_transpose(self, G, stream=None):
         """Lam = A^{-T} G through the stored factors."""
+        _check_rows(G, self.plan.n, "G")
         Gc, ldg, k, vec = _colmajor(G)
         L, ldl = _colmajor_empty(Gc.shape[0], k, Gc.device)
         _check(lib.slu_solve_transpose(self._h, _dev_ptr(Gc), ldg, k,
@@ -319,9 +340,12 @@ class Factor:
     def grad_values(self, Lam, X, stream=None):
         """-sum_c Lam(row_p, c) X(col_p, c) over A's pattern (CSC order)."""
         import torch
+        _check_rows(Lam, self.plan.n, "Lam")
+        _check_rows(X, self.plan.n, "X")
         Lc, ldl, k, _ = _colmajor(Lam)
         Xc, ldx, k2, _ = _colmajor(X)
-        assert k == k2
+        if k != k2:
+            raise ValueError(f"Lam has {k} columns, X has {k2}")
         out = torch.empty(self.plan.info["nnz_a"], dtype=torch.float64,
                           device=Lc.device)
         _check(lib.slu_grad_values(self._h, _dev_ptr(Lc), ldl, _dev_ptr(Xc),
