@@ -12,6 +12,7 @@
 //      storage layout, levels of the block dependency DAG, task lists,
 //      intra-block column schedules, value maps.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <climits>
 #include <cmath>
@@ -123,6 +124,27 @@ void stable_transpose(int64_t nsrc, const int64_t *sp, int64_t ndst, Dst dst,
         for (int64_t c = cut[t]; c < cut[t + 1]; ++c)
             for (int64_t e = sp[c]; e < sp[c + 1]; ++e) emit(f[dst(e)]++, c, e);
     });
+}
+
+// Cuts 0 = c_0 <= c_1 <= ... <= c_nt = nsrc of a range of columns whose
+// entry prefix is w(c) (nondecreasing, w(0) = 0): part t, columns
+// [c_t, c_{t+1}), holds about w(nsrc) / nt entries.
+template <class W>
+std::vector<int64_t> balanced_cuts(int64_t nsrc, W w, int nt) {
+    std::vector<int64_t> cut(nt + 1, nsrc);
+    cut[0] = 0;
+    const int64_t tot = w(nsrc);
+    for (int t = 1; t < nt; ++t) {
+        const int64_t goal = tot / nt * t + tot % nt * t / nt;
+        int64_t lo = 0, hi = nsrc;                 // last c with w(c) <= goal
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo + 1) / 2;
+            if (w(mid) <= goal) lo = mid;
+            else hi = mid - 1;
+        }
+        cut[t] = std::max(lo, cut[t - 1]);
+    }
+    return cut;
 }
 
 struct Sym {                      // symmetric pattern with diagonal
@@ -310,37 +332,56 @@ static slu_status build_blocks(slu_plan &P) {
         P.maxb = std::max<int32_t>(P.maxb, (int32_t)(P.ptr[b + 1] - P.ptr[b]));
     if (P.maxb > 65535)
         return fail(SLU_ERR_NOT_SUPPORTED, "block larger than 65535 rows");
+    // Both passes below walk the filled pattern block column by block
+    // column; block columns are independent, so threads take contiguous
+    // ranges of them balanced by entries, and pass 1's per-thread block
+    // lists are concatenated in column order.
+    const int nt = host_threads(p);
+    const std::vector<int64_t> cutJ = balanced_cuts(
+        p, [&](int64_t J) { return P.f_colptr[P.ptr[J]]; }, nt);
     // pass 1: non-empty blocks and their counts, block column by column
-    std::vector<int64_t> cnt(p, 0);
-    std::vector<int32_t> touched;
+    std::vector<int64_t> bcol_first(p + 1, 0);   // first block id of col J
+    std::vector<std::vector<BlockDesc>> tblk(nt);
+    std::vector<std::vector<int64_t>> tnnz(nt);
+    run_threads(nt, [&](int t) {
+        std::vector<int64_t> cnt(p, 0);
+        std::vector<int32_t> touched;
+        for (int32_t J = (int32_t)cutJ[t]; J < cutJ[t + 1]; ++J) {
+            touched.clear();
+            for (int64_t j = P.ptr[J]; j < P.ptr[J + 1]; ++j)
+                for (int64_t q = P.f_colptr[j]; q < P.f_colptr[j + 1]; ++q) {
+                    const int32_t I = P.rowblk[P.f_rowidx[q]];
+                    if (cnt[I]++ == 0) touched.push_back(I);
+                }
+            std::sort(touched.begin(), touched.end());
+            bcol_first[J] = (int64_t)tblk[t].size();   // local, offset below
+            for (int32_t I : touched) {
+                BlockDesc d;
+                std::memset(&d, 0, sizeof(d));
+                d.I = I;
+                d.J = J;
+                d.rows = (int32_t)(P.ptr[I + 1] - P.ptr[I]);
+                d.cols = (int32_t)(P.ptr[J + 1] - P.ptr[J]);
+                d.r0 = (int32_t)P.ptr[I];
+                d.c0 = (int32_t)P.ptr[J];
+                d.dense = (double)cnt[I] >= P.opts.dense_threshold *
+                                                ((double)d.rows * (double)d.cols);
+                d.doff = d.goff = -1;
+                tblk[t].push_back(d);
+                tnnz[t].push_back(cnt[I]);
+                cnt[I] = 0;
+            }
+        }
+    });
     P.blocks.clear();
     P.bnnz.clear();
-    std::vector<int64_t> bcol_first(p + 1, 0);   // first block id of col J
-    for (int32_t J = 0; J < p; ++J) {
-        touched.clear();
-        for (int64_t j = P.ptr[J]; j < P.ptr[J + 1]; ++j)
-            for (int64_t q = P.f_colptr[j]; q < P.f_colptr[j + 1]; ++q) {
-                const int32_t I = P.rowblk[P.f_rowidx[q]];
-                if (cnt[I]++ == 0) touched.push_back(I);
-            }
-        std::sort(touched.begin(), touched.end());
-        bcol_first[J] = (int64_t)P.blocks.size();
-        for (int32_t I : touched) {
-            BlockDesc d;
-            std::memset(&d, 0, sizeof(d));
-            d.I = I;
-            d.J = J;
-            d.rows = (int32_t)(P.ptr[I + 1] - P.ptr[I]);
-            d.cols = (int32_t)(P.ptr[J + 1] - P.ptr[J]);
-            d.r0 = (int32_t)P.ptr[I];
-            d.c0 = (int32_t)P.ptr[J];
-            d.dense = (double)cnt[I] >= P.opts.dense_threshold *
-                                            ((double)d.rows * (double)d.cols);
-            d.doff = d.goff = -1;
-            P.blocks.push_back(d);
-            P.bnnz.push_back(cnt[I]);
-            cnt[I] = 0;
-        }
+    for (int t = 0; t < nt; ++t) {
+        const int64_t base = (int64_t)P.blocks.size();
+        for (int64_t J = cutJ[t]; J < cutJ[t + 1]; ++J) bcol_first[J] += base;
+        P.blocks.insert(P.blocks.end(), tblk[t].begin(), tblk[t].end());
+        P.bnnz.insert(P.bnnz.end(), tnnz[t].begin(), tnnz[t].end());
+        std::vector<BlockDesc>().swap(tblk[t]);
+        std::vector<int64_t>().swap(tnnz[t]);
     }
     bcol_first[p] = (int64_t)P.blocks.size();
     const int64_t nb = (int64_t)P.blocks.size();
@@ -384,44 +425,47 @@ static slu_status build_blocks(slu_plan &P) {
     P.lrow.assign(roff, 0);
     P.f2s.assign(P.f_colptr[n], 0);
     P.dpos.assign(ndiag_slots, 0);
-    // pass 2: local CSC, filled -> storage map, diagonal positions
-    std::vector<int64_t> run(p, 0);             // running local position
-    std::vector<int32_t> bid(p, -1);
-    for (int32_t J = 0; J < p; ++J) {
-        for (int64_t b = bcol_first[J]; b < bcol_first[J + 1]; ++b) {
-            bid[P.blocks[b].I] = (int32_t)b;
-            run[P.blocks[b].I] = 0;
-        }
-        for (int64_t j = P.ptr[J]; j < P.ptr[J + 1]; ++j) {
-            const int32_t jj = (int32_t)(j - P.ptr[J]);
+    // pass 2: local CSC, filled -> storage map, diagonal positions (each
+    // block column writes only its own blocks' slots and its own entries)
+    run_threads(nt, [&](int tt) {
+        std::vector<int64_t> run(p, 0);             // running local position
+        std::vector<int32_t> bid(p, -1);
+        for (int32_t J = (int32_t)cutJ[tt]; J < cutJ[tt + 1]; ++J) {
+            for (int64_t b = bcol_first[J]; b < bcol_first[J + 1]; ++b) {
+                bid[P.blocks[b].I] = (int32_t)b;
+                run[P.blocks[b].I] = 0;
+            }
+            for (int64_t j = P.ptr[J]; j < P.ptr[J + 1]; ++j) {
+                const int32_t jj = (int32_t)(j - P.ptr[J]);
+                for (int64_t b = bcol_first[J]; b < bcol_first[J + 1]; ++b) {
+                    const BlockDesc &d = P.blocks[b];
+                    if (!d.dense) P.lcolptr[d.coff + jj] = (int32_t)run[d.I];
+                }
+                for (int64_t q = P.f_colptr[j]; q < P.f_colptr[j + 1]; ++q) {
+                    const int32_t r = P.f_rowidx[q];
+                    const int32_t I = P.rowblk[r];
+                    const BlockDesc &d = P.blocks[bid[I]];
+                    const int32_t rl = r - d.r0;
+                    int64_t t;
+                    if (d.dense) {
+                        t = (int64_t)jj * d.ld + rl;
+                    } else {
+                        t = run[I]++;
+                        P.lrow[d.roff + t] = (uint16_t)rl;
+                    }
+                    P.f2s[q] = d.voff + t;
+                    if (I == J && rl == jj)
+                        P.dpos[d.doff + jj] =
+                            d.dense ? rl : (int32_t)(t - P.lcolptr[d.coff + jj]);
+                }
+            }
             for (int64_t b = bcol_first[J]; b < bcol_first[J + 1]; ++b) {
                 const BlockDesc &d = P.blocks[b];
-                if (!d.dense) P.lcolptr[d.coff + jj] = (int32_t)run[d.I];
-            }
-            for (int64_t q = P.f_colptr[j]; q < P.f_colptr[j + 1]; ++q) {
-                const int32_t r = P.f_rowidx[q];
-                const int32_t I = P.rowblk[r];
-                const BlockDesc &d = P.blocks[bid[I]];
-                const int32_t rl = r - d.r0;
-                int64_t t;
-                if (d.dense) {
-                    t = (int64_t)jj * d.ld + rl;
-                } else {
-                    t = run[I]++;
-                    P.lrow[d.roff + t] = (uint16_t)rl;
-                }
-                P.f2s[q] = d.voff + t;
-                if (I == J && rl == jj)
-                    P.dpos[d.doff + jj] =
-                        d.dense ? rl : (int32_t)(t - P.lcolptr[d.coff + jj]);
+                if (!d.dense) P.lcolptr[d.coff + d.cols] = (int32_t)run[d.I];
+                bid[d.I] = -1;
             }
         }
-        for (int64_t b = bcol_first[J]; b < bcol_first[J + 1]; ++b) {
-            const BlockDesc &d = P.blocks[b];
-            if (!d.dense) P.lcolptr[d.coff + d.cols] = (int32_t)run[d.I];
-            bid[d.I] = -1;
-        }
-    }
+    });
     // intra-diagonal-block column schedule: height(jj) = 1 + max height of
     // the columns m < jj with U(m, jj) stored (0 if none); a column only
     // reads columns of smaller height, so each height is one parallel group.
@@ -1023,29 +1067,42 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
             return st;
         }
         build_levels_and_tasks(*P);
-        // flops per kernel class from the block of each column's rows
-        for (int64_t k = 0; k < n; ++k) {
-            const int32_t I = P->rowblk[k];
-            double lin = 0, lout = 0;
-            for (int64_t q = P->f_colptr[k]; q < P->f_colptr[k + 1]; ++q) {
-                const int32_t r = P->f_rowidx[q];
-                if (r <= k) continue;
-                if (P->rowblk[r] == I) lin += 1; else lout += 1;
+        // flops per kernel class from the block of each column's rows;
+        // threads sum contiguous column ranges (every term is an integer,
+        // so the sums are exact below 2^53 whatever their order)
+        const int ntc = host_threads(0);
+        const std::vector<int64_t> cutc = balanced_cuts(
+            n, [&](int64_t k) { return P->f_colptr[k]; }, ntc);
+        std::vector<std::array<double, 3>> fc(ntc, {0.0, 0.0, 0.0});
+        run_threads(ntc, [&](int t) {
+            for (int64_t k = cutc[t]; k < cutc[t + 1]; ++k) {
+                const int32_t I = P->rowblk[k];
+                double lin = 0, lout = 0;
+                for (int64_t q = P->f_colptr[k]; q < P->f_colptr[k + 1]; ++q) {
+                    const int32_t r = P->f_rowidx[q];
+                    if (r <= k) continue;
+                    if (P->rowblk[r] == I) lin += 1; else lout += 1;
+                }
+                fc[t][0] += lin + 2 * lin * lin;
+                fc[t][1] += lout + 4 * lin * lout;
+                fc[t][2] += 2 * lout * lout;
             }
-            P->flops_cls[0] += lin + 2 * lin * lin;
-            P->flops_cls[1] += lout + 4 * lin * lout;
-            P->flops_cls[2] += 2 * lout * lout;
-        }
+        });
+        for (int t = 0; t < ntc; ++t)
+            for (int c = 0; c < 3; ++c) P->flops_cls[c] += fc[t][c];
         // A entry -> storage slot, through the filled pattern: both columns
         // are sorted by row, so one walk per column finds every position
+        // (sq is a permutation, so the column ranges write disjoint slots)
         P->a2s.resize(nnz);
-        for (int64_t j = 0; j < n; ++j) {
-            int64_t f = P->f_colptr[j];
-            for (int64_t t = sp[j]; t < sp[j + 1]; ++t) {
-                while (P->f_rowidx[f] < si[t]) ++f;
-                P->a2s[sq[t]] = P->f2s[f];
+        run_threads(ntc, [&](int t) {
+            for (int64_t j = cutc[t]; j < cutc[t + 1]; ++j) {
+                int64_t f = P->f_colptr[j];
+                for (int64_t q = sp[j]; q < sp[j + 1]; ++q) {
+                    while (P->f_rowidx[f] < si[q]) ++f;
+                    P->a2s[sq[q]] = P->f2s[f];
+                }
             }
-        }
+        });
     } catch (const std::exception &e) {
         delete P;
         return fail(SLU_ERR_OUT_OF_MEMORY,
