@@ -199,11 +199,16 @@ void etree(int64_t n, const Sym &S, std::vector<int32_t> &parent) {
     }
 }
 
-// struct L(:,j) (strictly lower, sorted), columns in increasing order so
-// that children (always < parent) are complete before their parent:
-// struct L(:,j) = rows > j of S(:,j) united with struct L(:,c) minus {j} for
-// every child c.  Every list involved is sorted, so the union is built by
-// merging (linear in the sizes, no sort).
+// struct L(:,j) (strictly lower, sorted): the rows > j of S(:,j) united
+// with struct L(:,c) minus {j} for every child c of j.  Every list involved
+// is sorted, so the union is built by merging (linear in the sizes, no
+// sort).  A column needs only its children's columns, so the elimination
+// tree's subtrees are independent: the subtrees hanging below the nodes
+// with more than n / (8 nt) descendants go to threads whole (largest
+// first, to the least loaded thread) and are built in postorder, each
+// thread in a buffer of its own; the nodes above them follow on one thread
+// in increasing order (children always precede their parent), and the
+// columns are finally copied into Lp / Li in column order.
 void symbolic(int64_t n, const Sym &S, const std::vector<int32_t> &par,
               std::vector<int64_t> &Lp, std::vector<int32_t> &Li) {
     std::vector<int64_t> chp(n + 1, 0);
@@ -216,29 +221,87 @@ void symbolic(int64_t n, const Sym &S, const std::vector<int32_t> &par,
         for (int64_t j = 0; j < n; ++j)
             if (par[j] >= 0) ch[f[par[j]]++] = (int32_t)j;
     }
-    Lp.assign(n + 1, 0);
-    Li.clear();
-    std::vector<int32_t> col, tmp;
-    for (int64_t j = 0; j < n; ++j) {
+    const int nt = host_threads(0);
+    // where each column's list lives: buffer, offset, length
+    std::vector<int32_t> cbuf(n);
+    std::vector<int64_t> coff(n), clen(n);
+    std::vector<std::vector<int32_t>> buf(nt + 1);   // buf[nt]: upper nodes
+    auto build = [&](int64_t j, int b, std::vector<int32_t> &col,
+                     std::vector<int32_t> &tmp) {
         col.clear();
         {
-            const int32_t *b = S.i.data() + S.p[j], *e = S.i.data() + S.p[j + 1];
-            b = std::upper_bound(b, e, (int32_t)j);      // rows sorted
-            col.assign(b, e);
+            const int32_t *lo = S.i.data() + S.p[j], *hi = S.i.data() + S.p[j + 1];
+            lo = std::upper_bound(lo, hi, (int32_t)j);  // rows sorted
+            col.assign(lo, hi);
         }
         for (int64_t c = chp[j]; c < chp[j + 1]; ++c) {
             const int32_t k = ch[c];
-            const int32_t *b = Li.data() + Lp[k], *e = Li.data() + Lp[k + 1];
-            b = std::upper_bound(b, e, (int32_t)j);      // drop j itself
-            if (b == e) continue;
-            tmp.resize(col.size() + (size_t)(e - b));
-            auto end = std::set_union(col.begin(), col.end(), b, e, tmp.begin());
+            const int32_t *kb = buf[cbuf[k]].data() + coff[k];
+            const int32_t *lo = std::upper_bound(kb, kb + clen[k], (int32_t)j);
+            const int32_t *hi = kb + clen[k];            // drop j itself
+            if (lo == hi) continue;
+            tmp.resize(col.size() + (size_t)(hi - lo));
+            auto end = std::set_union(col.begin(), col.end(), lo, hi, tmp.begin());
             tmp.resize((size_t)(end - tmp.begin()));
             col.swap(tmp);
         }
-        Li.insert(Li.end(), col.begin(), col.end());
-        Lp[j + 1] = (int64_t)Li.size();
+        cbuf[j] = b;
+        coff[j] = (int64_t)buf[b].size();
+        clen[j] = (int64_t)col.size();
+        buf[b].insert(buf[b].end(), col.begin(), col.end());
+    };
+    // subtree sizes (children precede their parent)
+    std::vector<int64_t> sz(n, 1);
+    for (int64_t j = 0; j < n; ++j)
+        if (par[j] >= 0) sz[par[j]] += sz[j];
+    const int64_t grain = std::max<int64_t>(1, n / (8 * (int64_t)nt));
+    std::vector<int32_t> roots;
+    for (int64_t j = 0; j < n; ++j)
+        if (sz[j] <= grain && (par[j] < 0 || sz[par[j]] > grain))
+            roots.push_back((int32_t)j);
+    std::stable_sort(roots.begin(), roots.end(),
+                     [&](int32_t a, int32_t b) { return sz[a] > sz[b]; });
+    std::vector<std::vector<int32_t>> mine(nt);
+    {
+        std::vector<int64_t> load(nt, 0);
+        for (int32_t r : roots) {
+            const int t = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            mine[t].push_back(r);
+            load[t] += sz[r];
+        }
     }
+    run_threads(nt, [&](int t) {
+        std::vector<int32_t> col, tmp;
+        std::vector<std::pair<int32_t, int64_t>> st;   // (node, next child)
+        for (int32_t r : mine[t]) {
+            st.assign(1, {r, chp[r]});
+            while (!st.empty()) {
+                auto &top = st.back();
+                if (top.second < chp[top.first + 1]) {
+                    const int32_t c = ch[top.second++];
+                    st.push_back({c, chp[c]});
+                } else {
+                    build(top.first, t, col, tmp);
+                    st.pop_back();
+                }
+            }
+        }
+    });
+    {
+        std::vector<int32_t> col, tmp;
+        for (int64_t j = 0; j < n; ++j)
+            if (sz[j] > grain) build(j, nt, col, tmp);
+    }
+    Lp.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j) Lp[j + 1] = Lp[j] + clen[j];
+    Li.resize(Lp[n]);
+    const std::vector<int64_t> cut = balanced_cuts(
+        n, [&](int64_t j) { return Lp[j]; }, nt);
+    run_threads(nt, [&](int t) {
+        for (int64_t j = cut[t]; j < cut[t + 1]; ++j)
+            std::copy(buf[cbuf[j]].data() + coff[j],
+                      buf[cbuf[j]].data() + coff[j] + clen[j], Li.data() + Lp[j]);
+    });
 }
 
 int64_t idx_of(int64_t s, int64_t N, int64_t S) { return (s * N) / S; }
