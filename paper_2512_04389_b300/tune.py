@@ -11,8 +11,8 @@ GPU, so
 the fastest, timing with CUDA events on the current stream.  Results are
 cached in a JSON file (path from the ``SLU_TUNE_CACHE`` environment
 variable, default ``~/.cache/slu_b300_tune.json``) under a key made of the
-pattern's hash, the precision and the other plan options, so a pattern is
-tuned once.
+library sources' digest, the pattern's hash, the precision and the other
+plan options, so a pattern is tuned once per build of the library.
 """
 from __future__ import annotations
 
@@ -53,8 +53,28 @@ def candidates(blocking="irregular", n=None):
     return out
 
 
+_SOURCES = None
+
+
+def _source_digest():
+    """Digest of the library's sources: a timing measured with other kernels
+    does not carry over, so a rebuilt library tunes afresh."""
+    global _SOURCES
+    if _SOURCES is None:
+        h = hashlib.sha1()
+        d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+        for f in sorted(os.listdir(d)):
+            if f.endswith((".cu", ".cuh", ".cpp", ".hpp")):
+                with open(os.path.join(d, f), "rb") as fh:
+                    h.update(f.encode())
+                    h.update(fh.read())
+        _SOURCES = h.hexdigest()
+    return _SOURCES
+
+
 def _key(n, colptr, rowidx, opts):
     h = hashlib.sha1()
+    h.update(_source_digest().encode())
     h.update(np.int64(n).tobytes())
     h.update(np.ascontiguousarray(colptr, dtype=np.int64).tobytes())
     h.update(np.ascontiguousarray(rowidx, dtype=np.int32).tobytes())

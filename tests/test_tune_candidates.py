@@ -25,3 +25,14 @@ def test_candidate_counts():
     # n = 2304: S in {72, 288} (sample_points irrelevant) x max_num + 1
     assert len(T.candidates("irregular", 2304)) == 7
     assert T.candidates("regular") == [{"dense_threshold": t} for t in T.THRESHOLDS]
+
+
+def test_cache_key_covers_pattern_options_and_library(monkeypatch):
+    import numpy as np
+    cp, ri = np.array([0, 1, 2]), np.array([0, 1])
+    k0 = T._key(2, cp, ri, {"precision": "fp64"})
+    assert k0 == T._key(2, cp, ri, {"precision": "fp64"})
+    assert k0 != T._key(2, cp, ri, {"precision": "fp32"})
+    assert k0 != T._key(2, np.array([0, 2, 2]), np.array([0, 1]), {"precision": "fp64"})
+    monkeypatch.setattr(T, "_SOURCES", "another build")
+    assert k0 != T._key(2, cp, ri, {"precision": "fp64"})
