@@ -32,6 +32,15 @@
  *     and slu_last_error() describes the failure (thread-local string).
  *   - Plans and handles are opaque and freed only by their destroy call.
  *     A handle refers to its plan, which must outlive it.
+ *   - Sharing.  The first slu_factor of a plan copies the plan's arrays to
+ *     the current device, and every handle of that plan reads them there:
+ *     all handles of one plan must live on one device (analyse the pattern
+ *     again for another device), and the first slu_factor of a plan must
+ *     not run concurrently with another call on the same plan.  A handle
+ *     owns scratch buffers and recorded graphs: calls on one handle must
+ *     come from one host thread at a time, and their GPU work must not
+ *     overlap (one stream per handle, or streams ordered by events).
+ *     Different handles are independent.
  */
 #ifndef SLU_H
 #define SLU_H
