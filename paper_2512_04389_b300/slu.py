@@ -197,6 +197,22 @@ def _colmajor_empty(n, k, device):
     return X, max(1, n)
 
 
+def _pattern_arrays(n, colptr, rowidx):
+    """Contiguous int64 colptr / int32 rowidx, long enough for what the
+    library reads: colptr[0..n] and rowidx[0..colptr[n])."""
+    cp = np.ascontiguousarray(colptr, dtype=np.int64)
+    ri = np.ascontiguousarray(rowidx, dtype=np.int32)
+    if n < 0:
+        raise ValueError(f"n must be >= 0, got {n}")
+    if cp.ndim != 1 or cp.shape[0] != n + 1:
+        raise ValueError(f"colptr must have n + 1 = {n + 1} entries, "
+                         f"got shape {cp.shape}")
+    if ri.ndim != 1 or ri.shape[0] < max(int(cp[-1]), 0):
+        raise ValueError(f"rowidx must have colptr[n] = {int(cp[-1])} entries, "
+                         f"got shape {ri.shape}")
+    return cp, ri
+
+
 class Plan:
     """Result of host analysis (``slu_analyze``) for one sparsity pattern."""
 
@@ -205,8 +221,7 @@ class Plan:
         if isinstance(n, (list, tuple)):          # batch of matrices
             return self._init_batch(n, colptr, rowidx, opts)
         self.n = int(n)
-        self.colptr = np.ascontiguousarray(colptr, dtype=np.int64)
-        self.rowidx = np.ascontiguousarray(rowidx, dtype=np.int32)
+        self.colptr, self.rowidx = _pattern_arrays(self.n, colptr, rowidx)
         self.opts = default_opts(**opts)
         _check(lib.slu_analyze(self.n, _np(self.colptr), _np(self.rowidx),
                                C.byref(self.opts), C.byref(self._h)))
@@ -216,9 +231,14 @@ class Plan:
 
     def _init_batch(self, ns, colptrs, rowidxs, opts):
         k = len(ns)
+        if len(colptrs) != k or len(rowidxs) != k:
+            raise ValueError(f"{k} orders but {len(colptrs)} colptr and "
+                             f"{len(rowidxs)} rowidx arrays")
         self.members = [int(x) for x in ns]
-        self._cps = [np.ascontiguousarray(c, dtype=np.int64) for c in colptrs]
-        self._ris = [np.ascontiguousarray(r, dtype=np.int32) for r in rowidxs]
+        arrs = [_pattern_arrays(m, c, r)
+                for m, c, r in zip(self.members, colptrs, rowidxs)]
+        self._cps = [a[0] for a in arrs]
+        self._ris = [a[1] for a in arrs]
         na = np.asarray(self.members, dtype=np.int64)
         cpa = (C.c_void_p * k)(*[c.ctypes.data for c in self._cps])
         ria = (C.c_void_p * k)(*[r.ctypes.data for r in self._ris])

@@ -48,3 +48,34 @@ def test_empty_plan_values(plan):
     P0 = S.Plan(0, np.zeros(1, np.int64), np.zeros(0, np.int32))
     with pytest.raises(ValueError, match="CUDA"):
         S.Factor(P0, torch.zeros(0, dtype=torch.float64))
+
+
+@pytest.mark.parametrize("bad", ["short_colptr", "long_colptr", "short_rowidx",
+                                 "negative_n", "matrix_colptr"])
+def test_plan_rejects_short_pattern_arrays(bad):
+    """The library reads colptr[0..n] and rowidx[0..colptr[n]) from host
+    memory; arrays shorter than that are refused before the call."""
+    s = workloads.grid5(5)
+    n, cp, ri = s.n, s.colptr, s.rowidx
+    if bad == "short_colptr":
+        cp = cp[:-1]
+    elif bad == "long_colptr":
+        cp = np.append(cp, cp[-1])
+    elif bad == "short_rowidx":
+        ri = ri[:-1]
+    elif bad == "negative_n":
+        n = -1
+    else:
+        cp = cp[None, :]
+    with pytest.raises(ValueError):
+        S.Plan(n, cp, ri)
+
+
+def test_plan_accepts_longer_rowidx_and_batch_lengths():
+    s = workloads.grid5(5)
+    P = S.Plan(s.n, s.colptr, np.append(s.rowidx, [0, 0]))
+    assert P.info["nnz_a"] == s.nnz
+    with pytest.raises(ValueError, match="orders"):
+        S.Plan([s.n, s.n], [s.colptr], [s.rowidx, s.rowidx])
+    with pytest.raises(ValueError):
+        S.Plan([s.n, s.n], [s.colptr, s.colptr[:-1]], [s.rowidx, s.rowidx])
