@@ -342,6 +342,35 @@ slu_status slu_solve_refine_noalloc(const slu_handle *h, const double *B,
                                     int64_t ldx, void *stream,
                                     slu_solve_info *info);
 
+/* Plan cache.  The host analysis of a large pattern can take seconds (the
+ * irregular blocking costs more preprocessing than regular blocking, which
+ * Section 5.4 accepts for the faster factorization), and its result is
+ * plain host data: a plan can be written out and loaded again instead of
+ * analysing the pattern anew.  The paper has no counterpart.
+ *
+ * slu_plan_serialize: with buf == NULL stores the number of bytes the plan
+ * needs in *size.  Otherwise buf (host, *size bytes) receives the plan: a
+ * 48-byte header (magic, format version, byte-order mark, layout
+ * fingerprint, checksum of the payload, payload size, analysis time) and
+ * every host array and setting the factorization and the solves use; *size
+ * is set to the bytes written.  A buffer smaller than needed is
+ * SLU_ERR_INVALID_ARG with *size set to the size needed.
+ *
+ * slu_plan_deserialize: a new plan from such a buffer (host, read during the
+ * call only), equal field for field to the one written (the same digest).
+ * A buffer that is not a plan, is truncated, or fails its checksum is
+ * SLU_ERR_INVALID_ARG; one written by a build of the library whose plan
+ * layout or format version differs, or with another byte order, is
+ * SLU_ERR_NOT_SUPPORTED (analyse the pattern again).  The checksum catches
+ * corruption, not forgery: load only buffers this library wrote.
+ *
+ * slu_plan_digest: a 64-bit checksum of the plan's contents (the analysis
+ * time excluded), equal for equal plans; the checksum a serialized plan
+ * carries. */
+slu_status slu_plan_serialize(const slu_plan *plan, void *buf, int64_t *size);
+slu_status slu_plan_deserialize(const void *buf, int64_t size, slu_plan **out);
+slu_status slu_plan_digest(const slu_plan *plan, uint64_t *digest);
+
 void slu_plan_destroy(slu_plan *plan);
 void slu_handle_destroy(slu_handle *h);
 const char *slu_last_error(void);

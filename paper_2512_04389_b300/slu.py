@@ -72,7 +72,8 @@ EXPORTS = ["slu_opts_default", "slu_analyze", "slu_analyze_batch",
            "slu_plan_export", "slu_plan_export_blocks", "slu_plan_export_tasks",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
            "slu_export_factors", "slu_grad_values", "slu_set_profiling", "slu_handle_stats",
-           "slu_plan_flops", "slu_handle_trace", "slu_set_graph", "slu_solve_refine_noalloc", "slu_plan_destroy",
+           "slu_plan_flops", "slu_handle_trace", "slu_set_graph", "slu_solve_refine_noalloc",
+           "slu_plan_serialize", "slu_plan_deserialize", "slu_plan_digest", "slu_plan_destroy",
            "slu_handle_destroy", "slu_last_error"]
 
 
@@ -108,6 +109,9 @@ def _load():
     lib.slu_set_graph.argtypes = [P, C.c_int32]
     lib.slu_solve_refine_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P,
                                              C.c_int64, P, C.POINTER(SolveInfo)]
+    lib.slu_plan_serialize.argtypes = [P, P, C.POINTER(C.c_int64)]
+    lib.slu_plan_deserialize.argtypes = [P, C.c_int64, C.POINTER(P)]
+    lib.slu_plan_digest.argtypes = [P, C.POINTER(C.c_uint64)]
     lib.slu_plan_destroy.argtypes = [P]
     lib.slu_plan_destroy.restype = None
     lib.slu_handle_destroy.argtypes = [P]
@@ -228,6 +232,49 @@ class Plan:
         i = PlanInfo()
         _check(lib.slu_plan_query(self._h, C.byref(i)))
         self.info = {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+
+    @classmethod
+    def from_bytes(cls, data):
+        """A plan from ``to_bytes`` output (``slu_plan_deserialize``),
+        without repeating the analysis."""
+        self = cls.__new__(cls)
+        self._h = C.c_void_p()
+        buf = np.frombuffer(memoryview(data).cast("B"), dtype=np.uint8)
+        _check(lib.slu_plan_deserialize(_np(buf) if buf.size else None,
+                                        buf.size, C.byref(self._h)))
+        i = PlanInfo()
+        _check(lib.slu_plan_query(self._h, C.byref(i)))
+        self.info = {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+        self.n = int(self.info["n"])
+        self.opts = None
+        return self
+
+    def _serialized(self):
+        size = C.c_int64(0)
+        _check(lib.slu_plan_serialize(self._h, None, C.byref(size)))
+        buf = np.empty(size.value, np.uint8)
+        _check(lib.slu_plan_serialize(self._h, _np(buf), C.byref(size)))
+        return buf
+
+    def to_bytes(self):
+        """The plan as bytes (``slu_plan_serialize``), for a plan cache."""
+        return self._serialized().tobytes()
+
+    def save(self, path):
+        """Write the serialized plan to a file (no intermediate copy)."""
+        with open(path, "wb") as f:
+            f.write(memoryview(self._serialized()))
+
+    @classmethod
+    def load(cls, path):
+        """A plan from a file written by ``save``."""
+        return cls.from_bytes(np.fromfile(path, dtype=np.uint8))
+
+    def digest(self):
+        """64-bit checksum of the plan's contents (``slu_plan_digest``)."""
+        d = C.c_uint64(0)
+        _check(lib.slu_plan_digest(self._h, C.byref(d)))
+        return d.value
 
     def _init_batch(self, ns, colptrs, rowidxs, opts):
         k = len(ns)
