@@ -158,6 +158,9 @@ void slu_opts_default(slu_opts *opts);
 
 /* Host-only analysis (Sections 4.2-4.3, Algorithms 2 and 3; Algorithm 1's
  * block task lists).  colptr/rowidx: host, CSC of A's pattern (n x n).
+ * The analysis runs on up to 16 host threads (the hardware concurrency, or
+ * the environment variable SLU_HOST_THREADS when it is a positive number);
+ * the plan is the same for every thread count.
  * opts: host, NULL for defaults.  *out receives a new plan on success;
  * the caller keeps ownership of the arrays, which the plan copies.
  * Errors: SLU_ERR_INVALID_ARG for n outside [0, 2^31 - 2], a NULL array,

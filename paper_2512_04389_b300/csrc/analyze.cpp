@@ -16,6 +16,7 @@
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <exception>
 #include <new>
@@ -40,11 +41,17 @@ slu_status fail(slu_status st, const std::string &msg) {
 
 namespace {
 
-// Worker threads for the host passes over the pattern: up to the hardware
-// concurrency (16 at most), fewer when the per-thread count arrays of a
-// transpose (threads x destinations) would get large.
+// Worker threads for the host passes over the pattern: the hardware
+// concurrency, or SLU_HOST_THREADS from the environment when set to a
+// positive number, 16 at most, and fewer when the per-thread count arrays
+// of a transpose (threads x destinations) would get large.  The plan does
+// not depend on the count.
 int host_threads(int64_t ndst) {
     int64_t t = std::max(1u, std::thread::hardware_concurrency());
+    if (const char *e = std::getenv("SLU_HOST_THREADS")) {
+        const long v = std::strtol(e, nullptr, 10);
+        if (v > 0) t = v;
+    }
     t = std::min<int64_t>(t, 16);
     t = std::min<int64_t>(t, std::max<int64_t>(1, ((int64_t)1 << 26) / std::max<int64_t>(ndst, 1)));
     return (int)t;

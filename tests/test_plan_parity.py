@@ -159,3 +159,21 @@ def test_empty_and_single():
     # an entirely empty column still gets its diagonal
     P = S.Plan(3, np.array([0, 1, 1, 2]), np.array([0, 2]))
     assert P.info["nnz_sym"] == 3
+
+
+@pytest.mark.parametrize("name,mk,opts", [
+    ("grid7cd_16", lambda: workloads.grid7_cd(16), {}),
+    ("circuit_4000", lambda: workloads.circuit_bbd(n=4000, border=80,
+                                                   block_lo=16, block_hi=64),
+     dict(dense_threshold=0.1, b_min=8)),
+    ("random unsorted", lambda: _random_system(400, 0.01, 9), dict(b_min=8)),
+])
+def test_plan_independent_of_host_threads(name, mk, opts, monkeypatch):
+    """The threaded analysis gives the same plan (every field, by digest)
+    for 1, 2, 3, 7 and 16 host threads."""
+    s = mk()
+    digests = set()
+    for t in (1, 2, 3, 7, 16):
+        monkeypatch.setenv("SLU_HOST_THREADS", str(t))
+        digests.add(S.Plan(s.n, s.colptr, s.rowidx, **opts).digest())
+    assert len(digests) == 1
