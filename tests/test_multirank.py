@@ -36,7 +36,9 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_ranks_take_the_slowest_time():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    # the manager process is spawned too: forking a multi-threaded
+    # process (the library's host threads, torch's pools) can deadlock
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
