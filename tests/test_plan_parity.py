@@ -177,3 +177,58 @@ def test_plan_independent_of_host_threads(name, mk, opts, monkeypatch):
         monkeypatch.setenv("SLU_HOST_THREADS", str(t))
         digests.add(S.Plan(s.n, s.colptr, s.rowidx, **opts).digest())
     assert len(digests) == 1
+
+
+def test_size_limits():
+    """Local row indices inside a block are 16-bit: a block of more than
+    65535 rows is refused with NOT_SUPPORTED and one of exactly 65535 is
+    planned; an order beyond 32-bit row indices is refused before any array
+    is read."""
+    import ctypes as C
+    n = 70_000
+    cp = np.arange(n + 1, dtype=np.int64)       # diagonal pattern
+    ri = np.arange(n, dtype=np.int32)
+    with pytest.raises(S.SluError) as e:
+        S.Plan(n, cp, ri, blocking="regular", regular_block=n)
+    assert e.value.status == 7
+    P = S.Plan(n, cp, ri, blocking="regular", regular_block=65535)
+    assert P.info["max_block"] == 65535 and P.info["nblocks_1d"] == 2
+    out = C.c_void_p()
+    st = S.lib.slu_analyze(2 ** 31, cp.ctypes.data, ri.ctypes.data,
+                           C.byref(S.default_opts()), C.byref(out))
+    assert st == 1 and not out.value
+
+
+def _diag_system(n):
+    return _Sys(n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32),
+                np.full(n, 2.0))
+
+
+def _dense_system(n, seed=3):
+    rng = np.random.default_rng(seed)
+    V = rng.uniform(-1, 1, (n, n)) + n * np.eye(n)
+    return _Sys(n, np.arange(0, n * n + 1, n, dtype=np.int64),
+                np.tile(np.arange(n, dtype=np.int32), n), V.T.reshape(-1).copy())
+
+
+@pytest.mark.parametrize("name,mk,opts", [
+    ("diagonal 300", lambda: _diag_system(300), dict(b_min=8)),
+    ("diagonal 300 regular 7", lambda: _diag_system(300),
+     dict(blocking="regular", regular_block=7)),
+    ("dense 48", lambda: _dense_system(48), dict(b_min=4)),
+    ("dense 48 regular 13", lambda: _dense_system(48),
+     dict(blocking="regular", regular_block=13)),
+])
+def test_plan_bit_exact_degenerate(name, mk, opts):
+    """The two ends of the density range: no off-diagonal entry (no fill, no
+    flops, every block on level 0) and a fully dense pattern (Alg. 2's
+    quadratic profile)."""
+    s = mk()
+    _check_plan(s, opts)
+    P = S.Plan(s.n, s.colptr, s.rowidx, **opts)
+    if name.startswith("diagonal"):
+        assert P.info["flops"] == 0 and P.info["nlevels"] == 1
+        assert P.info["nnz_lu"] == s.n
+    else:
+        assert P.info["nnz_lu"] == s.n * s.n
+        assert np.array_equal(P.export()["blockptr"], np.arange(s.n + 1) ** 2)
