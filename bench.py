@@ -288,6 +288,19 @@ def batch_leg(torch, S, dev, args):
             "n_total": PB.info["n"]}
 
 
+def run_legs(extras, legs, *leg_args):
+    """Run the extra legs in order, each into extras[name]; a leg that
+    raises is recorded as {"error": ...} (traceback on stderr) and the rest
+    still run, so the headline line is always printed."""
+    import traceback
+    for name, fn in legs:
+        try:
+            extras[name] = fn(*leg_args)
+        except Exception as e:  # noqa: BLE001
+            traceback.print_exc()
+            extras[name] = {"error": f"{type(e).__name__}: {e}"}
+
+
 def small_grid_leg(torch, S, dev, args):
     """48 x 48 5-point grid (n = 2304), FP64, irregular blocking against
     regular 64 x 64 blocking in the same code, 1 RHS."""
@@ -570,11 +583,11 @@ def main():
         extras["regular128_fp32_ir"] = {"ms_per_step": msr32, "tuned": bestr32,
                                         "gflops": fl / (msr32 * 1e-3) / 1e9}
         del Freg32
-        extras["batch_256_grid5"] = batch_leg(torch, S, dev, args)
-        extras["grid5_48"] = small_grid_leg(torch, S, dev, args)
-        extras["autograd_theta_32"] = autograd_leg(torch, S, dev, args)
+        legs = [("batch_256_grid5", batch_leg), ("grid5_48", small_grid_leg),
+                ("autograd_theta_32", autograd_leg)]
         if not args.no_circuit:
-            extras["circuit_200k"] = circuit_leg(torch, S, dev, args)
+            legs.append(("circuit_200k", circuit_leg))
+        run_legs(extras, legs, torch, S, dev, args)
         out["extras"] = extras
         # end to end through the public API with host buffers
         vals_h = torch.from_numpy(np.ascontiguousarray(s.values)).pin_memory()

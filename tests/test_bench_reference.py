@@ -20,3 +20,19 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_extra_leg_failure_is_recorded_not_fatal():
+    """A failing extra leg is recorded as an error and the later legs still
+    run, so the bench always prints its line."""
+    import bench
+
+    def ok(a, b):
+        return {"sum": a + b}
+
+    def boom(a, b):
+        raise MemoryError("out of device memory")
+    extras = {}
+    bench.run_legs(extras, [("first", ok), ("second", boom), ("third", ok)], 1, 2)
+    assert extras["first"] == {"sum": 3} and extras["third"] == {"sum": 3}
+    assert extras["second"] == {"error": "MemoryError: out of device memory"}
