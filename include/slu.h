@@ -361,11 +361,11 @@ slu_status slu_solve_refine_noalloc(const slu_handle *h, const double *B,
  *
  * slu_plan_deserialize: a new plan from such a buffer (host, read during the
  * call only), equal field for field to the one written (the same digest).
- * A buffer that is not a plan, is truncated, or fails its checksum is
- * SLU_ERR_INVALID_ARG; one written by a build of the library whose plan
- * layout or format version differs, or with another byte order, is
- * SLU_ERR_NOT_SUPPORTED (analyse the pattern again).  The checksum catches
- * corruption, not forgery: load only buffers this library wrote.
+ * A buffer that is not a plan, is truncated, fails its checksum or
+ * describes a plan that fails slu_plan_check is SLU_ERR_INVALID_ARG; one
+ * written by a build of the library whose plan layout or format version
+ * differs, or with another byte order, is SLU_ERR_NOT_SUPPORTED (analyse
+ * the pattern again).
  *
  * slu_plan_digest: a 64-bit checksum of the plan's contents (the analysis
  * time excluded), equal for equal plans; the checksum a serialized plan
@@ -373,6 +373,17 @@ slu_status slu_solve_refine_noalloc(const slu_handle *h, const double *B,
 slu_status slu_plan_serialize(const slu_plan *plan, void *buf, int64_t *size);
 slu_status slu_plan_deserialize(const void *buf, int64_t size, slu_plan **out);
 slu_status slu_plan_digest(const slu_plan *plan, uint64_t *digest);
+
+/* Plan invariants (no counterpart in the paper): every index the
+ * factorization and the solves take from the plan lies inside the array or
+ * block it addresses, every offset array is nondecreasing and ends at its
+ * array's length, and every task relates the blocks its kernel expects
+ * (GESSM/TSTRF panels of their diagonal block, Schur sources L_KI and U_IJ
+ * of their target K,J with I < K,J, tiles inside their target).  Host only,
+ * linear in the plan's size; slu_plan_deserialize runs it on every loaded
+ * plan.  SLU_OK, or SLU_ERR_INVALID_ARG naming the first violated
+ * invariant in slu_last_error(). */
+slu_status slu_plan_check(const slu_plan *plan);
 
 void slu_plan_destroy(slu_plan *plan);
 void slu_handle_destroy(slu_handle *h);

@@ -73,7 +73,8 @@ EXPORTS = ["slu_opts_default", "slu_analyze", "slu_analyze_batch",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
            "slu_export_factors", "slu_grad_values", "slu_set_profiling", "slu_handle_stats",
            "slu_plan_flops", "slu_handle_trace", "slu_set_graph", "slu_solve_refine_noalloc",
-           "slu_plan_serialize", "slu_plan_deserialize", "slu_plan_digest", "slu_plan_destroy",
+           "slu_plan_serialize", "slu_plan_deserialize", "slu_plan_digest", "slu_plan_check",
+           "slu_plan_destroy",
            "slu_handle_destroy", "slu_last_error"]
 
 
@@ -112,6 +113,7 @@ def _load():
     lib.slu_plan_serialize.argtypes = [P, P, C.POINTER(C.c_int64)]
     lib.slu_plan_deserialize.argtypes = [P, C.c_int64, C.POINTER(P)]
     lib.slu_plan_digest.argtypes = [P, C.POINTER(C.c_uint64)]
+    lib.slu_plan_check.argtypes = [P]
     lib.slu_plan_destroy.argtypes = [P]
     lib.slu_plan_destroy.restype = None
     lib.slu_handle_destroy.argtypes = [P]
@@ -269,6 +271,11 @@ class Plan:
     def load(cls, path):
         """A plan from a file written by ``save``."""
         return cls.from_bytes(np.fromfile(path, dtype=np.uint8))
+
+    def check(self):
+        """Raise SluError unless every index the kernels take from the plan
+        is in range (``slu_plan_check``)."""
+        _check(lib.slu_plan_check(self._h))
 
     def digest(self):
         """64-bit checksum of the plan's contents (``slu_plan_digest``)."""

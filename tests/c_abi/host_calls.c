@@ -39,6 +39,7 @@ int main(void) {
     CHECK(slu_analyze(N, colptr, rowidx, &o, &p) == SLU_OK && p != NULL);
     slu_plan_info info;
     CHECK(slu_plan_query(p, &info) == SLU_OK);
+    CHECK(slu_plan_check(p) == SLU_OK);
     /* no fill for a tridiagonal pattern; Algorithm 2 ends at nnz */
     CHECK(info.n == N && info.nnz_a == nnz && info.nnz_lu == nnz);
     CHECK(info.flops == 3 * (N - 1));          /* l_k = u_k = 1: 1 + 2 */
@@ -73,6 +74,7 @@ int main(void) {
     CHECK(strstr(slu_last_error(), "out of range") != NULL);
     CHECK(slu_analyze(N, colptr, rowidx, &o, NULL) == SLU_ERR_INVALID_ARG);
     CHECK(slu_plan_query(NULL, &info) == SLU_ERR_INVALID_ARG);
+    CHECK(slu_plan_check(NULL) == SLU_ERR_INVALID_ARG);
 
     slu_plan_destroy(q);
     slu_plan_destroy(p);
