@@ -458,8 +458,15 @@ static slu_status build_blocks(slu_plan &P) {
     const int64_t nb = (int64_t)P.blocks.size();
     {
         int64_t ncol = 0;
-        for (const BlockDesc &d : P.blocks)
-            if (!d.dense) ncol += d.cols + 1;
+        for (int64_t b = 0; b < nb; ++b) {
+            const BlockDesc &d = P.blocks[b];
+            if (d.dense) continue;
+            ncol += d.cols + 1;
+            // local positions inside a sparse block are 32-bit
+            if (P.bnnz[b] > INT32_MAX)
+                return fail(SLU_ERR_NOT_SUPPORTED,
+                            "sparse block with more than 2^31 entries");
+        }
         if (ncol > INT32_MAX)
             return fail(SLU_ERR_NOT_SUPPORTED, "too many sparse block columns");
     }
