@@ -232,3 +232,34 @@ def test_plan_bit_exact_degenerate(name, mk, opts):
     else:
         assert P.info["nnz_lu"] == s.n * s.n
         assert np.array_equal(P.export()["blockptr"], np.arange(s.n + 1) ** 2)
+
+
+@pytest.mark.parametrize("name,mk,opts", [
+    ("grid5_48", lambda: workloads.grid5(48), {}),
+    ("grid7cd_12 regular 37", lambda: workloads.grid7_cd(12),
+     dict(blocking="regular", regular_block=37)),
+    ("circuit_3000", lambda: workloads.circuit_bbd(n=3000, border=60,
+                                                   block_lo=16, block_hi=64),
+     dict(b_min=8)),
+])
+def test_flops_by_kernel_class(name, mk, opts):
+    """The per-class flops behind the roofline fractions: column k of L has
+    l_in entries in its own block row and l_out below it; GETRF does
+    l_in + 2 l_in^2, the panels l_out + 4 l_in l_out, the Schur updates
+    2 l_out^2 (u_k = l_k by symmetry), summing to Table 3's count.
+    Recomputed from the oracle's fill pattern and the plan's boundaries."""
+    s = mk()
+    P = S.Plan(s.n, s.colptr, s.rowidx, **opts)
+    cp, ri, _ = OL.lu_pattern(OL.lu(s.n, s.colptr, s.rowidx, s.values))
+    blk = np.searchsorted(P.export()["ptr"], np.arange(s.n), side="right") - 1
+    want = np.zeros(3)
+    for k in range(s.n):
+        r = ri[cp[k]:cp[k + 1]]
+        r = r[r > k]
+        lin = float(np.sum(blk[r] == blk[k]))
+        lout = float(r.size) - lin
+        want += [lin + 2 * lin * lin, lout + 4 * lin * lout, 2 * lout * lout]
+    got = P.flops_by_class()
+    assert [got["getrf"], got["panel"], got["ssssm"]] == want.tolist()
+    assert sum(got.values()) == P.info["flops"] == OL.flops(
+        OL.lu(s.n, s.colptr, s.rowidx, s.values))
