@@ -379,7 +379,10 @@ slu_status slu_plan_digest(const slu_plan *plan, uint64_t *digest);
  * block it addresses, every offset array is nondecreasing and ends at its
  * array's length, and every task relates the blocks its kernel expects
  * (GESSM/TSTRF panels of their diagonal block, Schur sources L_KI and U_IJ
- * of their target K,J with I < K,J, tiles inside their target).  Host only,
+ * of their target K,J with I < K,J, tiles inside their target), and that
+ * the kernels' task lists carry every task of Algorithm 1 exactly once
+ * (chunks and tiles covering each task once, sources in ascending order
+ * per target).  Host only,
  * linear in the plan's size; slu_plan_deserialize runs it on every loaded
  * plan.  SLU_OK, or SLU_ERR_INVALID_ARG naming the first violated
  * invariant in slu_last_error(). */

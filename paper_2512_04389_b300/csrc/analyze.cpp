@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <exception>
+#include <map>
 #include <new>
 #include <numeric>
 #include <system_error>
@@ -1964,13 +1965,172 @@ std::string plan_violation(const slu_plan &P) {
     return std::string();
 }
 
+// Completeness of the execution splits (runs once plan_violation has found
+// every index in range): per level, the dense/sparse GETRF lists and the
+// solve's inverse split partition the level's GETRF list; every GESSM and
+// TSTRF task is carried by exactly one panel kernel, whose chunks cover its
+// vectors exactly once; every Schur source pair of the level is carried
+// exactly once, by the dense tiles (which cover their target exactly once)
+// or by the generic kernel, in ascending source order per target; every
+// inverse-eligible diagonal block gets both inverses in row chunks covering
+// it exactly once; and each sweep's pull pairs of a diagonal block are its
+// block list in order.
+std::string coverage_violation(const slu_plan &P) {
+#define REQ(c, what)                  \
+    do {                              \
+        if (!(c)) return (what);      \
+    } while (0)
+    const int64_t L = P.nlevels;
+    const std::vector<BlockDesc> &B = P.blocks;
+    const int esz = P.opts.precision == SLU_PREC_FP64 ? 8 : 4;
+    const int32_t kTile = P.opts.precision == SLU_PREC_FP32 ? 128 : 64;
+    auto key = [](int64_t type, int64_t a, int64_t b) {
+        return ((uint64_t)type << 62) | ((uint64_t)a << 31) | (uint64_t)b;
+    };
+    // chunk starts 0, step, 2 step, ... below `extent`, each exactly once
+    auto covers = [](std::vector<int32_t> &starts, int32_t step, int32_t extent) {
+        std::sort(starts.begin(), starts.end());
+        if ((int64_t)starts.size() != (extent + step - 1) / step) return false;
+        for (size_t i = 0; i < starts.size(); ++i)
+            if (starts[i] != (int32_t)i * step) return false;
+        return true;
+    };
+    for (int64_t lv = 0; lv < L; ++lv) {
+        const int64_t g0 = P.getrf_off[lv], g1 = P.getrf_off[lv + 1];
+        // GETRF: dense + sparse lists, and the solve split by positions
+        std::vector<int32_t> want(P.getrf.begin() + g0, P.getrf.begin() + g1), got;
+        got.insert(got.end(), P.gd.begin() + P.gd_off[lv], P.gd.begin() + P.gd_off[lv + 1]);
+        got.insert(got.end(), P.gs.begin() + P.gs_off[lv], P.gs.begin() + P.gs_off[lv + 1]);
+        std::sort(want.begin(), want.end());
+        std::sort(got.begin(), got.end());
+        REQ(got == want, "GETRF split");
+        std::vector<int32_t> pos(P.dv_pos.begin() + P.dv_off[lv], P.dv_pos.begin() + P.dv_off[lv + 1]);
+        pos.insert(pos.end(), P.dn_pos.begin() + P.dn_off[lv], P.dn_pos.begin() + P.dn_off[lv + 1]);
+        std::sort(pos.begin(), pos.end());
+        REQ((int64_t)pos.size() == g1 - g0, "solve split");
+        for (size_t i = 0; i < pos.size(); ++i) REQ(pos[i] == g0 + (int64_t)i, "solve split");
+        for (int64_t q = P.dv_off[lv]; q < P.dv_off[lv + 1]; ++q)
+            REQ(P.woff[B[P.getrf[P.dv_pos[q]]].I] >= 0, "solve split");
+        for (int64_t q = P.dn_off[lv]; q < P.dn_off[lv + 1]; ++q)
+            REQ(P.woff[B[P.getrf[P.dn_pos[q]]].I] < 0, "solve split");
+        // inverses: both triangles of every eligible block, 8-row chunks
+        std::map<uint64_t, std::vector<int32_t>> inv;
+        for (int64_t t = P.inv_off[lv]; t < P.inv_off[lv + 1]; ++t)
+            inv[key(P.inv_task[3 * t + 1], P.inv_task[3 * t], 0)].push_back(P.inv_task[3 * t + 2]);
+        size_t ninv = 0;
+        for (int64_t g = g0; g < g1; ++g) {
+            const int32_t db = P.getrf[g];
+            if (P.woff[B[db].I] < 0) continue;
+            for (int which = 0; which < 2; ++which) {
+                auto it = inv.find(key(which, db, 0));
+                REQ(it != inv.end() && covers(it->second, 8, B[db].rows), "inverse chunks");
+                ++ninv;
+            }
+        }
+        REQ(ninv == inv.size(), "inverse task of another level");
+        // panels: each task in exactly one kernel, its vectors covered once
+        std::map<uint64_t, std::vector<int32_t>> pd, pv;
+        std::map<uint64_t, int> ps, pg;
+        for (int64_t t = P.pd_off[lv]; t < P.pd_off[lv + 1]; ++t)
+            pd[key(P.pd_task[4 * t], P.pd_task[4 * t + 1], P.pd_task[4 * t + 2])]
+                .push_back(P.pd_task[4 * t + 3]);
+        for (int64_t t = P.pv_off[lv]; t < P.pv_off[lv + 1]; ++t)
+            pv[key(P.pv_task[4 * t], P.pv_task[4 * t + 1], P.pv_task[4 * t + 2])]
+                .push_back(P.pv_task[4 * t + 3]);
+        for (int64_t t = P.ps_off[lv]; t < P.ps_off[lv + 1]; ++t)
+            ++ps[key(P.ps_task[3 * t], P.ps_task[3 * t + 1], P.ps_task[3 * t + 2])];
+        for (int64_t t = P.pg_goff[lv]; t < P.pg_goff[lv + 1]; ++t)
+            ++pg[key(0, P.pg_gessm[2 * t], P.pg_gessm[2 * t + 1])];
+        for (int64_t t = P.pg_toff[lv]; t < P.pg_toff[lv + 1]; ++t)
+            ++pg[key(1, P.pg_tstrf[2 * t], P.pg_tstrf[2 * t + 1])];
+        size_t npanel = 0;
+        for (int type = 0; type < 2; ++type) {
+            const std::vector<int32_t> &task = type == 0 ? P.gessm : P.tstrf;
+            const std::vector<int64_t> &off = type == 0 ? P.gessm_off : P.tstrf_off;
+            for (int64_t e = off[lv]; e < off[lv + 1]; ++e) {
+                const int32_t tb = task[2 * e], db = task[2 * e + 1];
+                const uint64_t k = key(type, tb, db);
+                const int32_t nvec = type == 0 ? B[tb].cols : B[tb].rows;
+                const auto a = pd.find(k), b = pv.find(k);
+                const int kinds = (a != pd.end()) + (b != pv.end()) + (int)ps.count(k) +
+                                  (int)pg.count(k);
+                REQ(kinds == 1, "panel task carried by one kernel");
+                if (a != pd.end()) REQ(covers(a->second, 64, nvec), "panel chunks");
+                if (b != pv.end())
+                    REQ(covers(b->second, panel_vec_width(B[db].rows, esz), nvec), "panel vectors");
+                if (ps.count(k)) REQ(ps[k] == 1, "sparse panel task repeated");
+                if (pg.count(k)) REQ(pg[k] == 1, "generic panel task repeated");
+                ++npanel;
+            }
+        }
+        REQ(npanel == pd.size() + pv.size() + ps.size() + pg.size(), "panel task of another level");
+        // Schur updates: every source pair once, dense tiles covering targets
+        std::vector<std::array<int32_t, 3>> wantp, gotp;
+        for (int64_t k = P.tgt_off[lv]; k < P.tgt_off[lv + 1]; ++k)
+            for (int64_t q = P.srcoff[k]; q < P.srcoff[k + 1]; ++q)
+                wantp.push_back({P.tgt[k], P.src[2 * q], P.src[2 * q + 1]});
+        auto ascending = [&](const std::vector<int32_t> &sr, int64_t q0, int64_t q1) {
+            for (int64_t q = q0 + 1; q < q1; ++q)
+                if (B[sr[2 * q]].J <= B[sr[2 * q - 2]].J) return false;
+            return true;
+        };
+        std::map<std::array<int32_t, 3>, std::vector<std::pair<int32_t, int32_t>>> tiles;
+        for (int64_t t = P.gm_off[lv]; t < P.gm_off[lv + 1]; ++t)
+            tiles[{P.gm_task[5 * t], P.gm_task[5 * t + 1], P.gm_task[5 * t + 2]}].push_back(
+                {P.gm_task[5 * t + 3], P.gm_task[5 * t + 4]});
+        std::map<int32_t, int> dense_tgt;
+        for (auto &e : tiles) {
+            const int32_t tb = e.first[0], s0 = e.first[1], s1 = e.first[2];
+            REQ(++dense_tgt[tb] == 1, "dense target split over source ranges");
+            REQ(ascending(P.gm_src, s0, s1), "dense sources out of order");
+            for (int32_t q = s0; q < s1; ++q) gotp.push_back({tb, P.gm_src[2 * q], P.gm_src[2 * q + 1]});
+            std::vector<std::pair<int32_t, int32_t>> &rc = e.second;
+            std::sort(rc.begin(), rc.end());
+            const int32_t nr = (B[tb].rows + kTile - 1) / kTile, nc = (B[tb].cols + 63) / 64;
+            REQ((int64_t)rc.size() == (int64_t)nr * nc, "dense tiles of a target");
+            for (int32_t i = 0; i < nr; ++i)
+                for (int32_t j = 0; j < nc; ++j)
+                    REQ(rc[(size_t)i * nc + j] == std::make_pair(i * kTile, j * 64),
+                        "dense tiles of a target");
+        }
+        std::map<int32_t, int> generic_tgt;
+        for (int64_t k = P.gg_off[lv]; k < P.gg_off[lv + 1]; ++k) {
+            REQ(++generic_tgt[P.gg_tgt[k]] == 1, "generic target repeated");
+            REQ(ascending(P.gg_src, P.gg_srcoff[k], P.gg_srcoff[k + 1]), "generic sources out of order");
+            for (int64_t q = P.gg_srcoff[k]; q < P.gg_srcoff[k + 1]; ++q)
+                gotp.push_back({P.gg_tgt[k], P.gg_src[2 * q], P.gg_src[2 * q + 1]});
+        }
+        std::sort(wantp.begin(), wantp.end());
+        std::sort(gotp.begin(), gotp.end());
+        REQ(gotp == wantp, "Schur source pairs of the level");
+        // solve pulls: a diagonal block's pairs are its block list, in order
+        const std::vector<int64_t> *offs[4] = {&P.lrow_off, &P.urow_off, &P.ucol_off, &P.lcol_off};
+        const std::vector<int32_t> *ids[4] = {&P.lrow_blk, &P.urow_blk, &P.ucol_blk, &P.lcol_blk};
+        for (int sw = 0; sw < 4; ++sw) {
+            int64_t at = P.sp_off[sw][lv];
+            for (int64_t g = g0; g < g1; ++g) {
+                const int32_t db = P.getrf[g], I = B[db].I;
+                REQ(P.sd_pair0[sw][g] == at, "solve pairs of a block");
+                for (int64_t q = (*offs[sw])[I]; q < (*offs[sw])[I + 1]; ++q, ++at)
+                    REQ(at < P.sp_off[sw][lv + 1] && P.sp_pairs[sw][2 * at] == (*ids[sw])[q] &&
+                            P.sp_pairs[sw][2 * at + 1] == db,
+                        "solve pairs of a block");
+            }
+            REQ(at == P.sp_off[sw][lv + 1], "solve pairs of a level");
+        }
+    }
+#undef REQ
+    return std::string();
+}
+
 }  // namespace
 }  // namespace slu
 
 extern "C" slu_status slu_plan_check(const slu_plan *P) {
     if (!P) return fail(SLU_ERR_INVALID_ARG, "NULL plan");
     try {
-        const std::string v = plan_violation(*P);
+        std::string v = plan_violation(*P);
+        if (v.empty()) v = coverage_violation(*P);
         if (!v.empty()) return fail(SLU_ERR_INVALID_ARG, "plan invariant violated: " + v);
     } catch (const std::exception &e) {
         return fail(SLU_ERR_OUT_OF_MEMORY, std::string("plan check: ") + e.what());
