@@ -128,7 +128,7 @@ def test_serialization_lists_every_plan_field():
         if m:
             members |= {x.strip(" *") for x in m.group(1).split(",") if x.strip()}
     assert {"opts", "a2s", "f2s", "sp_off", "flops_cls", "dev"} <= members
-    cpp = open(os.path.join(CSRC, "analyze.cpp")).read()
+    cpp = open(os.path.join(CSRC, "plan_io.cpp")).read()
     macro = cpp[cpp.index("#define SLU_PLAN_FIELDS(X)"):]
     macro = macro[:macro.index("\n\n")]
     listed = set(re.findall(r"X\((\w+)\)", macro))
