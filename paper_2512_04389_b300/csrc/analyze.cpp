@@ -685,11 +685,16 @@ static void build_levels_and_tasks(slu_plan &P) {
     };
     const int32_t L = P.nlevels;
     std::vector<std::vector<int32_t>> lv_getrf(L), lv_gessm(L), lv_tstrf(L);
+    // a level's Schur targets; the source pairs of target t are
+    // lv_pairs[lv][2 first .. 2 (first + count)), in the order found
     struct Tgt {
         int32_t K, J, tb;
-        std::vector<int32_t> srcs;
+        int64_t first, count;
     };
     std::vector<std::vector<Tgt>> lv_ss(L);
+    std::vector<std::vector<int32_t>> lv_pairs(L);
+    std::vector<int32_t> trip;                  // (slot, lb, ub) as found
+    std::vector<int64_t> at;
     // walk block rows level by level (ascending I inside a level), so that
     // a target's slot is only ever looked up within its own level
     std::vector<std::vector<int32_t>> rows_of(L);
@@ -697,6 +702,7 @@ static void build_levels_and_tasks(slu_plan &P) {
     std::vector<int32_t> slot(nb, -1);
     for (int32_t lv = 0; lv < L; ++lv) {
         auto &vec = lv_ss[lv];
+        trip.clear();
         for (int32_t I : rows_of[lv]) {
             const int32_t db = P.diagblk[I];
             lv_getrf[lv].push_back(db);
@@ -716,12 +722,28 @@ static void build_levels_and_tasks(slu_plan &P) {
                     if (tb < 0) continue;
                     if (slot[tb] < 0) {
                         slot[tb] = (int32_t)vec.size();
-                        vec.push_back(Tgt{K, J, tb, {}});
+                        vec.push_back(Tgt{K, J, tb, 0, 0});
                     }
-                    vec[slot[tb]].srcs.push_back(lb);
-                    vec[slot[tb]].srcs.push_back(ub);
+                    trip.push_back(slot[tb]);
+                    trip.push_back(lb);
+                    trip.push_back(ub);
                 }
             }
+        }
+        // group the pairs by target, keeping their order (counting sort)
+        at.assign(vec.size() + 1, 0);
+        for (size_t t = 0; t < trip.size(); t += 3) at[trip[t] + 1]++;
+        for (size_t k = 0; k < vec.size(); ++k) {
+            vec[k].first = at[k];
+            vec[k].count = at[k + 1];
+            at[k + 1] += at[k];
+        }
+        auto &pairs = lv_pairs[lv];
+        pairs.resize(trip.size() / 3 * 2);
+        for (size_t t = 0; t < trip.size(); t += 3) {
+            const int64_t q = at[trip[t]]++;
+            pairs[2 * q] = trip[t + 1];
+            pairs[2 * q + 1] = trip[t + 2];
         }
         for (const Tgt &t : vec) slot[t.tb] = -1;
     }
@@ -739,6 +761,16 @@ static void build_levels_and_tasks(slu_plan &P) {
     P.tgt.clear();
     P.src.clear();
     P.srcoff.assign(1, 0);
+    {
+        size_t ntgt = 0, npair = 0;
+        for (int32_t lv = 0; lv < L; ++lv) {
+            ntgt += lv_ss[lv].size();
+            npair += lv_pairs[lv].size();
+        }
+        P.tgt.reserve(ntgt);
+        P.srcoff.reserve(ntgt + 1);
+        P.src.reserve(npair);
+    }
     for (int32_t lv = 0; lv < L; ++lv) {
         P.getrf.insert(P.getrf.end(), lv_getrf[lv].begin(), lv_getrf[lv].end());
         P.gessm.insert(P.gessm.end(), lv_gessm[lv].begin(), lv_gessm[lv].end());
@@ -747,11 +779,14 @@ static void build_levels_and_tasks(slu_plan &P) {
         std::sort(vec.begin(), vec.end(), [](const Tgt &a, const Tgt &b) {
             return a.K != b.K ? a.K < b.K : a.J < b.J;
         });
+        const auto &pairs = lv_pairs[lv];
         for (auto &t : vec) {
             P.tgt.push_back(t.tb);
-            P.src.insert(P.src.end(), t.srcs.begin(), t.srcs.end());
+            P.src.insert(P.src.end(), pairs.begin() + 2 * t.first,
+                         pairs.begin() + 2 * (t.first + t.count));
             P.srcoff.push_back((int64_t)P.src.size() / 2);
         }
+        std::vector<int32_t>().swap(lv_pairs[lv]);
         P.getrf_off[lv + 1] = (int64_t)P.getrf.size();
         for (int32_t db : lv_getrf[lv]) (P.blocks[db].dense ? P.gd : P.gs).push_back(db);
         P.gd_off[lv + 1] = (int64_t)P.gd.size();
@@ -774,6 +809,7 @@ static void build_levels_and_tasks(slu_plan &P) {
     const int32_t kTile = P.opts.precision == SLU_PREC_FP32 ? 128 : 64;
     P.gm_mid.assign(L, 0);
     P.gg_mid.assign(L, 0);
+    std::vector<int32_t> dense_pairs, other;
     for (int32_t lv = 0; lv < L; ++lv) {
       // pass 0: targets in a block row or column of the next level (needed
       // by its GETRF / GESSM / TSTRF); pass 1: the rest, which touch no
@@ -788,7 +824,8 @@ static void build_levels_and_tasks(slu_plan &P) {
             const BlockDesc &td = P.blocks[tb];
             const bool next = P.level[std::min(td.I, td.J)] == lv + 1;
             if (next != (pass == 0)) continue;
-            std::vector<int32_t> dense_pairs, other;
+            dense_pairs.clear();
+            other.clear();
             for (int64_t q = P.srcoff[k]; q < P.srcoff[k + 1]; ++q) {
                 const int32_t lb = P.src[2 * q], ub = P.src[2 * q + 1];
                 if (td.dense && P.blocks[lb].dense && P.blocks[ub].dense) {
