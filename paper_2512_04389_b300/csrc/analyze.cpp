@@ -1038,17 +1038,31 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         if (colptr[j + 1] < colptr[j])
             return fail(SLU_ERR_INVALID_ARG, "colptr not monotone");
     const int64_t nnz = colptr[n];
+    // row indices in range and no repeated (row, column): threads take
+    // column ranges, each stopping at its first bad entry; the entry
+    // reported is the earliest one, the one a sequential scan would meet
     try {
-        std::vector<int64_t> seen(n, -1);
-        for (int64_t j = 0; j < n; ++j)
-            for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
-                const int32_t r = rowidx[q];
-                if (r < 0 || r >= n)
-                    return fail(SLU_ERR_INVALID_ARG, "row index out of range");
-                if (seen[r] == j)
-                    return fail(SLU_ERR_INVALID_ARG, "duplicate entry");
-                seen[r] = j;
-            }
+        const int nt = host_threads(n);
+        const std::vector<int64_t> cut =
+            balanced_cuts(n, [&](int64_t j) { return colptr[j]; }, nt);
+        std::vector<int64_t> bad(nt, INT64_MAX);
+        std::vector<int> kind(nt, 0);
+        run_threads(nt, [&](int t) {
+            std::vector<int32_t> seen(n, -1);   // column that last held row r
+            for (int64_t j = cut[t]; j < cut[t + 1]; ++j)
+                for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
+                    const int32_t r = rowidx[q];
+                    if (r < 0 || r >= n || seen[r] == j) {
+                        bad[t] = q;
+                        kind[t] = (r < 0 || r >= n) ? 1 : 2;
+                        return;
+                    }
+                    seen[r] = (int32_t)j;
+                }
+        });
+        const int t = (int)(std::min_element(bad.begin(), bad.end()) - bad.begin());
+        if (kind[t] == 1) return fail(SLU_ERR_INVALID_ARG, "row index out of range");
+        if (kind[t] == 2) return fail(SLU_ERR_INVALID_ARG, "duplicate entry");
     } catch (const std::exception &) {
         return fail(SLU_ERR_OUT_OF_MEMORY, "host allocation in analyze");
     }

@@ -263,3 +263,21 @@ def test_flops_by_kernel_class(name, mk, opts):
     assert [got["getrf"], got["panel"], got["ssssm"]] == want.tolist()
     assert sum(got.values()) == P.info["flops"] == OL.flops(
         OL.lu(s.n, s.colptr, s.rowidx, s.values))
+
+
+@pytest.mark.parametrize("threads", ["1", "8"])
+def test_first_bad_entry_is_reported(threads, monkeypatch):
+    """With bad entries in several columns the analysis reports the one a
+    sequential scan meets first, whichever thread scans it."""
+    monkeypatch.setenv("SLU_HOST_THREADS", threads)
+    n = 2000
+    cp = np.arange(0, 2 * n + 1, 2, dtype=np.int64)      # two entries a column
+    base = np.stack([np.arange(n), (np.arange(n) + 1) % n], 1).reshape(-1)
+    for early, late, msg in ((("dup", 3), ("range", n - 5), "duplicate entry"),
+                             (("range", 3), ("dup", n - 5), "out of range")):
+        ri = base.astype(np.int32).copy()
+        for what, col in (early, late):
+            ri[2 * col + 1] = ri[2 * col] if what == "dup" else n + 7
+        with pytest.raises(S.SluError) as e:
+            S.Plan(n, cp, ri)
+        assert e.value.status == 1 and msg in str(e.value)
