@@ -382,10 +382,10 @@ slu_status slu_plan_digest(const slu_plan *plan, uint64_t *digest);
  * of their target K,J with I < K,J, tiles inside their target), and that
  * the kernels' task lists carry every task of Algorithm 1 exactly once
  * (chunks and tiles covering each task once, sources in ascending order
- * per target).  Host only,
- * linear in the plan's size; slu_plan_deserialize runs it on every loaded
- * plan.  SLU_OK, or SLU_ERR_INVALID_ARG naming the first violated
- * invariant in slu_last_error(). */
+ * per target).  Host only, N log N in the plan's size (3 s for a plan of
+ * 354 M filled entries); slu_plan_deserialize runs it on every loaded plan.
+ * SLU_OK, or SLU_ERR_INVALID_ARG naming the first violated invariant in
+ * slu_last_error(). */
 slu_status slu_plan_check(const slu_plan *plan);
 
 void slu_plan_destroy(slu_plan *plan);

@@ -16,9 +16,10 @@ using namespace slu;
 // Plan invariants: every index the factorization and the solves take from a
 // plan addresses an element of the array or block it names, every offset
 // array is nondecreasing and ends at its array's length, and every task pair
-// relates the blocks its kernel expects.  Host-only, linear in the plan's
-// size.  The analysis establishes these by construction; the check guards
-// plans loaded from bytes and the analysis itself in the tests.
+// relates the blocks its kernel expects (linear in the plan's size); then
+// the execution splits are complete (coverage_violation, N log N).  The
+// analysis establishes these by construction; the check guards plans loaded
+// from bytes and the analysis itself in the tests.
 
 namespace slu {
 namespace {
