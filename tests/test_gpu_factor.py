@@ -27,6 +27,7 @@ def _dev(x):
 
 def gpu_factor(s, **opts):
     P = S.Plan(s.n, s.colptr, s.rowidx, **opts)
+    P.check()                  # every index the kernels read is in range
     F = S.Factor(P, _dev(s.values))
     return P, F
 
