@@ -232,6 +232,9 @@ slu_status slu_plan_export_tasks(const slu_plan *plan, int64_t *getrf_off,
  * with SLU_ERR_SINGULAR a handle is still returned (factors not usable).
  * SLU_ERR_TIMEOUT reports that a tensor-core tile's bounded wait for its own
  * MMAs ran out (that tile's update was skipped; factors not usable).
+ * SLU_ERR_INVALID_ARG reports a NaN or infinite entry in values (found by
+ * the max|a| reduction on the device; slu_refactor reports it when info is
+ * requested).
  * The handle owns a second, non-blocking stream: each level's Schur updates
  * whose target lies outside the next level's block rows and columns run
  * there, forked from `stream` after the level's panels and joined back
@@ -239,6 +242,31 @@ slu_status slu_plan_export_tasks(const slu_plan *plan, int64_t *getrf_off,
  * earlier work on `stream` and completes before later work on it. */
 slu_status slu_factor(const slu_plan *plan, const double *values,
                       void *stream, slu_handle **out, slu_factor_info *info);
+
+/* Batch factorization of independent matrices (Section 2.2's level walk
+ * over many matrices at once; the batching form).  plans: count host
+ * pointers to single-matrix plans from slu_analyze, all with equal options
+ * (else SLU_ERR_NOT_SUPPORTED); values: count device pointers, values[q]
+ * float64[nnz_a of plans[q]] in the CSC order of that plan's pattern.  The
+ * call builds the batch plan of the members' patterns (the analysis of
+ * slu_analyze_batch, on the host, each member blocked on its own), gathers
+ * the values into one device array, and factors every member in the same
+ * per-level launches on `stream` (the deferred Schur updates on a second
+ * stream, as slu_factor).  out: host array of count handle pointers; out[q]
+ * behaves as slu_factor's handle for plans[q] (slu_solve,
+ * slu_solve_transpose, slu_export_factors, slu_refactor of that member
+ * alone, slu_handle_destroy), its factors equal to slu_factor's for that
+ * plan bit for bit.  The members' factors live in one shared device
+ * allocation, freed with the last of the count handles; each handle owns
+ * its own solve state.  The perturbation threshold tau uses max|a| over
+ * all members (as a slu_analyze_batch plan does); info (may be NULL)
+ * receives the batch's perturbation count and tau.  Synchronizes the
+ * stream.  Returns SLU_OK or SLU_ERR_SINGULAR (handles returned, as
+ * slu_factor); on any other status every out[q] is NULL and nothing is
+ * kept.  A member plan must not be destroyed while its handle lives. */
+slu_status slu_factor_batch(int32_t count, const slu_plan *const *plans,
+                            const double *const *values, void *stream,
+                            slu_handle **out, slu_factor_info *info);
 
 /* Re-run the factorization into an existing handle with new values of the
  * same pattern; no allocation.  Enqueues only (info may be NULL; if not
@@ -320,25 +348,30 @@ slu_status slu_plan_flops(const slu_plan *plan, double *out);
 /* Allocation-free refined solve (no counterpart in the paper).
  *
  * The same computation as slu_solve with refinement (and with the backward
- * error always computed), for callers that may not allocate device memory
- * when they solve: a process whose device memory is budgeted and handed out
- * entirely at start-up, an application whose framework owns all device
- * memory through its own pool, or a latency-critical loop that cannot
- * afford cudaMalloc's implicit synchronization.  slu_solve allocates its
- * refinement workspace on first use; this call allocates nothing (no
- * cudaMalloc, cudaFree or allocating library routine).  Its residual and
- * reduction scratch is a fixed array in the library's device image,
- * SLU_NOALLOC_MAX_ELEMS doubles plus 192 reduction words (about 8 MiB),
- * which every GPU that loads the library holds until the process exits.
+ * error always computed, per member for a slu_analyze_batch handle), for
+ * callers that may not allocate device memory when they solve: a process
+ * whose device memory is budgeted and handed out entirely at start-up, an
+ * application whose framework owns all device memory through its own pool,
+ * or a latency-critical loop that cannot afford cudaMalloc's implicit
+ * synchronization.  slu_solve allocates its refinement workspace on first
+ * use; this call allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine, and no host buffer either).  Its residual and reduction
+ * scratch is a fixed array in the library's device image,
+ * SLU_NOALLOC_MAX_ELEMS + 256 doubles (about 8 MiB), which every GPU that
+ * loads the library holds until the process exits.
  *
- * Arguments as slu_solve, except that X must not alias B and n * nrhs must
- * not exceed SLU_NOALLOC_MAX_ELEMS (else SLU_ERR_INVALID_ARG with a message
- * naming the limit).  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the one array and
- * it keeps the previous call's contents (the call clears what it needs
- * zeroed); calls whose GPU work overlaps race on it and must be ordered by
- * the caller.  Synchronizes the stream once per refinement iteration. */
+ * Arguments as slu_solve, except that X must not alias B, the current
+ * device must be the handle's (else SLU_ERR_INVALID_ARG), and the residual
+ * plus the reduction words must fit the array: n * nrhs <=
+ * SLU_NOALLOC_MAX_ELEMS and, rounded up to 32, plus 3 * nrhs words per
+ * matrix (one, or each member of a batch) plus one, <= SLU_NOALLOC_MAX_ELEMS
+ * + 256 (else SLU_ERR_INVALID_ARG with a message naming the limit).  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the previous call's contents (the call clears what it needs zeroed);
+ * calls whose GPU work overlaps race on it and must be ordered by the
+ * caller.  Synchronizes the stream once per refinement iteration. */
 #define SLU_NOALLOC_MAX_ELEMS (1 << 20)
 slu_status slu_solve_refine_noalloc(const slu_handle *h, const double *B,
                                     int64_t ldb, int32_t nrhs, double *X,

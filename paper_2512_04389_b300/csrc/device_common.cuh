@@ -202,6 +202,16 @@ BlockArgs block_args(const slu_plan *P);
 
 }  // namespace slu
 
+namespace slu {
+// One merged factorization behind the member handles of slu_factor_batch:
+// the batch plan and its handle, freed with the last member handle.
+struct BatchShared {
+    slu_plan *plan = nullptr;
+    slu_handle *h = nullptr;
+    int refs = 0;
+};
+}  // namespace slu
+
 // Handle: factor storage on one device plus refinement state.
 struct slu_handle {
     const slu_plan *plan = nullptr;
@@ -212,6 +222,9 @@ struct slu_handle {
     double *scal = nullptr;              // [0] max|A|, [1] ||A||_inf
     unsigned long long *cnt = nullptr;   // [0] perturbed pivots, [1] zero pivot
     double tau_rel = 0.0;
+    // member of a slu_factor_batch: storage, winv and a_vals point into the
+    // shared batch handle's arrays (not owned)
+    slu::BatchShared *batch = nullptr;
     // solve workspace (grown on demand)
     double *work = nullptr;
     int64_t work_elems = 0;

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "device_common.cuh"
@@ -32,14 +33,20 @@ namespace slu {
 // ---------------------------------------------------------------- kernels
 
 // out = max |v| (as the bit pattern of a non-negative double, which orders
-// like the value).
+// like the value); *bad = 1 when some value is NaN or infinite.
 __global__ void k_maxabs(int64_t n, const double *__restrict__ v,
-                         unsigned long long *__restrict__ out) {
+                         unsigned long long *__restrict__ out,
+                         unsigned long long *__restrict__ bad) {
     double m = 0.0;
+    bool nonfinite = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs(v[i]));
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = fabs(v[i]);
+        nonfinite |= !(a <= 1.7976931348623157e308);   // NaN or inf
+        m = fmax(m, a);
+    }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(~0u, m, o));
+    if (__any_sync(~0u, nonfinite) && (threadIdx.x & 31) == 0) atomicOr(bad, 1ull);
     if ((threadIdx.x & 31) == 0 && m > 0.0)
         atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
@@ -1405,13 +1412,20 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
         const int st = chunk & 1;
         unsigned char *base = smem + st * STAGE_BYTES;
         if (chunk >= 2) {               // the MMAs of chunk - 2 read this stage
-            ok = ok && wait_phase(smem_u32(&mbar[st]), phase[st]);
+            // CTA-uniform: if any thread's bounded wait ran out, nothing more
+            // is staged or issued (the stage may still be read) and the
+            // drain below waits for what was committed
+            const bool done = wait_phase(smem_u32(&mbar[st]), phase[st]);
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
+            }
             phase[st] ^= 1;
         }
         store(base);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0 && ok) {
+        if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_hi = smem_u32(base), a_lo = a_hi + A_BYTES;
             const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
@@ -1442,9 +1456,14 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
         }
         load(dl, du, k0);               // in flight while the tensor core works
     }
+    // drain: every committed chunk not yet waited for (chunk - 2 and
+    // chunk - 1, also after an expired wait, whose phase was not advanced);
+    // each wait is bounded and runs even when an earlier one expired, so
+    // TMEM is released only after the MMAs were given a second bound
     for (int c = max(0, chunk - 2); c < chunk; ++c) {
         const int st = c & 1;
-        ok = ok && wait_phase(smem_u32(&mbar[st]), phase[st]);
+        const bool done = wait_phase(smem_u32(&mbar[st]), phase[st]);
+        ok = __syncthreads_and(done) && ok;
         phase[st] ^= 1;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1751,14 +1770,15 @@ static slu_status run_factor(slu_handle *h, const double *values,
                  "cudaMemsetAsync(storage)") ||
         !cuda_ok(cudaMemsetAsync(h->scal, 0, 2 * sizeof(double), st),
                  "cudaMemsetAsync(scal)") ||
-        !cuda_ok(cudaMemsetAsync(h->cnt, 0, 3 * sizeof(unsigned long long), st),
+        !cuda_ok(cudaMemsetAsync(h->cnt, 0, 4 * sizeof(unsigned long long), st),
                  "cudaMemsetAsync(cnt)"))
         return SLU_ERR_CUDA;
     if (P->nnz_a > 0) {
         {
             LaunchScope ls_(h, SLU_KC_PREP, st);
             k_maxabs<<<grid_for(P->nnz_a, 256), 256, 0, st>>>(
-                P->nnz_a, values, reinterpret_cast<unsigned long long *>(h->scal));
+                P->nnz_a, values, reinterpret_cast<unsigned long long *>(h->scal),
+                h->cnt + 3);
         }
         {
             LaunchScope ls_(h, SLU_KC_PREP, st);
@@ -1891,7 +1911,7 @@ static slu_status run_factor(slu_handle *h, const double *values,
 
 static slu_status finish_info(slu_handle *h, cudaStream_t st,
                               slu_factor_info *info) {
-    unsigned long long c[3];
+    unsigned long long c[4];
     double s[2];
     if (!cuda_ok(cudaMemcpyAsync(c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, st),
                  "cudaMemcpyAsync(info)") ||
@@ -1903,6 +1923,7 @@ static slu_status finish_info(slu_handle *h, cudaStream_t st,
         info->nperturb = (int64_t)c[0];
         info->tau = h->tau_rel * s[0];
     }
+    if (c[3]) return fail(SLU_ERR_INVALID_ARG, "A holds a NaN or infinite value");
     if (c[2]) return fail(SLU_ERR_TIMEOUT, "a tensor-core wait exceeded its bound");
     if (c[1]) return fail(SLU_ERR_SINGULAR, "zero pivot (perturbation off)");
     return SLU_OK;
@@ -1927,11 +1948,21 @@ slu_status factor_into(slu_handle *h, const double *values, cudaStream_t st) {
 
 using namespace slu;
 
+static std::mutex g_batch_mu;
+
 extern "C" void slu_handle_destroy(slu_handle *h) {
     if (!h) return;
     int cur = -1;
     cudaGetDevice(&cur);
     if (h->device >= 0) cudaSetDevice(h->device);
+    BatchShared *shared = nullptr;
+    if (h->batch) {                  // member view: the arrays are the batch's
+        h->storage = nullptr;
+        h->winv = nullptr;
+        h->a_vals = nullptr;
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        if (--h->batch->refs == 0) shared = h->batch;
+    }
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
     for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.exec);
     if (h->xbuf) cudaFree(h->xbuf);
@@ -1946,6 +1977,11 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
         if (p) cudaFree(p);
     if (cur >= 0) cudaSetDevice(cur);
     delete h;
+    if (shared) {
+        slu_handle_destroy(shared->h);
+        slu_plan_destroy(shared->plan);
+        delete shared;
+    }
 }
 
 extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
@@ -1962,8 +1998,11 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
     cudaGetDevice(&h->device);
     h->prec = P->opts.precision;
     const bool fp64 = h->prec == SLU_PREC_FP64;
-    // Diagonal-block pivots are formed in FP64 for both storage precisions,
-    // so one threshold serves both: sqrt(eps64) ~ 2^-26 of max|A|.
+    // The pivot test and perturbation run in FP64 for both storage
+    // precisions (an FP32 pivot is read from FP32 storage, compared in FP64
+    // and stored back in FP32), with one threshold for both: sqrt(eps64) ~
+    // 2^-26 of max|A| (2^-12, sqrt(eps32), exceeds genuine pivots of the
+    // circuit matrices).
     if (P->opts.pivot_perturb)
         h->tau_rel = P->opts.pivot_tau_rel > 0 ? P->opts.pivot_tau_rel
                                                : std::ldexp(1.0, -26);
@@ -1972,7 +2011,7 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
         cuda_ok(cudaMalloc(&h->storage, std::max<int64_t>(1, P->storage) * esz),
                 "cudaMalloc(storage)") &&
         cuda_ok(cudaMalloc(&h->scal, 4 * sizeof(double)), "cudaMalloc") &&
-        cuda_ok(cudaMalloc(&h->cnt, 3 * sizeof(unsigned long long)), "cudaMalloc") &&
+        cuda_ok(cudaMalloc(&h->cnt, 4 * sizeof(unsigned long long)), "cudaMalloc") &&
         cuda_ok(cudaMalloc(&h->a_vals, std::max<int64_t>(1, P->nnz_a) * sizeof(double)),
                 "cudaMalloc(A)") &&
         cuda_ok(cudaMalloc(&h->part, std::max<int64_t>(1, P->part_elems) * 4 *
@@ -2007,6 +2046,184 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
     }
     *out = h;
     return st;
+}
+
+// Equal options, field by field (the struct has padding).
+static bool same_opts(const slu_opts &a, const slu_opts &b) {
+    return a.blocking == b.blocking && a.regular_block == b.regular_block &&
+           a.sample_points == b.sample_points && a.step == b.step &&
+           a.max_num == b.max_num && a.stride == b.stride && a.b_min == b.b_min &&
+           a.precision == b.precision && a.dense_threshold == b.dense_threshold &&
+           a.pivot_perturb == b.pivot_perturb && a.pivot_tau_rel == b.pivot_tau_rel &&
+           a.refine_tol == b.refine_tol && a.refine_max_iter == b.refine_max_iter &&
+           a.wait_budget_ms == b.wait_budget_ms;
+}
+
+// Where member q of batch plan M lives, checked against the member's own
+// plan: its blocks are M's blocks [b0, b0 + nblocks) (block columns shifted
+// by p0) with equal shapes, storage kinds and relative value offsets, and
+// its dense diagonal blocks' inverses equally shifted.  The factorization of
+// a block depends on that block's data and its own plan only, so the
+// member's slice of M's storage is then exactly what slu_factor on the
+// member's plan computes.
+struct MemberSlice { int64_t voff, woff, aoff; };
+static bool member_slice(const slu_plan *M, const slu_plan *Q, int32_t p0,
+                         int64_t b0, int64_t aoff, MemberSlice *out) {
+    const int64_t nb = (int64_t)Q->blocks.size();
+    if (b0 + nb > (int64_t)M->blocks.size()) return false;
+    const int64_t vbase = nb ? M->blocks[b0].voff - Q->blocks[0].voff : 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const BlockDesc &m = M->blocks[b0 + b], &q = Q->blocks[b];
+        if (m.I != q.I + p0 || m.J != q.J + p0 || m.rows != q.rows ||
+            m.cols != q.cols || m.dense != q.dense || m.ld != q.ld ||
+            m.voff != q.voff + vbase)
+            return false;
+    }
+    int64_t wbase = -1;
+    for (int32_t I = 0; I < Q->p; ++I) {
+        const int64_t wm = M->woff[p0 + I], wq = Q->woff[I];
+        if ((wm < 0) != (wq < 0)) return false;
+        if (wq < 0) continue;
+        if (wbase < 0) wbase = wm - wq;
+        if (wm != wq + wbase) return false;
+    }
+    out->voff = vbase;
+    out->woff = wbase < 0 ? 0 : wbase;
+    out->aoff = aoff;
+    return true;
+}
+
+extern "C" slu_status slu_factor_batch(int32_t count, const slu_plan *const *plans,
+                                       const double *const *values, void *stream,
+                                       slu_handle **out, slu_factor_info *info) {
+    if (count < 1 || !plans || !values || !out)
+        return fail(SLU_ERR_INVALID_ARG, "bad batch arguments");
+    for (int32_t q = 0; q < count; ++q) out[q] = nullptr;
+    for (int32_t q = 0; q < count; ++q) {
+        const slu_plan *Q = plans[q];
+        if (!Q) return fail(SLU_ERR_INVALID_ARG, "NULL plan in the batch");
+        if (Q->seg.size() > 2)
+            return fail(SLU_ERR_NOT_SUPPORTED, "a batch member is itself a batch plan");
+        if (!same_opts(Q->opts, plans[0]->opts))
+            return fail(SLU_ERR_NOT_SUPPORTED, "batch members differ in their options");
+        if (Q->nnz_a > 0 && !values[q])
+            return fail(SLU_ERR_INVALID_ARG, "values is NULL for a batch member");
+    }
+    // the batch plan: the members' patterns block-diagonally, each blocked
+    // on its own (the analysis of slu_analyze_batch)
+    std::vector<int64_t> ns(count);
+    std::vector<const int64_t *> cps(count);
+    std::vector<const int32_t *> ris(count);
+    for (int32_t q = 0; q < count; ++q) {
+        ns[q] = plans[q]->n;
+        cps[q] = plans[q]->a_colptr.data();
+        ris[q] = plans[q]->a_rowidx.data();
+    }
+    slu_plan *M = nullptr;
+    slu_status st = slu_analyze_batch(count, ns.data(), cps.data(), ris.data(),
+                                      &plans[0]->opts, &M);
+    if (st != SLU_OK) return st;
+    std::vector<MemberSlice> sl(count);
+    {
+        int32_t p0 = 0;
+        int64_t b0 = 0, aoff = 0;
+        for (int32_t q = 0; q < count; ++q) {
+            if (!member_slice(M, plans[q], p0, b0, aoff, &sl[q])) {
+                slu_plan_destroy(M);
+                return fail(SLU_ERR_NOT_SUPPORTED,
+                            "batch member's blocks differ from its own plan's");
+            }
+            p0 += plans[q]->p;
+            b0 += (int64_t)plans[q]->blocks.size();
+            aoff += plans[q]->nnz_a;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *vals = nullptr;
+    if (!cuda_ok(cudaMalloc(&vals, std::max<int64_t>(1, M->nnz_a) * sizeof(double)),
+                 "cudaMalloc(batch values)")) {
+        slu_plan_destroy(M);
+        return SLU_ERR_OUT_OF_MEMORY;
+    }
+    for (int32_t q = 0; q < count && st == SLU_OK; ++q)
+        if (plans[q]->nnz_a > 0 &&
+            !cuda_ok(cudaMemcpyAsync(vals + sl[q].aoff, values[q],
+                                     plans[q]->nnz_a * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s),
+                     "cudaMemcpyAsync(batch values)"))
+            st = SLU_ERR_CUDA;
+    slu_handle *H = nullptr;
+    if (st == SLU_OK) st = slu_factor(M, vals, stream, &H, info);  // synchronizes s
+    if (st != SLU_OK && H == nullptr) cudaStreamSynchronize(s);
+    cudaFree(vals);
+    if (H == nullptr) {
+        slu_plan_destroy(M);
+        return st;
+    }
+    const slu_status fst = st;                  // SLU_OK or SLU_ERR_SINGULAR
+    BatchShared *shared = new BatchShared();
+    shared->plan = M;
+    shared->h = H;
+    const size_t esz = H->prec == SLU_PREC_FP64 ? sizeof(double) : sizeof(float);
+    for (int32_t q = 0; q < count && st == fst; ++q) {
+        const slu_plan *Q = plans[q];
+        slu_status e = ensure_dev_plan(Q);
+        if (e != SLU_OK) { st = e; break; }
+        slu_handle *h = new slu_handle();
+        h->plan = Q;
+        h->device = H->device;
+        h->prec = H->prec;
+        h->tau_rel = H->tau_rel;
+        h->storage = static_cast<char *>(H->storage) + sl[q].voff * esz;
+        h->winv = static_cast<char *>(H->winv) + sl[q].woff * esz;
+        h->a_vals = H->a_vals + sl[q].aoff;
+        {
+            std::lock_guard<std::mutex> lock(g_batch_mu);
+            h->batch = shared;
+            shared->refs++;
+        }
+        // the member's max|A| entry is the batch's (the threshold the
+        // factorization used), its ||A||_inf its own
+        const double *anorm = H->anorm_seg ? H->anorm_seg + q : H->scal + 1;
+        const bool ok =
+            cuda_ok(cudaMalloc(&h->scal, 4 * sizeof(double)), "cudaMalloc") &&
+            cuda_ok(cudaMalloc(&h->cnt, 4 * sizeof(unsigned long long)), "cudaMalloc") &&
+            cuda_ok(cudaMalloc(&h->part, std::max<int64_t>(1, Q->part_elems) * 4 *
+                                             sizeof(double)),
+                    "cudaMalloc(solve partials)") &&
+            cuda_ok(cudaMemsetAsync(h->cnt, 0, 4 * sizeof(unsigned long long), s), "cudaMemsetAsync") &&
+            cuda_ok(cudaMemcpyAsync(h->scal, H->scal, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s), "cudaMemcpyAsync") &&
+            cuda_ok(cudaMemcpyAsync(h->scal + 1, anorm, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s), "cudaMemcpyAsync") &&
+            cuda_ok(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking),
+                    "cudaStreamCreate") &&
+            cuda_ok(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming),
+                    "cudaEventCreate") &&
+            cuda_ok(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming),
+                    "cudaEventCreate");
+        out[q] = h;
+        if (!ok) st = SLU_ERR_CUDA;
+    }
+    if (st == fst && !cuda_ok(cudaStreamSynchronize(s), "slu_factor_batch")) st = SLU_ERR_CUDA;
+    if (st != fst) {
+        const std::string msg = slu_last_error();
+        {
+            bool none = true;
+            for (int32_t q = 0; q < count; ++q) none = none && !out[q];
+            if (none) {                       // no member took a reference
+                slu_handle_destroy(H);
+                slu_plan_destroy(M);
+                delete shared;
+            }
+        }
+        for (int32_t q = 0; q < count; ++q) {
+            slu_handle_destroy(out[q]);
+            out[q] = nullptr;
+        }
+        return fail(st, msg);
+    }
+    return fst;
 }
 
 extern "C" slu_status slu_refactor(slu_handle *h, const double *values,

@@ -1164,7 +1164,8 @@ static slu_status backward_error(slu_handle *h, const double *B, int64_t ldb,
         for (int c = 0; c < nrhs; ++c) {
             const double *r = &hr[((size_t)q * nrhs + c) * 3];
             const double den = an[q] * r[1] + r[2];
-            worst = std::max(worst, den > 0 ? r[0] / den : 0.0);
+            const double v = den > 0 ? r[0] / den : 0.0;
+            if (!(v <= worst)) worst = v;     // a NaN term makes the result NaN
         }
     *be = worst;
     return SLU_OK;
@@ -1292,8 +1293,47 @@ extern "C" slu_status slu_solve_transpose(const slu_handle *h, const double *G,
 // the residual is fully rewritten before it is read.  Two calls whose work
 // overlaps on the GPU (different streams, or host threads) race on the
 // array, so callers must order them.
-constexpr int kNoallocRed = 3 * 64;
+constexpr int kNoallocRed = 256;
 static __device__ __align__(256) double g_noalloc_scratch[SLU_NOALLOC_MAX_ELEMS + kNoallocRed];
+
+// Scratch layout of one call: the residual R (n x nrhs) at the front, then,
+// from the next 32-double boundary, 3 reduction words per right-hand side and
+// matrix (one matrix, or every member of a batch plan), then the one word
+// that receives the backward error.
+__host__ __device__ constexpr int64_t noalloc_red_at(int64_t n, int nrhs) {
+    return ((n * nrhs + 31) / 32) * 32;
+}
+__host__ __device__ constexpr int64_t noalloc_words(int64_t n, int nrhs, int nseg) {
+    return noalloc_red_at(n, nrhs) + 3 * (int64_t)nseg * nrhs + 1;
+}
+
+// *out = max over members q and columns c of
+//   red[3(q nrhs + c)] / (anorm[q] red[3(q nrhs + c) + 1] + red[3(q nrhs + c) + 2]),
+// a term with a zero denominator counting as 0 and a NaN term making the
+// result NaN (the same reduction as slu_solve's, done on the device so that
+// nothing is staged in host memory).  One CTA.
+__global__ void k_be_max(int nseg, int nrhs, const double *__restrict__ red,
+                         const double *__restrict__ anorm, double *__restrict__ out) {
+    __shared__ double sw[32];
+    double w = 0.0;
+    for (int t = threadIdx.x; t < nseg * nrhs; t += blockDim.x) {
+        const double *r = red + 3 * (int64_t)t;
+        const double den = anorm[t / nrhs] * r[1] + r[2];
+        const double v = den > 0 ? r[0] / den : 0.0;
+        if (!(v <= w)) w = v;                 // NaN wins
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v = __shfl_xor_sync(~0u, w, o);
+        if (!(v <= w)) w = v;
+    }
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+            if (!(sw[k] <= w)) w = sw[k];
+        *out = w;
+    }
+}
 
 namespace {
 
@@ -1301,13 +1341,17 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double *g_noalloc_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device.  The name
+// Device address of the scratch array on the handle's device, which must be
+// the current one (the caller's stream belongs to it).  The name
 // g_noalloc_scratch in host code is only a host-side stand-in; its device
 // address comes from cudaGetSymbolAddress, taken once per device with that
 // device current.
-slu_status noalloc_scratch(double **out) {
+slu_status noalloc_scratch(const slu_handle *h, double **out) {
     int dev = -1;
     if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return SLU_ERR_CUDA;
+    if (dev != h->device)
+        return fail(SLU_ERR_INVALID_ARG,
+                    "the current device is not the handle's device");
     if (dev < 0 || dev >= kMaxDevices)
         return fail(SLU_ERR_NOT_SUPPORTED, "device index beyond 63");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -1322,42 +1366,46 @@ slu_status noalloc_scratch(double **out) {
     return SLU_OK;
 }
 
-// backward_error with caller-given reduction words instead of h->red.
+// backward_error with the reduction words and the result in the scratch
+// array (red, then *dbe) instead of the handle's workspace: per member of a
+// batch plan (k_norms_seg and the members' norms of A) as slu_solve does.
 slu_status backward_error_with(slu_handle *h, const double *B, int64_t ldb,
                                const double *X, int64_t ldx, int nrhs,
-                               double *R, double *red, cudaStream_t st,
-                               double *be) {
+                               double *R, double *red, double *dbe,
+                               cudaStream_t st, double *be) {
     const slu_plan *P = h->plan;
     const DevPlan *D = P->dev;
     const int64_t n = P->n;
+    const int nseg = h->anorm_seg ? (int)P->seg.size() - 1 : 1;
     {
         LaunchScope ls_(h, SLU_KC_RESID, st);
         k_residual<<<(int)((n * 32 + 255) / 256), 256, 0, st>>>(
             n, nrhs, D->a_rowptr, D->a_colidx, D->a_vpos, h->a_vals, B, ldb, X,
             ldx, R, n);
     }
-    if (!cuda_ok(cudaMemsetAsync(red, 0, 3 * nrhs * sizeof(double), st),
+    if (!cuda_ok(cudaMemsetAsync(red, 0, 3 * (size_t)nseg * nrhs * sizeof(double), st),
                  "cudaMemsetAsync"))
         return SLU_ERR_CUDA;
     {
         LaunchScope ls_(h, SLU_KC_RESID, st);
-        k_norms<<<148 * 2, 256, 0, st>>>(
-            n, nrhs, R, n, X, ldx, B, ldb,
-            reinterpret_cast<unsigned long long *>(red));
+        if (nseg > 1)
+            k_norms_seg<<<(int)((n + 255) / 256), 256, 0, st>>>(
+                n, nrhs, R, n, X, ldx, B, ldb, D->row_seg,
+                reinterpret_cast<unsigned long long *>(red));
+        else
+            k_norms<<<148 * 2, 256, 0, st>>>(
+                n, nrhs, R, n, X, ldx, B, ldb,
+                reinterpret_cast<unsigned long long *>(red));
     }
-    double hr[3 * 64 + 1];
-    if (!cuda_ok(cudaMemcpyAsync(hr, red, 3 * nrhs * sizeof(double),
-                                 cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
-        !cuda_ok(cudaMemcpyAsync(hr + 3 * 64, h->scal + 1, sizeof(double),
-                                 cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
+    {
+        LaunchScope ls_(h, SLU_KC_RESID, st);
+        k_be_max<<<1, 256, 0, st>>>(nseg, nrhs, red,
+                                    nseg > 1 ? h->anorm_seg : h->scal + 1, dbe);
+    }
+    if (!cuda_ok(cudaMemcpyAsync(be, dbe, sizeof(double), cudaMemcpyDeviceToHost, st),
+                 "cudaMemcpyAsync") ||
         !cuda_ok(cudaStreamSynchronize(st), "residual"))
         return SLU_ERR_CUDA;
-    double worst = 0.0;
-    for (int c = 0; c < nrhs; ++c) {
-        const double den = hr[3 * 64] * hr[3 * c + 1] + hr[3 * c + 2];
-        worst = std::max(worst, den > 0 ? hr[3 * c] / den : 0.0);
-    }
-    *be = worst;
     return SLU_OK;
 }
 
@@ -1375,9 +1423,12 @@ extern "C" slu_status slu_solve_refine_noalloc(const slu_handle *ch,
     if (nrhs < 0 || nrhs > 64 || ldb < n || ldx < n)
         return fail(SLU_ERR_INVALID_ARG, "bad nrhs or leading dimension");
     if (X == B) return fail(SLU_ERR_INVALID_ARG, "X must not alias B");
-    if (n * (int64_t)nrhs > SLU_NOALLOC_MAX_ELEMS)
+    const int nseg = h->anorm_seg ? (int)P->seg.size() - 1 : 1;
+    if (n * (int64_t)nrhs > SLU_NOALLOC_MAX_ELEMS ||
+        noalloc_words(n, nrhs, nseg) > SLU_NOALLOC_MAX_ELEMS + kNoallocRed)
         return fail(SLU_ERR_INVALID_ARG,
-                    "n * nrhs exceeds SLU_NOALLOC_MAX_ELEMS (1048576): use "
+                    "n * nrhs (plus 3 * nrhs reduction words per batch member) "
+                    "exceeds SLU_NOALLOC_MAX_ELEMS (1048576) + 256: use "
                     "slu_solve, which allocates its workspace");
     if (info) {
         info->iterations = 0;
@@ -1385,10 +1436,11 @@ extern "C" slu_status slu_solve_refine_noalloc(const slu_handle *ch,
     }
     if (nrhs == 0 || n == 0) return SLU_OK;
     double *scratch = nullptr;
-    slu_status s = noalloc_scratch(&scratch);
+    slu_status s = noalloc_scratch(h, &scratch);
     if (s != SLU_OK) return s;
     double *R = scratch;
-    double *red = scratch + SLU_NOALLOC_MAX_ELEMS;
+    double *red = scratch + noalloc_red_at(n, nrhs);
+    double *dbe = red + 3 * (int64_t)nseg * nrhs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int maxit = P->opts.refine_max_iter < 0  ? 0
                       : P->opts.refine_max_iter > 0 ? P->opts.refine_max_iter
@@ -1399,7 +1451,7 @@ extern "C" slu_status slu_solve_refine_noalloc(const slu_handle *ch,
     double be = 0.0;
     int it = 0;
     for (;;) {
-        s = backward_error_with(h, B, ldb, X, ldx, nrhs, R, red, st, &be);
+        s = backward_error_with(h, B, ldb, X, ldx, nrhs, R, red, dbe, st, &be);
         if (s != SLU_OK) return s;
         if (be <= P->opts.refine_tol || it >= maxit) break;
         s = solve_inplace(h, R, n, nrhs, false, st);

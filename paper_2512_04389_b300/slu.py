@@ -73,6 +73,7 @@ EXPORTS = ["slu_opts_default", "slu_analyze", "slu_analyze_batch",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
            "slu_export_factors", "slu_grad_values", "slu_set_profiling", "slu_handle_stats",
            "slu_plan_flops", "slu_handle_trace", "slu_set_graph", "slu_solve_refine_noalloc",
+           "slu_factor_batch",
            "slu_plan_serialize", "slu_plan_deserialize", "slu_plan_digest", "slu_plan_check",
            "slu_plan_destroy",
            "slu_handle_destroy", "slu_last_error"]
@@ -96,6 +97,7 @@ def _load():
     lib.slu_plan_export_tasks.argtypes = [P] + [P] * 10
     lib.slu_factor.argtypes = [P, P, P, C.POINTER(P), C.POINTER(FactorInfo)]
     lib.slu_refactor.argtypes = [P, P, P, C.POINTER(FactorInfo)]
+    lib.slu_factor_batch.argtypes = [C.c_int32, P, P, P, P, C.POINTER(FactorInfo)]
     lib.slu_solve.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
                               C.POINTER(SolveInfo)]
     lib.slu_solve_transpose.argtypes = [P, P, C.c_int64, C.c_int32, P,
@@ -355,6 +357,24 @@ class Plan:
         return out
 
 
+def factor_batch(plans, values, stream=None, allow_singular=False):
+    """``slu_factor_batch``: independent plans factored in the same level
+    walk; one Factor per plan (their factors equal ``Factor(plan, v)``'s)."""
+    count = len(plans)
+    if count != len(values):
+        raise ValueError(f"{count} plans but {len(values)} value vectors")
+    hp = (C.c_void_p * count)(*[p._h for p in plans])
+    vp = (C.c_void_p * count)(*[_values_ptr(v, p.info["nnz_a"])
+                                for p, v in zip(plans, values)])
+    out = (C.c_void_p * count)()
+    info = FactorInfo()
+    st = lib.slu_factor_batch(count, hp, vp, _stream_ptr(stream), out,
+                              C.byref(info))
+    _check(st, (0, 4) if allow_singular else (0,))
+    return [Factor._member(p, C.c_void_p(out[q]), values[q], st, info)
+            for q, p in enumerate(plans)]
+
+
 class Factor:
     """Factors of one matrix on the GPU (``slu_factor``)."""
 
@@ -370,6 +390,17 @@ class Factor:
         self.values = values
         self.nperturb = info.nperturb
         self.tau = info.tau
+
+    @classmethod
+    def _member(cls, plan, handle, values, st, info):
+        self = cls.__new__(cls)
+        self.plan = plan
+        self._h = handle
+        self.singular = st == 4
+        self.values = values
+        self.nperturb = info.nperturb
+        self.tau = info.tau
+        return self
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:

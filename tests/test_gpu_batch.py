@@ -82,3 +82,47 @@ def test_graph_replay_matches_plain_refactor():
     assert torch.equal(F.export_factors(), F2.export_factors())
     F.refactor(v)
     assert torch.equal(F.export_factors(), ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_factor_batch_of_independent_plans(prec):
+    """slu_factor_batch over independent plans: every member's factors equal
+    slu_factor's for its own plan bit for bit (FP64 also within 1e-10 of
+    the oracle), its solves equal the separate handle's, a refactor of one
+    member with new values equals a fresh factorization, and the members
+    can be released in any order."""
+    ms = _batch(count=10, seed=21)
+    plans = [S.Plan(m.n, m.colptr, m.rowidx, precision=prec) for m in ms]
+    vals = [_dev(m.values) for m in ms]
+    members = S.factor_batch(plans, vals)
+    assert len(members) == len(ms)
+    for q, (m, P, Fm) in enumerate(zip(ms, plans, members)):
+        F = S.Factor(P, vals[q])
+        g = Fm.export_factors()
+        assert torch.equal(g, F.export_factors())
+        if prec == "fp64":
+            Fo = OL.lu(m.n, m.colptr, m.rowidx, m.values)
+            _, _, pv = OL.lu_pattern(Fo)
+            assert np.abs(g.cpu().numpy() - pv).max() <= 1e-10 * np.abs(pv).max()
+        B = _dev(m.rhs[:, :1])
+        X1, i1 = Fm.solve(B, info=True)
+        X2, i2 = F.solve(B, info=True)
+        assert torch.equal(X1, X2) and i1 == i2
+        assert i1["backward_error"] <= (1e-13 if prec == "fp64" else 1e-14)
+    q = 3
+    v2 = vals[q] * 2.0
+    members[q].refactor(v2, sync_info=True)
+    F2 = S.Factor(plans[q], v2)
+    assert torch.equal(members[q].export_factors(), F2.export_factors())
+    order = np.random.default_rng(0).permutation(len(members))
+    for q in order:                     # the shared factors go with the last
+        members[q] = None
+
+
+def test_factor_batch_rejects_mixed_options():
+    ms = _batch(count=2, seed=22)
+    plans = [S.Plan(ms[0].n, ms[0].colptr, ms[0].rowidx, precision="fp64"),
+             S.Plan(ms[1].n, ms[1].colptr, ms[1].rowidx, precision="fp32")]
+    with pytest.raises(S.SluError) as ei:
+        S.factor_batch(plans, [_dev(m.values) for m in ms])
+    assert ei.value.status == 7

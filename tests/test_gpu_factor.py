@@ -280,3 +280,93 @@ def test_autotuner_picks_a_candidate_and_caches(tmp_path, monkeypatch):
     again, t2 = T.tune(s.n, s.colptr, s.rowidx, _dev(s.values), _dev(s.rhs),
                        precision="fp32")
     assert again == best and t2 == timings          # served from the cache
+
+
+# --- the benchmarked 40^3 configuration, with every option set the
+# autotuner may pick for it (so the plan the benchmark times is among them)
+
+@pytest.fixture(scope="module")
+def grid7cd_40_oracle():
+    s = workloads.grid7_cd(40)
+    Fo, pp, pr, pv = oracle_factor(s)
+    Xo = OL.solve(Fo, s.rhs)
+    return s, pp, pr, pv, Xo
+
+
+def _candidates_40():
+    from paper_2512_04389_b300 import tune as T
+    out = []
+    for prec in ("fp64", "fp32"):
+        for c in T.candidates("irregular", 64000):
+            out.append((prec, dict(c)))
+        for c in T.candidates("regular"):
+            out.append((prec, dict(c, blocking="regular", regular_block=128)))
+    return out
+
+
+@pytest.mark.parametrize(
+    "prec,opts", _candidates_40(),
+    ids=[f"{p}-" + "-".join(f"{k}{v}" for k, v in sorted(o.items()))
+         for p, o in _candidates_40()])
+def test_grid7cd_40_every_tuner_candidate_against_oracle(grid7cd_40_oracle,
+                                                         prec, opts):
+    """Full size, n = 64,000, 4 RHS: pattern bit-exact; FP64 factors
+    element-wise within 1e-10 of the oracle's and solutions within 1e-10
+    (backward error <= 1e-13); FP32 factors' error reported (<= 1e-4) and
+    the refined solve at backward error <= 1e-14."""
+    s, pp, pr, pv, Xo = grid7cd_40_oracle
+    P, F = gpu_factor(s, precision=prec, **opts)
+    e = P.export()
+    assert np.array_equal(e["colptr"], pp) and np.array_equal(e["rowidx"], pr)
+    err = factor_error(P, F, pv)
+    X, info = F.solve(_dev(s.rhs), info=True)
+    Xg = X.cpu().numpy()
+    xerr = np.abs(Xg - Xo).max() / np.abs(Xo).max()
+    be = OL.backward_error(s.n, s.colptr, s.rowidx, s.values, Xg, s.rhs)
+    print(f"{prec} {opts}: factor error {err:.2e}, solution error {xerr:.2e},"
+          f" backward error {be:.2e} ({info['iterations']} refinement steps)")
+    if prec == "fp64":
+        assert err <= FP64_TOL and xerr <= 1e-10 and be <= 1e-13
+    else:
+        assert err <= 1e-4 and be <= 1e-14 and info["backward_error"] <= 1e-14
+
+
+# --- failure statuses reached on the host side of the ABI
+
+def test_refinement_not_converged_status():
+    """FP32 factors, one refinement step, an unreachable tolerance:
+    SLU_ERR_NOT_CONVERGED (5), X holding the last iterate."""
+    s = workloads.grid7_cd(10, nrhs=2)
+    P, F = gpu_factor(s, b_min=8, precision="fp32", refine_max_iter=1,
+                      refine_tol=1e-300)
+    with pytest.raises(S.SluError) as ei:
+        F.solve(_dev(s.rhs))
+    assert ei.value.status == 5
+    X, info = F.solve(_dev(s.rhs), info=True, allow_not_converged=True)
+    assert not info["converged"] and info["iterations"] == 1
+    be = OL.backward_error(s.n, s.colptr, s.rowidx, s.values,
+                           X.cpu().numpy(), s.rhs)
+    assert be == pytest.approx(info["backward_error"], rel=1e-9)
+    assert be <= 1e-12          # the last iterate is still a refined solution
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_nonfinite_values_are_invalid(bad):
+    """A NaN or infinite entry of A is SLU_ERR_INVALID_ARG (1) from
+    slu_factor, and from slu_refactor when info is requested."""
+    s = workloads.grid5(12)
+    v = s.values.copy()
+    v[v.size // 2] = bad
+    P = S.Plan(s.n, s.colptr, s.rowidx, b_min=4)
+    with pytest.raises(S.SluError) as ei:
+        S.Factor(P, _dev(v))
+    assert ei.value.status == 1 and "NaN or infinite" in str(ei.value)
+    F = S.Factor(P, _dev(s.values))
+    with pytest.raises(S.SluError) as ei:
+        F.refactor(_dev(v), sync_info=True)
+    assert ei.value.status == 1
+    F.refactor(_dev(s.values), sync_info=True)        # usable again
+    X = F.solve(_dev(s.rhs))
+    be = OL.backward_error(s.n, s.colptr, s.rowidx, s.values,
+                           X.cpu().numpy(), s.rhs)
+    assert be <= 1e-13

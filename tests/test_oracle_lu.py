@@ -176,6 +176,25 @@ def test_backward_error_closed_form():
     assert OL.backward_error(n, ap, ai, ax, np.full(n, 0.5), np.ones(n)) == 0
 
 
+def test_matvec_and_backward_error_nonsymmetric_closed_form():
+    """A = [[4, -1, 0], [2, 5, 0], [0, 3, 1]]: row sums 5, 7, 4 (||A||_inf =
+    7) differ from column sums 6, 9, 1, and A^T x differs from A x, so a
+    transposed product or the wrong norm fails.  x1 = 1 gives A x1 = (3, 7,
+    4); b1 = A x1 + (0, 0.01, 0) has residual 0.01 and backward error
+    0.01 / (7 * 1 + 7.01).  x2 = (0, 2, 0), b2 = A x2 = (-2, 10, 6) exactly:
+    backward error 0, so the max over both columns is column 1's."""
+    A = np.array([[4.0, -1.0, 0.0], [2.0, 5.0, 0.0], [0.0, 3.0, 1.0]])
+    ap, ai, ax = dense_to_csc(A)
+    X = np.array([[1.0, 0.0], [1.0, 2.0], [1.0, 0.0]])
+    Y = OL.matvec(3, ap, ai, ax, X)
+    assert np.array_equal(Y, np.array([[3.0, -2.0], [7.0, 10.0], [4.0, 6.0]]))
+    B = Y.copy()
+    B[1, 0] += 0.01
+    be = OL.backward_error(3, ap, ai, ax, X, B)
+    assert np.isclose(be, 0.01 / (7.0 + 7.01), rtol=1e-12)
+    assert OL.backward_error(3, ap, ai, ax, X[:, 1], B[:, 1]) == 0.0
+
+
 def test_generator_shapes_match_named_configs():
     assert workloads.grid5(48).nnz == 11_328
     assert workloads.grid7_theta(32).nnz == 223_232

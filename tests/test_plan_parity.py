@@ -84,11 +84,14 @@ def test_plan_bit_exact_random_unsorted(n, density, seed, opts):
     _check_plan(_random_system(n, density, seed), opts)
 
 
-def _check_plan(s, opts):
+def _check_plan(s, opts, oracle=None):
     P = S.Plan(s.n, s.colptr, s.rowidx, **opts)
     o = S.default_opts(**opts)
-    F = OL.lu(s.n, s.colptr, s.rowidx, s.values)
-    pp, pr, _ = OL.lu_pattern(F)
+    if oracle is None:
+        F = OL.lu(s.n, s.colptr, s.rowidx, s.values)
+        pp, pr, _ = OL.lu_pattern(F)
+    else:
+        F, (pp, pr, _) = oracle
     e = P.export()
     assert np.array_equal(e["colptr"], pp)
     assert np.array_equal(e["rowidx"], pr)
@@ -126,6 +129,33 @@ def _check_plan(s, opts):
             srcs = t["src"][t["srcoff"][k]:t["srcoff"][k + 1]].tolist()
             got.append((tuple(tg[k].tolist()), srcs))
         assert got == pl["ssssm"][lv]
+
+
+@pytest.fixture(scope="module")
+def grid7cd_40_oracle():
+    s = workloads.grid7_cd(40)
+    F = OL.lu(s.n, s.colptr, s.rowidx, s.values)
+    return s, F, OL.lu_pattern(F)
+
+
+# The autotuned options of the 40^3 convection-diffusion plans the benchmark
+# times (FP64: max_num 1; FP32: S = 2000), and the paper's defaults.
+TUNED_40 = [
+    dict(dense_threshold=0.0, sample_points=1000, b_min=32, max_num=1),
+    dict(dense_threshold=0.0, sample_points=2000, b_min=32, max_num=3,
+         precision="fp32"),
+    dict(blocking="regular", regular_block=128, dense_threshold=0.0),
+]
+
+
+@pytest.mark.parametrize("opts", TUNED_40,
+                         ids=["fp64_S1000_m1", "fp32_S2000_m3", "regular128"])
+def test_plan_bit_exact_grid7cd_40_tuned(grid7cd_40_oracle, opts):
+    """Full size n = 64,000: the plans the benchmark factors are the
+    oracle's plans bit for bit (pattern, Algorithm 2, Algorithm 3, blocks,
+    dense flags, levels, every task list)."""
+    s, F, pat = grid7cd_40_oracle
+    _check_plan(s, opts, oracle=(F, pat))
 
 
 @pytest.mark.parametrize("bad", ["dup", "range", "colptr"])
