@@ -59,6 +59,10 @@ def parse():
                          "profiling captures of the FP32 kernels")
     ap.add_argument("--no-circuit", action="store_true",
                     help="skip the n = 200,000 circuit leg (about 2 minutes)")
+    ap.add_argument("--reference-grid", type=int, default=40,
+                    help="grid edge of the reference arm's oracle runs (40: the "
+                         "benchmark's input; smaller only for quick checks of "
+                         "the line's shape)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["grid7cd_40", "grid7cd_32", "grid7cd_24"],
                     help="40^3 is the benchmark; the smaller grids of the same "
@@ -232,20 +236,26 @@ def host_cpu():
     return {"model": model, "nproc": os.cpu_count()}
 
 
-def cpu_oracle_leg(m=32):
-    """The oracle as it stands on a bounded sample of the same workload
-    family (grid7_cd(m), same generator, seed 0, 4 RHS), one core."""
+def oracle_step(m):
+    """One oracle factor + solve of grid7_cd(m) (4 RHS): (seconds, flops).
+    Module level so that spawned worker processes can run it."""
     from oracle import lu as OL
     s = workloads.grid7_cd(m)
     t = time.perf_counter()
     F = OL.lu(s.n, s.colptr, s.rowidx, s.values)
     OL.solve(F, s.rhs)
     dt = time.perf_counter() - t
-    fl = OL.flops(F) + 2 * (len(F["Li"]) + len(F["Ui"])) * s.nrhs
+    return dt, OL.flops(F) + 2 * (len(F["Li"]) + len(F["Ui"])) * s.nrhs
+
+
+def cpu_oracle_leg(m=40):
+    """The oracle as it stands on the benchmark's own input (grid7_cd(40),
+    full size, seed 0, 4 RHS): one factor + solve on one host core."""
+    dt, fl = oracle_step(m)
     return {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": 1,
             "kind": "oracle", "host": host_cpu(),
-            "sample": f"grid7cd_{m} (n={s.n}, same generator, 4 RHS): "
-                      f"factor+solve {dt:.2f} s on 1 host core"}
+            "sample": f"grid7cd_{m} at full size (n={m ** 3}, 4 RHS): one "
+                      f"factor+solve, {dt:.1f} s on 1 host core"}
 
 
 def batch_leg(torch, S, dev, args):
@@ -269,6 +279,20 @@ def batch_leg(torch, S, dev, args):
         msb = timed(torch, step_b, args.steps, 2)
         _, ib = FB.solve(bb, info=True)
         FB.set_graph(False)
+    # the same batch with regular 64-row blocking of every member
+    PR = S.Plan([m.n for m in ms], [m.colptr for m in ms],
+                [m.rowidx for m in ms], precision="fp32", dense_threshold=0.0,
+                blocking="regular", regular_block=64)
+    FR = S.Factor(PR, vb)
+    with torch.cuda.stream(st):
+        FR.set_graph(True)
+
+        def step_r():
+            FR.refactor(vb)
+            FR.solve(bb)
+        msr = timed(torch, step_r, args.steps, 2)
+        FR.set_graph(False)
+    del FR, PR
     plans = [S.Plan(m.n, m.colptr, m.rowidx, precision="fp32",
                     dense_threshold=0.0) for m in ms]
     vs = [dev(m.values) for m in ms]
@@ -283,6 +307,7 @@ def batch_leg(torch, S, dev, args):
     fl = sum(p.info["flops"] + 2 * p.info["nnz_lu"] for p in plans)
     return {"ms_per_step": msb, "gflops": fl / (msb * 1e-3) / 1e9,
             "loop_ms_per_step": msl, "speedup_vs_loop": msl / msb,
+            "regular64_graph_ms_per_step": msr, "irregular_speedup": msr / msb,
             "backward_error_max_member": ib["backward_error"],
             "ir_iterations": ib["iterations"], "levels": PB.info["nlevels"],
             "n_total": PB.info["n"]}
@@ -308,9 +333,16 @@ def small_grid_leg(torch, S, dev, args):
     s = workloads.grid5(48)
     v, r = dev(s.values), dev(s.rhs)
     out = {}
+    from paper_2512_04389_b300.tune import candidates
     for name, opts in (("irregular", {}),
-                       ("regular64", dict(blocking="regular", regular_block=64))):
-        best, _ = tune(s.n, s.colptr, s.rowidx, v, r, precision="fp64", **opts)
+                       ("regular64", dict(blocking="regular", regular_block=64)),
+                       ("regular_tuned", None)):
+        if opts is None:           # block size and threshold both searched
+            best, _ = tune(s.n, s.colptr, s.rowidx, v, r, precision="fp64",
+                           cands=candidates("regular_sizes", s.n))
+            opts = {}
+        else:
+            best, _ = tune(s.n, s.colptr, s.rowidx, v, r, precision="fp64", **opts)
         P = S.Plan(s.n, s.colptr, s.rowidx, **opts, **best)
         F = S.Factor(P, v)
 
@@ -334,10 +366,13 @@ def circuit_leg(torch, S, dev, args):
     s = workloads.circuit_bbd()
     v, r = dev(s.values), dev(s.rhs)
     out = {"n": s.n, "nnz_a": s.nnz}
-    for prec in ("fp32", "fp64"):
+    for leg, prec, extra in (("fp32", "fp32", {}), ("fp64", "fp64", {}),
+                             ("fp32_regular128", "fp32",
+                              dict(blocking="regular", regular_block=128))):
         t0 = time.perf_counter()
         thr = 0.02 if prec == "fp32" else 0.05
-        P = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=thr)
+        P = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=thr,
+                   **extra)
         ana = time.perf_counter() - t0
         F = S.Factor(P, v)
 
@@ -346,7 +381,7 @@ def circuit_leg(torch, S, dev, args):
             F.solve(r)
         ms = timed(torch, step, 1, 1)
         _, info = F.solve(r, info=True)
-        out[prec] = {"ms_per_step": ms, "analyze_s": ana, "dense_threshold": thr,
+        out[leg] = {"ms_per_step": ms, "analyze_s": ana, "dense_threshold": thr,
                      "gflops": step_flops(P, s.nrhs) / (ms * 1e-3) / 1e9,
                      "backward_error": info["backward_error"],
                      "ir_iterations": info["iterations"],
@@ -354,6 +389,8 @@ def circuit_leg(torch, S, dev, args):
                      "levels": P.info["nlevels"]}
         del F, P
         torch.cuda.empty_cache()
+    out["irregular_speedup_fp32"] = (out["fp32_regular128"]["ms_per_step"] /
+                                     out["fp32"]["ms_per_step"])
     return out
 
 
@@ -366,45 +403,73 @@ def autograd_leg(torch, S, dev, args):
     P = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=0.0)
     v0, b0 = dev(s.values), dev(s.rhs[:, 0])
 
-    def step():
-        vv = v0.clone().requires_grad_(True)
-        bb = b0.clone().requires_grad_(True)
-        x = lu_solve(vv, bb, P)
-        (0.5 * (x * x).sum()).backward()
-    ms = timed(torch, step, args.steps, 2)
+    PR = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=0.0,
+                blocking="regular", regular_block=128)
+
+    def run(plan):
+        def step():
+            vv = v0.clone().requires_grad_(True)
+            bb = b0.clone().requires_grad_(True)
+            x = lu_solve(vv, bb, plan)
+            (0.5 * (x * x).sum()).backward()
+        return timed(torch, step, args.steps, 2)
+    ms = run(P)
+    msr = run(PR)
     return {"ms_per_step": ms, "n": s.n, "nnz_a": s.nnz,
+            "regular128_ms_per_step": msr, "irregular_speedup": msr / ms,
             "what": "factor + solve forward, transposed solve + gradient gather backward"}
 
 
+def reference_workers(steps):
+    """Worker processes for the reference arm: one per timed step, at most
+    one per host core and 16, and about 2 GB of host memory each (one
+    full-size oracle factorization holds under 1 GB)."""
+    try:
+        with open("/proc/meminfo") as f:
+            avail = next(int(l.split()[1]) for l in f if l.startswith("MemAvailable"))
+        by_mem = max(1, avail // (2 * 1024 * 1024))
+    except (OSError, StopIteration, ValueError):
+        by_mem = 4
+    return max(1, min(steps, os.cpu_count() or 1, 16, by_mem))
+
+
 def run_reference(args):
+    """The oracle as it stands on the benchmark's own input: every step is
+    one full-size factor + solve of grid7_cd(40).  The steps run as
+    independent processes spread over the host's cores (the oracle itself
+    is sequential), so value = steps x flops / wall time of the timed
+    steps.  Warm-up: untimed oracle runs of grid7_cd(12) that start the
+    workers and load the oracle's library."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle import lu as OL
-    m = 24
-    s = workloads.grid7_cd(m)
-    times, fl = [], 0
-    for i in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        F = OL.lu(s.n, s.colptr, s.rowidx, s.values)
-        OL.solve(F, s.rhs)
-        dt = time.perf_counter() - t
-        if i >= args.warmup:
-            times.append(dt)
-        fl = OL.flops(F) + 2 * (len(F["Li"]) + len(F["Ui"])) * s.nrhs
-    ms = 1e3 * sum(times) / len(times)
-    v = fl / (ms * 1e-3) / 1e9
-    sample = (f"each step: oracle factor+solve of grid7cd_{m} (n={s.n}), "
-              "the same generator as grid7cd_40 at a size one host core "
-              "finishes in about a second")
+    import multiprocessing as mp
+    m = args.reference_grid
+    wl = f"grid7cd_{m}"
+    cores = reference_workers(args.steps)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(oracle_step, [12] * max(args.warmup, cores), chunksize=1)
+        t0 = time.perf_counter()
+        res = pool.map(oracle_step, [m] * args.steps, chunksize=1)
+        wall = time.perf_counter() - t0
+    fl = res[0][1]
+    ms = 1e3 * wall / args.steps
+    v = args.steps * fl / wall / 1e9
+    per = sorted(r[0] for r in res)
+    sample = (f"each step: one oracle factor+solve of {wl} at full size "
+              f"(n={m ** 3}, 4 RHS); {args.steps} steps as independent "
+              f"processes on {cores} host cores, {wall:.1f} s wall, "
+              f"{per[len(per) // 2]:.1f} s median per step")
+    cfg = {"workload": wl, "n": m ** 3, "nrhs": 4,
+           "host_cores": os.cpu_count(), "workers": cores}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"grid7cd_{m} sample of {WORKLOAD}",
-                   "host_cores": os.cpu_count()},
-        "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1,
+        "config": cfg,
+        "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores,
                          "kind": "oracle", "sample": sample, "host": host_cpu()},
         "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
@@ -552,24 +617,24 @@ def main():
                                      "gflops": fl / (msr * 1e-3) / 1e9,
                                      "levels": preg.info["nlevels"]}
         del Freg
-        # best regular size (threshold 0, the tuned choice above) against
-        # the tuned irregular blocking
-        sweep = {}
-        for rb in (64, 256, 512):
-            pr = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular",
-                        regular_block=rb, dense_threshold=0.0)
-            Fr = S.Factor(pr, vals_d)
+        # the regular blocking tuned over block size and threshold (as many
+        # candidates as the irregular search), FP64 and FP32 + refinement
+        from paper_2512_04389_b300.tune import candidates
+        for prec in ("fp64", "fp32"):
+            bt, tt = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d, precision=prec,
+                          cands=candidates("regular_sizes", s.n))
+            pt = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, **bt)
+            Ft = S.Factor(pt, vals_d)
 
-            def stepr():
-                Fr.refactor(vals_d)
-                Fr.solve(rhs_d)
-            sweep[str(rb)] = timed(torch, stepr, 2, 1)
-            del Fr, pr
-        sweep["128"] = msr
-        best_rb = min(sweep, key=sweep.get)
-        extras["regular_best_fp64"] = {"ms_per_step_by_block": sweep,
-                                       "best_block": int(best_rb),
-                                       "best_ms": sweep[best_rb]}
+            def stept():
+                Ft.refactor(vals_d)
+                Ft.solve(rhs_d)
+            mst = timed(torch, stept, args.steps, 2)
+            extras[f"regular_tuned_{prec}"] = {
+                "ms_per_step": mst, "tuned": bt, "gflops": fl / (mst * 1e-3) / 1e9,
+                "levels": pt.info["nlevels"], "tuning_ms": tt,
+                "irregular_speedup": mst / (ms if prec == "fp64" else ms32)}
+            del Ft, pt
         bestr32, _ = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
                           precision="fp32", blocking="regular", regular_block=128)
         preg32 = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular",

@@ -28,16 +28,24 @@ THRESHOLDS = (0.0, 0.3)
 MAX_NUM = (3, 2, 1)
 SAMPLE_POINTS = (1000, 2000)
 B_MIN = (32, 8)
+REGULAR_BLOCKS = (32, 64, 128, 256)
 
 
 def candidates(blocking="irregular", n=None):
-    """Plan options tried by default.  Regular blocking: the thresholds.
-    Irregular blocking: threshold 0 with every (sample_points, b_min,
+    """Plan options tried by default.  Regular blocking: the thresholds
+    (block size fixed by the caller); "regular_sizes": block size and
+    threshold.  Irregular blocking: threshold 0 with every (sample_points, b_min,
     max_num), plus threshold 0.3 with the paper's defaults; candidates whose
     effective sample count S = min(sample_points, n / b_min) coincides are
     tried once (their plans are identical)."""
     if blocking == "regular":
         return [{"dense_threshold": t} for t in THRESHOLDS]
+    if blocking == "regular_sizes":
+        # the regular blocking's own search, over as many candidates as the
+        # irregular one: block size and threshold
+        return [{"blocking": "regular", "regular_block": b, "dense_threshold": t}
+                for b in REGULAR_BLOCKS for t in THRESHOLDS
+                if n is None or b <= max(n, 1)]
     out, seen = [], set()
     for sp in SAMPLE_POINTS:
         for bm in B_MIN:

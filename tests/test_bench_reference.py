@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl",
-                        "reference", "--steps", "1", "--warmup", "0"],
+                        "reference", "--steps", "2", "--warmup", "1",
+                        "--reference-grid", "12"],
                        capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
@@ -20,6 +21,8 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["config"]["workload"] == "grid7cd_12"
+    assert line["cpu_baseline"]["cores"] == line["config"]["workers"] >= 1
 
 
 def test_extra_leg_failure_is_recorded_not_fatal():
