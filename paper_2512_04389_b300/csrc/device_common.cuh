@@ -89,6 +89,17 @@ __device__ __forceinline__ int rowat(const uint16_t *rows, int t) {
     return rows ? (int)rows[t] : t;
 }
 
+// v != 0 (NaN counts as nonzero, -0 as zero) on the integer pipe: a double
+// comparison runs on the FP64 pipe, which on B300 issues about two
+// operations per SM and clock, so the zero tests that build skip masks use
+// the bit pattern instead.
+__device__ __forceinline__ bool nz(double v) {
+    return (__double_as_longlong(v) & 0x7fffffffffffffffll) != 0;
+}
+__device__ __forceinline__ bool nz(float v) {
+    return (__float_as_uint(v) & 0x7fffffffu) != 0;
+}
+
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 

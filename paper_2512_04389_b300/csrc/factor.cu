@@ -232,9 +232,9 @@ __device__ __forceinline__ int lu_compact(const SplitBlock<T> &B, int b, int k,
                 v[q] *= rcp;
                 B.at(i, k) = v[q];
             }
-            const bool nz = in && v[q] != T(0);
-            const unsigned m = __ballot_sync(0xffffffffu, nz);
-            if (nz) {
+            const bool live = in && nz(v[q]);
+            const unsigned m = __ballot_sync(0xffffffffu, live);
+            if (live) {
                 const int p = n + __popc(m & lt);
                 SLU_CHECK(p < b && i < b, 1);
                 I[p] = (uint16_t)i;
@@ -979,68 +979,130 @@ k_panel(const int32_t *__restrict__ gessm, int ngessm,
 
 // Explicit inverses of a dense diagonal block's factors.  One warp per
 // column j of L^{-1} (forward solve of L x = e_j) or U^{-1} (backward solve
-// of U x = e_j); lane l holds rows l, l + 32, ... of x in registers, the
-// factor's column mm is read coalesced, and x(mm) is broadcast by a shuffle
-// at each step.  Task (diag block, 0: L^{-1} / 1: U^{-1}, first column j0);
-// a CTA's 8 warps take columns j0 .. j0 + 7.
-constexpr int kInvRows = 12;      // rows per lane: blocks up to 384
+// of U x = e_j), x kept in shared memory; lane l owns rows l, l + 32, ...
+// (chunk q: rows 32q .. 32q + 31).  Step mm needs column mm of the factor
+// below mm (L) or above mm (U): it is loaded one step ahead into the warp's
+// second column buffer, and the load records which 32-row chunks of it
+// hold a nonzero.  The update x -= col * x(mm) then runs as a loop over the
+// set bits of that mask, so no FP64 instruction is issued for a chunk of
+// zeros (the FP64 pipe and the step chain bound this kernel; a predicated
+// FP64 instruction costs as much as an executed one).  Steps with x(mm) = 0
+// do nothing.  U's diagonal is inverted once per CTA, so a U^{-1} step
+// multiplies by the reciprocal.  Task (diag block, 0: L^{-1} / 1: U^{-1},
+// first column j0); a CTA's 8 warps take columns j0 .. j0 + 7.
+// Shared memory (T): the reciprocals (rounded up to 32), then per warp x
+// and two column buffers of the block's row count rounded up to 32.
+constexpr int kInvRows = 12;      // 32-row chunks: blocks up to 384
+__host__ __device__ constexpr size_t inv_smem_elems(int b) {
+    return (size_t)((b + 31) & ~31) * (1 + 3 * 8);
+}
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
       const T *__restrict__ val, T *__restrict__ winv,
       const int64_t *__restrict__ woff) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int32_t *tk = task + 3 * (int64_t)blockIdx.x;
     const BlockDesc d = bd[tk[0]];
-    const int which = tk[1], b = d.rows;
+    const int which = tk[1], b = d.rows, bs = (b + 31) & ~31;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = tk[2] + warp;
-    if (j >= b) return;
     const T *__restrict__ F = val + d.voff;           // dense LU, ld = b
-    T x[kInvRows];
+    T *s_rcp = reinterpret_cast<T *>(smem);
+    if (which == 1)                                   // uniform across the CTA
+        for (int e = threadIdx.x; e < b; e += blockDim.x)
+            s_rcp[e] = T(1) / F[(int64_t)e * b + e];
+    __syncthreads();
+    if (j >= b) return;
+    T *x = s_rcp + bs + (size_t)warp * 3 * bs;
+    T *const cb0 = x + bs, *const cb1 = x + 2 * bs;
+    for (int r = lane; r < bs; r += 32) x[r] = (r == j) ? T(1) : T(0);
+    const int nq = bs >> 5;
+    // column mm into c (rows the step uses, zeros elsewhere); returns the
+    // mask of its nonzero chunks.  All loads are issued before any vote.
+    auto fetch = [&](int mm, T *c) -> unsigned {
+        const T *col = F + (int64_t)mm * b;
+        T v[kInvRows];
 #pragma unroll
-    for (int q = 0; q < kInvRows; ++q) x[q] = (q * 32 + lane == j) ? T(1) : T(0);
-    if (which == 0) {
-        for (int mm = j; mm < b; ++mm) {
-            const T xm = __shfl_sync(~0u, x[(mm >> 5) % kInvRows], mm & 31);
-            if (xm == T(0)) continue;
-            const T *Lc = F + (int64_t)mm * b;
+        for (int q = 0; q < kInvRows; ++q) {
+            const int r = q * 32 + lane;
+            const bool in = q < nq && (which == 0 ? (r > mm && r < b) : (r < mm));
+            v[q] = in ? col[r] : T(0);
+        }
+        unsigned m = 0;
 #pragma unroll
-            for (int q = 0; q < kInvRows; ++q) {
-                const int r = q * 32 + lane;
-                if (r > mm && r < b) x[q] -= Lc[r] * xm;
+        for (int q = 0; q < kInvRows; ++q) {
+            if (q < nq) c[q * 32 + lane] = v[q];
+            if (__ballot_sync(~0u, nz(v[q]))) m |= 1u << q;
+        }
+        return m;
+    };
+    const int step = which == 0 ? 1 : -1, end = which == 0 ? b : -1;
+    unsigned mcur = fetch(j, cb0);
+    int cur = 0;
+    for (int mm = j; mm != end; mm += step) {
+        const unsigned mnext = (mm + step != end) ? fetch(mm + step, cur ? cb0 : cb1) : 0u;
+        __syncwarp();
+        T xm = x[mm];
+        if (which == 1) {
+            xm *= s_rcp[mm];
+            if (lane == 0) x[mm] = xm;
+        }
+        if (nz(xm)) {                                 // uniform across the warp
+            const T *c = cur ? cb1 : cb0;
+            for (unsigned m = mcur; m; m &= m - 1) {  // nonzero chunks only
+                const int r = (__ffs(m) - 1) * 32 + lane;
+                x[r] -= c[r] * xm;
             }
         }
-    } else {
-        for (int mm = j; mm >= 0; --mm) {
-            const T *Uc = F + (int64_t)mm * b;
-            const T own = __shfl_sync(~0u, x[(mm >> 5) % kInvRows], mm & 31);
-            const T xm = own / Uc[mm];
-#pragma unroll
-            for (int q = 0; q < kInvRows; ++q)
-                if (q * 32 + lane == mm) x[q] = xm;
-            if (xm == T(0)) continue;
-#pragma unroll
-            for (int q = 0; q < kInvRows; ++q) {
-                const int r = q * 32 + lane;
-                if (r < mm) x[q] -= Uc[r] * xm;
-            }
-        }
+        __syncwarp();
+        mcur = mnext;
+        cur ^= 1;
     }
     T *out = winv + woff[d.I] + (which ? (int64_t)b * b : 0) + (int64_t)j * b;
-#pragma unroll
-    for (int q = 0; q < kInvRows; ++q) {
-        const int r = q * 32 + lane;
-        if (r < b) out[r] = x[q];
+    for (int r = lane; r < b; r += 32) out[r] = x[r];
+}
+
+// Column-pair masks of a staged 16 x 64 slice S (S[kk * 64 + c]): bit kk of
+// pm[p] is set when S[kk][2p] or S[kk][2p + 1] is nonzero.  Warp w takes
+// pairs 4w .. 4w + 3, lane l row kk = l & 15 of pairs 4w + 2 (l >> 4) + {0,
+// 1}; rows kk >= nk count as zero.  All 256 threads.
+template <typename T>
+__device__ __forceinline__ void slice_pair_masks(const T *S, int nk,
+                                                 unsigned short *pm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kk = lane & 15, c = 8 * warp + 4 * (lane >> 4);
+    bool z0 = false, z1 = false;
+    if (kk < nk) {
+        const T *r = S + kk * 64 + c;
+        z0 = nz(r[0]) || nz(r[1]);
+        z1 = nz(r[2]) || nz(r[3]);
+    }
+    const unsigned m0 = __ballot_sync(~0u, z0), m1 = __ballot_sync(~0u, z1);
+    if (lane == 0) {
+        pm[4 * warp + 0] = (unsigned short)(m0 & 0xffffu);
+        pm[4 * warp + 1] = (unsigned short)(m1 & 0xffffu);
+        pm[4 * warp + 2] = (unsigned short)(m0 >> 16);
+        pm[4 * warp + 3] = (unsigned short)(m1 >> 16);
     }
 }
 
 // Dense GESSM / TSTRF through the inverses, one CTA per 64-wide chunk:
 //   GESSM: U_IJ(:, c0:c0+64) = L_II^{-1} B_IJ(:, c0:c0+64)
 //   TSTRF: L_JI(r0:r0+64, :) = B_JI(r0:r0+64, :) U_II^{-1}
-// The chunk of B is staged in shared memory (so the result can be written
-// in place), the triangular inverse is streamed in 16-deep k-slices, and a
-// 64 x 64 output tile is accumulated in registers (4 x 4 per thread) over
-// the nonzero triangle of the inverse only.
+// The chunk of B is staged in shared memory as X[k * 64 + t] (so the result
+// can be written in place), the triangular inverse is staged in 16-deep
+// k-slices Ts[kk * 64 + i], and each 64 x 64 block of outputs is
+// accumulated in registers.  Both products have the form out(row, col) =
+// sum_k A_k[row] B_k[col] with the vectors A_k, B_k rows of the staged
+// arrays (GESSM: A_k = Ts row, B_k = X row; TSTRF: A_k = X row, B_k = Ts
+// row), so the work runs as in the dense Schur tiles: warp w owns output
+// rows 8w .. 8w+7, lane l row 8w + (l & 7) and column 4g + (l >> 3) of the
+// 16 column groups g, and per column group it loops over only the k where
+// its row group of A_k and group g of B_k hold a nonzero (column-pair masks
+// of each slice; no FP64 work is issued for zeros).  A slice of X that is
+// all zero is skipped before its inverse slice is loaded.  The terms left
+// out are exact zeros.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
@@ -1053,39 +1115,28 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
     const BlockDesc d = bd[tk[1]];
     const BlockDesc dd = bd[tk[2]];
     const int c0 = tk[3], m = dd.rows, tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    const int lane = tid & 31, warp = tid >> 5;
     T *X = reinterpret_cast<T *>(smem);                 // m x 64 chunk, X[k * 64 + c]
     T *Ts = X + (size_t)m * 64;                          // 16 x 64 inverse slice
+    const int nsl = (m + KT - 1) / KT;
+    unsigned short *xpm = reinterpret_cast<unsigned short *>(Ts + KT * 64);  // [nsl][32]
+    unsigned short *tpm = xpm + (size_t)nsl * 32;                           // [32]
     const int64_t ld = d.ld;
     T *Bg = val + d.voff;
     const T *Inv = winv + woff[dd.I] + (type == 0 ? 0 : (int64_t)m * m);
     const int nv = min(64, (type == 0 ? d.cols : d.rows) - c0);
     // stage the chunk: GESSM columns c0.. (X[k][c] = B(k, c0 + c));
-    // TSTRF rows c0.. (X[k][r] = B(c0 + r, k)); flag the 16-deep k-slices
-    // of the chunk that hold a nonzero (all-zero slices contribute nothing)
-    // and, per k, whether row k of the chunk holds one (the warps staging a
-    // row ballot; m * 64 is a whole number of warps)
-    int *zrow = reinterpret_cast<int *>(Ts + KT * 64);
-    int *zflag = zrow + m;
-    const int lane = tid & 31, warp = tid >> 5;
+    // TSTRF rows c0.. (X[k][r] = B(c0 + r, k))
     if (d.dense) {
-        for (int e = tid; e < m + (m + KT - 1) / KT; e += 256) zrow[e] = 0;
-        __syncthreads();
         for (int e = tid; e < m * 64; e += 256) {
             const int k = e / 64, c = e % 64;
             T v = T(0);
             if (c < nv)
                 v = type == 0 ? Bg[(int64_t)(c0 + c) * ld + k] : Bg[(int64_t)k * ld + c0 + c];
             X[e] = v;
-            if (sizeof(T) == 8 && __ballot_sync(0xffffffffu, v != T(0)) && lane == 0) {
-                atomicOr(&zrow[k], 1);
-                atomicOr(&zflag[k / KT], 1);
-            }
         }
     } else {
-        // sparse panel block: scatter its pattern into the zeroed chunk (no
-        // zero-row skipping: every row is flagged)
-        for (int e = tid; e < m + (m + KT - 1) / KT; e += 256) zrow[e] = 1;
+        // sparse panel block: scatter its pattern into the zeroed chunk
         for (int e = tid; e < m * 64; e += 256) X[e] = T(0);
         __syncthreads();
         if (type == 0) {                 // columns c0 + c of B_IJ, rows k
@@ -1110,17 +1161,25 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
         }
     }
     __syncthreads();
+    for (int sl = 0; sl < nsl; ++sl)
+        slice_pair_masks<T>(X + (size_t)sl * KT * 64, min(KT, m - sl * KT), xpm + sl * 32);
+    __syncthreads();
+    const int rr = 8 * warp + (lane & 7), cc = lane >> 3;
     for (int ob = 0; ob < m; ob += 64) {       // output chunk along m
-        T acc[4][4];
+        T acc[16];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jx = 0; jx < 4; ++jx) acc[i][jx] = T(0);
+        for (int g = 0; g < 16; ++g) acc[g] = T(0);
         // GESSM: out(i, c) = sum_{k <= i} Linv(i, k) X(k, c), i in [ob, ob+64)
         // TSTRF: out(r, i) = sum_{k <= i} X(r, k) Uinv(k, i), i in [ob, ob+64)
         const int kend = min(m, ob + 64);
         for (int k0 = 0; k0 < kend; k0 += KT) {
-            if (sizeof(T) == 8 && !zflag[k0 / KT]) continue;  // uniform across the CTA
+            const unsigned short *xp = xpm + (k0 / KT) * 32;
+            // uniform across the CTA: a slice of X without a nonzero adds nothing
+            bool any = false;
+#pragma unroll
+            for (int p = 0; p < 32; ++p) any |= xp[p] != 0;
+            if (!any) continue;
+            const int kn = min(KT, m - k0);
             for (int e = tid; e < KT * 64; e += 256) {
                 int kk, ii;
                 T v = T(0);
@@ -1136,51 +1195,48 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
                 Ts[kk * 64 + ii] = v;
             }
             __syncthreads();
-            const int kn = min(KT, m - k0);
-            for (int kk = 0; kk < kn; ++kk) {
-                if (sizeof(T) == 8 && !zrow[k0 + kk]) continue;
-                T a[4], bv[4];
-                if (type == 0) {               // rows of out = ob + ty*4+i, cols = tx*4+jx
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) a[i] = Ts[kk * 64 + ty * 4 + i];
-#pragma unroll
-                    for (int jx = 0; jx < 4; ++jx) bv[jx] = X[(k0 + kk) * 64 + tx * 4 + jx];
-                } else {                       // rows = chunk rows ty*4+i, cols = ob + tx*4+jx
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) a[i] = X[(k0 + kk) * 64 + ty * 4 + i];
-#pragma unroll
-                    for (int jx = 0; jx < 4; ++jx) bv[jx] = Ts[kk * 64 + tx * 4 + jx];
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int jx = 0; jx < 4; ++jx) acc[i][jx] += a[i] * bv[jx];
-            }
+            slice_pair_masks<T>(Ts, kn, tpm);
             __syncthreads();
+            const unsigned short *apm = type == 0 ? tpm : xp;
+            const unsigned short *bpm = type == 0 ? xp : tpm;
+            const T *A = type == 0 ? Ts : X + (size_t)k0 * 64;
+            const T *B = type == 0 ? X + (size_t)k0 * 64 : Ts;
+            const unsigned amk = apm[4 * warp] | apm[4 * warp + 1] | apm[4 * warp + 2] |
+                                 apm[4 * warp + 3];
+            if (amk) {
+#pragma unroll
+                for (int g = 0; g < 16; ++g) {
+                    unsigned km = amk & (unsigned)(bpm[2 * g] | bpm[2 * g + 1]);
+                    while (km) {                          // uniform across the warp
+                        const int kk = __ffs(km) - 1;
+                        km &= km - 1;
+                        acc[g] += A[kk * 64 + rr] * B[kk * 64 + 4 * g + cc];
+                    }
+                }
+            }
+            __syncthreads();                              // Ts and tpm are rewritten next
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jx = 0; jx < 4; ++jx) {
-                // (row, column) of the panel block; a sparse block keeps only
-                // its pattern (the result is zero elsewhere)
-                int br, bc;
-                if (type == 0) { br = ob + ty * 4 + i; bc = c0 + tx * 4 + jx; }
-                else           { br = c0 + ty * 4 + i; bc = ob + tx * 4 + jx; }
-                const bool in = type == 0 ? (br < m && bc - c0 < nv)
-                                          : (br - c0 < nv && bc < m);
-                if (!in) continue;
-                if (d.dense) {
-                    Bg[(int64_t)bc * ld + br] = acc[i][jx];
-                } else {
-                    int64_t vb;
-                    int cn;
-                    const uint16_t *rw;
-                    colview(d, bc, a, vb, cn, rw);
-                    const int q = find_row(rw, cn, br);
-                    if (q >= 0) val[vb + q] = acc[i][jx];
-                }
+        for (int g = 0; g < 16; ++g) {
+            // (row, column) of the panel block; a sparse block keeps only
+            // its pattern (the result is zero elsewhere)
+            int br, bc;
+            if (type == 0) { br = ob + rr; bc = c0 + 4 * g + cc; }
+            else           { br = c0 + rr; bc = ob + 4 * g + cc; }
+            const bool in = type == 0 ? (br < m && bc - c0 < nv)
+                                      : (br - c0 < nv && bc < m);
+            if (!in) continue;
+            if (d.dense) {
+                Bg[(int64_t)bc * ld + br] = acc[g];
+            } else {
+                int64_t vb;
+                int cn;
+                const uint16_t *rw;
+                colview(d, bc, a, vb, cn, rw);
+                const int q = find_row(rw, cn, br);
+                if (q >= 0) val[vb + q] = acc[g];
             }
+        }
     }
 }
 
@@ -1496,12 +1552,23 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TN));
 }
 
-// SSSSM on dense tiles: a 64 x 64 tile of a dense target B_KJ minus the sum
-// over the level's dense sources of L_KI U_IJ, accumulated in registers
-// (4 x 4 per thread) over all sources and k-slices of 16, written once.
-// Slices are double-buffered: the next slice's global loads are in flight
-// (in registers) while the current one is multiplied from shared memory.
-// Sources run in ascending I, so the result is deterministic.
+// SSSSM on dense tiles (FP64): a 64 x 64 tile of a dense target B_KJ minus
+// the sum over the level's dense sources of L_KI U_IJ, accumulated in
+// registers over all sources and 16-deep k-slices and written once.  The
+// FP64 pipe bounds this kernel (about two FMAs per SM and clock on B300),
+// so the tile executes only products whose operands can both be nonzero,
+// at the granularity of 8 x 4 sub-tiles: warp w owns rows 8w .. 8w+7, lane
+// l row 8w + (l & 7) and column 4g + (l >> 3) of each of the 16 column
+// groups g (16 accumulators).  While staging a slice, the warps record
+// which 8-row groups of every column k of the A slice and which column
+// pairs of every row k of the B slice hold a nonzero; warp w then runs,
+// for each column group g, a loop over the k at which both its row group
+// of A(:, k) and group g of B(k, :) hold one (set bits of a 16-bit mask,
+// warp-uniform, so no FP64 instruction is issued for a skipped product).
+// The terms left out are exact zeros: the result is the dense one.  Slices
+// are double-buffered (the next slice's global loads are in flight in
+// registers while the current one is multiplied), sources run in ascending
+// I and k ascending within them, so the result is deterministic.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
@@ -1509,17 +1576,18 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
     constexpr int TM = 64, TN = 64, KT = 16, PAD = 16 / sizeof(T);
     __shared__ __align__(16) T As[2][KT][TM];
     __shared__ __align__(16) T Bs[2][KT][TN + PAD];
+    // sAg[buf][k][h] bit j: rows 32h + 8j .. +7 of A(:, k) hold a nonzero;
+    // sBp[buf][p] bit k: columns 2p, 2p + 1 of B(k, :) hold a nonzero
+    __shared__ unsigned char sAg[2][KT][2];
+    __shared__ unsigned short sBp[2][TN / 2];
     const int32_t *tk = task + 5 * (int64_t)blockIdx.x;
     const BlockDesc d = bd[tk[0]];
     const int s0 = tk[1], s1 = tk[2], r0 = tk[3], c0 = tk[4];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    T acc[4][4];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    T acc[TN / 4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int g = 0; g < TN / 4; ++g) acc[g] = T(0);
     if (s0 >= s1) return;
-    // slice state: source s, k offset k0 within it
     int s = s0, k0 = 0;
     BlockDesc dl = bd[src[2 * s]], du = bd[src[2 * s + 1]];
     T ra[4], rb[4];
@@ -1542,45 +1610,31 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
             rb[q] = (gk < K && gc < d.cols) ? B[(int64_t)gc * U.ld + gk] : T(0);
         }
     };
-    // Per-k liveness of a slice: column k of the A slice and row k of the
-    // B slice both nonzero.  Warp w stages A rows 32 (w % 2) .. + 31 of
-    // columns k = w / 2 + 4 q, and B rows k = lane % 16 of two columns per
-    // q, so one ballot per q gives the warp's share; lane 0 records it and
-    // the consumers OR the eight records after the barrier.
-    __shared__ unsigned sA[2][8], sB[2][8];
-    const int warp = tid >> 5, lane = tid & 31;
+    // Staging map: A element e = tid + 256 q is (row e % 64, k e / 64), so
+    // warp w's lanes are rows 32 (w & 1) .. + 31 of k = (w + 8 q) / 2 and its
+    // ballot gives four 8-row groups; B element e is (k e % 16, column
+    // e / 16), so the warp holds column pair w + 8 q, lanes 0-15 and 16-31
+    // one column each over k = 0 .. 15.
     auto store = [&](int buf) {
-        unsigned fa = 0, fb = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = tid + 256 * q;
             As[buf][e / TM][e % TM] = ra[q];
-            fa |= (__ballot_sync(0xffffffffu, ra[q] != T(0)) ? 1u : 0u) << q;
+            const unsigned m = __ballot_sync(0xffffffffu, nz(ra[q]));
+            if (lane == 0)
+                sAg[buf][(warp + 8 * q) >> 1][warp & 1] =
+                    (unsigned char)(((m & 0xffu) ? 1u : 0u) | ((m & 0xff00u) ? 2u : 0u) |
+                                    ((m & 0xff0000u) ? 4u : 0u) | ((m & 0xff000000u) ? 8u : 0u));
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = tid + 256 * q;
             Bs[buf][e % KT][e / KT] = rb[q];
-            const unsigned m = __ballot_sync(0xffffffffu, rb[q] != T(0));
-            fb |= (m | (m >> 16)) & 0xffffu;
-        }
-        if (lane == 0) {
-            sA[buf][warp] = fa;
-            sB[buf][warp] = fb;
+            const unsigned m = __ballot_sync(0xffffffffu, nz(rb[q]));
+            if (lane == 0) sBp[buf][warp + 8 * q] = (unsigned short)((m | (m >> 16)) & 0xffffu);
         }
     };
-    auto live_mask = [&](int buf) {
-        unsigned ma = 0, mb = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            const unsigned fa = sA[buf][w];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if ((fa >> q) & 1u) ma |= 1u << (w / 2 + 4 * q);
-            mb |= sB[buf][w];
-        }
-        return ma & mb;
-    };
+    const int rr = 8 * warp + (lane & 7), cc = lane >> 3;
     load(dl, du, 0);
     store(0);
     __syncthreads();
@@ -1595,22 +1649,18 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
             if (ns != s) { nl = bd[src[2 * ns]]; nu = bd[src[2 * ns + 1]]; }
             load(nl, nu, nk0);
         }
-        // FP64 is bound by the FP64 pipe, so zero columns are skipped; FP32
-        // is bound by latency, and the mask would only lengthen the chain
-        const unsigned live = sizeof(T) == 8 ? live_mask(buf) : 0xffffu;
-        if (live) {
+        // k mask of this warp's row group (lane k of the first 16 reads it)
+        const unsigned amk = __ballot_sync(
+            0xffffffffu, lane < KT && ((sAg[buf][lane & (KT - 1)][warp >> 2] >> (warp & 3)) & 1u));
+        if (amk) {
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                if (!((live >> k) & 1u)) continue;     // uniform across the CTA
-                T a[4], b[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[buf][k][ty * 4 + i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = Bs[buf][k][tx * 4 + j];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+            for (int g = 0; g < TN / 4; ++g) {
+                unsigned km = amk & (unsigned)(sBp[buf][2 * g] | sBp[buf][2 * g + 1]);
+                while (km) {                                // uniform across the warp
+                    const int k = __ffs(km) - 1;
+                    km &= km - 1;
+                    acc[g] += As[buf][k][rr] * Bs[buf][k][4 * g + cc];
+                }
             }
         }
         if (!more) break;
@@ -1622,14 +1672,12 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
         dl = nl;
         du = nu;
     }
+    const int r = r0 + rr;
+    if (r < d.rows) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int c = c0 + tx * 4 + j;
-        if (c >= d.cols) continue;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = r0 + ty * 4 + i;
-            if (r < d.rows) val[d.voff + (int64_t)c * d.ld + r] -= acc[i][j];
+        for (int g = 0; g < TN / 4; ++g) {
+            const int c = c0 + 4 * g + cc;
+            if (c < d.cols && nz(acc[g])) val[d.voff + (int64_t)c * d.ld + r] -= acc[g];
         }
     }
 }
@@ -1750,6 +1798,7 @@ static slu_status set_smem_limits(size_t generic) {
               cuda_ok(cudaFuncSetAttribute(k_getrf_dense<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_inv<T>, attr, (int)kStageSmem), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_inv<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_grp<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_vec<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_ssssm_tc, attr, (int)tc::SMEM), "smem");
@@ -1829,7 +1878,7 @@ static slu_status run_factor(slu_handle *h, const double *values,
         const int64_t i0 = P->inv_off[lv], i1 = P->inv_off[lv + 1];
         if (i1 > i0) {
             LaunchScope ls_(h, SLU_KC_INV, st, (int)(i1 - i0));
-            k_inv<T><<<(int)(i1 - i0), 256, 0, st>>>(
+            k_inv<T><<<(int)(i1 - i0), 256, inv_smem_elems(P->inv_maxb) * sizeof(T), st>>>(
                 D->inv_task + 3 * i0, D->bd, val, static_cast<T *>(h->winv), D->woff);
         }
         const int64_t d0 = P->pd_off[lv], d1 = P->pd_off[lv + 1];
