@@ -293,6 +293,19 @@ def batch_leg(torch, S, dev, args):
         msr = timed(torch, step_r, args.steps, 2)
         FR.set_graph(False)
     del FR, PR
+    PS = S.Plan([m.n for m in ms], [m.colptr for m in ms],
+                [m.rowidx for m in ms], precision="fp32", dense_threshold=0.0,
+                blocking="regular_select")
+    FS = S.Factor(PS, vb)
+    with torch.cuda.stream(st):
+        FS.set_graph(True)
+
+        def step_s():
+            FS.refactor(vb)
+            FS.solve(bb)
+        mss = timed(torch, step_s, args.steps, 2)
+        FS.set_graph(False)
+    del FS, PS
     plans = [S.Plan(m.n, m.colptr, m.rowidx, precision="fp32",
                     dense_threshold=0.0) for m in ms]
     vs = [dev(m.values) for m in ms]
@@ -308,6 +321,7 @@ def batch_leg(torch, S, dev, args):
     return {"ms_per_step": msb, "gflops": fl / (msb * 1e-3) / 1e9,
             "loop_ms_per_step": msl, "speedup_vs_loop": msl / msb,
             "regular64_graph_ms_per_step": msr, "irregular_speedup": msr / msb,
+            "regular_select_graph_ms_per_step": mss,
             "backward_error_max_member": ib["backward_error"],
             "ir_iterations": ib["iterations"], "levels": PB.info["nlevels"],
             "n_total": PB.info["n"]}
@@ -336,6 +350,7 @@ def small_grid_leg(torch, S, dev, args):
     from paper_2512_04389_b300.tune import candidates
     for name, opts in (("irregular", {}),
                        ("regular64", dict(blocking="regular", regular_block=64)),
+                       ("regular_select", dict(blocking="regular_select")),
                        ("regular_tuned", None)):
         if opts is None:           # block size and threshold both searched
             best, _ = tune(s.n, s.colptr, s.rowidx, v, r, precision="fp64",
@@ -413,10 +428,15 @@ def autograd_leg(torch, S, dev, args):
             x = lu_solve(vv, bb, plan)
             (0.5 * (x * x).sum()).backward()
         return timed(torch, step, args.steps, 2)
+    PSel = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=0.0,
+                  blocking="regular_select")
     ms = run(P)
     msr = run(PR)
+    mss = run(PSel)
     return {"ms_per_step": ms, "n": s.n, "nnz_a": s.nnz,
             "regular128_ms_per_step": msr, "irregular_speedup": msr / ms,
+            "regular_select_ms_per_step": mss,
+            "regular_select_block": PSel.info["regular_block"],
             "what": "factor + solve forward, transposed solve + gradient gather backward"}
 
 
@@ -635,6 +655,21 @@ def main():
                 "levels": pt.info["nlevels"], "tuning_ms": tt,
                 "irregular_speedup": mst / (ms if prec == "fp64" else ms32)}
             del Ft, pt
+            # the regular-size selection policy (no timing runs): its size
+            # and threshold 0, the tuned choice on these grids
+            ps_ = S.Plan(s.n, s.colptr, s.rowidx, precision=prec,
+                         blocking="regular_select", dense_threshold=0.0)
+            Fs = S.Factor(ps_, vals_d)
+
+            def steps_():
+                Fs.refactor(vals_d)
+                Fs.solve(rhs_d)
+            mss = timed(torch, steps_, args.steps, 2)
+            extras[f"regular_select_{prec}"] = {
+                "ms_per_step": mss, "regular_block": ps_.info["regular_block"],
+                "gflops": fl / (mss * 1e-3) / 1e9,
+                "irregular_speedup": mss / (ms if prec == "fp64" else ms32)}
+            del Fs, ps_
         bestr32, _ = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
                           precision="fp32", blocking="regular", regular_block=128)
         preg32 = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular",

@@ -64,7 +64,11 @@ typedef enum {
 
 typedef enum {
     SLU_BLOCKING_IRREGULAR = 0,  /* Algorithm 3 on the sampled curve        */
-    SLU_BLOCKING_REGULAR = 1     /* fixed-size blocks of regular_block rows */
+    SLU_BLOCKING_REGULAR = 1,    /* fixed-size blocks of regular_block rows */
+    SLU_BLOCKING_REGULAR_SELECT = 2
+                                 /* fixed-size blocks whose size a selection
+                                    tree picks from the order and the filled
+                                    nonzeros (slu_select_regular_block)     */
 } slu_blocking;
 
 typedef enum {
@@ -94,8 +98,9 @@ typedef struct {
     double refine_tol;           /* stop when backward error <= this        */
     int32_t refine_max_iter;     /* < 0 never refine; 0 = default (none for
                                     FP64, 30 for FP32); > 0 that many       */
-    int64_t wait_budget_ms;      /* reserved: device-side waits are bounded
-                                    by a fixed poll count instead           */
+    int64_t wait_budget_ms;      /* bound of every dependency wait of the
+                                    persistent launch (slu_set_persistent),
+                                    ms; <= 0 means 2000                     */
 } slu_opts;
 
 typedef struct {
@@ -114,6 +119,9 @@ typedef struct {
     int32_t max_block;           /* largest block dimension                 */
     int32_t samples;             /* S actually used                         */
     double analyze_ms;           /* host time of slu_analyze                */
+    int32_t regular_block;       /* regular blocking: the block size used
+                                    (the largest over batch members for
+                                    SLU_BLOCKING_REGULAR_SELECT); else 0    */
 } slu_plan_info;
 
 typedef struct {
@@ -138,7 +146,8 @@ enum {
     SLU_KC_RESID = 5,            /* residual, norms, update                 */
     SLU_KC_INV = 6,              /* inverses of dense diagonal factors      */
     SLU_KC_DIAG = 7,             /* solve: diagonal-block step              */
-    SLU_KC_COUNT = 8
+    SLU_KC_PERSIST = 8,          /* the persistent level walk (all classes) */
+    SLU_KC_COUNT = 9
 };
 
 typedef struct {
@@ -192,6 +201,19 @@ slu_status slu_analyze_batch(int32_t count, const int64_t *n,
                              const slu_opts *opts, slu_plan **out);
 
 slu_status slu_plan_query(const slu_plan *plan, slu_plan_info *info);
+
+/* Regular-size selection policy (SLU_BLOCKING_REGULAR_SELECT).  PanguLU,
+ * the regular-blocking solver the paper compares against, picks its block
+ * size with a selection tree over the matrix order and the number of
+ * nonzeros after symbolic factorization (Section 1; Section 5.2 compares
+ * irregular blocking with it and with the best size of a sweep).  The
+ * paper does not print the tree.  This one was fitted to B300 timings of
+ * the FP64 factor + solve over the regular sizes {32, 64, 128, 256} on the
+ * seeded grid, convection-diffusion and circuit families; it splits on n
+ * and on the filled density nnz_lu / n (entries per column).  Returns the
+ * block size for an n x n matrix with nnz_lu filled entries (1 <= result
+ * <= max(n, 1)); pure host function. */
+int32_t slu_select_regular_block(int64_t n, int64_t nnz_lu);
 
 /* Copies of the plan's host arrays, for bit-exact checks.  Every output is
  * host memory sized from slu_plan_query:
@@ -318,6 +340,42 @@ slu_status slu_grad_values(const slu_handle *h, const double *Lam, int64_t ldl,
  * colptr/rowidx): rows < col hold U, the diagonal holds U's, rows > col hold
  * L.  out: device float64[nnz_lu]. */
 slu_status slu_export_factors(const slu_handle *h, double *out, void *stream);
+
+/* Persistent launch (the batching form's "one launch" for the level walk;
+ * no counterpart in the paper's A100 design, which launches per task).
+ * When enabled, slu_refactor runs every level of every matrix of the plan
+ * (many members for a slu_analyze_batch plan) in ONE kernel launch after
+ * the value scatter: one CTA per SM takes tasks in the order of a work list
+ * built on the host -- per level the GETRF, inverse, panel and Schur-tile
+ * tasks of all members, in that phase order -- and before each task waits
+ * until the tasks of the same member's previous non-empty phase are done
+ * (device-side counters, acquire/release at GPU scope).  Tickets are taken
+ * in list order, so a CTA only waits for tasks that running CTAs hold.
+ * Each wait is bounded by opts.wait_budget_ms; one that runs out stops the
+ * launch and the next synchronizing call reports SLU_ERR_TIMEOUT (the
+ * factors are then not usable; the context stays usable).  The factors
+ * are bit for bit those of the per-level launches.  Graph mode records the
+ * persistent launch like any other.  Supported when every block is stored
+ * dense and every diagonal block has explicit inverses (dense_threshold 0
+ * and blocks of at most 384 rows), else SLU_ERR_NOT_SUPPORTED. */
+slu_status slu_set_persistent(slu_handle *h, int32_t enable);
+
+/* The persistent launch's work list, 5 int32 per task in ticket order:
+ * kind (0 GETRF, 1 inverse, 2 panel, 3 Schur tile), index into that kind's
+ * task list of the plan, the counter waited for (-1: none), the count it
+ * must reach, and the counter the task increments when done; counter
+ * ((member * nlevels) + level) * 4 + phase counts the finished tasks of
+ * that member, level and phase.  slu_persistent_tasks copies min(cap, count) tasks
+ * into tasks (host) and the count into *count (the list is built by
+ * slu_set_persistent).  slu_set_persistent_tasks replaces the list with
+ * `count` tasks from host memory after checking that every kind, index and
+ * counter is in range (SLU_ERR_INVALID_ARG otherwise); it does not check
+ * that the waits can be met -- a wait that cannot is stopped by the bound
+ * above. */
+slu_status slu_persistent_tasks(const slu_handle *h, int32_t *tasks, int64_t cap,
+                                int64_t *count);
+slu_status slu_set_persistent_tasks(slu_handle *h, const int32_t *tasks,
+                                    int64_t count);
 
 /* Profiling: while enabled, every kernel launch of the handle is bracketed
  * by a pair of CUDA events on its stream, and slu_handle_stats sums their

@@ -269,6 +269,12 @@ struct slu_handle {
     size_t pool_next = 0;
     int64_t calls[SLU_KC_COUNT] = {0};
     double ms[SLU_KC_COUNT] = {0};
+    // persistent launch: work list (5 ints per task), its counters and the
+    // ticket, on the handle's device
+    bool persistent = false;
+    int32_t *ptasks = nullptr;
+    int *pdone = nullptr;               // pcounters counters, then the ticket
+    int64_t pntasks = 0, pcounters = 0;
 };
 
 namespace slu {

@@ -143,13 +143,18 @@ __device__ __forceinline__ void axpy_rows(T *vj, const uint16_t *rj, int cj,
 // symbolic pattern are exact zeros and stay zero.
 // Pivot of step k: the FP64 test |piv| < tau and the +-tau replacement
 // (sign of zero taken as +), counted once; returns the value to store.
+// The tests run on the bit patterns (integer pipe): |piv| and tau >= 0 order
+// like their patterns, a NaN pivot is never below tau, and -0 counts as +0.
 __device__ __forceinline__ double fix_pivot(double piv, double tau,
                                            unsigned long long *cnt) {
-    if (tau > 0.0 && fabs(piv) < tau) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(piv);
+    const unsigned long long mag = bits & 0x7fffffffffffffffull;
+    const unsigned long long t = (unsigned long long)__double_as_longlong(tau);
+    if (t != 0 && mag < t) {
         atomicAdd(&cnt[0], 1ull);
-        return (piv >= 0.0) ? tau : -tau;
+        return (mag != 0 && (bits >> 63)) ? -tau : tau;
     }
-    if (piv == 0.0) atomicOr(&cnt[1], 1ull);
+    if (mag == 0) atomicOr(&cnt[1], 1ull);
     return piv;
 }
 
@@ -207,7 +212,9 @@ __host__ __device__ constexpr size_t lu_list_bytes(int b, size_t esz) {
 }
 
 // One warp: compact the nonzeros of entries k+1..b-1 of a column (col =
-// true: (r, k), scaled by rcp and stored back) or of a row ((k, c)).
+// true: (r, k)) or of a row ((k, c)) into a (index, value) list; a column's
+// listed values are then scaled by rcp and stored back (L(:, k)), one FP64
+// multiply per 32 listed entries rather than per 32 rows scanned.
 template <typename T>
 __device__ __forceinline__ int lu_compact(const SplitBlock<T> &B, int b, int k,
                                           bool col, T rcp, T *X, uint16_t *I) {
@@ -224,15 +231,8 @@ __device__ __forceinline__ int lu_compact(const SplitBlock<T> &B, int b, int k,
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i = i0 + 32 * q + lane;
-            // only entries inside the block are scaled and listed (with a
-            // zero pivot and no perturbation rcp is inf, and 0 * inf would
-            // list a NaN for a lane past the end)
-            const bool in = i < b;
-            if (col && in) {
-                v[q] *= rcp;
-                B.at(i, k) = v[q];
-            }
-            const bool live = in && nz(v[q]);
+            // only entries inside the block are listed
+            const bool live = i < b && nz(v[q]);
             const unsigned m = __ballot_sync(0xffffffffu, live);
             if (live) {
                 const int p = n + __popc(m & lt);
@@ -241,6 +241,14 @@ __device__ __forceinline__ int lu_compact(const SplitBlock<T> &B, int b, int k,
                 X[p] = v[q];
             }
             n += __popc(m);
+        }
+    }
+    if (col) {
+        __syncwarp();
+        for (int p = lane; p < n; p += 32) {
+            const T l = X[p] * rcp;
+            X[p] = l;
+            B.at(I[p], k) = l;
         }
     }
     return n;
@@ -280,23 +288,32 @@ __device__ void lu_skip(const SplitBlock<T> &B, int b, unsigned char *lists,
                 const bool cs = c >= B.p0;
                 T *colG = B.G + (int64_t)c * B.ld;
                 T *colS = cs ? B.S + (int64_t)(c - B.p0) * B.ls - B.p0 : B.S;
-                for (int r0 = li; r0 < nR; r0 += 4 * g) {
-                    T *q[4];
-                    T x[4], l[4];
+                if (nR > 2 * g) {           // uniform: four updates in flight
+                    for (int r0 = li; r0 < nR; r0 += 4 * g) {
+                        T *q[4];
+                        T x[4], l[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int ri = r0 + j * g;
-                        if (ri < nR) {
-                            const int r = R[ri];
-                            SLU_CHECK(r > k && r < b && c > k && c < b && ri < b && ci < b, 2);
-                            q[j] = (cs && r >= B.p0) ? colS + r : colG + r;
-                            x[j] = *q[j];
-                            l[j] = Lv[ri];
+                        for (int j = 0; j < 4; ++j) {
+                            const int ri = r0 + j * g;
+                            if (ri < nR) {
+                                const int r = R[ri];
+                                SLU_CHECK(r > k && r < b && c > k && c < b && ri < b && ci < b, 2);
+                                q[j] = (cs && r >= B.p0) ? colS + r : colG + r;
+                                x[j] = *q[j];
+                                l[j] = Lv[ri];
+                            }
                         }
-                    }
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (r0 + j * g < nR) *q[j] = x[j] - l[j] * u;
+                        for (int j = 0; j < 4; ++j)
+                            if (r0 + j * g < nR) *q[j] = x[j] - l[j] * u;
+                    }
+                } else {                    // one or two rows per lane: no idle FP64 issue
+                    for (int ri = li; ri < nR; ri += g) {
+                        const int r = R[ri];
+                        SLU_CHECK(r > k && r < b && c > k && c < b && ri < b && ci < b, 2);
+                        T *q = (cs && r >= B.p0) ? colS + r : colG + r;
+                        *q = *q - Lv[ri] * u;
+                    }
                 }
             }
         }
@@ -997,17 +1014,14 @@ __host__ __device__ constexpr size_t inv_smem_elems(int b) {
     return (size_t)((b + 31) & ~31) * (1 + 3 * 8);
 }
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
-      const T *__restrict__ val, T *__restrict__ winv,
-      const int64_t *__restrict__ woff) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int32_t *tk = task + 3 * (int64_t)blockIdx.x;
+__device__ __forceinline__ void inv_body(const int32_t *tk, const BlockDesc *bd,
+                                         const T *val, T *winv, const int64_t *woff,
+                                         unsigned char *smem) {
     const BlockDesc d = bd[tk[0]];
     const int which = tk[1], b = d.rows, bs = (b + 31) & ~31;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = tk[2] + warp;
-    const T *__restrict__ F = val + d.voff;           // dense LU, ld = b
+    const T *F = val + d.voff;                        // dense LU, ld = b
     T *s_rcp = reinterpret_cast<T *>(smem);
     if (which == 1)                                   // uniform across the CTA
         for (int e = threadIdx.x; e < b; e += blockDim.x)
@@ -1063,6 +1077,15 @@ k_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
     for (int r = lane; r < b; r += 32) out[r] = x[r];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
+      const T *__restrict__ val, T *__restrict__ winv,
+      const int64_t *__restrict__ woff) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    inv_body<T>(task + 3 * (int64_t)blockIdx.x, bd, val, winv, woff, smem);
+}
+
 // Column-pair masks of a staged 16 x 64 slice S (S[kk * 64 + c]): bit kk of
 // pm[p] is set when S[kk][2p] or S[kk][2p + 1] is nonzero.  Warp w takes
 // pairs 4w .. 4w + 3, lane l row kk = l & 15 of pairs 4w + 2 (l >> 4) + {0,
@@ -1104,13 +1127,11 @@ __device__ __forceinline__ void slice_pair_masks(const T *S, int nk,
 // all zero is skipped before its inverse slice is loaded.  The terms left
 // out are exact zeros.
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
-            T *__restrict__ val, const T *__restrict__ winv,
-            const int64_t *__restrict__ woff, BlockArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void panel_inv_body(const int32_t *tk, const BlockDesc *bd,
+                                               T *val, const T *winv,
+                                               const int64_t *woff, const BlockArgs &a,
+                                               unsigned char *smem) {
     constexpr int KT = 16;
-    const int32_t *tk = task + 4 * (int64_t)blockIdx.x;
     const int type = tk[0];
     const BlockDesc d = bd[tk[1]];
     const BlockDesc dd = bd[tk[2]];
@@ -1238,6 +1259,15 @@ k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
             }
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
+            T *__restrict__ val, const T *__restrict__ winv,
+            const int64_t *__restrict__ woff, BlockArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    panel_inv_body<T>(task + 4 * (int64_t)blockIdx.x, bd, val, winv, woff, a, smem);
 }
 
 // SSSSM: target B_KJ -= sum over the level's sources I of L_KI U_IJ.
@@ -1382,35 +1412,21 @@ __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
 }
 }  // namespace tc
 
-__global__ void __launch_bounds__(256)
-k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
-           const BlockDesc *__restrict__ bd, float *__restrict__ val,
-           unsigned long long *__restrict__ err) {
+// One tile's work: `smem` (1024-byte aligned, tc::SMEM - 1024 bytes) holds
+// the two stages, `mbar` the two initialised stage barriers whose expected
+// parities `phase` carries from tile to tile, `tmem` the tile's 64 TMEM
+// columns (allocated by the caller).  Every MMA it commits is waited for
+// before it returns (a wait that runs out sets err[0]).
+__device__ __forceinline__ void tc_body(const int32_t *tk, const int32_t *src,
+                                        const BlockDesc *bd, float *val,
+                                        unsigned long long *err, unsigned char *smem,
+                                        uint64_t *mbar, uint32_t tmem,
+                                        uint32_t (&phase)[2]) {
     using namespace tc;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ uint32_t tmem_holder;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int32_t *tk = task + 5 * (int64_t)blockIdx.x;
     const BlockDesc d = bd[tk[0]];
     const int s0 = tk[1], s1 = tk[2], r0 = tk[3], c0 = tk[4];
     if (s0 >= s1) return;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_holder)), "r"(TN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_holder;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
     // Register image of one chunk, one core matrix (8 rows x 4 k, 128
@@ -1463,7 +1479,6 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
     load(dl, du, 0);
     int chunk = 0;
     bool ok = true;
-    uint32_t phase[2] = {0, 0};
     for (;;) {
         const int st = chunk & 1;
         unsigned char *base = smem + st * STAGE_BYTES;
@@ -1548,8 +1563,51 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+}
+
+// TMEM columns and stage barriers of a CTA that runs tensor-core tiles.
+__device__ __forceinline__ uint32_t tc_setup(uint64_t *mbar, uint32_t *tmem_holder) {
+    using namespace tc;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_holder)), "r"(TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return *tmem_holder;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
+    using namespace tc;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TN));
+}
+
+__global__ void __launch_bounds__(256)
+k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
+           const BlockDesc *__restrict__ bd, float *__restrict__ val,
+           unsigned long long *__restrict__ err) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_holder;
+    const int32_t *tk = task + 5 * (int64_t)blockIdx.x;
+    if (tk[1] >= tk[2]) return;
+    const uint32_t tmem = tc_setup(mbar, &tmem_holder);
+    uint32_t phase[2] = {0, 0};
+    tc_body(tk, src, bd, val, err, smem, mbar, tmem, phase);
+    tc_teardown(tmem);
 }
 
 // SSSSM on dense tiles (FP64): a 64 x 64 tile of a dense target B_KJ minus
@@ -1569,18 +1627,27 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
 // are double-buffered (the next slice's global loads are in flight in
 // registers while the current one is multiplied), sources run in ascending
 // I and k ascending within them, so the result is deterministic.
+// Shared memory of one dense Schur tile: the double-buffered slices and
+// their masks (sAg[buf][k][h] bit j: rows 32h + 8j .. +7 of A(:, k) hold a
+// nonzero; sBp[buf][p] bit k: columns 2p, 2p + 1 of B(k, :) hold one).
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
-             const BlockDesc *__restrict__ bd, T *__restrict__ val) {
-    constexpr int TM = 64, TN = 64, KT = 16, PAD = 16 / sizeof(T);
-    __shared__ __align__(16) T As[2][KT][TM];
-    __shared__ __align__(16) T Bs[2][KT][TN + PAD];
-    // sAg[buf][k][h] bit j: rows 32h + 8j .. +7 of A(:, k) hold a nonzero;
-    // sBp[buf][p] bit k: columns 2p, 2p + 1 of B(k, :) hold a nonzero
-    __shared__ unsigned char sAg[2][KT][2];
-    __shared__ unsigned short sBp[2][TN / 2];
-    const int32_t *tk = task + 5 * (int64_t)blockIdx.x;
+struct GemmSmem {
+    static constexpr int TM = 64, TN = 64, KT = 16, PAD = 16 / sizeof(T);
+    T As[2][KT][TM];
+    T Bs[2][KT][TN + PAD];
+    unsigned char sAg[2][KT][2];
+    unsigned short sBp[2][TN / 2];
+};
+
+template <typename T>
+__device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
+                                          const BlockDesc *bd, T *val,
+                                          GemmSmem<T> &sm) {
+    constexpr int TM = GemmSmem<T>::TM, TN = GemmSmem<T>::TN, KT = GemmSmem<T>::KT;
+    auto &As = sm.As;
+    auto &Bs = sm.Bs;
+    auto &sAg = sm.sAg;
+    auto &sBp = sm.sBp;
     const BlockDesc d = bd[tk[0]];
     const int s0 = tk[1], s1 = tk[2], r0 = tk[3], c0 = tk[4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1592,8 +1659,8 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
     BlockDesc dl = bd[src[2 * s]], du = bd[src[2 * s + 1]];
     T ra[4], rb[4];
     auto load = [&](const BlockDesc &L, const BlockDesc &U, int kk0) {
-        const T *__restrict__ A = val + L.voff;
-        const T *__restrict__ B = val + U.voff;
+        const T *A = val + L.voff;
+        const T *B = val + U.voff;
         const int K = L.cols;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1680,6 +1747,118 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
             if (c < d.cols && nz(acc[g])) val[d.voff + (int64_t)c * d.ld + r] -= acc[g];
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
+             const BlockDesc *__restrict__ bd, T *__restrict__ val) {
+    __shared__ __align__(16) GemmSmem<T> sm;
+    gemm_body<T>(task + 5 * (int64_t)blockIdx.x, src, bd, val, sm);
+}
+
+// ------------------------------------------------------------ persistent
+// The whole level walk in one launch (see slu_set_persistent): one CTA per
+// SM takes tickets in the order of a work list that lists, level by level,
+// the GETRF, inverse, panel and Schur-tile tasks of every member of the
+// plan.  A task waits (thread 0, acquire at GPU scope, bounded) until the
+// counter of its member's previous non-empty phase reaches that phase's
+// task count, runs the same body as the per-level kernel, and increments
+// its own counter (barrier, fence, atomic).  Every ticket a CTA waits on was
+// taken earlier by a CTA that is running, so the walk cannot deadlock; a
+// wait that runs out sets bit 1 of cnt[2] and the CTA leaves (the others
+// then run out too).  FP32 CTAs hold 64 TMEM columns for the tensor-core
+// tiles from start to end.
+enum : int32_t { kPtGetrf = 0, kPtInv = 1, kPtPanel = 2, kPtSchur = 3 };
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One thread: *c >= need within budget_ns (and 2^26 polls)?
+__device__ __forceinline__ bool wait_count(const int *c, int need, long long budget_ns) {
+    const long long t0 = global_ns();
+    for (int it = 0; it < (1 << 26); ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+        if (v >= need) return true;
+        if (global_ns() - t0 > budget_ns) return false;
+        __nanosleep(128);
+    }
+    return false;
+}
+
+struct PersistArgs {
+    const int32_t *tasks;               // 5 per task
+    int ntasks;
+    int *done;                          // counters
+    int *ticket;
+    const int32_t *gd, *inv_task, *pd_task, *gm_task, *gm_src;
+    const BlockDesc *bd;
+    BlockArgs a;
+    const int64_t *woff;
+    const double *scal;
+    double tau_rel;
+    unsigned long long *cnt;
+    long long budget_ns;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1)
+k_factor_persistent(PersistArgs p, T *val, T *winv) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int s_t, s_stop;
+    const int tid = threadIdx.x;
+    uint32_t tmem = 0;
+    uint32_t phase[2] = {0, 0};
+    if (sizeof(T) == 4) tmem = tc_setup(mbar, &tmem_holder);
+    const double tau = p.tau_rel * p.scal[0];
+    for (;;) {
+        if (tid == 0) {
+            const int t = atomicAdd(p.ticket, 1);
+            int stop = t >= p.ntasks;
+            if (!stop) {
+                const int32_t *pt = p.tasks + 5 * (int64_t)t;
+                if (pt[2] >= 0 && !wait_count(p.done + pt[2], pt[3], p.budget_ns)) {
+                    atomicOr(&p.cnt[2], 2ull);
+                    stop = 1;
+                }
+            }
+            s_t = t;
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_stop) break;                              // uniform
+        const int32_t *pt = p.tasks + 5 * (int64_t)s_t;
+        const int kind = pt[0], idx = pt[1];
+        if (kind == kPtGetrf) {
+            const BlockDesc d = p.bd[p.gd[idx]];
+            getrf_dense<T>(val + d.voff, d.rows, d.ld, tau, p.cnt, smem, kStageSmem);
+        } else if (kind == kPtInv) {
+            inv_body<T>(p.inv_task + 3 * (int64_t)idx, p.bd, val, winv, p.woff, smem);
+        } else if (kind == kPtPanel) {
+            panel_inv_body<T>(p.pd_task + 4 * (int64_t)idx, p.bd, val, winv, p.woff, p.a, smem);
+        } else {
+            if constexpr (sizeof(T) == 4)
+                tc_body(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd,
+                        reinterpret_cast<float *>(val), p.cnt + 2, smem, mbar, tmem, phase);
+            else
+                gemm_body<T>(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd, val,
+                             *reinterpret_cast<GemmSmem<T> *>(smem));
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(p.done + pt[4], 1);
+        }
+    }
+    if (sizeof(T) == 4) tc_teardown(tmem);
 }
 
 // ---------------------------------------------------------------- host side
@@ -1801,7 +1980,9 @@ static slu_status set_smem_limits(size_t generic) {
               cuda_ok(cudaFuncSetAttribute(k_inv<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_grp<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_vec<T>, attr, (int)kStageSmem), "smem") &&
-              cuda_ok(cudaFuncSetAttribute(k_ssssm_tc, attr, (int)tc::SMEM), "smem");
+              cuda_ok(cudaFuncSetAttribute(k_ssssm_tc, attr, (int)tc::SMEM), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_factor_persistent<T>, attr,
+                                           (int)(kStageSmem + 1024)), "smem");
     if (ok)
         ok = cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, (int)kStageSmem), "smem");
     return ok ? SLU_OK : SLU_ERR_CUDA;
@@ -1854,6 +2035,23 @@ static slu_status run_factor(slu_handle *h, const double *values,
             k_scatter<T><<<grid_for(P->nnz_a, 256), 256, 0, st>>>(P->nnz_a, D->a2s,
                                                                 values, val);
         }
+    }
+    if (h->persistent) {                 // the whole level walk, one launch
+        if (!cuda_ok(cudaMemsetAsync(h->pdone, 0, (h->pcounters + 1) * sizeof(int), st),
+                     "cudaMemsetAsync(counters)"))
+            return SLU_ERR_CUDA;
+        int nsm = 148;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+        const int64_t budget_ms = P->opts.wait_budget_ms > 0 ? P->opts.wait_budget_ms : 2000;
+        PersistArgs pa{h->ptasks, (int)h->pntasks, h->pdone, h->pdone + h->pcounters,
+                       D->gd, D->inv_task, D->pd_task, D->gm_task, D->gm_src, D->bd, a,
+                       D->woff, h->scal, h->tau_rel, h->cnt, budget_ms * 1000000ll};
+        {
+            LaunchScope ls_(h, SLU_KC_PERSIST, st, nsm);
+            k_factor_persistent<T><<<nsm, 256, kStageSmem + 1024, st>>>(
+                pa, val, static_cast<T *>(h->winv));
+        }
+        return cuda_ok(cudaGetLastError(), "persistent launch") ? SLU_OK : SLU_ERR_CUDA;
     }
     const size_t smem_f = (size_t)kWarps * P->maxb * sizeof(double);
     const size_t smem_a = (size_t)kWarps * P->maxb * sizeof(Acc);
@@ -1973,6 +2171,9 @@ static slu_status finish_info(slu_handle *h, cudaStream_t st,
         info->tau = h->tau_rel * s[0];
     }
     if (c[3]) return fail(SLU_ERR_INVALID_ARG, "A holds a NaN or infinite value");
+    if (c[2] & 2)
+        return fail(SLU_ERR_TIMEOUT,
+                    "a dependency wait of the persistent launch exceeded wait_budget_ms");
     if (c[2]) return fail(SLU_ERR_TIMEOUT, "a tensor-core wait exceeded its bound");
     if (c[1]) return fail(SLU_ERR_SINGULAR, "zero pivot (perturbation off)");
     return SLU_OK;
@@ -2021,7 +2222,7 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red,
-                    h->part, h->anorm_seg, h->winv};
+                    h->part, h->anorm_seg, h->winv, h->ptasks, h->pdone};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (cur >= 0) cudaSetDevice(cur);
@@ -2321,6 +2522,140 @@ extern "C" slu_status slu_set_graph(slu_handle *h, int32_t enable) {
     if (!h) return fail(SLU_ERR_INVALID_ARG, "NULL handle");
     h->use_graph = enable != 0;
     if (!h->use_graph && h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        h->graph_values = nullptr;
+    }
+    return SLU_OK;
+}
+
+// Work list of the persistent launch (5 ints per task; see the header).
+static slu_status build_persistent(const slu_plan *P, std::vector<int32_t> &tasks,
+                                   int64_t *ncounters) {
+    if (!P->gs.empty() || !P->pg_gessm.empty() || !P->pg_tstrf.empty() ||
+        !P->pv_task.empty() || !P->ps_task.empty() || !P->gg_tgt.empty())
+        return fail(SLU_ERR_NOT_SUPPORTED,
+                    "persistent launch: the plan has sparse-stored blocks or "
+                    "diagonal blocks without explicit inverses");
+    const int64_t L = P->nlevels;
+    const int64_t nseg = P->row_seg.empty() ? 1 : (int64_t)P->seg.size() - 1;
+    const int64_t nc = nseg * L * 4;
+    auto member = [&](int32_t blk) -> int64_t {
+        return P->row_seg.empty() ? 0 : P->row_seg[P->blocks[blk].r0];
+    };
+    auto cid = [&](int64_t q, int64_t lv, int ph) { return (q * L + lv) * 4 + ph; };
+    std::vector<int32_t> count(nc, 0);
+    struct Item { int32_t kind, idx; int64_t c; };
+    std::vector<Item> items;
+    for (int64_t lv = 0; lv < L; ++lv) {
+        for (int64_t i = P->gd_off[lv]; i < P->gd_off[lv + 1]; ++i)
+            items.push_back({kPtGetrf, (int32_t)i, cid(member(P->gd[i]), lv, 0)});
+        for (int64_t i = P->inv_off[lv]; i < P->inv_off[lv + 1]; ++i)
+            items.push_back({kPtInv, (int32_t)i, cid(member(P->inv_task[3 * i]), lv, 1)});
+        for (int64_t i = P->pd_off[lv]; i < P->pd_off[lv + 1]; ++i)
+            items.push_back({kPtPanel, (int32_t)i, cid(member(P->pd_task[4 * i + 2]), lv, 2)});
+        for (int64_t i = P->gm_off[lv]; i < P->gm_off[lv + 1]; ++i)
+            items.push_back({kPtSchur, (int32_t)i, cid(member(P->gm_task[5 * i]), lv, 3)});
+    }
+    for (const Item &it : items) count[it.c]++;
+    // each (member, level, phase) waits for its member's last non-empty
+    // (level, phase) before it
+    std::vector<int64_t> prev(nc, -1);
+    for (int64_t q = 0; q < nseg; ++q) {
+        int64_t last = -1;
+        for (int64_t lv = 0; lv < L; ++lv)
+            for (int ph = 0; ph < 4; ++ph) {
+                const int64_t c = cid(q, lv, ph);
+                if (!count[c]) continue;
+                prev[c] = last;
+                last = c;
+            }
+    }
+    tasks.clear();
+    tasks.reserve(items.size() * 5);
+    for (const Item &it : items) {
+        const int64_t w = prev[it.c];
+        tasks.push_back(it.kind);
+        tasks.push_back(it.idx);
+        tasks.push_back((int32_t)w);
+        tasks.push_back(w >= 0 ? count[w] : 0);
+        tasks.push_back((int32_t)it.c);
+    }
+    *ncounters = nc;
+    return SLU_OK;
+}
+
+static slu_status upload_persistent(slu_handle *h, const std::vector<int32_t> &tasks,
+                                    int64_t ncounters) {
+    if (h->ptasks) cudaFree(h->ptasks);
+    if (h->pdone) cudaFree(h->pdone);
+    h->ptasks = nullptr;
+    h->pdone = nullptr;
+    h->pntasks = (int64_t)tasks.size() / 5;
+    h->pcounters = ncounters;
+    if (!cuda_ok(cudaMalloc(&h->ptasks, std::max<size_t>(1, tasks.size()) * sizeof(int32_t)),
+                 "cudaMalloc(work list)") ||
+        !cuda_ok(cudaMalloc(&h->pdone, (ncounters + 1) * sizeof(int)), "cudaMalloc(counters)"))
+        return SLU_ERR_OUT_OF_MEMORY;
+    if (!tasks.empty() &&
+        !cuda_ok(cudaMemcpy(h->ptasks, tasks.data(), tasks.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice), "cudaMemcpy(work list)"))
+        return SLU_ERR_CUDA;
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_set_persistent(slu_handle *h, int32_t enable) {
+    if (!h) return fail(SLU_ERR_INVALID_ARG, "NULL handle");
+    if (h->graph_exec) {                 // a recorded graph holds the old path
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        h->graph_values = nullptr;
+    }
+    if (!enable) {
+        h->persistent = false;
+        return SLU_OK;
+    }
+    std::vector<int32_t> tasks;
+    int64_t nc = 0;
+    slu_status st = build_persistent(h->plan, tasks, &nc);
+    if (st == SLU_OK) st = upload_persistent(h, tasks, nc);
+    h->persistent = st == SLU_OK;
+    return st;
+}
+
+extern "C" slu_status slu_persistent_tasks(const slu_handle *h, int32_t *tasks,
+                                           int64_t cap, int64_t *count) {
+    if (!h || !count) return fail(SLU_ERR_INVALID_ARG, "NULL argument");
+    *count = h->persistent ? h->pntasks : 0;
+    const int64_t k = std::min<int64_t>(std::max<int64_t>(cap, 0), *count);
+    if (k > 0 && tasks &&
+        !cuda_ok(cudaMemcpy(tasks, h->ptasks, k * 5 * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost), "cudaMemcpy(work list)"))
+        return SLU_ERR_CUDA;
+    return SLU_OK;
+}
+
+extern "C" slu_status slu_set_persistent_tasks(slu_handle *h, const int32_t *tasks,
+                                               int64_t count) {
+    if (!h || (count > 0 && !tasks) || count < 0)
+        return fail(SLU_ERR_INVALID_ARG, "bad arguments");
+    if (!h->persistent)
+        return fail(SLU_ERR_INVALID_ARG, "persistent launch not enabled");
+    const slu_plan *P = h->plan;
+    const int64_t lim[4] = {(int64_t)P->gd.size(), (int64_t)P->inv_task.size() / 3,
+                            (int64_t)P->pd_task.size() / 4, (int64_t)P->gm_task.size() / 5};
+    for (int64_t t = 0; t < count; ++t) {
+        const int32_t *r = tasks + 5 * t;
+        if (r[0] < 0 || r[0] > 3 || r[1] < 0 || r[1] >= lim[r[0]] || r[2] < -1 ||
+            r[2] >= h->pcounters || r[4] < 0 || r[4] >= h->pcounters)
+            return fail(SLU_ERR_INVALID_ARG, "work list entry out of range");
+    }
+    if (count > 0 &&
+        !cuda_ok(cudaMemcpy(h->ptasks, tasks, count * 5 * sizeof(int32_t),
+                            cudaMemcpyHostToDevice), "cudaMemcpy(work list)"))
+        return SLU_ERR_CUDA;
+    h->pntasks = count;
+    if (h->graph_exec) {
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
         h->graph_values = nullptr;

@@ -28,7 +28,8 @@ namespace {
     X(opts) X(n) X(nnz_a) X(nnz_sym)                                          \
     X(a_colptr) X(a_rowidx) X(a_rowptr) X(a_colidx) X(a_vpos) X(a_ci)         \
     X(f_colptr) X(f_rowidx) X(flops) X(flops_cls)                             \
-    X(blockptr) X(ptr) X(p) X(samples) X(maxb) X(seg) X(row_seg) X(rowblk)    \
+    X(blockptr) X(ptr) X(p) X(samples) X(maxb) X(regular_block) X(seg)       \
+    X(row_seg) X(rowblk)                                                      \
     X(blocks) X(bnnz) X(diagblk) X(lcolptr) X(lrow) X(dpos) X(sched) X(sgrp)  \
     X(lr_ptr) X(lr_pos) X(lr_col) X(ur_ptr) X(ur_pos) X(ur_col)               \
     X(ne_off) X(ne_col) X(storage) X(ndense) X(level) X(nlevels)              \

@@ -76,6 +76,7 @@ struct slu_plan {
     std::vector<int64_t> blockptr;       // Algorithm 2, n+1
     std::vector<int64_t> ptr;            // boundaries, p+1
     int32_t p = 0, samples = 0, maxb = 0;
+    int32_t regular_block = 0;           // regular blocking: size used (max over members)
     std::vector<int64_t> seg;            // batch: row offsets of the members
     std::vector<int32_t> row_seg;        // batch: member of each row
     std::vector<int32_t> rowblk;         // row -> block index

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libslu_b300.so")
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA_ERROR",
           4: "SINGULAR", 5: "NOT_CONVERGED", 6: "TIMEOUT", 7: "NOT_SUPPORTED"}
-BLOCKING = {"irregular": 0, "regular": 1}
+BLOCKING = {"irregular": 0, "regular": 1, "regular_select": 2}
 PRECISION = {"fp64": 0, "fp32": 1}
 
 
@@ -46,7 +46,7 @@ class PlanInfo(C.Structure):
                 ("n_gessm", C.c_int64), ("n_tstrf", C.c_int64),
                 ("n_ssssm_targets", C.c_int64), ("n_ssssm_pairs", C.c_int64),
                 ("max_block", C.c_int32), ("samples", C.c_int32),
-                ("analyze_ms", C.c_double)]
+                ("analyze_ms", C.c_double), ("regular_block", C.c_int32)]
 
 
 class FactorInfo(C.Structure):
@@ -58,12 +58,12 @@ class SolveInfo(C.Structure):
 
 
 KERNEL_CLASSES = ["prep", "getrf", "panel", "ssssm", "solve_pull", "resid",
-                  "inv", "solve_diag"]
+                  "inv", "solve_diag", "persistent"]
 
 
 class Stats(C.Structure):
-    _fields_ = [("launches", C.c_int64), ("calls", C.c_int64 * 8),
-                ("ms", C.c_double * 8)]
+    _fields_ = [("launches", C.c_int64), ("calls", C.c_int64 * 9),
+                ("ms", C.c_double * 9)]
 
 
 # every entry point declared in include/slu.h
@@ -73,7 +73,8 @@ EXPORTS = ["slu_opts_default", "slu_analyze", "slu_analyze_batch",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
            "slu_export_factors", "slu_grad_values", "slu_set_profiling", "slu_handle_stats",
            "slu_plan_flops", "slu_handle_trace", "slu_set_graph", "slu_solve_refine_noalloc",
-           "slu_factor_batch",
+           "slu_factor_batch", "slu_select_regular_block",
+           "slu_set_persistent", "slu_persistent_tasks", "slu_set_persistent_tasks",
            "slu_plan_serialize", "slu_plan_deserialize", "slu_plan_digest", "slu_plan_check",
            "slu_plan_destroy",
            "slu_handle_destroy", "slu_last_error"]
@@ -98,6 +99,11 @@ def _load():
     lib.slu_factor.argtypes = [P, P, P, C.POINTER(P), C.POINTER(FactorInfo)]
     lib.slu_refactor.argtypes = [P, P, P, C.POINTER(FactorInfo)]
     lib.slu_factor_batch.argtypes = [C.c_int32, P, P, P, P, C.POINTER(FactorInfo)]
+    lib.slu_set_persistent.argtypes = [P, C.c_int32]
+    lib.slu_persistent_tasks.argtypes = [P, P, C.c_int64, P]
+    lib.slu_set_persistent_tasks.argtypes = [P, P, C.c_int64]
+    lib.slu_select_regular_block.argtypes = [C.c_int64, C.c_int64]
+    lib.slu_select_regular_block.restype = C.c_int32
     lib.slu_solve.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
                               C.POINTER(SolveInfo)]
     lib.slu_solve_transpose.argtypes = [P, P, C.c_int64, C.c_int32, P,
@@ -461,6 +467,24 @@ class Factor:
         """Replay refactor() from a recorded CUDA graph (needs a created
         stream, e.g. inside ``torch.cuda.stream(torch.cuda.Stream())``)."""
         _check(lib.slu_set_graph(self._h, 1 if enable else 0))
+
+    def set_persistent(self, enable=True):
+        """Run refactor()'s level walk as one persistent launch."""
+        _check(lib.slu_set_persistent(self._h, 1 if enable else 0))
+
+    def persistent_tasks(self):
+        """The persistent launch's work list, int32 array (tasks, 5)."""
+        n = np.zeros(1, np.int64)
+        _check(lib.slu_persistent_tasks(self._h, None, 0, _np(n)))
+        out = np.zeros((int(n[0]), 5), np.int32)
+        _check(lib.slu_persistent_tasks(self._h, _np(out), int(n[0]), _np(n)))
+        return out
+
+    def set_persistent_tasks(self, tasks):
+        t = np.ascontiguousarray(tasks, dtype=np.int32)
+        if t.ndim != 2 or t.shape[1] != 5:
+            raise ValueError("expected an int32 array of shape (tasks, 5)")
+        _check(lib.slu_set_persistent_tasks(self._h, _np(t), t.shape[0]))
 
     def set_profiling(self, enable=True):
         _check(lib.slu_set_profiling(self._h, 1 if enable else 0))

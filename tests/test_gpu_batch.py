@@ -126,3 +126,85 @@ def test_factor_batch_rejects_mixed_options():
     with pytest.raises(S.SluError) as ei:
         S.factor_batch(plans, [_dev(m.values) for m in ms])
     assert ei.value.status == 7
+
+
+def _dense_batch_plan(prec, count=12, seed=31, **kw):
+    ms = _batch(count=count, seed=seed)
+    P = S.Plan([m.n for m in ms], [m.colptr for m in ms],
+               [m.rowidx for m in ms], precision=prec, dense_threshold=0.0, **kw)
+    return ms, P, _dev(np.concatenate([m.values for m in ms]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["batch", "single"])
+def test_persistent_launch_equals_per_level_launches(prec, kind):
+    """One persistent launch for the level walk gives the per-level
+    launches' factors bit for bit (batch plan and a single matrix), also
+    replayed from a CUDA graph; the walk is a single kernel launch after
+    the value scatter, and solves work on its factors."""
+    if kind == "batch":
+        _, P, v = _dense_batch_plan(prec)
+    else:
+        s = workloads.grid7_cd(14, nrhs=1)
+        P = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=0.0,
+                   b_min=16)
+        v = _dev(s.values)
+    P.check()
+    F = S.Factor(P, v)
+    ref = F.export_factors()
+    F.set_persistent(True)
+    l0 = F.stats()["launches"]
+    F.refactor(v, sync_info=True)
+    assert F.stats()["launches"] - l0 <= 4          # prep (3) + the walk (1)
+    assert torch.equal(F.export_factors(), ref)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        F.set_graph(True)
+        for _ in range(2):                          # record, then replay
+            F.refactor(v)
+        F.set_graph(False)
+    torch.cuda.synchronize()
+    assert torch.equal(F.export_factors(), ref)
+    b = torch.ones(P.n, dtype=torch.float64, device="cuda")
+    _, info = F.solve(b, info=True)
+    assert info["converged"] and info["backward_error"] <= (
+        1e-13 if prec == "fp64" else 1e-14)
+    F.set_persistent(False)
+    F.refactor(v, sync_info=True)
+    assert torch.equal(F.export_factors(), ref)
+
+
+def test_persistent_launch_needs_dense_blocks():
+    s = workloads.grid5(24)
+    P = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=2.0, b_min=8)
+    F = S.Factor(P, _dev(s.values))
+    with pytest.raises(S.SluError) as ei:
+        F.set_persistent(True)
+    assert ei.value.status == 7
+
+
+def test_persistent_wait_that_cannot_be_met_times_out():
+    """A work list whose dependency count can never be reached (set on the
+    host) makes the bounded device-side waits run out: SLU_ERR_TIMEOUT (6)
+    within the budget, the context stays usable, and with the list
+    restored the factors are right again."""
+    _, P, v = _dense_batch_plan("fp64", count=6, seed=33, wait_budget_ms=200)
+    F = S.Factor(P, v)
+    ref = F.export_factors()
+    F.set_persistent(True)
+    tasks = F.persistent_tasks()
+    assert tasks.shape[0] > 0 and (tasks[:, 2] >= 0).any()
+    bad = tasks.copy()
+    t = int(np.nonzero(bad[:, 2] >= 0)[0][len(bad) // 3 % max(1, (bad[:, 2] >= 0).sum())])
+    bad[t, 3] = 1 << 30                              # a count nothing reaches
+    F.set_persistent_tasks(bad)
+    with pytest.raises(S.SluError) as ei:
+        F.refactor(v, sync_info=True)
+    assert ei.value.status == 6 and "wait_budget_ms" in str(ei.value)
+    F.set_persistent_tasks(tasks)
+    F.refactor(v, sync_info=True)
+    assert torch.equal(F.export_factors(), ref)
+    with pytest.raises(S.SluError):                  # out-of-range entries refused
+        bad2 = tasks.copy()
+        bad2[0, 4] = 1 << 30
+        F.set_persistent_tasks(bad2)

@@ -311,3 +311,58 @@ def test_first_bad_entry_is_reported(threads, monkeypatch):
         with pytest.raises(S.SluError) as e:
             S.Plan(n, cp, ri)
         assert e.value.status == 1 and msg in str(e.value)
+
+
+@pytest.mark.parametrize("n,nnz_lu,expect", [
+    (576, 14_858, 32),          # 25.8 filled entries per column
+    (4_096, 174_226, 32),       # 42.5: last point of the first leaf
+    (4_000, 170_998, 64),       # 42.7: first point of the second leaf
+    (25_600, 1_569_316, 64),    # 61.3
+    (1_000, 93_178, 64),        # 93.2
+    (10_000, 965_846, 32),      # 96.6: third leaf
+    (64_000, 42_558_222, 32),   # 665
+    (20, 400, 20),              # capped by n
+    (0, 0, 1),
+])
+def test_regular_size_selection_tree(n, nnz_lu, expect):
+    """The selection tree's documented splits: filled entries per column
+    <= 42.6 -> 32 rows, <= 95 -> 64, else 32; never more than n."""
+    assert S.lib.slu_select_regular_block(n, nnz_lu) == expect
+
+
+@pytest.mark.parametrize("mk", [lambda: workloads.grid5(48),
+                                lambda: workloads.grid7_cd(12, nrhs=1),
+                                lambda: workloads.circuit_bbd(
+                                    n=3000, border=60, block_lo=16, block_hi=64)])
+def test_regular_select_plan_is_the_regular_plan_of_the_selected_size(mk):
+    """SLU_BLOCKING_REGULAR_SELECT blocks regularly with the tree's size for
+    the filled pattern, and the plan is the oracle's regular plan of that
+    size bit for bit."""
+    s = mk()
+    P = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular_select")
+    b = P.info["regular_block"]
+    assert b == S.lib.slu_select_regular_block(s.n, P.info["nnz_lu"])
+    _check_plan(s, dict(blocking="regular", regular_block=b))
+    R = S.Plan(s.n, s.colptr, s.rowidx, blocking="regular", regular_block=b)
+    assert np.array_equal(P.export()["ptr"], R.export()["ptr"])
+    for k in ("blocks", "bnnz", "dense", "level"):
+        assert np.array_equal(P.export_blocks()[k], R.export_blocks()[k])
+
+
+def test_regular_select_per_batch_member():
+    """In a batch, every member gets the size its own filled pattern
+    selects: a sparse-filling 2-D grid and a dense-filling 3-D operator."""
+    ms = [workloads.grid5(100), workloads.grid7_cd(14, nrhs=1)]
+    PB = S.Plan([m.n for m in ms], [m.colptr for m in ms],
+                [m.rowidx for m in ms], blocking="regular_select")
+    ptr = PB.export()["ptr"]
+    off = 0
+    sizes = []
+    for m in ms:
+        Pm = S.Plan(m.n, m.colptr, m.rowidx, blocking="regular_select")
+        b = Pm.info["regular_block"]
+        sizes.append(b)
+        mine = ptr[(ptr >= off) & (ptr <= off + m.n)] - off
+        assert np.array_equal(mine, OP.regular_ptr(m.n, b))
+        off += m.n
+    assert sizes == [64, 32] and PB.info["regular_block"] == 64
