@@ -263,11 +263,16 @@ def batch_leg(torch, S, dev, args):
     FP64 refinement on 1 RHS each: one batch plan (per-member irregular
     blocking, levels merged, factorization replayed from a CUDA graph)
     against a loop of per-matrix factor + solve calls."""
+    from paper_2512_04389_b300.tune import tune, candidates
     ms = workloads.batch_grid5(count=256, seed=0)
-    PB = S.Plan([m.n for m in ms], [m.colptr for m in ms],
-                [m.rowidx for m in ms], precision="fp32", dense_threshold=0.0)
+    ns, cps, ris = [m.n for m in ms], [m.colptr for m in ms], [m.rowidx for m in ms]
     vb = dev(np.concatenate([m.values for m in ms]))
     bb = dev(np.concatenate([m.rhs[:, 0] for m in ms]))
+    # the irregular and the regular blocking each tuned on the batch plan
+    best_i, _ = tune(ns, cps, ris, vb, bb, precision="fp32")
+    best_r, _ = tune(ns, cps, ris, vb, bb, precision="fp32",
+                     cands=candidates("regular_sizes"))
+    PB = S.Plan(ns, cps, ris, precision="fp32", **best_i)
     FB = S.Factor(PB, vb)
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
@@ -279,10 +284,29 @@ def batch_leg(torch, S, dev, args):
         msb = timed(torch, step_b, args.steps, 2)
         _, ib = FB.solve(bb, info=True)
         FB.set_graph(False)
-    # the same batch with regular 64-row blocking of every member
-    PR = S.Plan([m.n for m in ms], [m.colptr for m in ms],
-                [m.rowidx for m in ms], precision="fp32", dense_threshold=0.0,
-                blocking="regular", regular_block=64)
+    # the level walk of all members as one persistent launch (the tuned
+    # blocking with every block dense, which the persistent kernel needs)
+    pers = dict(best_i, dense_threshold=0.0)
+    PP = S.Plan(ns, cps, ris, precision="fp32", **pers)
+    FP = S.Factor(PP, vb)
+    with torch.cuda.stream(st):
+        FP.set_graph(True)
+
+        def step_pl():
+            FP.refactor(vb)
+            FP.solve(bb)
+        msp_levels = timed(torch, step_pl, args.steps, 2)
+        FP.set_persistent(True)
+        l0 = FP.stats()["launches"]
+        FP.refactor(vb)
+        torch.cuda.synchronize()
+        pl_launches = FP.stats()["launches"] - l0
+        msp = timed(torch, step_pl, args.steps, 2)
+        FP.set_graph(False)
+    FP.set_persistent(False)
+    del FP, PP
+    # the same batch with the tuned regular blocking of every member
+    PR = S.Plan(ns, cps, ris, precision="fp32", **best_r)
     FR = S.Factor(PR, vb)
     with torch.cuda.stream(st):
         FR.set_graph(True)
@@ -306,8 +330,8 @@ def batch_leg(torch, S, dev, args):
         mss = timed(torch, step_s, args.steps, 2)
         FS.set_graph(False)
     del FS, PS
-    plans = [S.Plan(m.n, m.colptr, m.rowidx, precision="fp32",
-                    dense_threshold=0.0) for m in ms]
+    plans = [S.Plan(m.n, m.colptr, m.rowidx, precision="fp32", **best_i)
+             for m in ms]
     vs = [dev(m.values) for m in ms]
     rs = [dev(m.rhs[:, 0]) for m in ms]
     fs = [S.Factor(p, v) for p, v in zip(plans, vs)]
@@ -320,7 +344,11 @@ def batch_leg(torch, S, dev, args):
     fl = sum(p.info["flops"] + 2 * p.info["nnz_lu"] for p in plans)
     return {"ms_per_step": msb, "gflops": fl / (msb * 1e-3) / 1e9,
             "loop_ms_per_step": msl, "speedup_vs_loop": msl / msb,
-            "regular64_graph_ms_per_step": msr, "irregular_speedup": msr / msb,
+            "tuned": best_i, "regular_tuned": best_r,
+            "persistent": {"options": pers, "graph_ms_per_step": msp,
+                           "per_level_graph_ms_per_step": msp_levels,
+                           "factor_launches": pl_launches},
+            "regular_tuned_graph_ms_per_step": msr, "irregular_speedup": msr / msb,
             "regular_select_graph_ms_per_step": mss,
             "backward_error_max_member": ib["backward_error"],
             "ir_iterations": ib["iterations"], "levels": PB.info["nlevels"],
@@ -414,12 +442,15 @@ def autograd_leg(torch, S, dev, args):
     FP64: forward solve plus backward (transposed solve through the stored
     factors and the gradient gather), loss 1/2 ||x||^2."""
     from paper_2512_04389_b300.autograd import lu_solve
+    from paper_2512_04389_b300.tune import tune, candidates
     s = workloads.grid7_theta(32)
-    P = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=0.0)
     v0, b0 = dev(s.values), dev(s.rhs[:, 0])
+    best_i, _ = tune(s.n, s.colptr, s.rowidx, v0, b0, precision="fp64")
+    best_r, _ = tune(s.n, s.colptr, s.rowidx, v0, b0, precision="fp64",
+                     cands=candidates("regular_sizes", s.n))
+    P = S.Plan(s.n, s.colptr, s.rowidx, **best_i)
 
-    PR = S.Plan(s.n, s.colptr, s.rowidx, dense_threshold=0.0,
-                blocking="regular", regular_block=128)
+    PR = S.Plan(s.n, s.colptr, s.rowidx, **best_r)
 
     def run(plan):
         def step():
@@ -434,7 +465,8 @@ def autograd_leg(torch, S, dev, args):
     msr = run(PR)
     mss = run(PSel)
     return {"ms_per_step": ms, "n": s.n, "nnz_a": s.nnz,
-            "regular128_ms_per_step": msr, "irregular_speedup": msr / ms,
+            "tuned": best_i, "regular_tuned": best_r,
+            "regular_tuned_ms_per_step": msr, "irregular_speedup": msr / ms,
             "regular_select_ms_per_step": mss,
             "regular_select_block": PSel.info["regular_block"],
             "what": "factor + solve forward, transposed solve + gradient gather backward"}

@@ -101,6 +101,11 @@ typedef struct {
     int64_t wait_budget_ms;      /* bound of every dependency wait of the
                                     persistent launch (slu_set_persistent),
                                     ms; <= 0 means 2000                     */
+    int32_t tc_passes;           /* FP32 dense Schur tiles on the tensor
+                                    cores: 3 = split precision 3xTF32 (the
+                                    products keep FP32 accuracy), 1 = one
+                                    TF32 pass with FP32 accumulation
+                                    (refinement recovers the accuracy)      */
 } slu_opts;
 
 typedef struct {
@@ -201,6 +206,57 @@ slu_status slu_analyze_batch(int32_t count, const int64_t *n,
                              const slu_opts *opts, slu_plan **out);
 
 slu_status slu_plan_query(const slu_plan *plan, slu_plan_info *info);
+
+/* General-matrix front end (host; the paper's inputs arrive reordered and
+ * its solvers pivot statically, Sections 1 and 2.1).  slu_reorder computes
+ * for an n x n matrix (CSC, host; rows within a column in any order):
+ *   SLU_REORDER_SCALE: a maximum-product transversal -- the row matched to
+ *     each column so that the product of the matched |a_ij| is largest, by
+ *     shortest augmenting paths on the costs log(max_i |a_ij|) - log |a_ij|
+ *     -- and, from its optimal duals, row and column scales under which
+ *     every matched entry has magnitude 1 and no entry exceeds 1 (MC64's
+ *     option 5 objective and scaling); needs values;
+ *   SLU_REORDER_ORDER: a fill-reducing symmetric ordering, nested dissection
+ *     of the graph of B + B^T (B: A with the matched entries, or A's own
+ *     diagonal without SCALE, on the diagonal) by recursive bisection at the
+ *     middle level of a breadth-first level structure from a pseudo-
+ *     peripheral node; separators after the parts they split; parts of at
+ *     most `leaf` nodes keep their order.
+ * Outputs (host, n each): rowperm, colperm with the reordered matrix
+ *   R(k, l) = rowscale[rowperm[k]] * A(rowperm[k], colperm[l]) * colscale[colperm[l]],
+ * whose diagonal holds the matched entries; rowscale, colscale may be NULL
+ * (all ones without SCALE).  A x = b is then R y = b' with
+ * b'[k] = rowscale[rowperm[k]] b[rowperm[k]] and x[colperm[l]] =
+ * colscale[colperm[l]] y[l] (slu_permute_scale).  Errors: SLU_ERR_SINGULAR
+ * when A is structurally singular (no perfect matching, or an empty
+ * column), SLU_ERR_INVALID_ARG for a bad pattern or flags, NaN or infinite
+ * values. */
+#define SLU_REORDER_SCALE 1
+#define SLU_REORDER_ORDER 2
+slu_status slu_reorder(int64_t n, const int64_t *colptr, const int32_t *rowidx,
+                       const double *values, int32_t flags, int32_t leaf,
+                       int32_t *rowperm, int32_t *colperm, double *rowscale,
+                       double *colscale);
+
+/* R in CSC (rows sorted) from A and slu_reorder's outputs (host): out_colptr
+ * int64[n+1], out_rowidx int32[nnz], out_values double[nnz] (may be NULL;
+ * values may then be NULL).  rowscale / colscale NULL mean ones.
+ * SLU_ERR_INVALID_ARG when rowperm or colperm is not a permutation. */
+slu_status slu_reorder_apply(int64_t n, const int64_t *colptr, const int32_t *rowidx,
+                             const double *values, const int32_t *rowperm,
+                             const int32_t *colperm, const double *rowscale,
+                             const double *colscale, int64_t *out_colptr,
+                             int32_t *out_rowidx, double *out_values);
+
+/* Device gather / scatter with scaling for the reordered system (all
+ * device memory, column-major n x nrhs): inverse = 0:
+ *   Y(k, c) = scale[perm[k]] X(perm[k], c)     (b' from b, with rowperm, rowscale)
+ * inverse = 1:
+ *   Y(perm[k], c) = scale[perm[k]] X(k, c)     (x from y, with colperm, colscale)
+ * scale may be NULL (ones); X and Y must not overlap. */
+slu_status slu_permute_scale(int64_t n, int32_t nrhs, const int32_t *perm,
+                             const double *scale, const double *X, int64_t ldx,
+                             double *Y, int64_t ldy, int32_t inverse, void *stream);
 
 /* Regular-size selection policy (SLU_BLOCKING_REGULAR_SELECT).  PanguLU,
  * the regular-blocking solver the paper compares against, picks its block
@@ -345,11 +401,14 @@ slu_status slu_export_factors(const slu_handle *h, double *out, void *stream);
  * no counterpart in the paper's A100 design, which launches per task).
  * When enabled, slu_refactor runs every level of every matrix of the plan
  * (many members for a slu_analyze_batch plan) in ONE kernel launch after
- * the value scatter: one CTA per SM takes tasks in the order of a work list
- * built on the host -- per level the GETRF, inverse, panel and Schur-tile
- * tasks of all members, in that phase order -- and before each task waits
- * until the tasks of the same member's previous non-empty phase are done
- * (device-side counters, acquire/release at GPU scope).  Tickets are taken
+ * the value scatter: persistent CTAs (one per SM for FP64, two for FP32)
+ * take tasks in the order of a work list built on the host -- per level the
+ * GETRF, inverse, panel and Schur-tile tasks of all members, in that phase
+ * order, the Schur tiles split into those the next level reads and the
+ * deferred rest -- and before each task wait until the member's tasks it
+ * depends on are done (device-side counters, acquire/release at GPU scope:
+ * the previous phase of the member's chain, and the deferred tiles that may
+ * touch the task's blocks).  Tickets are taken
  * in list order, so a CTA only waits for tasks that running CTAs hold.
  * Each wait is bounded by opts.wait_budget_ms; one that runs out stops the
  * launch and the next synchronizing call reports SLU_ERR_TIMEOUT (the
@@ -360,16 +419,18 @@ slu_status slu_export_factors(const slu_handle *h, double *out, void *stream);
  * and blocks of at most 384 rows), else SLU_ERR_NOT_SUPPORTED. */
 slu_status slu_set_persistent(slu_handle *h, int32_t enable);
 
-/* The persistent launch's work list, 5 int32 per task in ticket order:
- * kind (0 GETRF, 1 inverse, 2 panel, 3 Schur tile), index into that kind's
- * task list of the plan, the counter waited for (-1: none), the count it
- * must reach, and the counter the task increments when done; counter
- * ((member * nlevels) + level) * 4 + phase counts the finished tasks of
- * that member, level and phase.  slu_persistent_tasks copies min(cap, count) tasks
+/* The persistent launch's work list, 7 int32 per task in ticket order:
+ * kind (0 GETRF, 1 inverse, 2 panel, 3 Schur tile read by the next level,
+ * 4 deferred Schur tile), index into that kind's task list of the plan, two
+ * (counter, count) waits (counter -1: none), and the counter the task
+ * increments when done; counter ((member * nlevels) + level) * 5 + kind
+ * counts the finished tasks of that member, level and kind.
+ * slu_persistent_tasks copies min(cap, count) tasks
  * into tasks (host) and the count into *count (the list is built by
  * slu_set_persistent).  slu_set_persistent_tasks replaces the list with
- * `count` tasks from host memory after checking that every kind, index and
- * counter is in range (SLU_ERR_INVALID_ARG otherwise); it does not check
+ * `count` tasks (at most the built list's length) from host memory after
+ * checking that every kind, index and counter is in range
+ * (SLU_ERR_INVALID_ARG otherwise); it does not check
  * that the waits can be met -- a wait that cannot is stopped by the bound
  * above. */
 slu_status slu_persistent_tasks(const slu_handle *h, int32_t *tasks, int64_t cap,

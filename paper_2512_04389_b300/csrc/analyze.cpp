@@ -387,6 +387,7 @@ extern "C" void slu_opts_default(slu_opts *o) {
     o->refine_tol = 1e-14;
     o->refine_max_iter = 0;
     o->wait_budget_ms = 2000;
+    o->tc_passes = 3;
 }
 
 extern "C" const char *slu_last_error(void) { return g_err.c_str(); }
@@ -1032,6 +1033,8 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         return fail(SLU_ERR_INVALID_ARG, "bad blocking parameters");
     if (o.precision != SLU_PREC_FP64 && o.precision != SLU_PREC_FP32)
         return fail(SLU_ERR_INVALID_ARG, "unknown precision");
+    if (o.tc_passes != 1 && o.tc_passes != 3)
+        return fail(SLU_ERR_INVALID_ARG, "tc_passes must be 1 or 3");
     if (!(o.dense_threshold >= 0.0))
         return fail(SLU_ERR_INVALID_ARG, "dense_threshold must be >= 0");
     if (colptr[0] != 0) return fail(SLU_ERR_INVALID_ARG, "colptr[0] must be 0");

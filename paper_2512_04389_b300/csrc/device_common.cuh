@@ -274,7 +274,7 @@ struct slu_handle {
     bool persistent = false;
     int32_t *ptasks = nullptr;
     int *pdone = nullptr;               // pcounters counters, then the ticket
-    int64_t pntasks = 0, pcounters = 0;
+    int64_t pntasks = 0, pcap = 0, pcounters = 0;
 };
 
 namespace slu {

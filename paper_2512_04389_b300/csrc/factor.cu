@@ -1077,13 +1077,66 @@ __device__ __forceinline__ void inv_body(const int32_t *tk, const BlockDesc *bd,
     for (int r = lane; r < b; r += 32) out[r] = x[r];
 }
 
+// FP32 inverses: the same column solves with x held in registers and every
+// 32-row chunk updated at every step.  FP32 FMAs are cheap on B300 (64x the
+// FP64 rate), so the masks of the FP64 body would only lengthen the chain.
+template <typename T>
+__device__ __forceinline__ void inv_body_reg(const int32_t *tk, const BlockDesc *bd,
+                                             const T *val, T *winv, const int64_t *woff) {
+    const BlockDesc d = bd[tk[0]];
+    const int which = tk[1], b = d.rows;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = tk[2] + warp;
+    if (j >= b) return;
+    const T *F = val + d.voff;           // dense LU, ld = b
+    T x[kInvRows];
+#pragma unroll
+    for (int q = 0; q < kInvRows; ++q) x[q] = (q * 32 + lane == j) ? T(1) : T(0);
+    if (which == 0) {
+        for (int mm = j; mm < b; ++mm) {
+            const T xm = __shfl_sync(~0u, x[(mm >> 5) % kInvRows], mm & 31);
+            if (xm == T(0)) continue;
+            const T *Lc = F + (int64_t)mm * b;
+#pragma unroll
+            for (int q = 0; q < kInvRows; ++q) {
+                const int r = q * 32 + lane;
+                if (r > mm && r < b) x[q] -= Lc[r] * xm;
+            }
+        }
+    } else {
+        for (int mm = j; mm >= 0; --mm) {
+            const T *Uc = F + (int64_t)mm * b;
+            const T own = __shfl_sync(~0u, x[(mm >> 5) % kInvRows], mm & 31);
+            const T xm = own / Uc[mm];
+#pragma unroll
+            for (int q = 0; q < kInvRows; ++q)
+                if (q * 32 + lane == mm) x[q] = xm;
+            if (xm == T(0)) continue;
+#pragma unroll
+            for (int q = 0; q < kInvRows; ++q) {
+                const int r = q * 32 + lane;
+                if (r < mm) x[q] -= Uc[r] * xm;
+            }
+        }
+    }
+    T *out = winv + woff[d.I] + (which ? (int64_t)b * b : 0) + (int64_t)j * b;
+#pragma unroll
+    for (int q = 0; q < kInvRows; ++q) {
+        const int r = q * 32 + lane;
+        if (r < b) out[r] = x[q];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
       const T *__restrict__ val, T *__restrict__ winv,
       const int64_t *__restrict__ woff) {
     extern __shared__ __align__(16) unsigned char smem[];
-    inv_body<T>(task + 3 * (int64_t)blockIdx.x, bd, val, winv, woff, smem);
+    if constexpr (sizeof(T) == 4)
+        inv_body_reg<T>(task + 3 * (int64_t)blockIdx.x, bd, val, winv, woff);
+    else
+        inv_body<T>(task + 3 * (int64_t)blockIdx.x, bd, val, winv, woff, smem);
 }
 
 // Column-pair masks of a staged 16 x 64 slice S (S[kk * 64 + c]): bit kk of
@@ -1261,13 +1314,160 @@ __device__ __forceinline__ void panel_inv_body(const int32_t *tk, const BlockDes
     }
 }
 
+// FP32 panels through the inverses: the dense 64 x 64 register tiles (4 x 4
+// per thread) over the inverse's triangle, every product executed (FP32
+// FMAs are cheap; the masked FP64 body's bookkeeping would dominate).
+template <typename T>
+__device__ __forceinline__ void panel_inv_dense_body(const int32_t *tk, const BlockDesc *bd,
+                                                     T *val, const T *winv,
+                                                     const int64_t *woff, const BlockArgs &a,
+                                                     unsigned char *smem) {
+    constexpr int KT = 16;
+    const int type = tk[0];
+    const BlockDesc d = bd[tk[1]];
+    const BlockDesc dd = bd[tk[2]];
+    const int c0 = tk[3], m = dd.rows, tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    T *X = reinterpret_cast<T *>(smem);                 // m x 64 chunk, X[k * 64 + c]
+    T *Ts = X + (size_t)m * 64;                          // 16 x 64 inverse slice
+    const int64_t ld = d.ld;
+    T *Bg = val + d.voff;
+    const T *Inv = winv + woff[dd.I] + (type == 0 ? 0 : (int64_t)m * m);
+    const int nv = min(64, (type == 0 ? d.cols : d.rows) - c0);
+    // stage the chunk: GESSM columns c0.. (X[k][c] = B(k, c0 + c));
+    // TSTRF rows c0.. (X[k][r] = B(c0 + r, k)); flag the 16-deep k-slices
+    // of the chunk that hold a nonzero (all-zero slices contribute nothing)
+    // and, per k, whether row k of the chunk holds one (the warps staging a
+    // row ballot; m * 64 is a whole number of warps)
+    int *zrow = reinterpret_cast<int *>(Ts + KT * 64);
+    int *zflag = zrow + m;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (d.dense) {
+        for (int e = tid; e < m + (m + KT - 1) / KT; e += 256) zrow[e] = 0;
+        __syncthreads();
+        for (int e = tid; e < m * 64; e += 256) {
+            const int k = e / 64, c = e % 64;
+            T v = T(0);
+            if (c < nv)
+                v = type == 0 ? Bg[(int64_t)(c0 + c) * ld + k] : Bg[(int64_t)k * ld + c0 + c];
+            X[e] = v;
+            if (sizeof(T) == 8 && __ballot_sync(0xffffffffu, v != T(0)) && lane == 0) {
+                atomicOr(&zrow[k], 1);
+                atomicOr(&zflag[k / KT], 1);
+            }
+        }
+    } else {
+        // sparse panel block: scatter its pattern into the zeroed chunk (no
+        // zero-row skipping: every row is flagged)
+        for (int e = tid; e < m + (m + KT - 1) / KT; e += 256) zrow[e] = 1;
+        for (int e = tid; e < m * 64; e += 256) X[e] = T(0);
+        __syncthreads();
+        if (type == 0) {                 // columns c0 + c of B_IJ, rows k
+            for (int c = warp; c < nv; c += 8) {
+                int64_t vb;
+                int cn;
+                const uint16_t *rw;
+                colview(d, c0 + c, a, vb, cn, rw);
+                for (int e = lane; e < cn; e += 32) X[rw[e] * 64 + c] = val[vb + e];
+            }
+        } else {                         // rows c0 .. c0 + nv of B_JI, columns k
+            for (int k = warp; k < m; k += 8) {
+                int64_t vb;
+                int cn;
+                const uint16_t *rw;
+                colview(d, k, a, vb, cn, rw);
+                for (int e = lane; e < cn; e += 32) {
+                    const int r = rw[e] - c0;
+                    if (r >= 0 && r < nv) X[k * 64 + r] = val[vb + e];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int ob = 0; ob < m; ob += 64) {       // output chunk along m
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jx = 0; jx < 4; ++jx) acc[i][jx] = T(0);
+        // GESSM: out(i, c) = sum_{k <= i} Linv(i, k) X(k, c), i in [ob, ob+64)
+        // TSTRF: out(r, i) = sum_{k <= i} X(r, k) Uinv(k, i), i in [ob, ob+64)
+        const int kend = min(m, ob + 64);
+        for (int k0 = 0; k0 < kend; k0 += KT) {
+            if (sizeof(T) == 8 && !zflag[k0 / KT]) continue;  // uniform across the CTA
+            for (int e = tid; e < KT * 64; e += 256) {
+                int kk, ii;
+                T v = T(0);
+                if (type == 0) {               // Ts[kk][ii] = Linv(ob + ii, k0 + kk)
+                    ii = e % 64; kk = e / 64;
+                    const int gi = ob + ii, gk = k0 + kk;
+                    if (gi < m && gk < m) v = Inv[(int64_t)gk * m + gi];
+                } else {                       // Ts[kk][ii] = Uinv(k0 + kk, ob + ii)
+                    kk = e % KT; ii = e / KT;
+                    const int gi = ob + ii, gk = k0 + kk;
+                    if (gi < m && gk < m) v = Inv[(int64_t)gi * m + gk];
+                }
+                Ts[kk * 64 + ii] = v;
+            }
+            __syncthreads();
+            const int kn = min(KT, m - k0);
+            for (int kk = 0; kk < kn; ++kk) {
+                if (sizeof(T) == 8 && !zrow[k0 + kk]) continue;
+                T a[4], bv[4];
+                if (type == 0) {               // rows of out = ob + ty*4+i, cols = tx*4+jx
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] = Ts[kk * 64 + ty * 4 + i];
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx) bv[jx] = X[(k0 + kk) * 64 + tx * 4 + jx];
+                } else {                       // rows = chunk rows ty*4+i, cols = ob + tx*4+jx
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] = X[(k0 + kk) * 64 + ty * 4 + i];
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx) bv[jx] = Ts[kk * 64 + tx * 4 + jx];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx) acc[i][jx] += a[i] * bv[jx];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jx = 0; jx < 4; ++jx) {
+                // (row, column) of the panel block; a sparse block keeps only
+                // its pattern (the result is zero elsewhere)
+                int br, bc;
+                if (type == 0) { br = ob + ty * 4 + i; bc = c0 + tx * 4 + jx; }
+                else           { br = c0 + ty * 4 + i; bc = ob + tx * 4 + jx; }
+                const bool in = type == 0 ? (br < m && bc - c0 < nv)
+                                          : (br - c0 < nv && bc < m);
+                if (!in) continue;
+                if (d.dense) {
+                    Bg[(int64_t)bc * ld + br] = acc[i][jx];
+                } else {
+                    int64_t vb;
+                    int cn;
+                    const uint16_t *rw;
+                    colview(d, bc, a, vb, cn, rw);
+                    const int q = find_row(rw, cn, br);
+                    if (q >= 0) val[vb + q] = acc[i][jx];
+                }
+            }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_panel_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
             T *__restrict__ val, const T *__restrict__ winv,
             const int64_t *__restrict__ woff, BlockArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    panel_inv_body<T>(task + 4 * (int64_t)blockIdx.x, bd, val, winv, woff, a, smem);
+    if constexpr (sizeof(T) == 4)
+        panel_inv_dense_body<T>(task + 4 * (int64_t)blockIdx.x, bd, val, winv, woff, a, smem);
+    else
+        panel_inv_body<T>(task + 4 * (int64_t)blockIdx.x, bd, val, winv, woff, a, smem);
 }
 
 // SSSSM: target B_KJ -= sum over the level's sources I of L_KI U_IJ.
@@ -1421,7 +1621,7 @@ __device__ __forceinline__ void tc_body(const int32_t *tk, const int32_t *src,
                                         const BlockDesc *bd, float *val,
                                         unsigned long long *err, unsigned char *smem,
                                         uint64_t *mbar, uint32_t tmem,
-                                        uint32_t (&phase)[2]) {
+                                        uint32_t (&phase)[2], int passes) {
     using namespace tc;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const BlockDesc d = bd[tk[0]];
@@ -1454,24 +1654,34 @@ __device__ __forceinline__ void tc_body(const int32_t *tk, const int32_t *src,
             rb[j] = (gk < K && gc < d.cols) ? Bm[(int64_t)gc * U.ld + gk] : 0.f;
         }
     };
+    // three passes: hi and lo parts; one pass: the FP32 values as they are
+    // (the TF32 MMA reads their upper 19 bits)
     auto store = [&](unsigned char *base) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int q = warp + 8 * j;
-            float hi, lo;
-            split(ra[j], hi, lo);
             const uint32_t o = kmaj(8 * (q & 15) + lr, 4 * (q >> 4) + lk);
-            *reinterpret_cast<float *>(base + o) = hi;
-            *reinterpret_cast<float *>(base + A_BYTES + o) = lo;
+            if (passes == 3) {
+                float hi, lo;
+                split(ra[j], hi, lo);
+                *reinterpret_cast<float *>(base + o) = hi;
+                *reinterpret_cast<float *>(base + A_BYTES + o) = lo;
+            } else {
+                *reinterpret_cast<float *>(base + o) = ra[j];
+            }
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int q = warp + 8 * j;
-            float hi, lo;
-            split(rb[j], hi, lo);
             const uint32_t o = kmaj(8 * (q & 7) + lr, 4 * (q >> 3) + lk);
-            *reinterpret_cast<float *>(base + 2 * A_BYTES + o) = hi;
-            *reinterpret_cast<float *>(base + 2 * A_BYTES + B_BYTES + o) = lo;
+            if (passes == 3) {
+                float hi, lo;
+                split(rb[j], hi, lo);
+                *reinterpret_cast<float *>(base + 2 * A_BYTES + o) = hi;
+                *reinterpret_cast<float *>(base + 2 * A_BYTES + B_BYTES + o) = lo;
+            } else {
+                *reinterpret_cast<float *>(base + 2 * A_BYTES + o) = rb[j];
+            }
         }
     };
     int s = s0, k0 = 0;
@@ -1504,8 +1714,7 @@ __device__ __forceinline__ void tc_body(const int32_t *tk, const int32_t *src,
             for (int kk = 0; kk < KC / 8; ++kk) {
                 const uint32_t off = kk * 2 * LBO;
                 const uint32_t pa[3] = {a_hi, a_hi, a_lo}, pb[3] = {b_hi, b_lo, b_hi};
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
+                for (int t = 0; t < passes; ++t) {
                     const uint32_t acc = (chunk > 0 || kk > 0 || t > 0) ? 1u : 0u;
                     asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
                                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
@@ -1595,7 +1804,7 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
 __global__ void __launch_bounds__(256)
 k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
            const BlockDesc *__restrict__ bd, float *__restrict__ val,
-           unsigned long long *__restrict__ err) {
+           unsigned long long *__restrict__ err, int passes) {
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -1606,7 +1815,7 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
     if (tk[1] >= tk[2]) return;
     const uint32_t tmem = tc_setup(mbar, &tmem_holder);
     uint32_t phase[2] = {0, 0};
-    tc_body(tk, src, bd, val, err, smem, mbar, tmem, phase);
+    tc_body(tk, src, bd, val, err, smem, mbar, tmem, phase, passes);
     tc_teardown(tmem);
 }
 
@@ -1758,18 +1967,24 @@ k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
 }
 
 // ------------------------------------------------------------ persistent
-// The whole level walk in one launch (see slu_set_persistent): one CTA per
-// SM takes tickets in the order of a work list that lists, level by level,
-// the GETRF, inverse, panel and Schur-tile tasks of every member of the
-// plan.  A task waits (thread 0, acquire at GPU scope, bounded) until the
-// counter of its member's previous non-empty phase reaches that phase's
-// task count, runs the same body as the per-level kernel, and increments
-// its own counter (barrier, fence, atomic).  Every ticket a CTA waits on was
+// The whole level walk in one launch (see slu_set_persistent): persistent
+// CTAs (one per SM for FP64, two for FP32) take tickets in the order of a
+// work list that lists, level by level, the GETRF, inverse, panel and
+// Schur-tile tasks of every member of the plan, the Schur tiles split as in
+// the per-level walk into those the next level reads and the deferred
+// rest.  A task waits (thread 0, acquire at GPU scope, bounded) until two
+// counters of its member reach their phases' task counts, runs the same
+// body as the per-level kernel, and increments its own counter (barrier,
+// fence, atomic).  Every ticket a CTA waits on was
 // taken earlier by a CTA that is running, so the walk cannot deadlock; a
 // wait that runs out sets bit 1 of cnt[2] and the CTA leaves (the others
 // then run out too).  FP32 CTAs hold 64 TMEM columns for the tensor-core
 // tiles from start to end.
-enum : int32_t { kPtGetrf = 0, kPtInv = 1, kPtPanel = 2, kPtSchur = 3 };
+enum : int32_t { kPtGetrf = 0, kPtInv = 1, kPtPanel = 2, kPtSchur = 3, kPtSchurLate = 4 };
+constexpr int kPtInts = 7;   // kind, idx, wait1, need1, wait2, need2, done
+// Dynamic shared memory of a persistent CTA (plus 1 KB for alignment).
+template <typename T>
+__host__ __device__ constexpr size_t persist_smem() { return sizeof(T) == 4 ? 108 * 1024 : kStageSmem; }
 
 __device__ __forceinline__ long long global_ns() {
     long long t;
@@ -1791,7 +2006,7 @@ __device__ __forceinline__ bool wait_count(const int *c, int need, long long bud
 }
 
 struct PersistArgs {
-    const int32_t *tasks;               // 5 per task
+    const int32_t *tasks;               // kPtInts per task
     int ntasks;
     int *done;                          // counters
     int *ticket;
@@ -1803,10 +2018,11 @@ struct PersistArgs {
     double tau_rel;
     unsigned long long *cnt;
     long long budget_ns;
+    int tc_passes;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 k_factor_persistent(PersistArgs p, T *val, T *winv) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -1824,8 +2040,9 @@ k_factor_persistent(PersistArgs p, T *val, T *winv) {
             const int t = atomicAdd(p.ticket, 1);
             int stop = t >= p.ntasks;
             if (!stop) {
-                const int32_t *pt = p.tasks + 5 * (int64_t)t;
-                if (pt[2] >= 0 && !wait_count(p.done + pt[2], pt[3], p.budget_ns)) {
+                const int32_t *pt = p.tasks + kPtInts * (int64_t)t;
+                if ((pt[2] >= 0 && !wait_count(p.done + pt[2], pt[3], p.budget_ns)) ||
+                    (pt[4] >= 0 && !wait_count(p.done + pt[4], pt[5], p.budget_ns))) {
                     atomicOr(&p.cnt[2], 2ull);
                     stop = 1;
                 }
@@ -1835,19 +2052,28 @@ k_factor_persistent(PersistArgs p, T *val, T *winv) {
         }
         __syncthreads();
         if (s_stop) break;                              // uniform
-        const int32_t *pt = p.tasks + 5 * (int64_t)s_t;
+        const int32_t *pt = p.tasks + kPtInts * (int64_t)s_t;
         const int kind = pt[0], idx = pt[1];
         if (kind == kPtGetrf) {
             const BlockDesc d = p.bd[p.gd[idx]];
-            getrf_dense<T>(val + d.voff, d.rows, d.ld, tau, p.cnt, smem, kStageSmem);
+            getrf_dense<T>(val + d.voff, d.rows, d.ld, tau, p.cnt, smem, persist_smem<T>());
         } else if (kind == kPtInv) {
-            inv_body<T>(p.inv_task + 3 * (int64_t)idx, p.bd, val, winv, p.woff, smem);
+            if constexpr (sizeof(T) == 4)
+                inv_body_reg<T>(p.inv_task + 3 * (int64_t)idx, p.bd, val, winv, p.woff);
+            else
+                inv_body<T>(p.inv_task + 3 * (int64_t)idx, p.bd, val, winv, p.woff, smem);
         } else if (kind == kPtPanel) {
-            panel_inv_body<T>(p.pd_task + 4 * (int64_t)idx, p.bd, val, winv, p.woff, p.a, smem);
+            if constexpr (sizeof(T) == 4)
+                panel_inv_dense_body<T>(p.pd_task + 4 * (int64_t)idx, p.bd, val, winv,
+                                        p.woff, p.a, smem);
+            else
+                panel_inv_body<T>(p.pd_task + 4 * (int64_t)idx, p.bd, val, winv, p.woff,
+                                  p.a, smem);
         } else {
             if constexpr (sizeof(T) == 4)
                 tc_body(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd,
-                        reinterpret_cast<float *>(val), p.cnt + 2, smem, mbar, tmem, phase);
+                        reinterpret_cast<float *>(val), p.cnt + 2, smem, mbar, tmem, phase,
+                        p.tc_passes);
             else
                 gemm_body<T>(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd, val,
                              *reinterpret_cast<GemmSmem<T> *>(smem));
@@ -1855,7 +2081,7 @@ k_factor_persistent(PersistArgs p, T *val, T *winv) {
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            atomicAdd(p.done + pt[4], 1);
+            atomicAdd(p.done + pt[6], 1);
         }
     }
     if (sizeof(T) == 4) tc_teardown(tmem);
@@ -1982,7 +2208,7 @@ static slu_status set_smem_limits(size_t generic) {
               cuda_ok(cudaFuncSetAttribute(k_panel_vec<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_ssssm_tc, attr, (int)tc::SMEM), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_factor_persistent<T>, attr,
-                                           (int)(kStageSmem + 1024)), "smem");
+                                           (int)(persist_smem<T>() + 1024)), "smem");
     if (ok)
         ok = cuda_ok(cudaFuncSetAttribute(k_ssssm<T, Acc>, attr, (int)kStageSmem), "smem");
     return ok ? SLU_OK : SLU_ERR_CUDA;
@@ -2042,13 +2268,15 @@ static slu_status run_factor(slu_handle *h, const double *values,
             return SLU_ERR_CUDA;
         int nsm = 148;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+        nsm *= sizeof(T) == 4 ? 2 : 1;       // resident CTAs per SM
         const int64_t budget_ms = P->opts.wait_budget_ms > 0 ? P->opts.wait_budget_ms : 2000;
         PersistArgs pa{h->ptasks, (int)h->pntasks, h->pdone, h->pdone + h->pcounters,
                        D->gd, D->inv_task, D->pd_task, D->gm_task, D->gm_src, D->bd, a,
-                       D->woff, h->scal, h->tau_rel, h->cnt, budget_ms * 1000000ll};
+                       D->woff, h->scal, h->tau_rel, h->cnt, budget_ms * 1000000ll,
+                       P->opts.tc_passes};
         {
             LaunchScope ls_(h, SLU_KC_PERSIST, st, nsm);
-            k_factor_persistent<T><<<nsm, 256, kStageSmem + 1024, st>>>(
+            k_factor_persistent<T><<<nsm, 256, persist_smem<T>() + 1024, st>>>(
                 pa, val, static_cast<T *>(h->winv));
         }
         return cuda_ok(cudaGetLastError(), "persistent launch") ? SLU_OK : SLU_ERR_CUDA;
@@ -2125,7 +2353,7 @@ static slu_status run_factor(slu_handle *h, const double *values,
                 if (sizeof(T) == 4)
                     k_ssssm_tc<<<(int)(mb - ma), 256, tc::SMEM, ss>>>(
                         D->gm_task + 5 * ma, D->gm_src, D->bd,
-                        reinterpret_cast<float *>(val), h->cnt + 2);
+                        reinterpret_cast<float *>(val), h->cnt + 2, P->opts.tc_passes);
                 else
                     k_ssssm_gemm<T><<<(int)(mb - ma), 256, 0, ss>>>(
                         D->gm_task + 5 * ma, D->gm_src, D->bd, val);
@@ -2306,7 +2534,7 @@ static bool same_opts(const slu_opts &a, const slu_opts &b) {
            a.precision == b.precision && a.dense_threshold == b.dense_threshold &&
            a.pivot_perturb == b.pivot_perturb && a.pivot_tau_rel == b.pivot_tau_rel &&
            a.refine_tol == b.refine_tol && a.refine_max_iter == b.refine_max_iter &&
-           a.wait_budget_ms == b.wait_budget_ms;
+           a.wait_budget_ms == b.wait_budget_ms && a.tc_passes == b.tc_passes;
 }
 
 // Where member q of batch plan M lives, checked against the member's own
@@ -2529,7 +2757,14 @@ extern "C" slu_status slu_set_graph(slu_handle *h, int32_t enable) {
     return SLU_OK;
 }
 
-// Work list of the persistent launch (5 ints per task; see the header).
+// Work list of the persistent launch (kPtInts per task; see the header).
+// Phases per level: 0 GETRF, 1 inverses, 2 panels, 3 Schur tiles the next
+// level reads, 4 the deferred Schur tiles.  For member q, counter
+// ((q L) + level) 5 + phase counts finished tasks.  The main chain 0 -> 1 ->
+// 2 -> 3 -> next level's 0 is wait 1; wait 2 orders the deferred tiles: a
+// level's GETRF, inverse and panel tasks wait for the deferred tiles of two
+// levels back (which may target their blocks), its Schur tiles for those of
+// the level before (every target receives its updates in level order).
 static slu_status build_persistent(const slu_plan *P, std::vector<int32_t> &tasks,
                                    int64_t *ncounters) {
     if (!P->gs.empty() || !P->pg_gessm.empty() || !P->pg_tstrf.empty() ||
@@ -2537,13 +2772,14 @@ static slu_status build_persistent(const slu_plan *P, std::vector<int32_t> &task
         return fail(SLU_ERR_NOT_SUPPORTED,
                     "persistent launch: the plan has sparse-stored blocks or "
                     "diagonal blocks without explicit inverses");
+    constexpr int NP = 5;
     const int64_t L = P->nlevels;
     const int64_t nseg = P->row_seg.empty() ? 1 : (int64_t)P->seg.size() - 1;
-    const int64_t nc = nseg * L * 4;
+    const int64_t nc = nseg * L * NP;
     auto member = [&](int32_t blk) -> int64_t {
         return P->row_seg.empty() ? 0 : P->row_seg[P->blocks[blk].r0];
     };
-    auto cid = [&](int64_t q, int64_t lv, int ph) { return (q * L + lv) * 4 + ph; };
+    auto cid = [&](int64_t q, int64_t lv, int ph) { return (q * L + lv) * NP + ph; };
     std::vector<int32_t> count(nc, 0);
     struct Item { int32_t kind, idx; int64_t c; };
     std::vector<Item> items;
@@ -2554,31 +2790,49 @@ static slu_status build_persistent(const slu_plan *P, std::vector<int32_t> &task
             items.push_back({kPtInv, (int32_t)i, cid(member(P->inv_task[3 * i]), lv, 1)});
         for (int64_t i = P->pd_off[lv]; i < P->pd_off[lv + 1]; ++i)
             items.push_back({kPtPanel, (int32_t)i, cid(member(P->pd_task[4 * i + 2]), lv, 2)});
-        for (int64_t i = P->gm_off[lv]; i < P->gm_off[lv + 1]; ++i)
+        for (int64_t i = P->gm_off[lv]; i < P->gm_mid[lv]; ++i)
             items.push_back({kPtSchur, (int32_t)i, cid(member(P->gm_task[5 * i]), lv, 3)});
+        for (int64_t i = P->gm_mid[lv]; i < P->gm_off[lv + 1]; ++i)
+            items.push_back({kPtSchurLate, (int32_t)i, cid(member(P->gm_task[5 * i]), lv, 4)});
     }
     for (const Item &it : items) count[it.c]++;
-    // each (member, level, phase) waits for its member's last non-empty
-    // (level, phase) before it
-    std::vector<int64_t> prev(nc, -1);
+    // per counter its two waits
+    std::vector<int64_t> w1(nc, -1), w2(nc, -1);
+    std::vector<int64_t> late(L + 1, -1);   // late[l + 1]: last non-empty phase 4 at level <= l
     for (int64_t q = 0; q < nseg; ++q) {
-        int64_t last = -1;
-        for (int64_t lv = 0; lv < L; ++lv)
+        int64_t main = -1;
+        for (int64_t lv = 0; lv < L; ++lv) {
+            const int64_t c4 = cid(q, lv, 4);
+            late[lv + 1] = count[c4] ? c4 : late[lv];
+        }
+        for (int64_t lv = 0; lv < L; ++lv) {
             for (int ph = 0; ph < 4; ++ph) {
                 const int64_t c = cid(q, lv, ph);
                 if (!count[c]) continue;
-                prev[c] = last;
-                last = c;
+                w1[c] = main;
+                w2[c] = ph < 3 ? (lv >= 1 ? late[lv - 1] : -1) : late[lv];
+                main = c;
             }
+            const int64_t c4 = cid(q, lv, 4);
+            if (count[c4]) {
+                // after the panels of its level (the last main phase before
+                // the Schur tiles), and after the deferred tiles before it
+                const int64_t c3 = cid(q, lv, 3);
+                w1[c4] = count[c3] ? w1[c3] : main;
+                w2[c4] = late[lv];
+            }
+        }
     }
     tasks.clear();
-    tasks.reserve(items.size() * 5);
+    tasks.reserve(items.size() * kPtInts);
     for (const Item &it : items) {
-        const int64_t w = prev[it.c];
+        const int64_t a = w1[it.c], b = w2[it.c];
         tasks.push_back(it.kind);
         tasks.push_back(it.idx);
-        tasks.push_back((int32_t)w);
-        tasks.push_back(w >= 0 ? count[w] : 0);
+        tasks.push_back((int32_t)a);
+        tasks.push_back(a >= 0 ? count[a] : 0);
+        tasks.push_back((int32_t)b);
+        tasks.push_back(b >= 0 ? count[b] : 0);
         tasks.push_back((int32_t)it.c);
     }
     *ncounters = nc;
@@ -2591,7 +2845,8 @@ static slu_status upload_persistent(slu_handle *h, const std::vector<int32_t> &t
     if (h->pdone) cudaFree(h->pdone);
     h->ptasks = nullptr;
     h->pdone = nullptr;
-    h->pntasks = (int64_t)tasks.size() / 5;
+    h->pntasks = (int64_t)tasks.size() / kPtInts;
+    h->pcap = h->pntasks;
     h->pcounters = ncounters;
     if (!cuda_ok(cudaMalloc(&h->ptasks, std::max<size_t>(1, tasks.size()) * sizeof(int32_t)),
                  "cudaMalloc(work list)") ||
@@ -2629,7 +2884,7 @@ extern "C" slu_status slu_persistent_tasks(const slu_handle *h, int32_t *tasks,
     *count = h->persistent ? h->pntasks : 0;
     const int64_t k = std::min<int64_t>(std::max<int64_t>(cap, 0), *count);
     if (k > 0 && tasks &&
-        !cuda_ok(cudaMemcpy(tasks, h->ptasks, k * 5 * sizeof(int32_t),
+        !cuda_ok(cudaMemcpy(tasks, h->ptasks, k * kPtInts * sizeof(int32_t),
                             cudaMemcpyDeviceToHost), "cudaMemcpy(work list)"))
         return SLU_ERR_CUDA;
     return SLU_OK;
@@ -2642,16 +2897,20 @@ extern "C" slu_status slu_set_persistent_tasks(slu_handle *h, const int32_t *tas
     if (!h->persistent)
         return fail(SLU_ERR_INVALID_ARG, "persistent launch not enabled");
     const slu_plan *P = h->plan;
-    const int64_t lim[4] = {(int64_t)P->gd.size(), (int64_t)P->inv_task.size() / 3,
-                            (int64_t)P->pd_task.size() / 4, (int64_t)P->gm_task.size() / 5};
+    const int64_t lim[5] = {(int64_t)P->gd.size(), (int64_t)P->inv_task.size() / 3,
+                            (int64_t)P->pd_task.size() / 4, (int64_t)P->gm_task.size() / 5,
+                            (int64_t)P->gm_task.size() / 5};
+    if (count > h->pcap)
+        return fail(SLU_ERR_INVALID_ARG, "work list longer than the built one");
     for (int64_t t = 0; t < count; ++t) {
-        const int32_t *r = tasks + 5 * t;
-        if (r[0] < 0 || r[0] > 3 || r[1] < 0 || r[1] >= lim[r[0]] || r[2] < -1 ||
-            r[2] >= h->pcounters || r[4] < 0 || r[4] >= h->pcounters)
+        const int32_t *r = tasks + kPtInts * t;
+        if (r[0] < 0 || r[0] > 4 || r[1] < 0 || r[1] >= lim[r[0]] || r[2] < -1 ||
+            r[2] >= h->pcounters || r[4] < -1 || r[4] >= h->pcounters || r[6] < 0 ||
+            r[6] >= h->pcounters)
             return fail(SLU_ERR_INVALID_ARG, "work list entry out of range");
     }
     if (count > 0 &&
-        !cuda_ok(cudaMemcpy(h->ptasks, tasks, count * 5 * sizeof(int32_t),
+        !cuda_ok(cudaMemcpy(h->ptasks, tasks, count * kPtInts * sizeof(int32_t),
                             cudaMemcpyHostToDevice), "cudaMemcpy(work list)"))
         return SLU_ERR_CUDA;
     h->pntasks = count;

@@ -45,7 +45,7 @@ namespace {
     X(lrow_blk) X(urow_blk) X(ucol_blk) X(lcol_blk) X(a2s) X(f2s)
 
 // Changes whenever the meaning of a field changes without a change of layout.
-constexpr uint32_t kPlanFormat = 1;
+constexpr uint32_t kPlanFormat = 2;
 constexpr char kPlanMagic[8] = {'S', 'L', 'U', 'P', 'L', 'A', 'N', 0};
 constexpr uint32_t kEndian = 0x01020304u;
 
@@ -124,7 +124,7 @@ void put(S &s, const slu_opts &o) {     // member by member: no padding bytes
     put(s, o.step); put(s, o.max_num); put(s, o.stride); put(s, o.b_min);
     put(s, o.precision); put(s, o.dense_threshold); put(s, o.pivot_perturb);
     put(s, o.pivot_tau_rel); put(s, o.refine_tol); put(s, o.refine_max_iter);
-    put(s, o.wait_budget_ms);
+    put(s, o.wait_budget_ms); put(s, o.tc_passes);
 }
 template <class S, class T>
 void put(S &s, const std::vector<T> &v) {   // element types have no padding
@@ -146,7 +146,7 @@ void get(Reader &r, slu_opts &o) {
     get(r, o.step); get(r, o.max_num); get(r, o.stride); get(r, o.b_min);
     get(r, o.precision); get(r, o.dense_threshold); get(r, o.pivot_perturb);
     get(r, o.pivot_tau_rel); get(r, o.refine_tol); get(r, o.refine_max_iter);
-    get(r, o.wait_budget_ms);
+    get(r, o.wait_budget_ms); get(r, o.tc_passes);
 }
 template <class T>
 void get(Reader &r, std::vector<T> &v) {

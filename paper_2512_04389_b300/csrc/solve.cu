@@ -1273,6 +1273,36 @@ extern "C" slu_status slu_solve_transpose(const slu_handle *h, const double *G,
     return s;
 }
 
+// Reordered systems: Y(k) = scale[perm[k]] X(perm[k]) (gather) or
+// Y(perm[k]) = scale[perm[k]] X(k) (scatter), column by column.
+__global__ void k_permute_scale(int64_t n, int nrhs, const int32_t *__restrict__ perm,
+                                const double *__restrict__ scale,
+                                const double *__restrict__ X, int64_t ldx,
+                                double *__restrict__ Y, int64_t ldy, int inverse) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t % n, c = t / n;
+        const int64_t p = perm[k];
+        const double s = scale ? scale[p] : 1.0;
+        if (inverse) Y[p + c * ldy] = s * X[k + c * ldx];
+        else         Y[k + c * ldy] = s * X[p + c * ldx];
+    }
+}
+
+extern "C" slu_status slu_permute_scale(int64_t n, int32_t nrhs, const int32_t *perm,
+                                        const double *scale, const double *X, int64_t ldx,
+                                        double *Y, int64_t ldy, int32_t inverse,
+                                        void *stream) {
+    if (n < 0 || nrhs < 0 || ldx < n || ldy < n || (n > 0 && nrhs > 0 && (!perm || !X || !Y)))
+        return fail(SLU_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0 || nrhs == 0) return SLU_OK;
+    const int64_t tot = n * nrhs;
+    const int grid = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
+    k_permute_scale<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        n, nrhs, perm, scale, X, ldx, Y, ldy, inverse);
+    return cuda_ok(cudaGetLastError(), "permute launch") ? SLU_OK : SLU_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free refined solve.
 //

@@ -34,7 +34,8 @@ class Opts(C.Structure):
                 ("b_min", C.c_int32), ("precision", C.c_int32),
                 ("dense_threshold", C.c_double), ("pivot_perturb", C.c_int32),
                 ("pivot_tau_rel", C.c_double), ("refine_tol", C.c_double),
-                ("refine_max_iter", C.c_int32), ("wait_budget_ms", C.c_int64)]
+                ("refine_max_iter", C.c_int32), ("wait_budget_ms", C.c_int64),
+                ("tc_passes", C.c_int32)]
 
 
 class PlanInfo(C.Structure):
@@ -75,6 +76,7 @@ EXPORTS = ["slu_opts_default", "slu_analyze", "slu_analyze_batch",
            "slu_plan_flops", "slu_handle_trace", "slu_set_graph", "slu_solve_refine_noalloc",
            "slu_factor_batch", "slu_select_regular_block",
            "slu_set_persistent", "slu_persistent_tasks", "slu_set_persistent_tasks",
+           "slu_reorder", "slu_reorder_apply", "slu_permute_scale",
            "slu_plan_serialize", "slu_plan_deserialize", "slu_plan_digest", "slu_plan_check",
            "slu_plan_destroy",
            "slu_handle_destroy", "slu_last_error"]
@@ -102,6 +104,10 @@ def _load():
     lib.slu_set_persistent.argtypes = [P, C.c_int32]
     lib.slu_persistent_tasks.argtypes = [P, P, C.c_int64, P]
     lib.slu_set_persistent_tasks.argtypes = [P, P, C.c_int64]
+    lib.slu_reorder.argtypes = [C.c_int64, P, P, P, C.c_int32, C.c_int32, P, P, P, P]
+    lib.slu_reorder_apply.argtypes = [C.c_int64, P, P, P, P, P, P, P, P, P, P]
+    lib.slu_permute_scale.argtypes = [C.c_int64, C.c_int32, P, P, P, C.c_int64, P,
+                                      C.c_int64, C.c_int32, P]
     lib.slu_select_regular_block.argtypes = [C.c_int64, C.c_int64]
     lib.slu_select_regular_block.restype = C.c_int32
     lib.slu_solve.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
@@ -363,6 +369,70 @@ class Plan:
         return out
 
 
+class Reordering:
+    """``slu_reorder``: static-pivot matching and scaling (``scale``) and a
+    nested-dissection ordering (``order``) of a general matrix (host CSC).
+    ``matrix()`` gives the reordered CSC; ``rhs(b)`` / ``solution(y)`` map a
+    CUDA right-hand side to the reordered system and its solution back
+    (``slu_permute_scale``)."""
+
+    def __init__(self, n, colptr, rowidx, values=None, scale=True, order=True,
+                 leaf=64):
+        self.n = int(n)
+        self.colptr, self.rowidx = _pattern_arrays(self.n, colptr, rowidx)
+        self.values = None if values is None else np.ascontiguousarray(values, np.float64)
+        if self.values is not None and self.values.size != self.rowidx.size:
+            raise ValueError("values must have one entry per pattern entry")
+        flags = (1 if scale else 0) | (2 if order else 0)
+        self.rowperm = np.zeros(self.n, np.int32)
+        self.colperm = np.zeros(self.n, np.int32)
+        self.rowscale = np.ones(self.n)
+        self.colscale = np.ones(self.n)
+        _check(lib.slu_reorder(self.n, _np(self.colptr), _np(self.rowidx),
+                               None if self.values is None else _np(self.values),
+                               flags, int(leaf), _np(self.rowperm), _np(self.colperm),
+                               _np(self.rowscale), _np(self.colscale)))
+        self._dev = None
+
+    def matrix(self):
+        """(colptr, rowidx, values) of the reordered, scaled matrix."""
+        cp = np.zeros(self.n + 1, np.int64)
+        ri = np.zeros(self.rowidx.size, np.int32)
+        va = None if self.values is None else np.zeros(self.rowidx.size)
+        _check(lib.slu_reorder_apply(
+            self.n, _np(self.colptr), _np(self.rowidx),
+            None if self.values is None else _np(self.values),
+            _np(self.rowperm), _np(self.colperm), _np(self.rowscale),
+            _np(self.colscale), _np(cp), _np(ri), None if va is None else _np(va)))
+        return cp, ri, va
+
+    def _device(self, device):
+        import torch
+        if self._dev is None:
+            self._dev = tuple(torch.as_tensor(a, device=device) for a in
+                              (self.rowperm, self.colperm, self.rowscale, self.colscale))
+        return self._dev
+
+    def _map(self, X, inverse, stream):
+        import torch
+        _check_rows(X, self.n, "X")
+        Xc, ldx, k, vec = _colmajor(X)
+        Y, ldy = _colmajor_empty(Xc.shape[0], k, Xc.device)
+        rp, cpm, rs, cs = self._device(Xc.device)
+        perm, sc = (cpm, cs) if inverse else (rp, rs)
+        _check(lib.slu_permute_scale(self.n, k, C.c_void_p(perm.data_ptr()),
+                                     C.c_void_p(sc.data_ptr()), _dev_ptr(Xc), ldx,
+                                     _dev_ptr(Y), ldy, 1 if inverse else 0,
+                                     _stream_ptr(stream)))
+        return Y.reshape(-1) if vec else Y
+
+    def rhs(self, B, stream=None):
+        return self._map(B, False, stream)
+
+    def solution(self, Y, stream=None):
+        return self._map(Y, True, stream)
+
+
 def factor_batch(plans, values, stream=None, allow_singular=False):
     """``slu_factor_batch``: independent plans factored in the same level
     walk; one Factor per plan (their factors equal ``Factor(plan, v)``'s)."""
@@ -473,17 +543,17 @@ class Factor:
         _check(lib.slu_set_persistent(self._h, 1 if enable else 0))
 
     def persistent_tasks(self):
-        """The persistent launch's work list, int32 array (tasks, 5)."""
+        """The persistent launch's work list, int32 array (tasks, 7)."""
         n = np.zeros(1, np.int64)
         _check(lib.slu_persistent_tasks(self._h, None, 0, _np(n)))
-        out = np.zeros((int(n[0]), 5), np.int32)
+        out = np.zeros((int(n[0]), 7), np.int32)
         _check(lib.slu_persistent_tasks(self._h, _np(out), int(n[0]), _np(n)))
         return out
 
     def set_persistent_tasks(self, tasks):
         t = np.ascontiguousarray(tasks, dtype=np.int32)
-        if t.ndim != 2 or t.shape[1] != 5:
-            raise ValueError("expected an int32 array of shape (tasks, 5)")
+        if t.ndim != 2 or t.shape[1] != 7:
+            raise ValueError("expected an int32 array of shape (tasks, 7)")
         _check(lib.slu_set_persistent_tasks(self._h, _np(t), t.shape[0]))
 
     def set_profiling(self, enable=True):

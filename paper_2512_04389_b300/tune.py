@@ -81,11 +81,15 @@ def _source_digest():
 
 
 def _key(n, colptr, rowidx, opts):
+    """Cache key; a batch (lists of the members' n, colptr, rowidx) hashes
+    every member in order."""
     h = hashlib.sha1()
     h.update(_source_digest().encode())
-    h.update(np.int64(n).tobytes())
-    h.update(np.ascontiguousarray(colptr, dtype=np.int64).tobytes())
-    h.update(np.ascontiguousarray(rowidx, dtype=np.int32).tobytes())
+    members = zip(n, colptr, rowidx) if isinstance(n, (list, tuple)) else [(n, colptr, rowidx)]
+    for m, cp, ri in members:
+        h.update(np.int64(m).tobytes())
+        h.update(np.ascontiguousarray(cp, dtype=np.int64).tobytes())
+        h.update(np.ascontiguousarray(ri, dtype=np.int32).tobytes())
     h.update(json.dumps(sorted(opts.items()), default=str).encode())
     return h.hexdigest()
 
@@ -119,10 +123,18 @@ def tune(n, colptr, rowidx, values, rhs, cands=None, reps=2, use_cache=True,
     ``Plan`` together with ``opts``; ``timings`` maps each candidate (as
     JSON) to its factor + solve milliseconds.  ``values`` and ``rhs`` are
     CUDA float64 tensors, ``opts`` the fixed plan options (precision,
-    blocking, ...)."""
+    blocking, ...).  ``n``, ``colptr``, ``rowidx`` may be lists (a batch:
+    the candidates are tried on the batch plan, all of them, since members
+    of different orders merge different candidates)."""
     import torch
     if cands is None:
-        cands = candidates(opts.get("blocking", "irregular"), n)
+        cands = candidates(opts.get("blocking", "irregular"),
+                           None if isinstance(n, (list, tuple)) else n)
+        if opts.get("precision") == "fp32":
+            # FP32 dense Schur tiles: split-precision 3xTF32 or one TF32
+            # pass (refinement makes up the difference; the timing includes
+            # its iterations)
+            cands = cands + [dict(c, tc_passes=1) for c in cands]
     key = _key(n, colptr, rowidx, dict(opts, cands=cands))
     cache = _load() if use_cache else {}
     if key in cache:

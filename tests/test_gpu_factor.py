@@ -370,3 +370,53 @@ def test_nonfinite_values_are_invalid(bad):
     be = OL.backward_error(s.n, s.colptr, s.rowidx, s.values,
                            X.cpu().numpy(), s.rhs)
     assert be <= 1e-13
+
+
+def test_fp32_single_pass_tf32_tiles_refine_to_full_accuracy():
+    """FP32 factors whose dense Schur tiles take one TF32 pass (FP32
+    accumulation): the factor error against the oracle is reported (TF32
+    keeps 10 mantissa bits, so it is larger than the 3xTF32 tiles'), and
+    refinement still reaches backward error <= 1e-14."""
+    s = workloads.grid7_cd(16, nrhs=2)
+    Fo, pp, pr, pv = oracle_factor(s)
+    errs = {}
+    for passes in (3, 1):
+        P, F = gpu_factor(s, precision="fp32", dense_threshold=0.0, b_min=16,
+                          tc_passes=passes)
+        errs[passes] = factor_error(P, F, pv)
+        X, info = F.solve(_dev(s.rhs), info=True)
+        be = OL.backward_error(s.n, s.colptr, s.rowidx, s.values,
+                               X.cpu().numpy(), s.rhs)
+        print(f"tc_passes {passes}: factor error {errs[passes]:.2e}, "
+              f"{info['iterations']} refinement steps, backward error {be:.2e}")
+        assert be <= 1e-14 and info["converged"]
+    assert errs[3] <= 1e-4 and errs[1] <= 1e-2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_general_matrix_through_the_front_end(prec):
+    """A 12^3 operator with rows and columns scrambled independently and
+    rescaled over six orders of magnitude cannot be factored without row
+    exchanges as given; the front end (matching + scaling + nested
+    dissection, slu_reorder) makes it factorable, and the solution mapped
+    back (slu_permute_scale) solves the original system."""
+    from conftest import dense_to_csc
+    s = workloads.grid7_cd(12, nrhs=1)
+    rng = np.random.default_rng(8)
+    p, q = rng.permutation(s.n), rng.permutation(s.n)
+    d1, d2 = 10.0 ** rng.uniform(-3, 3, s.n), 10.0 ** rng.uniform(-3, 3, s.n)
+    A = (d1[:, None] * s.dense() * d2[None, :])[np.ix_(p, q)]
+    cp, ri, vx = dense_to_csc(A)
+    x_true = rng.standard_normal(s.n)
+    b = A @ x_true
+    R = S.Reordering(s.n, cp, ri, vx, scale=True, order=True)
+    rcp, rri, rvx = R.matrix()
+    P, F = gpu_factor(workloads.SparseSystem(s.n, rcp, rri, rvx, np.zeros((s.n, 1))),
+                      precision=prec, b_min=16)
+    y, info = F.solve(R.rhs(_dev(b)), info=True)
+    x = R.solution(y).cpu().numpy()
+    be = OL.backward_error(s.n, cp, ri, vx, x, b)
+    err = np.abs(x - x_true).max() / np.abs(x_true).max()
+    print(f"{prec}: backward error {be:.2e} (original system), solution error {err:.2e}, "
+          f"{info['iterations']} refinement steps")
+    assert be <= 1e-13 and err <= 1e-9
