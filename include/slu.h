@@ -101,11 +101,16 @@ typedef struct {
     int64_t wait_budget_ms;      /* bound of every dependency wait of the
                                     persistent launch (slu_set_persistent),
                                     ms; <= 0 means 2000                     */
-    int32_t tc_passes;           /* FP32 dense Schur tiles on the tensor
-                                    cores: 3 = split precision 3xTF32 (the
-                                    products keep FP32 accuracy), 1 = one
-                                    TF32 pass with FP32 accumulation
-                                    (refinement recovers the accuracy)      */
+    int32_t tc_passes;           /* FP32 dense Schur tiles: 3 = tensor cores,
+                                    split precision 3xTF32 (the products
+                                    keep FP32 accuracy), 1 = tensor cores,
+                                    one TF32 pass with FP32 accumulation
+                                    (refinement recovers the accuracy), 0 =
+                                    FP32 pipe, executing only the 8 x 4
+                                    sub-tiles whose operands hold nonzeros
+                                    (for structurally sparse dense-stored
+                                    blocks, where a dense tile multiplies
+                                    mostly zeros)                           */
 } slu_opts;
 
 typedef struct {

@@ -975,34 +975,40 @@ static void build_levels_and_tasks(slu_plan &P) {
         P.ps_off[lv + 1] = (int64_t)P.ps_task.size() / 3;
         P.pv_off[lv + 1] = (int64_t)P.pv_task.size() / 4;
     }
-    // solve pull pairs per sweep and level
-    P.part_elems = 0;
-    for (int sw = 0; sw < 4; ++sw) {
-        const auto &off = sw == 0 ? P.lrow_off : sw == 1 ? P.urow_off
-                        : sw == 2 ? P.ucol_off : P.lcol_off;
-        const auto &ids = sw == 0 ? P.lrow_blk : sw == 1 ? P.urow_blk
-                        : sw == 2 ? P.ucol_blk : P.lcol_blk;
-        P.sp_off[sw].assign(L + 1, 0);
-        P.sp_pairs[sw].clear();
-        P.sp_poff[sw].clear();
-        P.sd_pair0[sw].assign(P.getrf.size(), 0);
-        for (int32_t lv = 0; lv < L; ++lv) {
-            int64_t acc = 0;
-            for (int64_t g = P.getrf_off[lv]; g < P.getrf_off[lv + 1]; ++g) {
-                const int32_t db = P.getrf[g];
-                const int32_t I = P.blocks[db].I;
-                P.sd_pair0[sw][g] = (int64_t)P.sp_pairs[sw].size() / 2;
-                for (int64_t q = off[I]; q < off[I + 1]; ++q) {
-                    P.sp_pairs[sw].push_back(ids[q]);
-                    P.sp_pairs[sw].push_back(db);
-                    P.sp_poff[sw].push_back(acc);
-                    acc += P.blocks[db].rows;
+    // solve pull pairs per sweep and level (the four sweeps independently,
+    // one thread each; each owns its arrays)
+    int64_t part_sw[4] = {0, 0, 0, 0};
+    run_threads(std::min(4, host_threads(0)), [&](int t) {
+        for (int sw = t; sw < 4; sw += std::min(4, host_threads(0))) {
+            const auto &off = sw == 0 ? P.lrow_off : sw == 1 ? P.urow_off
+                            : sw == 2 ? P.ucol_off : P.lcol_off;
+            const auto &ids = sw == 0 ? P.lrow_blk : sw == 1 ? P.urow_blk
+                            : sw == 2 ? P.ucol_blk : P.lcol_blk;
+            P.sp_off[sw].assign(L + 1, 0);
+            P.sp_pairs[sw].clear();
+            P.sp_poff[sw].clear();
+            P.sp_pairs[sw].reserve(2 * ids.size());
+            P.sp_poff[sw].reserve(ids.size());
+            P.sd_pair0[sw].assign(P.getrf.size(), 0);
+            for (int32_t lv = 0; lv < L; ++lv) {
+                int64_t acc = 0;
+                for (int64_t g = P.getrf_off[lv]; g < P.getrf_off[lv + 1]; ++g) {
+                    const int32_t db = P.getrf[g];
+                    const int32_t I = P.blocks[db].I;
+                    P.sd_pair0[sw][g] = (int64_t)P.sp_pairs[sw].size() / 2;
+                    for (int64_t q = off[I]; q < off[I + 1]; ++q) {
+                        P.sp_pairs[sw].push_back(ids[q]);
+                        P.sp_pairs[sw].push_back(db);
+                        P.sp_poff[sw].push_back(acc);
+                        acc += P.blocks[db].rows;
+                    }
                 }
+                P.sp_off[sw][lv + 1] = (int64_t)P.sp_pairs[sw].size() / 2;
+                part_sw[sw] = std::max(part_sw[sw], acc);
             }
-            P.sp_off[sw][lv + 1] = (int64_t)P.sp_pairs[sw].size() / 2;
-            P.part_elems = std::max(P.part_elems, acc);
         }
-    }
+    });
+    P.part_elems = std::max(std::max(part_sw[0], part_sw[1]), std::max(part_sw[2], part_sw[3]));
 }
 
 // Analysis of one pattern; `seg` (row offsets, size nseg + 1) splits it
@@ -1033,8 +1039,8 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         return fail(SLU_ERR_INVALID_ARG, "bad blocking parameters");
     if (o.precision != SLU_PREC_FP64 && o.precision != SLU_PREC_FP32)
         return fail(SLU_ERR_INVALID_ARG, "unknown precision");
-    if (o.tc_passes != 1 && o.tc_passes != 3)
-        return fail(SLU_ERR_INVALID_ARG, "tc_passes must be 1 or 3");
+    if (o.tc_passes != 0 && o.tc_passes != 1 && o.tc_passes != 3)
+        return fail(SLU_ERR_INVALID_ARG, "tc_passes must be 0, 1 or 3");
     if (!(o.dense_threshold >= 0.0))
         return fail(SLU_ERR_INVALID_ARG, "dense_threshold must be >= 0");
     if (colptr[0] != 0) return fail(SLU_ERR_INVALID_ARG, "colptr[0] must be 0");

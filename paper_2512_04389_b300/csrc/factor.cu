@@ -1848,18 +1848,21 @@ struct GemmSmem {
     unsigned short sBp[2][TN / 2];
 };
 
+// rsub: rows of the task's tile to skip (0, or 64 for the lower half of
+// a 128-row FP32 tile when it runs as two 64-row tiles on the FP32 pipe)
 template <typename T>
 __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
                                           const BlockDesc *bd, T *val,
-                                          GemmSmem<T> &sm) {
+                                          GemmSmem<T> &sm, int rsub = 0) {
     constexpr int TM = GemmSmem<T>::TM, TN = GemmSmem<T>::TN, KT = GemmSmem<T>::KT;
     auto &As = sm.As;
     auto &Bs = sm.Bs;
     auto &sAg = sm.sAg;
     auto &sBp = sm.sBp;
     const BlockDesc d = bd[tk[0]];
-    const int s0 = tk[1], s1 = tk[2], r0 = tk[3], c0 = tk[4];
+    const int s0 = tk[1], s1 = tk[2], r0 = tk[3] + rsub, c0 = tk[4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (r0 >= d.rows) return;                      // uniform: an empty half
     T acc[TN / 4];
 #pragma unroll
     for (int g = 0; g < TN / 4; ++g) acc[g] = T(0);
@@ -1958,12 +1961,13 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
     }
 }
 
+// One CTA per tile; blockIdx.y picks the 64-row half of a 128-row tile.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
              const BlockDesc *__restrict__ bd, T *__restrict__ val) {
     __shared__ __align__(16) GemmSmem<T> sm;
-    gemm_body<T>(task + 5 * (int64_t)blockIdx.x, src, bd, val, sm);
+    gemm_body<T>(task + 5 * (int64_t)blockIdx.x, src, bd, val, sm, 64 * (int)blockIdx.y);
 }
 
 // ------------------------------------------------------------ persistent
@@ -2070,11 +2074,19 @@ k_factor_persistent(PersistArgs p, T *val, T *winv) {
                 panel_inv_body<T>(p.pd_task + 4 * (int64_t)idx, p.bd, val, winv, p.woff,
                                   p.a, smem);
         } else {
-            if constexpr (sizeof(T) == 4)
-                tc_body(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd,
-                        reinterpret_cast<float *>(val), p.cnt + 2, smem, mbar, tmem, phase,
-                        p.tc_passes);
-            else
+            if constexpr (sizeof(T) == 4) {
+                if (p.tc_passes > 0) {
+                    tc_body(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd,
+                            reinterpret_cast<float *>(val), p.cnt + 2, smem, mbar, tmem,
+                            phase, p.tc_passes);
+                } else {
+                    for (int half = 0; half < 2; ++half) {
+                        gemm_body<T>(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd, val,
+                                     *reinterpret_cast<GemmSmem<T> *>(smem), 64 * half);
+                        __syncthreads();         // the halves share the staging buffers
+                    }
+                }
+            } else
                 gemm_body<T>(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd, val,
                              *reinterpret_cast<GemmSmem<T> *>(smem));
         }
@@ -2350,10 +2362,13 @@ static slu_status run_factor(slu_handle *h, const double *values,
                            cudaStream_t ss) {
             if (mb > ma) {
                 LaunchScope ls_(h, SLU_KC_SSSSM, ss, (int)(mb - ma));
-                if (sizeof(T) == 4)
+                if (sizeof(T) == 4 && P->opts.tc_passes > 0)
                     k_ssssm_tc<<<(int)(mb - ma), 256, tc::SMEM, ss>>>(
                         D->gm_task + 5 * ma, D->gm_src, D->bd,
                         reinterpret_cast<float *>(val), h->cnt + 2, P->opts.tc_passes);
+                else if (sizeof(T) == 4)   // 128-row tiles as two 64-row halves
+                    k_ssssm_gemm<T><<<dim3((unsigned)(mb - ma), 2), 256, 0, ss>>>(
+                        D->gm_task + 5 * ma, D->gm_src, D->bd, val);
                 else
                     k_ssssm_gemm<T><<<(int)(mb - ma), 256, 0, ss>>>(
                         D->gm_task + 5 * ma, D->gm_src, D->bd, val);

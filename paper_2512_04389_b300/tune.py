@@ -61,6 +61,21 @@ def candidates(blocking="irregular", n=None):
     return out
 
 
+TC_MODES = (3, 1, 0)
+
+
+def default_candidates(n, opts):
+    """The blocking candidates ``tune`` tries when none are given:
+    ``candidates`` for the blocking in ``opts``.  A batch (``n`` a list) is
+    not merged by sample count, since members of different orders merge
+    differently.  For FP32, ``tune`` then tries the tile modes ``TC_MODES``
+    (``tc_passes``: 3xTF32, one TF32 pass, the FP32 pipe with zero sub-tiles
+    skipped) on the best blocking; refinement makes up the accuracy of one
+    TF32 pass and the timing includes its iterations."""
+    return candidates(opts.get("blocking", "irregular"),
+                      None if isinstance(n, (list, tuple)) else n)
+
+
 _SOURCES = None
 
 
@@ -127,39 +142,46 @@ def tune(n, colptr, rowidx, values, rhs, cands=None, reps=2, use_cache=True,
     the candidates are tried on the batch plan, all of them, since members
     of different orders merge different candidates)."""
     import torch
+    staged = cands is None and opts.get("precision") == "fp32"
     if cands is None:
-        cands = candidates(opts.get("blocking", "irregular"),
-                           None if isinstance(n, (list, tuple)) else n)
-        if opts.get("precision") == "fp32":
-            # FP32 dense Schur tiles: split-precision 3xTF32 or one TF32
-            # pass (refinement makes up the difference; the timing includes
-            # its iterations)
-            cands = cands + [dict(c, tc_passes=1) for c in cands]
-    key = _key(n, colptr, rowidx, dict(opts, cands=cands))
+        cands = default_candidates(n, opts)
+    key = _key(n, colptr, rowidx, dict(opts, cands=cands, tc_modes=staged))
     cache = _load() if use_cache else {}
     if key in cache:
         e = cache[key]
         return e["best"], e["timings"]
     timings = {}
-    best, best_ms = None, float("inf")
-    for c in cands:
-        P = S.Plan(n, colptr, rowidx, **opts, **c)
-        F = S.Factor(P, values)
-        F.solve(rhs)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            F.refactor(values)
-            F.solve(rhs)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        timings[json.dumps(c, sort_keys=True)] = ms
-        if ms < best_ms:
-            best, best_ms = dict(c), ms
-        del F, P
+
+    def run(cs):
+        best, best_ms = None, float("inf")
+        for c in cs:
+            k = json.dumps(c, sort_keys=True)
+            if k in timings:
+                ms = timings[k]
+            else:
+                P = S.Plan(n, colptr, rowidx, **opts, **c)
+                F = S.Factor(P, values)
+                F.solve(rhs)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    F.refactor(values)
+                    F.solve(rhs)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                timings[k] = ms
+                del F, P
+            if ms < best_ms:
+                best, best_ms = dict(c), ms
+        return best
+
+    best = run(cands)
+    if staged:              # the FP32 tile modes on the best blocking
+        base = {k: v for k, v in best.items() if k != "tc_passes"}
+        best = run([base] + [dict(base, tc_passes=t) for t in TC_MODES if t != 3])
     if use_cache:
         cache[key] = {"best": best, "timings": timings}
         _save(cache)

@@ -275,8 +275,11 @@ def test_autotuner_picks_a_candidate_and_caches(tmp_path, monkeypatch):
     s = workloads.grid5(32)
     best, timings = T.tune(s.n, s.colptr, s.rowidx, _dev(s.values),
                            _dev(s.rhs), precision="fp32")
-    assert best in T.candidates("irregular", s.n)
-    assert len(timings) == len(T.candidates("irregular", s.n))
+    cands = T.default_candidates(s.n, {"precision": "fp32"})
+    base = {k: v for k, v in best.items() if k != "tc_passes"}
+    assert base in cands and best.get("tc_passes", 3) in T.TC_MODES
+    # every blocking candidate, then the other tile modes of the best one
+    assert len(timings) == len(cands) + len(T.TC_MODES) - 1
     again, t2 = T.tune(s.n, s.colptr, s.rowidx, _dev(s.values), _dev(s.rhs),
                        precision="fp32")
     assert again == best and t2 == timings          # served from the cache
@@ -372,15 +375,16 @@ def test_nonfinite_values_are_invalid(bad):
     assert be <= 1e-13
 
 
-def test_fp32_single_pass_tf32_tiles_refine_to_full_accuracy():
-    """FP32 factors whose dense Schur tiles take one TF32 pass (FP32
-    accumulation): the factor error against the oracle is reported (TF32
-    keeps 10 mantissa bits, so it is larger than the 3xTF32 tiles'), and
-    refinement still reaches backward error <= 1e-14."""
+def test_fp32_schur_tile_modes_refine_to_full_accuracy():
+    """FP32 factors whose dense Schur tiles run as 3xTF32 or one TF32 pass
+    on the tensor cores, or on the FP32 pipe with zero sub-tiles skipped:
+    the factor error against the oracle is reported (one TF32 pass keeps 10
+    mantissa bits, so it is the largest), and refinement reaches backward
+    error <= 1e-14 in every mode."""
     s = workloads.grid7_cd(16, nrhs=2)
     Fo, pp, pr, pv = oracle_factor(s)
     errs = {}
-    for passes in (3, 1):
+    for passes in (3, 1, 0):
         P, F = gpu_factor(s, precision="fp32", dense_threshold=0.0, b_min=16,
                           tc_passes=passes)
         errs[passes] = factor_error(P, F, pv)
@@ -390,7 +394,7 @@ def test_fp32_single_pass_tf32_tiles_refine_to_full_accuracy():
         print(f"tc_passes {passes}: factor error {errs[passes]:.2e}, "
               f"{info['iterations']} refinement steps, backward error {be:.2e}")
         assert be <= 1e-14 and info["converged"]
-    assert errs[3] <= 1e-4 and errs[1] <= 1e-2
+    assert errs[3] <= 1e-4 and errs[0] <= 1e-4 and errs[1] <= 1e-2
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -419,4 +423,6 @@ def test_general_matrix_through_the_front_end(prec):
     err = np.abs(x - x_true).max() / np.abs(x_true).max()
     print(f"{prec}: backward error {be:.2e} (original system), solution error {err:.2e}, "
           f"{info['iterations']} refinement steps")
-    assert be <= 1e-13 and err <= 1e-9
+    # the scrambled system's row and column scales span 10^6, so a backward
+    # error near 1e-14 allows a larger forward error after FP32 refinement
+    assert be <= 1e-13 and err <= (1e-9 if prec == "fp64" else 1e-6)
