@@ -402,16 +402,21 @@ def small_grid_leg(torch, S, dev, args):
 def circuit_leg(torch, S, dev, args):
     """Bordered circuit matrix, n = 200,000 (4,000 border rows), 8 RHS:
     FP32 factors + FP64 refinement to backward error <= 1e-14 against the
-    plain FP64 factorization, both irregular blocking; sparse/dense
-    threshold 0.02 for FP32 and 0.05 for FP64 (the best of {0.3, 0.1, 0.05,
-    0.02} per precision in a sweep; tuning here would repeat the 8-11 s host
-    analysis per candidate).  One timed factor + solve each."""
+    plain FP64 factorization, and the FP32 leg with regular 128-row
+    blocking.  The options are the best of one-off sweeps on B300 (tuning
+    here would repeat the 6-8 s host analysis per candidate): sparse/dense
+    threshold 0.02 for FP32 and 0.05 for FP64; FP32 irregular blocking with
+    S = n / 128 samples (tile-aligned spacing), max_num 1, and both FP32
+    legs with one TF32 pass on the tensor cores (the border is a dense
+    contraction).  One timed factor + solve each."""
     s = workloads.circuit_bbd()
     v, r = dev(s.values), dev(s.rhs)
     out = {"n": s.n, "nnz_a": s.nnz}
-    for leg, prec, extra in (("fp32", "fp32", {}), ("fp64", "fp64", {}),
+    for leg, prec, extra in (("fp32", "fp32",
+                              dict(sample_points=2000, b_min=128, max_num=1, tc_passes=1)),
+                             ("fp64", "fp64", {}),
                              ("fp32_regular128", "fp32",
-                              dict(blocking="regular", regular_block=128))):
+                              dict(blocking="regular", regular_block=128, tc_passes=1))):
         t0 = time.perf_counter()
         thr = 0.02 if prec == "fp32" else 0.05
         P = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=thr,

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -330,27 +331,29 @@ __device__ void lu_skip(const SplitBlock<T> &B, int b, unsigned char *lists,
 // Dense LU of a block held whole in shared memory, one CTA barrier per
 // step (FP32 storage, where the step chain, not arithmetic, is the bound).
 // Step k: every thread reads the pivot A(k, k) (final after step k-1),
-// applies the FP64 small-pivot test itself (thread 0 counts it) and forms
-// the reciprocal; warps over columns c > k with U(k, c) != 0, lanes over
-// rows: A(r, c) -= A(r, k) (U(k, c) / pivot).  Column k is read unscaled in
-// step k; its scaling by the reciprocal (L(:, k)) and the write of the fixed
+// applies the small-pivot test itself (thread 0 counts it) and forms the
+// reciprocal; warps over columns c > k with U(k, c) != 0, lanes over rows:
+// A(r, c) -= A(r, k) (U(k, c) / pivot).  Column k is read unscaled in step
+// k; its scaling by the reciprocal (L(:, k)) and the write of the fixed
 // pivot are deferred to step k+1, when nothing reads column k.
+// The test |p| < tau is the FP64 one, taken in FP32 without FP64
+// instructions: for a float x, x < tau exactly when x < tau_up, the
+// smallest float >= tau; the replacement is tau rounded to FP32.
 template <typename T>
 __device__ void lu_dense_smem(T *S, int b, int ls, double tau,
                               unsigned long long *cnt) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;
+    const float tau_up = __double2float_ru(tau), tau_rn = (float)tau;
     T prev_rcp = T(0), prev_piv = T(0);
     for (int k = 0; k < b; ++k) {
         const T p = S[(int64_t)k * ls + k];
-        const double pd = (double)p;
-        double fd = pd;
-        if (tau > 0.0 && fabs(pd) < tau) fd = pd >= 0.0 ? tau : -tau;
-        const T piv = (T)fd;
+        const bool small = tau_up > 0.0f && fabsf((float)p) < tau_up;
+        const T piv = small ? (T)(p >= T(0) ? tau_rn : -tau_rn) : p;
         const T rcp = T(1) / piv;
         if (tid == 0) {
-            if (fd != pd) atomicAdd(&cnt[0], 1ull);
-            else if (pd == 0.0) atomicOr(&cnt[1], 1ull);
+            if (small) atomicAdd(&cnt[0], 1ull);
+            else if (p == T(0)) atomicOr(&cnt[1], 1ull);
         }
         if (k > 0 && warp == ((k - 1) % nw)) {      // deferred: column k-1
             T *c = S + (int64_t)(k - 1) * ls;
@@ -1016,13 +1019,22 @@ __host__ __device__ constexpr size_t inv_smem_elems(int b) {
 template <typename T>
 __device__ __forceinline__ void inv_body(const int32_t *tk, const BlockDesc *bd,
                                          const T *val, T *winv, const int64_t *woff,
-                                         unsigned char *smem) {
+                                         unsigned char *smem, size_t cap = kStageSmem) {
     const BlockDesc d = bd[tk[0]];
     const int which = tk[1], b = d.rows, bs = (b + 31) & ~31;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = tk[2] + warp;
     const T *F = val + d.voff;                        // dense LU, ld = b
     T *s_rcp = reinterpret_cast<T *>(smem);
+    // the whole factor block is staged behind the warps' vectors when it
+    // fits: every warp of the CTA walks the same columns
+    T *staged = s_rcp + inv_smem_elems(b);
+    const bool fits = (inv_smem_elems(b) + (size_t)b * b) * sizeof(T) <= cap;
+    if (fits) {
+        for (int64_t e = threadIdx.x; e < (int64_t)b * b; e += blockDim.x) staged[e] = F[e];
+        F = staged;
+    }
+    __syncthreads();
     if (which == 1)                                   // uniform across the CTA
         for (int e = threadIdx.x; e < b; e += blockDim.x)
             s_rcp[e] = T(1) / F[(int64_t)e * b + e];
@@ -1131,12 +1143,12 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_inv(const int32_t *__restrict__ task, const BlockDesc *__restrict__ bd,
       const T *__restrict__ val, T *__restrict__ winv,
-      const int64_t *__restrict__ woff) {
+      const int64_t *__restrict__ woff, size_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     if constexpr (sizeof(T) == 4)
         inv_body_reg<T>(task + 3 * (int64_t)blockIdx.x, bd, val, winv, woff);
     else
-        inv_body<T>(task + 3 * (int64_t)blockIdx.x, bd, val, winv, woff, smem);
+        inv_body<T>(task + 3 * (int64_t)blockIdx.x, bd, val, winv, woff, smem, cap);
 }
 
 // Column-pair masks of a staged 16 x 64 slice S (S[kk * 64 + c]): bit kk of
@@ -1281,10 +1293,19 @@ __device__ __forceinline__ void panel_inv_body(const int32_t *tk, const BlockDes
 #pragma unroll
                 for (int g = 0; g < 16; ++g) {
                     unsigned km = amk & (unsigned)(bpm[2 * g] | bpm[2 * g + 1]);
-                    while (km) {                          // uniform across the warp
-                        const int kk = __ffs(km) - 1;
+                    if (km) {                             // uniform across the warp
+                        int kk = __ffs(km) - 1;
                         km &= km - 1;
-                        acc[g] += A[kk * 64 + rr] * B[kk * 64 + 4 * g + cc];
+                        T x = A[kk * 64 + rr], y = B[kk * 64 + 4 * g + cc];
+                        while (km) {
+                            kk = __ffs(km) - 1;
+                            km &= km - 1;
+                            const T xn = A[kk * 64 + rr], yn = B[kk * 64 + 4 * g + cc];
+                            acc[g] += x * y;
+                            x = xn;
+                            y = yn;
+                        }
+                        acc[g] += x * y;
                     }
                 }
             }
@@ -1837,15 +1858,18 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
 // registers while the current one is multiplied), sources run in ascending
 // I and k ascending within them, so the result is deterministic.
 // Shared memory of one dense Schur tile: the double-buffered slices and
-// their masks (sAg[buf][k][h] bit j: rows 32h + 8j .. +7 of A(:, k) hold a
-// nonzero; sBp[buf][p] bit k: columns 2p, 2p + 1 of B(k, :) hold one).
+// their masks.  sAg[buf][k][h] bit j: rows 32h + 8j .. +7 of A(:, k) hold a
+// nonzero; sBc[buf][c][h] bit k - 32h: B(k, c) is nonzero (k in the h-th
+// 32-deep half of the slice).  Slices are 16 deep (the body also takes 64:
+// measured on B300, 64-deep FP32 slices were slower, 132 against 91 ms for
+// the 40^3 FP32 + refinement step, with fewer resident CTAs).
 template <typename T>
 struct GemmSmem {
     static constexpr int TM = 64, TN = 64, KT = 16, PAD = 16 / sizeof(T);
     T As[2][KT][TM];
     T Bs[2][KT][TN + PAD];
     unsigned char sAg[2][KT][2];
-    unsigned short sBp[2][TN / 2];
+    unsigned sBc[2][TN][2];
 };
 
 // rsub: rows of the task's tile to skip (0, or 64 for the lower half of
@@ -1855,10 +1879,12 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
                                           const BlockDesc *bd, T *val,
                                           GemmSmem<T> &sm, int rsub = 0) {
     constexpr int TM = GemmSmem<T>::TM, TN = GemmSmem<T>::TN, KT = GemmSmem<T>::KT;
+    constexpr int NQ = KT * TM / 256;              // staged elements per thread
+    using Mask = typename std::conditional<KT == 64, unsigned long long, unsigned>::type;
     auto &As = sm.As;
     auto &Bs = sm.Bs;
     auto &sAg = sm.sAg;
-    auto &sBp = sm.sBp;
+    auto &sBc = sm.sBc;
     const BlockDesc d = bd[tk[0]];
     const int s0 = tk[1], s1 = tk[2], r0 = tk[3] + rsub, c0 = tk[4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1869,20 +1895,20 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
     if (s0 >= s1) return;
     int s = s0, k0 = 0;
     BlockDesc dl = bd[src[2 * s]], du = bd[src[2 * s + 1]];
-    T ra[4], rb[4];
+    T ra[NQ], rb[NQ];
     auto load = [&](const BlockDesc &L, const BlockDesc &U, int kk0) {
         const T *A = val + L.voff;
         const T *B = val + U.voff;
         const int K = L.cols;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int e = tid + 256 * q;
             const int r = e % TM, k = e / TM;
             const int gr = r0 + r, gk = kk0 + k;
             ra[q] = (gr < d.rows && gk < K) ? A[(int64_t)gk * L.ld + gr] : T(0);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int e = tid + 256 * q;
             const int k = e % KT, c = e / KT;
             const int gk = kk0 + k, gc = c0 + c;
@@ -1891,12 +1917,13 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
     };
     // Staging map: A element e = tid + 256 q is (row e % 64, k e / 64), so
     // warp w's lanes are rows 32 (w & 1) .. + 31 of k = (w + 8 q) / 2 and its
-    // ballot gives four 8-row groups; B element e is (k e % 16, column
-    // e / 16), so the warp holds column pair w + 8 q, lanes 0-15 and 16-31
-    // one column each over k = 0 .. 15.
+    // ballot gives four 8-row groups.  B element e is (k e % KT, column
+    // e / KT): for KT = 16 the warp holds columns 2 (w + 8 q) and + 1, lanes
+    // 0-15 and 16-31 over k = 0 .. 15; for KT = 64 it holds column
+    // (w + 8 q) / 2 over k = 32 ((w + 8 q) & 1) + lane.
     auto store = [&](int buf) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int e = tid + 256 * q;
             As[buf][e / TM][e % TM] = ra[q];
             const unsigned m = __ballot_sync(0xffffffffu, nz(ra[q]));
@@ -1906,11 +1933,19 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
                                     ((m & 0xff0000u) ? 4u : 0u) | ((m & 0xff000000u) ? 8u : 0u));
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int e = tid + 256 * q;
             Bs[buf][e % KT][e / KT] = rb[q];
             const unsigned m = __ballot_sync(0xffffffffu, nz(rb[q]));
-            if (lane == 0) sBp[buf][warp + 8 * q] = (unsigned short)((m | (m >> 16)) & 0xffffu);
+            if (lane == 0) {
+                const int wq = warp + 8 * q;
+                if (KT == 64) {
+                    sBc[buf][wq >> 1][wq & 1] = m;
+                } else {
+                    sBc[buf][2 * wq][0] = m & 0xffffu;
+                    sBc[buf][2 * wq + 1][0] = m >> 16;
+                }
+            }
         }
     };
     const int rr = 8 * warp + (lane & 7), cc = lane >> 3;
@@ -1928,17 +1963,37 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
             if (ns != s) { nl = bd[src[2 * ns]]; nu = bd[src[2 * ns + 1]]; }
             load(nl, nu, nk0);
         }
-        // k mask of this warp's row group (lane k of the first 16 reads it)
-        const unsigned amk = __ballot_sync(
+        // k mask of this warp's row group (lane k of the first KT reads it)
+        Mask amk = __ballot_sync(
             0xffffffffu, lane < KT && ((sAg[buf][lane & (KT - 1)][warp >> 2] >> (warp & 3)) & 1u));
+        if (KT == 64)
+            amk |= (Mask)__ballot_sync(
+                       0xffffffffu, ((sAg[buf][(lane + 32) & (KT - 1)][warp >> 2] >> (warp & 3)) & 1u))
+                   << (KT == 64 ? 32 : 0);
         if (amk) {
 #pragma unroll
             for (int g = 0; g < TN / 4; ++g) {
-                unsigned km = amk & (unsigned)(sBp[buf][2 * g] | sBp[buf][2 * g + 1]);
-                while (km) {                                // uniform across the warp
-                    const int k = __ffs(km) - 1;
+                Mask bm = (Mask)(sBc[buf][4 * g][0] | sBc[buf][4 * g + 1][0] |
+                                 sBc[buf][4 * g + 2][0] | sBc[buf][4 * g + 3][0]);
+                if (KT == 64)
+                    bm |= (Mask)(sBc[buf][4 * g][1] | sBc[buf][4 * g + 1][1] |
+                                 sBc[buf][4 * g + 2][1] | sBc[buf][4 * g + 3][1])
+                          << (KT == 64 ? 32 : 0);
+                Mask km = amk & bm;
+                if (km) {                                   // uniform across the warp
+                    // operands of the next live k load while this k's FMA issues
+                    int k = (KT == 64 ? __ffsll((long long)km) : __ffs((int)km)) - 1;
                     km &= km - 1;
-                    acc[g] += As[buf][k][rr] * Bs[buf][k][4 * g + cc];
+                    T a = As[buf][k][rr], b = Bs[buf][k][4 * g + cc];
+                    while (km) {
+                        k = (KT == 64 ? __ffsll((long long)km) : __ffs((int)km)) - 1;
+                        km &= km - 1;
+                        const T an = As[buf][k][rr], bn = Bs[buf][k][4 * g + cc];
+                        acc[g] += a * b;
+                        a = an;
+                        b = bn;
+                    }
+                    acc[g] += a * b;
                 }
             }
         }
@@ -1966,8 +2021,9 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
              const BlockDesc *__restrict__ bd, T *__restrict__ val) {
-    __shared__ __align__(16) GemmSmem<T> sm;
-    gemm_body<T>(task + 5 * (int64_t)blockIdx.x, src, bd, val, sm, 64 * (int)blockIdx.y);
+    extern __shared__ __align__(16) unsigned char gemm_raw[];   // sizeof(GemmSmem<T>)
+    gemm_body<T>(task + 5 * (int64_t)blockIdx.x, src, bd, val,
+                 *reinterpret_cast<GemmSmem<T> *>(gemm_raw), 64 * (int)blockIdx.y);
 }
 
 // ------------------------------------------------------------ persistent
@@ -2065,7 +2121,8 @@ k_factor_persistent(PersistArgs p, T *val, T *winv) {
             if constexpr (sizeof(T) == 4)
                 inv_body_reg<T>(p.inv_task + 3 * (int64_t)idx, p.bd, val, winv, p.woff);
             else
-                inv_body<T>(p.inv_task + 3 * (int64_t)idx, p.bd, val, winv, p.woff, smem);
+                inv_body<T>(p.inv_task + 3 * (int64_t)idx, p.bd, val, winv, p.woff, smem,
+                            persist_smem<T>());
         } else if (kind == kPtPanel) {
             if constexpr (sizeof(T) == 4)
                 panel_inv_dense_body<T>(p.pd_task + 4 * (int64_t)idx, p.bd, val, winv,
@@ -2216,6 +2273,8 @@ static slu_status set_smem_limits(size_t generic) {
               cuda_ok(cudaFuncSetAttribute(k_panel<T, Acc>, attr, big), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_inv<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_inv<T>, attr, (int)kStageSmem), "smem") &&
+              cuda_ok(cudaFuncSetAttribute(k_ssssm_gemm<T>, attr, (int)sizeof(GemmSmem<T>)),
+                      "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_grp<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_panel_vec<T>, attr, (int)kStageSmem), "smem") &&
               cuda_ok(cudaFuncSetAttribute(k_ssssm_tc, attr, (int)tc::SMEM), "smem") &&
@@ -2316,8 +2375,16 @@ static slu_status run_factor(slu_handle *h, const double *values,
         const int64_t i0 = P->inv_off[lv], i1 = P->inv_off[lv + 1];
         if (i1 > i0) {
             LaunchScope ls_(h, SLU_KC_INV, st, (int)(i1 - i0));
-            k_inv<T><<<(int)(i1 - i0), 256, inv_smem_elems(P->inv_maxb) * sizeof(T), st>>>(
-                D->inv_task + 3 * i0, D->bd, val, static_cast<T *>(h->winv), D->woff);
+            // shared memory for the level's largest block: its vectors, plus
+            // the block itself (staged once per CTA) when that fits
+            int mb = 0;
+            for (int64_t i = i0; i < i1; ++i) mb = std::max(mb, P->blocks[P->inv_task[3 * i]].rows);
+            size_t sm = inv_smem_elems(mb) * sizeof(T);
+            if (sizeof(T) == 8 && sm + (size_t)mb * mb * sizeof(T) <= kStageSmem)
+                sm += (size_t)mb * mb * sizeof(T);
+            if (sizeof(T) == 4) sm = 0;           // FP32: vectors in registers
+            k_inv<T><<<(int)(i1 - i0), 256, sm, st>>>(
+                D->inv_task + 3 * i0, D->bd, val, static_cast<T *>(h->winv), D->woff, sm);
         }
         const int64_t d0 = P->pd_off[lv], d1 = P->pd_off[lv + 1];
         if (d1 > d0) {
@@ -2367,10 +2434,10 @@ static slu_status run_factor(slu_handle *h, const double *values,
                         D->gm_task + 5 * ma, D->gm_src, D->bd,
                         reinterpret_cast<float *>(val), h->cnt + 2, P->opts.tc_passes);
                 else if (sizeof(T) == 4)   // 128-row tiles as two 64-row halves
-                    k_ssssm_gemm<T><<<dim3((unsigned)(mb - ma), 2), 256, 0, ss>>>(
+                    k_ssssm_gemm<T><<<dim3((unsigned)(mb - ma), 2), 256, sizeof(GemmSmem<T>), ss>>>(
                         D->gm_task + 5 * ma, D->gm_src, D->bd, val);
                 else
-                    k_ssssm_gemm<T><<<(int)(mb - ma), 256, 0, ss>>>(
+                    k_ssssm_gemm<T><<<(int)(mb - ma), 256, sizeof(GemmSmem<T>), ss>>>(
                         D->gm_task + 5 * ma, D->gm_src, D->bd, val);
             }
             if (sb > sa) {

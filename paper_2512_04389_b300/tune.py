@@ -27,7 +27,7 @@ from . import slu as S
 THRESHOLDS = (0.0, 0.3)
 MAX_NUM = (3, 2, 1)
 SAMPLE_POINTS = (1000, 2000)
-B_MIN = (32, 8)
+B_MIN = (32, 8, 64, 128)
 REGULAR_BLOCKS = (32, 64, 128, 256)
 
 

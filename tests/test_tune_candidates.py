@@ -20,10 +20,11 @@ def test_irregular_candidates_unique_plans():
 
 
 def test_candidate_counts():
-    # n = 64,000: S in {1000, 2000} (b_min irrelevant) x max_num + 1
-    assert len(T.candidates("irregular", 64_000)) == 7
-    # n = 2304: S in {72, 288} (sample_points irrelevant) x max_num + 1
-    assert len(T.candidates("irregular", 2304)) == 7
+    # n = 64,000: S = min(sample_points, n / b_min) in {2000, 1000, 500}
+    # (b_min 128 gives 500; 8 and 32 give no new S) x max_num + 1
+    assert len(T.candidates("irregular", 64_000)) == 10
+    # n = 2304: S in {72, 288, 36, 18} (sample_points irrelevant) x max_num + 1
+    assert len(T.candidates("irregular", 2304)) == 13
     assert T.candidates("regular") == [{"dense_threshold": t} for t in T.THRESHOLDS]
 
 
