@@ -6,11 +6,13 @@
  * "A Structure-Aware Irregular Blocking Method for Sparse LU Factorization"
  * (Hu et al.), and solves with the factors.
  *
- *   slu_analyze  host only: symmetric pattern, symbolic factorization,
+ *   slu_analyze  host: symmetric pattern, symbolic factorization,
  *                diagonal block pointer (Section 4.2, Algorithm 2),
  *                percentage sampling and irregular blocking (Section 4.3,
  *                Algorithm 3) or regular blocking, and the block task plan
  *                of the right-looking blocked LU (Section 2.2, Algorithm 1).
+ *                slu_analyze_device runs the symbolic factorization and
+ *                Algorithms 2 and 3 on the GPU, with the same plan.
  *   slu_factor   GPU: value scatter, then per level of the block dependency
  *                structure GETRF / GESSM / TSTRF / SSSSM (Algorithm 1's four
  *                block operations), each block sparse or dense by density.
@@ -113,6 +115,25 @@ typedef struct {
                                     mostly zeros)                           */
 } slu_opts;
 
+/* Phases of slu_analyze, the index of slu_plan_info.phase_ms:
+ *   INPUT     checks of the pattern, A's CSR view and its sorted columns;
+ *   SYMBOLIC  pattern(A + A^T), elimination tree, struct L, filled L+U
+ *             pattern (Section 1, the symbolic factorization);
+ *   BLOCKING  Algorithm 2's diagonal block pointer, the sampling of Section
+ *             4.3 with Algorithm 3, or the regular sizes;
+ *   BLOCKS    non-empty blocks, storage layout, local patterns;
+ *   TASKS     levels of the block DAG and the per-level task lists;
+ *   MAPS      flop counts per kernel class and the A -> storage map. */
+enum {
+    SLU_PHASE_INPUT = 0,
+    SLU_PHASE_SYMBOLIC = 1,
+    SLU_PHASE_BLOCKING = 2,
+    SLU_PHASE_BLOCKS = 3,
+    SLU_PHASE_TASKS = 4,
+    SLU_PHASE_MAPS = 5,
+    SLU_PHASE_COUNT = 6
+};
+
 typedef struct {
     int64_t n;
     int64_t nnz_a;               /* entries of the input pattern            */
@@ -132,6 +153,7 @@ typedef struct {
     int32_t regular_block;       /* regular blocking: the block size used
                                     (the largest over batch members for
                                     SLU_BLOCKING_REGULAR_SELECT); else 0    */
+    double phase_ms[SLU_PHASE_COUNT]; /* analyze_ms by phase (SLU_PHASE_*)  */
 } slu_plan_info;
 
 typedef struct {
@@ -209,6 +231,29 @@ slu_status slu_analyze_batch(int32_t count, const int64_t *n,
                              const int64_t *const *colptr,
                              const int32_t *const *rowidx,
                              const slu_opts *opts, slu_plan **out);
+
+/* slu_analyze / slu_analyze_batch with the steps that walk the pattern
+ * entry by entry on the current GPU, enqueued on `stream`: the symmetric
+ * pattern, the elimination tree, struct L and the filled L+U pattern (the
+ * symbolic factorization of Section 1), Algorithm 2's per-row counts and
+ * prefix sum (Section 4.2), and the sampling of the percentage curve with
+ * Algorithm 3 (Section 4.3, one CTA per batch member).  The pattern checks,
+ * the block plan and the task lists stay on the host.  The plan equals
+ * slu_analyze's (slu_plan_digest is the same); slu_plan_info.phase_ms
+ * reports the device phases' time including their copies.  The pattern
+ * stays host memory; the call returns when the device work has finished
+ * and uses temporary device memory (about 16 bytes per entry of pattern(A
+ * + A^T) and per filled entry) allocated stream-ordered from the device's
+ * default pool.  Errors: those of slu_analyze, SLU_ERR_OUT_OF_MEMORY when a
+ * device allocation fails, SLU_ERR_CUDA when a CUDA call fails. */
+slu_status slu_analyze_device(int64_t n, const int64_t *colptr,
+                              const int32_t *rowidx, const slu_opts *opts,
+                              void *stream, slu_plan **out);
+slu_status slu_analyze_batch_device(int32_t count, const int64_t *n,
+                                    const int64_t *const *colptr,
+                                    const int32_t *const *rowidx,
+                                    const slu_opts *opts, void *stream,
+                                    slu_plan **out);
 
 slu_status slu_plan_query(const slu_plan *plan, slu_plan_info *info);
 

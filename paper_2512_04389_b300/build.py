@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libslu_b300.so")
 SOURCES = ["analyze.cpp", "plan_io.cpp", "plan_check.cpp", "reorder.cpp", "factor.cu",
-           "solve.cu"]
+           "solve.cu", "symbolic.cu"]
 HEADERS = ["slu_internal.hpp", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1013,11 +1013,14 @@ static void build_levels_and_tasks(slu_plan &P) {
 
 // Analysis of one pattern; `seg` (row offsets, size nseg + 1) splits it
 // into independent diagonal segments (a batch of matrices laid out block-
-// diagonally), each blocked on its own.
+// diagonally), each blocked on its own.  With `device` the symbolic
+// factorization, Algorithm 2, the sampling and Algorithm 3 run on the
+// current GPU, enqueued on `stream`.
 static slu_status analyze_impl(int64_t n, const int64_t *colptr,
                                const int32_t *rowidx, const slu_opts *opts,
                                const std::vector<int64_t> &seg,
-                               slu_plan **out) {
+                               slu_plan **out, bool device = false,
+                               void *stream = nullptr) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!out) return fail(SLU_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -1078,6 +1081,14 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
     }
     slu_plan *P = new (std::nothrow) slu_plan();
     if (!P) return fail(SLU_ERR_OUT_OF_MEMORY, "plan allocation");
+    // phase k's time runs from the previous mark (the start of the call
+    // for the first) to mark(k)
+    auto tm = t0;
+    auto mark = [&](int k) {
+        const auto now = std::chrono::steady_clock::now();
+        P->phase_ms[k] = std::chrono::duration<double, std::milli>(now - tm).count();
+        tm = now;
+    };
     try {
         P->opts = o;
         P->n = n;
@@ -1120,53 +1131,79 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
                 si[at] = (int32_t)r;
                 sq[at] = P->a_vpos[t];
             });
-        std::vector<int64_t> Lp;
-        std::vector<int32_t> Li;
-        {
-            Sym S;
-            symmetrize(n, sp.data(), si.data(), P->a_rowptr.data(),
-                       P->a_colidx.data(), S);
-            P->nnz_sym = S.p[n];
-            std::vector<int32_t> parent;
-            etree(n, S, parent);
-            symbolic(n, S, parent, Lp, Li);
-        }
-        // filled L+U pattern: column j = U rows (k < j with j in L(:,k),
-        // ascending), the diagonal j, then L rows (ascending)
-        std::vector<int64_t> ucnt(n, 0);
-        P->f_colptr.assign(n + 1, 0);
-        stable_transpose(
-            n, Lp.data(), n, [&](int64_t q) { return Li[q]; },
-            [&](int64_t j, int64_t c) { ucnt[j] = c; },
-            [&](int64_t j) {
-                if (j == 0) {
-                    for (int64_t i = 0; i < n; ++i)
-                        P->f_colptr[i + 1] = P->f_colptr[i] + ucnt[i] + 1 + (Lp[i + 1] - Lp[i]);
-                    P->f_rowidx.resize(P->f_colptr[n]);
-                }
-                return P->f_colptr[j];
-            },
-            [&](int64_t at, int64_t k, int64_t) { P->f_rowidx[at] = (int32_t)k; });
-        run_threads(host_threads(0), [&](int t) {
-            const int nt = host_threads(0);
-            for (int64_t j = t; j < n; j += nt) {
-                int64_t f = P->f_colptr[j] + ucnt[j];
-                P->f_rowidx[f++] = (int32_t)j;
-                for (int64_t q = Lp[j]; q < Lp[j + 1]; ++q) P->f_rowidx[f++] = Li[q];
+        mark(SLU_PHASE_INPUT);
+        std::vector<std::vector<int64_t>> dev_ptr;   // device Algorithm 3
+        DeviceSymbolicTimes dtm;
+        if (device) {
+            // symbolic factorization, Algorithm 2, sampling and Algorithm 3
+            // on the GPU (same results as the host branch below)
+            const slu_status ds = device_symbolic(
+                n, colptr, rowidx, seg, o, o.blocking == SLU_BLOCKING_IRREGULAR,
+                stream, *P, dev_ptr, dtm);
+            if (ds != SLU_OK) {
+                delete P;
+                return ds;
             }
-        });
-        // flops = sum_k (l_k + 2 l_k u_k); by symmetry u_k = l_k
-        P->flops = 0;
-        for (int64_t k = 0; k < n; ++k) {
-            const int64_t l = Lp[k + 1] - Lp[k];
-            P->flops += l + 2 * l * l;
+            // flops = sum_k (l_k + 2 l_k^2), l_k the entries of column k
+            // below the diagonal; the column holds l_k + 1 + u_k entries,
+            // u_k = (blockptr[k + 1] - blockptr[k] - 1) / 2 above it
+            P->flops = 0;
+            for (int64_t k = 0; k < n; ++k) {
+                const int64_t u = (P->blockptr[k + 1] - P->blockptr[k] - 1) / 2;
+                const int64_t l = P->f_colptr[k + 1] - P->f_colptr[k] - 1 - u;
+                P->flops += l + 2 * l * l;
+            }
+            mark(SLU_PHASE_SYMBOLIC);
+        } else {
+            std::vector<int64_t> Lp;
+            std::vector<int32_t> Li;
+            {
+                Sym S;
+                symmetrize(n, sp.data(), si.data(), P->a_rowptr.data(),
+                           P->a_colidx.data(), S);
+                P->nnz_sym = S.p[n];
+                std::vector<int32_t> parent;
+                etree(n, S, parent);
+                symbolic(n, S, parent, Lp, Li);
+            }
+            // filled L+U pattern: column j = U rows (k < j with j in L(:,k),
+            // ascending), the diagonal j, then L rows (ascending)
+            std::vector<int64_t> ucnt(n, 0);
+            P->f_colptr.assign(n + 1, 0);
+            stable_transpose(
+                n, Lp.data(), n, [&](int64_t q) { return Li[q]; },
+                [&](int64_t j, int64_t c) { ucnt[j] = c; },
+                [&](int64_t j) {
+                    if (j == 0) {
+                        for (int64_t i = 0; i < n; ++i)
+                            P->f_colptr[i + 1] = P->f_colptr[i] + ucnt[i] + 1 + (Lp[i + 1] - Lp[i]);
+                        P->f_rowidx.resize(P->f_colptr[n]);
+                    }
+                    return P->f_colptr[j];
+                },
+                [&](int64_t at, int64_t k, int64_t) { P->f_rowidx[at] = (int32_t)k; });
+            run_threads(host_threads(0), [&](int t) {
+                const int nt = host_threads(0);
+                for (int64_t j = t; j < n; j += nt) {
+                    int64_t f = P->f_colptr[j] + ucnt[j];
+                    P->f_rowidx[f++] = (int32_t)j;
+                    for (int64_t q = Lp[j]; q < Lp[j + 1]; ++q) P->f_rowidx[f++] = Li[q];
+                }
+            });
+            // flops = sum_k (l_k + 2 l_k u_k); by symmetry u_k = l_k
+            P->flops = 0;
+            for (int64_t k = 0; k < n; ++k) {
+                const int64_t l = Lp[k + 1] - Lp[k];
+                P->flops += l + 2 * l * l;
+            }
+            std::vector<int64_t>().swap(Lp);
+            std::vector<int32_t>().swap(Li);
+            mark(SLU_PHASE_SYMBOLIC);
+            // Algorithm 2 on the filled pattern
+            P->blockptr.assign(n + 1, 0);
+            diagonal_block_pointer(n, P->f_colptr.data(), P->f_rowidx.data(),
+                                   P->blockptr.data());
         }
-        std::vector<int64_t>().swap(Lp);
-        std::vector<int32_t>().swap(Li);
-        // Algorithm 2 on the filled pattern
-        P->blockptr.assign(n + 1, 0);
-        diagonal_block_pointer(n, P->f_colptr.data(), P->f_rowidx.data(),
-                               P->blockptr.data());
         // blocking, segment by segment: for a block-diagonal pattern the
         // diagonal block pointer of segment [s0, s1) is bp[s0 + k] - bp[s0]
         P->seg = seg;
@@ -1176,7 +1213,12 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         for (size_t q = 0; q + 1 < seg.size(); ++q) {
             const int64_t s0 = seg[q], N = seg[q + 1] - seg[q];
             if (N == 0) continue;
-            if (o.blocking == SLU_BLOCKING_IRREGULAR) {
+            if (o.blocking == SLU_BLOCKING_IRREGULAR && device) {
+                ps = dev_ptr[q];
+                P->samples = std::max<int32_t>(
+                    P->samples, (int32_t)std::max<int64_t>(
+                                    1, std::min<int64_t>(o.sample_points, N / o.b_min)));
+            } else if (o.blocking == SLU_BLOCKING_IRREGULAR) {
                 bps.resize(N + 1);
                 for (int64_t k = 0; k <= N; ++k)
                     bps[k] = P->blockptr[s0 + k] - P->blockptr[s0];
@@ -1206,12 +1248,19 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
             for (size_t q = 0; q + 1 < seg.size(); ++q)
                 for (int64_t r = seg[q]; r < seg[q + 1]; ++r) P->row_seg[r] = (int32_t)q;
         }
+        mark(SLU_PHASE_BLOCKING);
+        if (device) {           // the device's Algorithm 2 / 3 time
+            P->phase_ms[SLU_PHASE_SYMBOLIC] -= dtm.blocking_ms;
+            P->phase_ms[SLU_PHASE_BLOCKING] += dtm.blocking_ms;
+        }
         const slu_status st = build_blocks(*P);
         if (st != SLU_OK) {
             delete P;
             return st;
         }
+        mark(SLU_PHASE_BLOCKS);
         build_levels_and_tasks(*P);
+        mark(SLU_PHASE_TASKS);
         // flops per kernel class from the block of each column's rows;
         // threads sum contiguous column ranges (every term is an integer,
         // so the sums are exact below 2^53 whatever their order)
@@ -1253,6 +1302,7 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         return fail(SLU_ERR_OUT_OF_MEMORY,
                     std::string("host allocation in analyze: ") + e.what());
     }
+    mark(SLU_PHASE_MAPS);
     P->analyze_ms = std::chrono::duration<double, std::milli>(
                         std::chrono::steady_clock::now() - t0).count();
     *out = P;
@@ -1282,10 +1332,18 @@ extern "C" slu_status slu_analyze(int64_t n, const int64_t *colptr,
                         std::vector<int64_t>{0, std::max<int64_t>(n, 0)}, out);
 }
 
-extern "C" slu_status slu_analyze_batch(int32_t count, const int64_t *n,
-                                        const int64_t *const *colptr,
-                                        const int32_t *const *rowidx,
-                                        const slu_opts *opts, slu_plan **out) {
+extern "C" slu_status slu_analyze_device(int64_t n, const int64_t *colptr,
+                                         const int32_t *rowidx, const slu_opts *opts,
+                                         void *stream, slu_plan **out) {
+    return analyze_impl(n, colptr, rowidx, opts,
+                        std::vector<int64_t>{0, std::max<int64_t>(n, 0)}, out, true,
+                        stream);
+}
+
+static slu_status batch_impl(int32_t count, const int64_t *n,
+                             const int64_t *const *colptr,
+                             const int32_t *const *rowidx, const slu_opts *opts,
+                             slu_plan **out, bool device, void *stream) {
     if (!out) return fail(SLU_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (count < 1 || !n || !colptr || !rowidx)
@@ -1332,7 +1390,22 @@ extern "C" slu_status slu_analyze_batch(int32_t count, const int64_t *n,
             cp[seg[q] + j + 1] = (int64_t)ri.size();
         }
     }
-    return analyze_impl(N, cp.data(), ri.data(), opts, seg, out);
+    return analyze_impl(N, cp.data(), ri.data(), opts, seg, out, device, stream);
+}
+
+extern "C" slu_status slu_analyze_batch(int32_t count, const int64_t *n,
+                                        const int64_t *const *colptr,
+                                        const int32_t *const *rowidx,
+                                        const slu_opts *opts, slu_plan **out) {
+    return batch_impl(count, n, colptr, rowidx, opts, out, false, nullptr);
+}
+
+extern "C" slu_status slu_analyze_batch_device(int32_t count, const int64_t *n,
+                                               const int64_t *const *colptr,
+                                               const int32_t *const *rowidx,
+                                               const slu_opts *opts, void *stream,
+                                               slu_plan **out) {
+    return batch_impl(count, n, colptr, rowidx, opts, out, true, stream);
 }
 
 extern "C" slu_status slu_plan_query(const slu_plan *P, slu_plan_info *info) {
@@ -1357,6 +1430,7 @@ extern "C" slu_status slu_plan_query(const slu_plan *P, slu_plan_info *info) {
     info->samples = P->samples;
     info->regular_block = P->regular_block;
     info->analyze_ms = P->analyze_ms;
+    for (int k = 0; k < SLU_PHASE_COUNT; ++k) info->phase_ms[k] = P->phase_ms[k];
     return SLU_OK;
 }
 

@@ -18,8 +18,8 @@ using namespace slu;
 // and the solves read, in one fixed order, and drives the byte format, the
 // digest and a layout fingerprint (field names and element sizes), so a
 // field added to, removed from or retyped in slu_plan changes the
-// fingerprint and old buffers are refused.  analyze_ms (a timing) travels
-// in the header, outside the digest; the device mirror is never written.
+// fingerprint and old buffers are refused.  analyze_ms and phase_ms (timings)
+// travel in the header, outside the digest; the device mirror is never written.
 
 namespace slu {
 namespace {
@@ -45,7 +45,7 @@ namespace {
     X(lrow_blk) X(urow_blk) X(ucol_blk) X(lcol_blk) X(a2s) X(f2s)
 
 // Changes whenever the meaning of a field changes without a change of layout.
-constexpr uint32_t kPlanFormat = 2;
+constexpr uint32_t kPlanFormat = 3;
 constexpr char kPlanMagic[8] = {'S', 'L', 'U', 'P', 'L', 'A', 'N', 0};
 constexpr uint32_t kEndian = 0x01020304u;
 
@@ -202,8 +202,9 @@ struct Header {
     uint64_t fingerprint, digest;
     int64_t payload;
     double analyze_ms;
+    double phase_ms[SLU_PHASE_COUNT];
 };
-static_assert(sizeof(Header) == 48, "serialized header layout");
+static_assert(sizeof(Header) == 48 + 8 * SLU_PHASE_COUNT, "serialized header layout");
 
 }  // namespace
 }  // namespace slu
@@ -240,6 +241,7 @@ extern "C" slu_status slu_plan_serialize(const slu_plan *P, void *buf,
     hd.digest = payload_digest(*P);
     hd.payload = c.bytes;
     hd.analyze_ms = P->analyze_ms;
+    std::memcpy(hd.phase_ms, P->phase_ms, sizeof(hd.phase_ms));
     unsigned char *b = static_cast<unsigned char *>(buf);
     std::memcpy(b, &hd, sizeof(hd));
     Writer w{b + sizeof(hd)};
@@ -303,6 +305,7 @@ extern "C" slu_status slu_plan_deserialize(const void *buf, int64_t size,
                     std::string("host allocation in deserialize: ") + e.what());
     }
     P->analyze_ms = hd.analyze_ms;
+    std::memcpy(P->phase_ms, hd.phase_ms, sizeof(hd.phase_ms));
     *out = P;
     return SLU_OK;
 }

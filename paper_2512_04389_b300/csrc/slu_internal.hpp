@@ -60,6 +60,7 @@ struct slu_plan {
     slu_opts opts;
     int64_t n = 0, nnz_a = 0, nnz_sym = 0;
     double analyze_ms = 0;
+    double phase_ms[SLU_PHASE_COUNT] = {};
     // input pattern (copied) and its CSR view for the FP64 residual
     std::vector<int64_t> a_colptr;
     std::vector<int32_t> a_rowidx;
@@ -182,4 +183,22 @@ namespace slu {
 void set_error(const std::string &msg);
 slu_status fail(slu_status st, const std::string &msg);
 void free_dev_plan(slu_plan *plan);
+
+// Device analysis (symbolic.cu) of a checked pattern (CSC, host arrays,
+// rows in any order; `seg` its diagonal segments): sets P.nnz_sym,
+// P.f_colptr, P.f_rowidx and P.blockptr exactly as the host analysis does
+// and, when `irregular`, seg_ptr[q] = Algorithm 3's boundaries of segment q
+// (local rows, empty for an empty segment).  Work runs on the current
+// device, enqueued on `stream` (a cudaStream_t); returns after it finished.
+struct DeviceSymbolicTimes {
+    double symbolic_ms = 0;     // pattern, tree, struct L, filled pattern
+    double blocking_ms = 0;     // Algorithm 2, sampling, Algorithm 3
+    int64_t sweeps = 0;         // relaxation sweeps of the elimination tree
+    int64_t samples = 0;        // largest S over the segments
+};
+slu_status device_symbolic(int64_t n, const int64_t *colptr, const int32_t *rowidx,
+                           const std::vector<int64_t> &seg, const slu_opts &o,
+                           bool irregular, void *stream, slu_plan &P,
+                           std::vector<std::vector<int64_t>> &seg_ptr,
+                           DeviceSymbolicTimes &tm);
 }  // namespace slu

@@ -47,7 +47,17 @@ class PlanInfo(C.Structure):
                 ("n_gessm", C.c_int64), ("n_tstrf", C.c_int64),
                 ("n_ssssm_targets", C.c_int64), ("n_ssssm_pairs", C.c_int64),
                 ("max_block", C.c_int32), ("samples", C.c_int32),
-                ("analyze_ms", C.c_double), ("regular_block", C.c_int32)]
+                ("analyze_ms", C.c_double), ("regular_block", C.c_int32),
+                ("phase_ms", C.c_double * 6)]
+
+
+PHASES = ("input", "symbolic", "blocking", "blocks", "tasks", "maps")
+
+
+def _info_dict(i):
+    d = {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+    d["phase_ms"] = dict(zip(PHASES, list(i.phase_ms)))
+    return d
 
 
 class FactorInfo(C.Structure):
@@ -69,7 +79,7 @@ class Stats(C.Structure):
 
 # every entry point declared in include/slu.h
 EXPORTS = ["slu_opts_default", "slu_analyze", "slu_analyze_batch",
-           "slu_plan_query",
+           "slu_analyze_device", "slu_analyze_batch_device", "slu_plan_query",
            "slu_plan_export", "slu_plan_export_blocks", "slu_plan_export_tasks",
            "slu_factor", "slu_refactor", "slu_solve", "slu_solve_transpose",
            "slu_export_factors", "slu_grad_values", "slu_set_profiling", "slu_handle_stats",
@@ -94,6 +104,9 @@ def _load():
     lib.slu_analyze.argtypes = [C.c_int64, P, P, C.POINTER(Opts), C.POINTER(P)]
     lib.slu_analyze_batch.argtypes = [C.c_int32, P, P, P, C.POINTER(Opts),
                                       C.POINTER(P)]
+    lib.slu_analyze_device.argtypes = [C.c_int64, P, P, C.POINTER(Opts), P, C.POINTER(P)]
+    lib.slu_analyze_batch_device.argtypes = [C.c_int32, P, P, P, C.POINTER(Opts), P,
+                                             C.POINTER(P)]
     lib.slu_plan_query.argtypes = [P, C.POINTER(PlanInfo)]
     lib.slu_plan_export.argtypes = [P, P, P, P, P]
     lib.slu_plan_export_blocks.argtypes = [P, P, P, P, P, P]
@@ -234,20 +247,31 @@ def _pattern_arrays(n, colptr, rowidx):
 
 
 class Plan:
-    """Result of host analysis (``slu_analyze``) for one sparsity pattern."""
+    """Result of the analysis (``slu_analyze``) of one sparsity pattern, or
+    of a batch when ``n``, ``colptr`` and ``rowidx`` are lists.  With
+    ``device=True`` the symbolic factorization and Algorithms 2 / 3 run on
+    the current GPU (``slu_analyze_device``) on ``stream`` (the current
+    torch stream when None); the plan is the same."""
 
-    def __init__(self, n, colptr, rowidx, **opts):
+    def __init__(self, n, colptr, rowidx, device=False, stream=None, **opts):
         self._h = C.c_void_p()
+        self.device = bool(device)
+        self._stream = stream
         if isinstance(n, (list, tuple)):          # batch of matrices
             return self._init_batch(n, colptr, rowidx, opts)
         self.n = int(n)
         self.colptr, self.rowidx = _pattern_arrays(self.n, colptr, rowidx)
         self.opts = default_opts(**opts)
-        _check(lib.slu_analyze(self.n, _np(self.colptr), _np(self.rowidx),
-                               C.byref(self.opts), C.byref(self._h)))
+        if self.device:
+            _check(lib.slu_analyze_device(self.n, _np(self.colptr), _np(self.rowidx),
+                                          C.byref(self.opts), _stream_ptr(stream),
+                                          C.byref(self._h)))
+        else:
+            _check(lib.slu_analyze(self.n, _np(self.colptr), _np(self.rowidx),
+                                   C.byref(self.opts), C.byref(self._h)))
         i = PlanInfo()
         _check(lib.slu_plan_query(self._h, C.byref(i)))
-        self.info = {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+        self.info = _info_dict(i)
 
     @classmethod
     def from_bytes(cls, data):
@@ -255,12 +279,13 @@ class Plan:
         without repeating the analysis."""
         self = cls.__new__(cls)
         self._h = C.c_void_p()
+        self.device = False
         buf = np.frombuffer(memoryview(data).cast("B"), dtype=np.uint8)
         _check(lib.slu_plan_deserialize(_np(buf) if buf.size else None,
                                         buf.size, C.byref(self._h)))
         i = PlanInfo()
         _check(lib.slu_plan_query(self._h, C.byref(i)))
-        self.info = {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+        self.info = _info_dict(i)
         self.n = int(self.info["n"])
         self.opts = None
         return self
@@ -311,12 +336,16 @@ class Plan:
         cpa = (C.c_void_p * k)(*[c.ctypes.data for c in self._cps])
         ria = (C.c_void_p * k)(*[r.ctypes.data for r in self._ris])
         self.opts = default_opts(**opts)
-        _check(lib.slu_analyze_batch(k, _np(na), cpa, ria, C.byref(self.opts),
-                                     C.byref(self._h)))
+        if self.device:
+            _check(lib.slu_analyze_batch_device(k, _np(na), cpa, ria, C.byref(self.opts),
+                                                _stream_ptr(self._stream), C.byref(self._h)))
+        else:
+            _check(lib.slu_analyze_batch(k, _np(na), cpa, ria, C.byref(self.opts),
+                                         C.byref(self._h)))
         self.n = int(na.sum())
         i = PlanInfo()
         _check(lib.slu_plan_query(self._h, C.byref(i)))
-        self.info = {kk: getattr(i, kk) for kk, _ in PlanInfo._fields_}
+        self.info = _info_dict(i)
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -67,8 +67,30 @@ int main(void) {
     slu_plan *bad = (slu_plan *)1;
     CHECK(slu_plan_deserialize(buf, size, &bad) == SLU_ERR_INVALID_ARG && bad == NULL);
 
+    /* the phase times add up to the analysis time */
+    double sum = 0;
+    for (int k = 0; k < SLU_PHASE_COUNT; ++k) {
+        CHECK(info.phase_ms[k] >= 0);
+        sum += info.phase_ms[k];
+    }
+    CHECK(sum <= info.analyze_ms * (1 + 1e-9) + 1e-6);
+
+    /* device analysis: the plan of the host analysis, or SLU_ERR_CUDA when
+     * the process has no GPU */
+    slu_plan *dp = NULL;
+    const slu_status ds = slu_analyze_device(N, colptr, rowidx, &o, NULL, &dp);
+    CHECK(ds == SLU_OK || (ds == SLU_ERR_CUDA && dp == NULL));
+    if (ds == SLU_OK) {
+        uint64_t d3 = 0;
+        CHECK(slu_plan_digest(dp, &d3) == SLU_OK && d3 == d1);
+        slu_plan_destroy(dp);
+    }
+
     /* errors are statuses with a message, never a crash */
     rowidx[1] = N;                              /* row out of range */
+    slu_plan *dr = (slu_plan *)1;
+    CHECK(slu_analyze_device(N, colptr, rowidx, &o, NULL, &dr) == SLU_ERR_INVALID_ARG &&
+          dr == NULL);
     slu_plan *r = (slu_plan *)1;
     CHECK(slu_analyze(N, colptr, rowidx, &o, &r) == SLU_ERR_INVALID_ARG && r == NULL);
     CHECK(strstr(slu_last_error(), "out of range") != NULL);

@@ -117,11 +117,14 @@ def _checksum(payload):
     return h ^ (h >> 31)
 
 
+HEADER = 96      # magic, format, byte order, fingerprint, digest, payload, timings
+
+
 def test_checksum_definition():
     s = workloads.grid5(10)
     P = S.Plan(s.n, s.colptr, s.rowidx)
     b = P.to_bytes()
-    assert struct.unpack_from("<Q", b, 24)[0] == _checksum(b[48:]) == P.digest()
+    assert struct.unpack_from("<Q", b, 24)[0] == _checksum(b[HEADER:]) == P.digest()
 
 
 def test_loader_refuses_inconsistent_plan_with_valid_checksum():
@@ -129,9 +132,9 @@ def test_loader_refuses_inconsistent_plan_with_valid_checksum():
     b = bytearray(S.Plan(s.n, s.colptr, s.rowidx).to_bytes())
     # payload: 72 bytes of options, n, nnz_a, nnz_sym, then A's column
     # pointers (count, then n + 1 values); break the second pointer
-    at = 48 + 72 + 24 + 8 + 8
+    at = HEADER + 72 + 24 + 8 + 8
     struct.pack_into("<q", b, at, 10 ** 9)
-    struct.pack_into("<Q", b, 24, _checksum(bytes(b[48:])))
+    struct.pack_into("<Q", b, 24, _checksum(bytes(b[HEADER:])))
     with pytest.raises(S.SluError) as e:
         S.Plan.from_bytes(bytes(b))
     assert e.value.status == 1 and "invariant" in str(e.value)
