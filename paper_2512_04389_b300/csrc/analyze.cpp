@@ -13,6 +13,7 @@
 //      intra-block column schedules, value maps.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
@@ -217,7 +218,7 @@ void etree(int64_t n, const Sym &S, std::vector<int32_t> &parent) {
 // in increasing order (children always precede their parent), and the
 // columns are finally copied into Lp / Li in column order.
 void symbolic(int64_t n, const Sym &S, const std::vector<int32_t> &par,
-              std::vector<int64_t> &Lp, std::vector<int32_t> &Li) {
+              std::vector<int64_t> &Lp, big_vector<int32_t> &Li) {
     std::vector<int64_t> chp(n + 1, 0);
     for (int64_t j = 0; j < n; ++j)
         if (par[j] >= 0) chp[par[j] + 1]++;
@@ -500,8 +501,8 @@ static slu_status build_blocks(slu_plan &P) {
     }
     P.storage = voff;
     P.lcolptr.assign(coff, 0);
-    P.lrow.assign(roff, 0);
-    P.f2s.assign(P.f_colptr[n], 0);
+    P.lrow.resize(roff);                  // every slot written by pass 2
+    P.f2s.resize(P.f_colptr[n]);
     P.dpos.assign(ndiag_slots, 0);
     // pass 2: local CSC, filled -> storage map, diagonal positions (each
     // block column writes only its own blocks' slots and its own entries)
@@ -675,7 +676,17 @@ static void build_levels_and_tasks(slu_plan &P) {
         maxlev = std::max(maxlev, P.level[I]);
     }
     P.nlevels = maxlev + 1;
+    const int32_t L = P.nlevels;
+    // (K, J) -> block id (-1 if empty): a p x p table when it is small, else
+    // a binary search of column J's blocks (ascending in I)
+    std::vector<int32_t> table;
+    if ((int64_t)p * p <= ((int64_t)1 << 24)) {
+        table.assign((size_t)p * p, -1);
+        for (int64_t b = 0; b < nb; ++b)
+            table[(size_t)P.blocks[b].I * p + P.blocks[b].J] = (int32_t)b;
+    }
     auto find = [&](int32_t K, int32_t J) -> int32_t {
+        if (!table.empty()) return table[(size_t)K * p + J];
         if (K == J) return P.diagblk[J];
         const auto &w = (K > J) ? lower_col[J] : upper_col[J];
         auto it = std::lower_bound(
@@ -684,179 +695,209 @@ static void build_levels_and_tasks(slu_plan &P) {
         if (it != w.end() && P.blocks[*it].I == K) return *it;
         return -1;
     };
-    const int32_t L = P.nlevels;
-    std::vector<std::vector<int32_t>> lv_getrf(L), lv_gessm(L), lv_tstrf(L);
-    // a level's Schur targets; the source pairs of target t are
-    // lv_pairs[lv][2 first .. 2 (first + count)), in the order found
+    // block rows of each level, ascending
+    std::vector<std::vector<int32_t>> rows_of(L);
+    for (int32_t I = 0; I < p; ++I) rows_of[P.level[I]].push_back(I);
+    // tile rows: 128 for FP32 (one tensor-core MMA tile), 64 for FP64;
+    // tile columns: 64
+    const int32_t kTile = P.opts.precision == SLU_PREC_FP32 ? 128 : 64;
+    // The lists of one level depend on nothing built for another level, so
+    // threads take whole levels; the lists are then concatenated in level
+    // order.  Inside a level: Schur targets ordered by (K, J), the source
+    // pairs of a target in the order found (block rows I ascending, then
+    // lower_col[I], then upper_row[I]); the execution split takes first the
+    // targets in a block row or column of the next level (needed by its
+    // GETRF / GESSM / TSTRF), then the rest, and splits each target's pairs
+    // into dense tiles (dense target, dense sources) and the generic rest.
     struct Tgt {
         int32_t K, J, tb;
         int64_t first, count;
     };
-    std::vector<std::vector<Tgt>> lv_ss(L);
-    std::vector<std::vector<int32_t>> lv_pairs(L);
-    std::vector<int32_t> trip;                  // (slot, lb, ub) as found
-    std::vector<int64_t> at;
-    // walk block rows level by level (ascending I inside a level), so that
-    // a target's slot is only ever looked up within its own level
-    std::vector<std::vector<int32_t>> rows_of(L);
-    for (int32_t I = 0; I < p; ++I) rows_of[P.level[I]].push_back(I);
-    std::vector<int32_t> slot(nb, -1);
-    for (int32_t lv = 0; lv < L; ++lv) {
-        auto &vec = lv_ss[lv];
-        trip.clear();
-        for (int32_t I : rows_of[lv]) {
-            const int32_t db = P.diagblk[I];
-            lv_getrf[lv].push_back(db);
-            for (int32_t b : upper_row[I]) {
-                lv_gessm[lv].push_back(b);
-                lv_gessm[lv].push_back(db);
-            }
-            for (int32_t b : lower_col[I]) {
-                lv_tstrf[lv].push_back(b);
-                lv_tstrf[lv].push_back(db);
-            }
-            for (int32_t lb : lower_col[I]) {
-                const int32_t K = P.blocks[lb].I;
-                for (int32_t ub : upper_row[I]) {
-                    const int32_t J = P.blocks[ub].J;
-                    const int32_t tb = find(K, J);
-                    if (tb < 0) continue;
-                    if (slot[tb] < 0) {
-                        slot[tb] = (int32_t)vec.size();
-                        vec.push_back(Tgt{K, J, tb, 0, 0});
+    struct Lvl {                      // indices relative to the level
+        std::vector<int32_t> getrf, gessm, tstrf, gd, gs, tgt, src;
+        std::vector<int64_t> srcend;  // per target, end of its pairs in src
+        std::vector<int32_t> gm_task, gm_src, gg_tgt, gg_src;
+        std::vector<int64_t> gg_srcend;
+        int64_t gm_mid = 0, gg_mid = 0;
+    };
+    std::vector<Lvl> lvl(L);
+    std::atomic<int32_t> next_lv{0};
+    run_threads(std::min<int>(host_threads(nb), std::max(1, L)), [&](int) {
+        std::vector<int32_t> slot(nb, -1), trip, pairs, dense_pairs, other;
+        std::vector<int64_t> at;
+        std::vector<Tgt> vec;
+        for (int32_t lv; (lv = next_lv.fetch_add(1)) < L;) {
+            Lvl &o = lvl[lv];
+            vec.clear();
+            trip.clear();
+            for (int32_t I : rows_of[lv]) {
+                const int32_t db = P.diagblk[I];
+                o.getrf.push_back(db);
+                for (int32_t b : upper_row[I]) {
+                    o.gessm.push_back(b);
+                    o.gessm.push_back(db);
+                }
+                for (int32_t b : lower_col[I]) {
+                    o.tstrf.push_back(b);
+                    o.tstrf.push_back(db);
+                }
+                for (int32_t lb : lower_col[I]) {
+                    const int32_t K = P.blocks[lb].I;
+                    for (int32_t ub : upper_row[I]) {
+                        const int32_t J = P.blocks[ub].J;
+                        const int32_t tb = find(K, J);
+                        if (tb < 0) continue;
+                        if (slot[tb] < 0) {
+                            slot[tb] = (int32_t)vec.size();
+                            vec.push_back(Tgt{K, J, tb, 0, 0});
+                        }
+                        trip.push_back(slot[tb]);
+                        trip.push_back(lb);
+                        trip.push_back(ub);
                     }
-                    trip.push_back(slot[tb]);
-                    trip.push_back(lb);
-                    trip.push_back(ub);
+                }
+            }
+            // group the pairs by target, keeping their order (counting sort)
+            at.assign(vec.size() + 1, 0);
+            for (size_t t = 0; t < trip.size(); t += 3) at[trip[t] + 1]++;
+            for (size_t k = 0; k < vec.size(); ++k) {
+                vec[k].first = at[k];
+                vec[k].count = at[k + 1];
+                at[k + 1] += at[k];
+            }
+            pairs.resize(trip.size() / 3 * 2);
+            for (size_t t = 0; t < trip.size(); t += 3) {
+                const int64_t q = at[trip[t]]++;
+                pairs[2 * q] = trip[t + 1];
+                pairs[2 * q + 1] = trip[t + 2];
+            }
+            for (const Tgt &t : vec) slot[t.tb] = -1;
+            std::sort(vec.begin(), vec.end(), [](const Tgt &x, const Tgt &y) {
+                return x.K != y.K ? x.K < y.K : x.J < y.J;
+            });
+            o.tgt.reserve(vec.size());
+            o.srcend.reserve(vec.size());
+            o.src.reserve(pairs.size());
+            for (const Tgt &t : vec) {
+                o.tgt.push_back(t.tb);
+                o.src.insert(o.src.end(), pairs.begin() + 2 * t.first,
+                             pairs.begin() + 2 * (t.first + t.count));
+                o.srcend.push_back((int64_t)o.src.size() / 2);
+            }
+            for (int32_t db : o.getrf) (P.blocks[db].dense ? o.gd : o.gs).push_back(db);
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1) {
+                    o.gm_mid = (int64_t)o.gm_task.size() / 5;
+                    o.gg_mid = (int64_t)o.gg_tgt.size();
+                }
+                for (size_t k = 0; k < o.tgt.size(); ++k) {
+                    const int32_t tb = o.tgt[k];
+                    const BlockDesc &td = P.blocks[tb];
+                    const bool next = P.level[std::min(td.I, td.J)] == lv + 1;
+                    if (next != (pass == 0)) continue;
+                    dense_pairs.clear();
+                    other.clear();
+                    for (int64_t q = k ? o.srcend[k - 1] : 0; q < o.srcend[k]; ++q) {
+                        const int32_t lb = o.src[2 * q], ub = o.src[2 * q + 1];
+                        auto &to = td.dense && P.blocks[lb].dense && P.blocks[ub].dense
+                                       ? dense_pairs : other;
+                        to.push_back(lb);
+                        to.push_back(ub);
+                    }
+                    if (!dense_pairs.empty()) {
+                        const int32_t s0 = (int32_t)(o.gm_src.size() / 2);
+                        o.gm_src.insert(o.gm_src.end(), dense_pairs.begin(), dense_pairs.end());
+                        const int32_t s1 = (int32_t)(o.gm_src.size() / 2);
+                        for (int32_t r0 = 0; r0 < td.rows; r0 += kTile)
+                            for (int32_t c0 = 0; c0 < td.cols; c0 += 64) {
+                                const int32_t t5[5] = {tb, s0, s1, r0, c0};
+                                o.gm_task.insert(o.gm_task.end(), t5, t5 + 5);
+                            }
+                    }
+                    if (!other.empty()) {
+                        o.gg_tgt.push_back(tb);
+                        o.gg_src.insert(o.gg_src.end(), other.begin(), other.end());
+                        o.gg_srcend.push_back((int64_t)o.gg_src.size() / 2);
+                    }
                 }
             }
         }
-        // group the pairs by target, keeping their order (counting sort)
-        at.assign(vec.size() + 1, 0);
-        for (size_t t = 0; t < trip.size(); t += 3) at[trip[t] + 1]++;
-        for (size_t k = 0; k < vec.size(); ++k) {
-            vec[k].first = at[k];
-            vec[k].count = at[k + 1];
-            at[k + 1] += at[k];
+    });
+    // concatenation in level order (each level's slice copied by a thread
+    // of its own, first touching its pages); offsets per level
+    const int ntc = std::min<int>(host_threads(0), std::max(1, L));
+    auto concat = [&](std::vector<int32_t> Lvl::*f, auto &out, std::vector<int64_t> *off,
+                      int64_t per) {
+        std::vector<int64_t> at(L + 1, 0);
+        for (int32_t lv = 0; lv < L; ++lv) at[lv + 1] = at[lv] + (int64_t)(lvl[lv].*f).size();
+        out.resize((size_t)at[L]);
+        if (off) {
+            off->assign(L + 1, 0);
+            for (int32_t lv = 0; lv <= L; ++lv) (*off)[lv] = at[lv] / per;
         }
-        auto &pairs = lv_pairs[lv];
-        pairs.resize(trip.size() / 3 * 2);
-        for (size_t t = 0; t < trip.size(); t += 3) {
-            const int64_t q = at[trip[t]]++;
-            pairs[2 * q] = trip[t + 1];
-            pairs[2 * q + 1] = trip[t + 2];
-        }
-        for (const Tgt &t : vec) slot[t.tb] = -1;
-    }
-    P.getrf_off.assign(L + 1, 0);
-    P.gessm_off.assign(L + 1, 0);
-    P.tstrf_off.assign(L + 1, 0);
-    P.tgt_off.assign(L + 1, 0);
-    P.getrf.clear();
-    P.gd_off.assign(L + 1, 0);
-    P.gs_off.assign(L + 1, 0);
-    P.gd.clear();
-    P.gs.clear();
-    P.gessm.clear();
-    P.tstrf.clear();
-    P.tgt.clear();
-    P.src.clear();
-    P.srcoff.assign(1, 0);
-    {
-        size_t ntgt = 0, npair = 0;
-        for (int32_t lv = 0; lv < L; ++lv) {
-            ntgt += lv_ss[lv].size();
-            npair += lv_pairs[lv].size();
-        }
-        P.tgt.reserve(ntgt);
-        P.srcoff.reserve(ntgt + 1);
-        P.src.reserve(npair);
-    }
-    for (int32_t lv = 0; lv < L; ++lv) {
-        P.getrf.insert(P.getrf.end(), lv_getrf[lv].begin(), lv_getrf[lv].end());
-        P.gessm.insert(P.gessm.end(), lv_gessm[lv].begin(), lv_gessm[lv].end());
-        P.tstrf.insert(P.tstrf.end(), lv_tstrf[lv].begin(), lv_tstrf[lv].end());
-        auto &vec = lv_ss[lv];
-        std::sort(vec.begin(), vec.end(), [](const Tgt &a, const Tgt &b) {
-            return a.K != b.K ? a.K < b.K : a.J < b.J;
+        std::atomic<int32_t> nx{0};
+        run_threads(ntc, [&](int) {
+            for (int32_t lv; (lv = nx.fetch_add(1)) < L;) {
+                const auto &v = lvl[lv].*f;
+                std::copy(v.begin(), v.end(), out.begin() + at[lv]);
+            }
         });
-        const auto &pairs = lv_pairs[lv];
-        for (auto &t : vec) {
-            P.tgt.push_back(t.tb);
-            P.src.insert(P.src.end(), pairs.begin() + 2 * t.first,
-                         pairs.begin() + 2 * (t.first + t.count));
-            P.srcoff.push_back((int64_t)P.src.size() / 2);
-        }
-        std::vector<int32_t>().swap(lv_pairs[lv]);
-        P.getrf_off[lv + 1] = (int64_t)P.getrf.size();
-        for (int32_t db : lv_getrf[lv]) (P.blocks[db].dense ? P.gd : P.gs).push_back(db);
-        P.gd_off[lv + 1] = (int64_t)P.gd.size();
-        P.gs_off[lv + 1] = (int64_t)P.gs.size();
-        P.gessm_off[lv + 1] = (int64_t)P.gessm.size() / 2;
-        P.tstrf_off[lv + 1] = (int64_t)P.tstrf.size() / 2;
-        P.tgt_off[lv + 1] = (int64_t)P.tgt.size();
-    }
-    // execution split of the SSSSM targets (same updates, same order per
-    // target: the dense tiles of a level run before its generic targets)
-    P.gm_off.assign(L + 1, 0);
-    P.gg_off.assign(L + 1, 0);
-    P.gm_task.clear();
-    P.gm_src.clear();
-    P.gg_tgt.clear();
-    P.gg_src.clear();
+    };
+    concat(&Lvl::getrf, P.getrf, &P.getrf_off, 1);
+    concat(&Lvl::gessm, P.gessm, &P.gessm_off, 2);
+    concat(&Lvl::tstrf, P.tstrf, &P.tstrf_off, 2);
+    concat(&Lvl::gd, P.gd, &P.gd_off, 1);
+    concat(&Lvl::gs, P.gs, &P.gs_off, 1);
+    concat(&Lvl::tgt, P.tgt, &P.tgt_off, 1);
+    concat(&Lvl::src, P.src, nullptr, 1);
+    concat(&Lvl::gg_tgt, P.gg_tgt, &P.gg_off, 1);
+    concat(&Lvl::gg_src, P.gg_src, nullptr, 1);
+    P.srcoff.assign(1, 0);
+    P.srcoff.reserve(P.tgt.size() + 1);
     P.gg_srcoff.assign(1, 0);
-    // tile rows: 128 for FP32 (one tensor-core MMA tile), 64 for FP64;
-    // tile columns: 64
-    const int32_t kTile = P.opts.precision == SLU_PREC_FP32 ? 128 : 64;
+    P.gg_srcoff.reserve(P.gg_tgt.size() + 1);
+    {
+        int64_t sb = 0, gb = 0;
+        for (const Lvl &o : lvl) {
+            for (int64_t e : o.srcend) P.srcoff.push_back(sb + e);
+            for (int64_t e : o.gg_srcend) P.gg_srcoff.push_back(gb + e);
+            sb += (int64_t)o.src.size() / 2;
+            gb += (int64_t)o.gg_src.size() / 2;
+        }
+    }
+    // dense tiles: source pair indices become global
+    P.gm_off.assign(L + 1, 0);
     P.gm_mid.assign(L, 0);
     P.gg_mid.assign(L, 0);
-    std::vector<int32_t> dense_pairs, other;
-    for (int32_t lv = 0; lv < L; ++lv) {
-      // pass 0: targets in a block row or column of the next level (needed
-      // by its GETRF / GESSM / TSTRF); pass 1: the rest, which touch no
-      // block of the next level
-      for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-            P.gm_mid[lv] = (int64_t)P.gm_task.size() / 5;
-            P.gg_mid[lv] = (int64_t)P.gg_tgt.size();
+    {
+        int64_t nt5 = 0, nsrc = 0;
+        for (const Lvl &o : lvl) {
+            nt5 += (int64_t)o.gm_task.size();
+            nsrc += (int64_t)o.gm_src.size();
         }
-        for (int64_t k = P.tgt_off[lv]; k < P.tgt_off[lv + 1]; ++k) {
-            const int32_t tb = P.tgt[k];
-            const BlockDesc &td = P.blocks[tb];
-            const bool next = P.level[std::min(td.I, td.J)] == lv + 1;
-            if (next != (pass == 0)) continue;
-            dense_pairs.clear();
-            other.clear();
-            for (int64_t q = P.srcoff[k]; q < P.srcoff[k + 1]; ++q) {
-                const int32_t lb = P.src[2 * q], ub = P.src[2 * q + 1];
-                if (td.dense && P.blocks[lb].dense && P.blocks[ub].dense) {
-                    dense_pairs.push_back(lb);
-                    dense_pairs.push_back(ub);
-                } else {
-                    other.push_back(lb);
-                    other.push_back(ub);
-                }
+        P.gm_task.resize((size_t)nt5);
+        P.gm_src.resize((size_t)nsrc);
+        int64_t tat = 0, sat = 0;
+        for (int32_t lv = 0; lv < L; ++lv) {
+            const Lvl &o = lvl[lv];
+            const int32_t base = (int32_t)(sat / 2);
+            for (size_t t = 0; t < o.gm_task.size(); t += 5) {
+                int32_t *d = P.gm_task.data() + tat + t;
+                d[0] = o.gm_task[t];
+                d[1] = o.gm_task[t + 1] + base;
+                d[2] = o.gm_task[t + 2] + base;
+                d[3] = o.gm_task[t + 3];
+                d[4] = o.gm_task[t + 4];
             }
-            if (!dense_pairs.empty()) {
-                const int32_t s0 = (int32_t)(P.gm_src.size() / 2);
-                P.gm_src.insert(P.gm_src.end(), dense_pairs.begin(), dense_pairs.end());
-                const int32_t s1 = (int32_t)(P.gm_src.size() / 2);
-                for (int32_t r0 = 0; r0 < td.rows; r0 += kTile)
-                    for (int32_t c0 = 0; c0 < td.cols; c0 += 64) {
-                        const int32_t t5[5] = {tb, s0, s1, r0, c0};
-                        P.gm_task.insert(P.gm_task.end(), t5, t5 + 5);
-                    }
-            }
-            if (!other.empty()) {
-                P.gg_tgt.push_back(tb);
-                P.gg_src.insert(P.gg_src.end(), other.begin(), other.end());
-                P.gg_srcoff.push_back((int64_t)P.gg_src.size() / 2);
-            }
+            std::copy(o.gm_src.begin(), o.gm_src.end(), P.gm_src.begin() + sat);
+            P.gm_mid[lv] = tat / 5 + o.gm_mid;
+            P.gg_mid[lv] = P.gg_off[lv] + o.gg_mid;
+            tat += (int64_t)o.gm_task.size();
+            sat += (int64_t)o.gm_src.size();
+            P.gm_off[lv + 1] = tat / 5;
         }
-      }
-        P.gm_off[lv + 1] = (int64_t)P.gm_task.size() / 5;
-        P.gg_off[lv + 1] = (int64_t)P.gg_tgt.size();
     }
+    std::vector<Lvl>().swap(lvl);
     auto flat = [&](std::vector<std::vector<int32_t>> &v,
                     std::vector<int64_t> &off, std::vector<int32_t> &ids) {
         off.assign(p + 1, 0);
@@ -1094,10 +1135,21 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         P->n = n;
         P->nnz_a = nnz;
         P->a_colptr.assign(colptr, colptr + n + 1);
-        P->a_rowidx.assign(rowidx, rowidx + nnz);
+        // copies by column ranges on the threads (first touch of the pages)
+        P->a_rowidx.resize(nnz);
         P->a_ci.resize(nnz);
-        for (int64_t j = 0; j < n; ++j)
-            for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) P->a_ci[q] = (int32_t)j;
+        {
+            const int nt = host_threads(0);
+            const std::vector<int64_t> cut =
+                balanced_cuts(n, [&](int64_t j) { return colptr[j]; }, nt);
+            run_threads(nt, [&](int t) {
+                for (int64_t j = cut[t]; j < cut[t + 1]; ++j)
+                    for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
+                        P->a_rowidx[q] = rowidx[q];
+                        P->a_ci[q] = (int32_t)j;
+                    }
+            });
+        }
         // CSR view of A for the residual (columns ascending in every row)
         P->a_rowptr.assign(n + 1, 0);
         P->a_colidx.resize(nnz);
@@ -1117,8 +1169,8 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
         // A's columns with rows ascending and their input positions: the
         // transpose of the CSR view, taken in row order
         std::vector<int64_t> sp(n + 1, 0);
-        std::vector<int32_t> si(nnz);
-        std::vector<int64_t> sq(nnz);
+        big_vector<int32_t> si(nnz);
+        big_vector<int64_t> sq(nnz);
         stable_transpose(
             n, P->a_rowptr.data(), n, [&](int64_t t) { return P->a_colidx[t]; },
             [&](int64_t j, int64_t c) { sp[j + 1] = c; },
@@ -1156,7 +1208,7 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
             mark(SLU_PHASE_SYMBOLIC);
         } else {
             std::vector<int64_t> Lp;
-            std::vector<int32_t> Li;
+            big_vector<int32_t> Li;
             {
                 Sym S;
                 symmetrize(n, sp.data(), si.data(), P->a_rowptr.data(),
@@ -1197,7 +1249,7 @@ static slu_status analyze_impl(int64_t n, const int64_t *colptr,
                 P->flops += l + 2 * l * l;
             }
             std::vector<int64_t>().swap(Lp);
-            std::vector<int32_t>().swap(Li);
+            big_vector<int32_t>().swap(Li);
             mark(SLU_PHASE_SYMBOLIC);
             // Algorithm 2 on the filled pattern
             P->blockptr.assign(n + 1, 0);
@@ -1466,7 +1518,7 @@ extern "C" slu_status slu_plan_export_tasks(
     int32_t *tgt, int64_t *srcoff, int32_t *src) {
     if (!P) return fail(SLU_ERR_INVALID_ARG, "NULL plan");
     const auto &B = P->blocks;
-    auto cp = [](int64_t *dst, const std::vector<int64_t> &v) {
+    auto cp = [](int64_t *dst, const auto &v) {
         if (dst) std::memcpy(dst, v.data(), v.size() * 8);
     };
     cp(getrf_off, P->getrf_off);

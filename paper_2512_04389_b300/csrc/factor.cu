@@ -2158,8 +2158,8 @@ k_factor_persistent(PersistArgs p, T *val, T *winv) {
 
 // ---------------------------------------------------------------- host side
 
-template <typename V>
-static bool upload(const std::vector<V> &h, V **d) {
+template <typename V, typename A>
+static bool upload(const std::vector<V, A> &h, V **d) {
     *d = nullptr;
     if (h.empty()) return true;
     if (!cuda_ok(cudaMalloc(d, h.size() * sizeof(V)), "cudaMalloc(plan)"))

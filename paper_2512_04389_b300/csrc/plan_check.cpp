@@ -24,8 +24,8 @@ using namespace slu;
 namespace slu {
 namespace {
 
-template <class V>
-bool offsets(const std::vector<V> &v, size_t size, int64_t last) {
+template <class V, class A>
+bool offsets(const std::vector<V, A> &v, size_t size, int64_t last) {
     if (v.size() != size || (size && (v.front() != 0 || (int64_t)v.back() != last)))
         return false;
     for (size_t i = 1; i < v.size(); ++i)
@@ -412,7 +412,7 @@ std::string coverage_violation(const slu_plan &P) {
             ++pg[key(1, P.pg_tstrf[2 * t], P.pg_tstrf[2 * t + 1])];
         size_t npanel = 0;
         for (int type = 0; type < 2; ++type) {
-            const std::vector<int32_t> &task = type == 0 ? P.gessm : P.tstrf;
+            const auto &task = type == 0 ? P.gessm : P.tstrf;
             const std::vector<int64_t> &off = type == 0 ? P.gessm_off : P.tstrf_off;
             for (int64_t e = off[lv]; e < off[lv + 1]; ++e) {
                 const int32_t tb = task[2 * e], db = task[2 * e + 1];
@@ -436,7 +436,7 @@ std::string coverage_violation(const slu_plan &P) {
         for (int64_t k = P.tgt_off[lv]; k < P.tgt_off[lv + 1]; ++k)
             for (int64_t q = P.srcoff[k]; q < P.srcoff[k + 1]; ++q)
                 wantp.push_back({P.tgt[k], P.src[2 * q], P.src[2 * q + 1]});
-        auto ascending = [&](const std::vector<int32_t> &sr, int64_t q0, int64_t q1) {
+        auto ascending = [&](const auto &sr, int64_t q0, int64_t q1) {
             for (int64_t q = q0 + 1; q < q1; ++q)
                 if (B[sr[2 * q]].J <= B[sr[2 * q - 2]].J) return false;
             return true;

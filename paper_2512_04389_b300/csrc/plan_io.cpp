@@ -126,8 +126,8 @@ void put(S &s, const slu_opts &o) {     // member by member: no padding bytes
     put(s, o.pivot_tau_rel); put(s, o.refine_tol); put(s, o.refine_max_iter);
     put(s, o.wait_budget_ms); put(s, o.tc_passes);
 }
-template <class S, class T>
-void put(S &s, const std::vector<T> &v) {   // element types have no padding
+template <class S, class T, class A>
+void put(S &s, const std::vector<T, A> &v) {   // element types have no padding
     const int64_t c = (int64_t)v.size();
     put(s, c);
     s.raw(v.data(), v.size() * sizeof(T));
@@ -148,8 +148,8 @@ void get(Reader &r, slu_opts &o) {
     get(r, o.pivot_tau_rel); get(r, o.refine_tol); get(r, o.refine_max_iter);
     get(r, o.wait_budget_ms); get(r, o.tc_passes);
 }
-template <class T>
-void get(Reader &r, std::vector<T> &v) {
+template <class T, class A>
+void get(Reader &r, std::vector<T, A> &v) {
     int64_t c = 0;
     get(r, c);
     if (!r.ok || c < 0 || (uint64_t)c > r.left() / sizeof(T)) {
@@ -165,7 +165,8 @@ void get(Reader &r, T (&a)[N]) {
 }
 
 template <class T> uint64_t elem_size(const T &) { return sizeof(T); }
-template <class T> uint64_t elem_size(const std::vector<T> &) { return 1000 + sizeof(T); }
+template <class T, class A>
+uint64_t elem_size(const std::vector<T, A> &) { return 1000 + sizeof(T); }
 template <class T, size_t N> uint64_t elem_size(const T (&a)[N]) {
     return N * 1000000 + elem_size(a[0]);
 }

@@ -18,7 +18,9 @@
 // diagonal) of its rows and columns.
 #pragma once
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/slu.h"
@@ -42,6 +44,31 @@ static_assert(sizeof(BlockDesc) == 64, "BlockDesc layout");
 
 struct DevPlan;            // device mirror, defined in device_common.cuh
 
+// Allocator of the plan's pattern-sized arrays: resize() leaves the new
+// elements uninitialized, so that the (threaded) pass that writes every one
+// of them is the first to touch their pages; explicit values (assign,
+// resize(n, v)) are stored as usual.
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = UninitAlloc<U>;
+    };
+    UninitAlloc() = default;
+    template <class U>
+    UninitAlloc(const UninitAlloc<U> &) noexcept {}
+    template <class U>
+    void construct(U *p) noexcept {
+        ::new (static_cast<void *>(p)) U;
+    }
+    template <class U, class... A>
+    void construct(U *p, A &&...a) {
+        ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using big_vector = std::vector<T, UninitAlloc<T>>;
+
 }  // namespace slu
 
 // Vectors per warp of the dense-panel substitution kernel: lane v owns
@@ -63,14 +90,14 @@ struct slu_plan {
     double phase_ms[SLU_PHASE_COUNT] = {};
     // input pattern (copied) and its CSR view for the FP64 residual
     std::vector<int64_t> a_colptr;
-    std::vector<int32_t> a_rowidx;
+    slu::big_vector<int32_t> a_rowidx;
     std::vector<int64_t> a_rowptr;       // CSR of A
-    std::vector<int32_t> a_colidx;
-    std::vector<int64_t> a_vpos;         // CSR entry -> position in values
-    std::vector<int32_t> a_ci;           // column of each CSC entry of A
+    slu::big_vector<int32_t> a_colidx;
+    slu::big_vector<int64_t> a_vpos;     // CSR entry -> position in values
+    slu::big_vector<int32_t> a_ci;       // column of each CSC entry of A
     // filled, structurally symmetric L+U pattern (rows sorted)
     std::vector<int64_t> f_colptr;
-    std::vector<int32_t> f_rowidx;
+    slu::big_vector<int32_t> f_rowidx;
     int64_t flops = 0;
     double flops_cls[3] = {0, 0, 0};     // getrf, panel, ssssm
     // blocking
@@ -86,7 +113,7 @@ struct slu_plan {
     std::vector<int64_t> bnnz;
     std::vector<int32_t> diagblk;        // I -> block id of (I, I)
     std::vector<int32_t> lcolptr;
-    std::vector<uint16_t> lrow;
+    slu::big_vector<uint16_t> lrow;
     std::vector<int32_t> dpos, sched, sgrp;
     // strict lower part of each sparse diagonal block by rows: row r of
     // diagonal block I spans [lr_ptr[doff + I + r], lr_ptr[doff + I + r + 1])
@@ -115,20 +142,20 @@ struct slu_plan {
     // GETRF list: with explicit inverses (dv) and without (dn)
     std::vector<int64_t> dv_off, dn_off;
     std::vector<int32_t> dv_pos, dn_pos;
-    std::vector<int32_t> gessm;          // pairs (blk(I,J), blk(I,I))
-    std::vector<int32_t> tstrf;          // pairs (blk(J,I), blk(I,I))
-    std::vector<int32_t> tgt;            // target block ids
-    std::vector<int64_t> srcoff;         // per target, into src pairs
-    std::vector<int32_t> src;            // pairs (blk(K,I), blk(I,J))
+    slu::big_vector<int32_t> gessm;      // pairs (blk(I,J), blk(I,I))
+    slu::big_vector<int32_t> tstrf;      // pairs (blk(J,I), blk(I,I))
+    slu::big_vector<int32_t> tgt;        // target block ids
+    slu::big_vector<int64_t> srcoff;     // per target, into src pairs
+    slu::big_vector<int32_t> src;        // pairs (blk(K,I), blk(I,J))
     // execution split of SSSSM per level: dense tiles (dense target, dense
     // sources) and the generic remainder
     std::vector<int64_t> gm_off;         // per level, into gm_task
-    std::vector<int32_t> gm_task;        // 5 per tile: tgt, s0, s1, r0, c0
-    std::vector<int32_t> gm_src;         // pairs (blk(K,I), blk(I,J))
+    slu::big_vector<int32_t> gm_task;    // 5 per tile: tgt, s0, s1, r0, c0
+    slu::big_vector<int32_t> gm_src;     // pairs (blk(K,I), blk(I,J))
     std::vector<int64_t> gg_off;         // per level, into gg_tgt
-    std::vector<int32_t> gg_tgt;
+    slu::big_vector<int32_t> gg_tgt;
     std::vector<int64_t> gg_srcoff;
-    std::vector<int32_t> gg_src;
+    slu::big_vector<int32_t> gg_src;
     // per level, the first gm / gg entry of the deferred part: targets whose
     // block row and column both lie beyond the next level (they may run
     // while the next level factors its diagonal blocks and panels)
@@ -173,8 +200,8 @@ struct slu_plan {
     std::vector<int32_t> ucol_blk;       // (I', I), I' < I
     std::vector<int32_t> lcol_blk;       // (K, I),  K > I
     // value maps
-    std::vector<int64_t> a2s;            // A entry -> storage slot
-    std::vector<int64_t> f2s;            // filled entry -> storage slot
+    slu::big_vector<int64_t> a2s;        // A entry -> storage slot
+    slu::big_vector<int64_t> f2s;        // filled entry -> storage slot
     // device mirror (lazily uploaded)
     slu::DevPlan *dev = nullptr;
 };

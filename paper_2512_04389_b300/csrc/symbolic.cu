@@ -48,7 +48,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "slu_internal.hpp"
@@ -530,18 +532,111 @@ slu_status dev_sort(Ctx &cx, uint64_t **keys, uint64_t **alt, int64_t m, int bit
     return SLU_OK;
 }
 
-template <class T>
-slu_status to_host(Ctx &cx, std::vector<T> &dst, const T *src, int64_t count) {
+// Copies between pageable host memory and the device through two pinned
+// staging buffers (kept for the process, grown on demand): the DMA of one
+// chunk overlaps the threaded host copy of the previous one, and the host
+// threads touch the pageable pages in parallel.
+struct Staging {
+    std::mutex mu;
+    void *buf[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    size_t bytes = 0;
+};
+Staging &staging() {
+    static Staging *s = new Staging();          // outlives every caller
+    return *s;
+}
+constexpr size_t kChunk = (size_t)32 << 20;
+
+void par_copy(void *dst, const void *src, size_t bytes) {
+    const int nt = (int)std::min<size_t>(
+        std::min<size_t>(16, std::max(1u, std::thread::hardware_concurrency())),
+        std::max<size_t>(1, bytes >> 21));
+    const size_t per = (bytes / nt + 4095) & ~(size_t)4095;
+    std::vector<std::thread> th;
+    try {
+        for (int t = 1; t < nt && per * t < bytes; ++t)
+            th.emplace_back([=] {
+                const size_t a = per * t, e = std::min(bytes, per * (t + 1));
+                std::memcpy(static_cast<char *>(dst) + a, static_cast<const char *>(src) + a, e - a);
+            });
+    } catch (const std::exception &) {
+    }
+    const size_t done = per * (th.size() + 1);
+    std::memcpy(dst, src, std::min(bytes, per));
+    if (done < bytes)
+        std::memcpy(static_cast<char *>(dst) + done, static_cast<const char *>(src) + done,
+                    bytes - done);
+    for (auto &x : th) x.join();
+}
+
+// host (pageable) <-> device through the staging buffers; returns after
+// the copy has finished
+slu_status staged_copy(Ctx &cx, void *dst, const void *src, size_t bytes, bool to_device) {
+    if (bytes == 0) return SLU_OK;
+    Staging &sg = staging();
+    std::lock_guard<std::mutex> lock(sg.mu);
+    if (!sg.buf[0]) {
+        for (int k = 0; k < 2; ++k)
+            if (cudaHostAlloc(&sg.buf[k], kChunk, cudaHostAllocDefault) != cudaSuccess ||
+                cudaEventCreateWithFlags(&sg.ev[k], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                for (int j = 0; j < 2; ++j) {
+                    if (sg.buf[j]) cudaFreeHost(sg.buf[j]);
+                    if (sg.ev[j]) cudaEventDestroy(sg.ev[j]);
+                    sg.buf[j] = nullptr;
+                    sg.ev[j] = nullptr;
+                }
+                return fail(SLU_ERR_OUT_OF_MEMORY, "pinned staging allocation in analyze");
+            }
+        sg.bytes = kChunk;
+    }
+    const size_t nchunk = (bytes + kChunk - 1) / kChunk;
+    auto len = [&](size_t c) { return std::min(kChunk, bytes - c * kChunk); };
+    char *d = static_cast<char *>(dst);
+    const char *s = static_cast<const char *>(src);
+    if (to_device) {
+        // host copy of chunk c into buffer c % 2 (after the DMA of chunk
+        // c - 2 out of it finished), then its DMA
+        for (size_t c = 0; c < nchunk; ++c) {
+            const int k = (int)(c & 1);
+            if (c >= 2 && cudaEventSynchronize(sg.ev[k]) != cudaSuccess)
+                return cuda_err("copy to device");
+            par_copy(sg.buf[k], s + c * kChunk, len(c));
+            if (cudaMemcpyAsync(d + c * kChunk, sg.buf[k], len(c), cudaMemcpyHostToDevice,
+                                cx.st) != cudaSuccess ||
+                cudaEventRecord(sg.ev[k], cx.st) != cudaSuccess)
+                return cuda_err("copy to device");
+        }
+        if (cudaStreamSynchronize(cx.st) != cudaSuccess) return cuda_err("copy to device");
+        return SLU_OK;
+    }
+    // DMA of chunk c into buffer c % 2, then the host copy of chunk c - 1
+    for (size_t c = 0; c <= nchunk; ++c) {
+        if (c < nchunk) {
+            const int k = (int)(c & 1);
+            if (cudaMemcpyAsync(sg.buf[k], s + c * kChunk, len(c), cudaMemcpyDeviceToHost,
+                                cx.st) != cudaSuccess ||
+                cudaEventRecord(sg.ev[k], cx.st) != cudaSuccess)
+                return cuda_err("copy to host");
+        }
+        if (c > 0) {
+            const int k = (int)((c - 1) & 1);
+            if (cudaEventSynchronize(sg.ev[k]) != cudaSuccess) return cuda_err("copy to host");
+            par_copy(d + (c - 1) * kChunk, sg.buf[k], len(c - 1));
+        }
+    }
+    return SLU_OK;
+}
+
+template <class T, class A>
+slu_status to_host(Ctx &cx, std::vector<T, A> &dst, const T *src, int64_t count) {
     try {
         dst.resize((size_t)count);
     } catch (const std::exception &) {
         return fail(SLU_ERR_OUT_OF_MEMORY, "host allocation in analyze");
     }
-    if (count > 0 &&
-        cudaMemcpyAsync(dst.data(), src, sizeof(T) * (size_t)count,
-                        cudaMemcpyDeviceToHost, cx.st) != cudaSuccess)
-        return cuda_err("copy to host");
-    return SLU_OK;
+    return staged_copy(cx, dst.data(), src, sizeof(T) * (size_t)count, false);
 }
 
 template <class T>
@@ -573,14 +668,12 @@ slu_status symbolic_on_device(Ctx &cx, int64_t n, const int64_t *colptr,
     const int64_t m = 2 * nnz + n;
     uint64_t *ka = cx.ar.get<uint64_t>(m), *kb = cx.ar.get<uint64_t>(m);
     if (!dcp || !dri || !ka || !kb) return fail(SLU_ERR_OUT_OF_MEMORY, "device allocation in analyze");
-    if (cudaMemcpyAsync(dcp, colptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, cx.st) !=
-            cudaSuccess ||
-        (nnz > 0 && cudaMemcpyAsync(dri, rowidx, sizeof(int32_t) * nnz,
-                                    cudaMemcpyHostToDevice, cx.st) != cudaSuccess))
-        return cuda_err("copy to device");
+    slu_status s = staged_copy(cx, dcp, colptr, sizeof(int64_t) * (n + 1), true);
+    if (s == SLU_OK) s = staged_copy(cx, dri, rowidx, sizeof(int32_t) * nnz, true);
+    if (s != SLU_OK) return s;
     k_sym_keys<<<cx.grid(32 * n, 32), kThreads, 0, cx.st>>>(n, dcp, dri, b, ka);
     SLU_DEV_CHECK("symmetric pattern");
-    slu_status s = dev_sort(cx, &ka, &kb, m, bits);
+    s = dev_sort(cx, &ka, &kb, m, bits);
     if (s != SLU_OK) return s;
     cx.ar.drop(dcp);
     cx.ar.drop(dri);
