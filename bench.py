@@ -404,7 +404,7 @@ def circuit_leg(torch, S, dev, args):
     FP32 factors + FP64 refinement to backward error <= 1e-14 against the
     plain FP64 factorization, and the FP32 leg with regular 128-row
     blocking.  The options are the best of one-off sweeps on B300 (tuning
-    here would repeat the 6-8 s host analysis per candidate): sparse/dense
+    here would repeat the 2-4 s analysis per candidate): sparse/dense
     threshold 0.02 for FP32 and 0.05 for FP64; FP32 irregular blocking with
     S = n / 128 samples (tile-aligned spacing), max_num 1, and both FP32
     legs with one TF32 pass on the tensor cores (the border is a dense
@@ -420,8 +420,17 @@ def circuit_leg(torch, S, dev, args):
         t0 = time.perf_counter()
         thr = 0.02 if prec == "fp32" else 0.05
         P = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=thr,
-                   **extra)
+                   device=True, **extra)
         ana = time.perf_counter() - t0
+        if leg == "fp32":           # the host analysis of the same plan, once
+            t0 = time.perf_counter()
+            PH = S.Plan(s.n, s.colptr, s.rowidx, precision=prec, dense_threshold=thr,
+                        **extra)
+            out["analysis"] = {"device_s": ana, "device_phase_ms": P.info["phase_ms"],
+                               "host_s": time.perf_counter() - t0,
+                               "host_phase_ms": PH.info["phase_ms"],
+                               "same_plan": PH.digest() == P.digest()}
+            del PH
         F = S.Factor(P, v)
 
         def step():
@@ -555,7 +564,16 @@ def main():
     # sparse/dense switch picked by the autotuner (cached per pattern)
     best64, tun64 = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
                          precision=args.precision)
-    plan = S.Plan(s.n, s.colptr, s.rowidx, precision=args.precision, **best64)
+    # the plan from the device analysis (symbolic factorization and
+    # Algorithms 2 / 3 on the GPU); the host analysis gives the same plan
+    plan = S.Plan(s.n, s.colptr, s.rowidx, precision=args.precision, device=True, **best64)
+    host_plan = S.Plan(s.n, s.colptr, s.rowidx, precision=args.precision, **best64)
+    assert host_plan.digest() == plan.digest()
+    analysis = {"device_ms": plan.info["analyze_ms"],
+                "device_phase_ms": plan.info["phase_ms"],
+                "host_ms": host_plan.info["analyze_ms"],
+                "host_phase_ms": host_plan.info["phase_ms"]}
+    del host_plan
     fl = step_flops(plan, s.nrhs)
     F = S.Factor(plan, vals_d)
 
@@ -592,7 +610,7 @@ def main():
                       "flops_factor": plan.info["flops"],
                       "blocks_1d": plan.info["nblocks_1d"],
                       "levels": plan.info["nlevels"],
-                      "analyze_ms": plan.info["analyze_ms"],
+                      "analyze_ms": plan.info["analyze_ms"], "analysis": analysis,
                       "factor_ms": ms_factor, "solve_ms": ms_solve,
                       "tuned": best64, "tuning_ms": tun64,
                       "backward_error": sinfo["backward_error"],

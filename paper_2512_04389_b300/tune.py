@@ -159,7 +159,8 @@ def tune(n, colptr, rowidx, values, rhs, cands=None, reps=2, use_cache=True,
             if k in timings:
                 ms = timings[k]
             else:
-                P = S.Plan(n, colptr, rowidx, **opts, **c)
+                # the device analysis gives the host analysis's plan, faster
+                P = S.Plan(n, colptr, rowidx, device=True, **opts, **c)
                 F = S.Factor(P, values)
                 F.solve(rhs)
                 torch.cuda.synchronize()
