@@ -488,6 +488,25 @@ slu_status slu_persistent_tasks(const slu_handle *h, int32_t *tasks, int64_t cap
 slu_status slu_set_persistent_tasks(slu_handle *h, const int32_t *tasks,
                                     int64_t count);
 
+/* Persistent solve: every sweep of slu_solve, slu_solve_transpose and the
+ * refinement runs as ONE launch per four right-hand sides instead of two
+ * per level.  Persistent CTAs take tasks in the order of a work list built
+ * on the host at the first solve -- per level, in the sweep's order, the
+ * pulls of already solved blocks into the level's blocks (one per source
+ * block and row chunk), then the level's diagonal blocks -- and before each
+ * task wait until what it reads is done (device-side counters, acquire and
+ * release at GPU scope: a pull waits for the block row whose solution it
+ * reads, a diagonal block for every pull into it).  A block therefore
+ * starts as soon as its own sources are solved, with no barrier per level.
+ * Each wait is bounded by opts.wait_budget_ms; one that runs out stops the
+ * launch, and the next solve that synchronizes (refinement, or info
+ * requested) reports SLU_ERR_TIMEOUT.  The solutions are bit for bit those
+ * of the per-level launches (same operations in the same order).  Supported
+ * when every diagonal block has explicit inverses (dense and at most 384
+ * rows, e.g. dense_threshold 0), else SLU_ERR_NOT_SUPPORTED; enable = 0
+ * returns to the per-level launches. */
+slu_status slu_set_persistent_solve(slu_handle *h, int32_t enable);
+
 /* Profiling: while enabled, every kernel launch of the handle is bracketed
  * by a pair of CUDA events on its stream, and slu_handle_stats sums their
  * durations per kernel class (it synchronizes on every recorded event).  Enabling

@@ -202,6 +202,27 @@ __device__ void unstage_block(const BlockDesc &d, const BlockArgs &a,
     for (int64_t e = threadIdx.x; e < nnz; e += blockDim.x) val[d.voff + e] = v.v[e];
 }
 
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One thread: *c >= need within budget_ns (and 2^26 polls)?  The load is
+// an acquire at GPU scope: what the counter's writers stored before their
+// release is visible after it.
+__device__ __forceinline__ bool wait_count(const int *c, int need, long long budget_ns) {
+    const long long t0 = global_ns();
+    for (int it = 0; it < (1 << 26); ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+        if (v >= need) return true;
+        if (global_ns() - t0 > budget_ns) return false;
+        __nanosleep(128);
+    }
+    return false;
+}
+
 inline bool cuda_ok(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return true;
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -275,6 +296,19 @@ struct slu_handle {
     int32_t *ptasks = nullptr;
     int *pdone = nullptr;               // pcounters counters, then the ticket
     int64_t pntasks = 0, pcap = 0, pcounters = 0;
+    // persistent solve: one work list per sweep (kStInts ints per task),
+    // the counters of a sweep (2 p) and its ticket, on the handle's device
+    // (levels run concurrently, so each sweep's partial sums get offsets
+    // of their own: spoff, into spart of spart_elems doubles)
+    bool persistent_solve = false;
+    int32_t *stasks[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t *spoff[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t sntasks[4] = {0, 0, 0, 0};
+    int *sdone = nullptr;
+    double *spart = nullptr;
+    int64_t spart_elems = 0;
+    int sgrid[4] = {0, 0, 0, 0};        // persistent CTAs and shared memory
+    size_t ssmem[4] = {0, 0, 0, 0};     // per sweep (set up when enabled)
 };
 
 namespace slu {

@@ -2046,25 +2046,6 @@ constexpr int kPtInts = 7;   // kind, idx, wait1, need1, wait2, need2, done
 template <typename T>
 __host__ __device__ constexpr size_t persist_smem() { return sizeof(T) == 4 ? 108 * 1024 : kStageSmem; }
 
-__device__ __forceinline__ long long global_ns() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// One thread: *c >= need within budget_ns (and 2^26 polls)?
-__device__ __forceinline__ bool wait_count(const int *c, int need, long long budget_ns) {
-    const long long t0 = global_ns();
-    for (int it = 0; it < (1 << 26); ++it) {
-        int v;
-        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
-        if (v >= need) return true;
-        if (global_ns() - t0 > budget_ns) return false;
-        __nanosleep(128);
-    }
-    return false;
-}
-
 struct PersistArgs {
     const int32_t *tasks;               // kPtInts per task
     int ntasks;
@@ -2532,7 +2513,9 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red,
-                    h->part, h->anorm_seg, h->winv, h->ptasks, h->pdone};
+                    h->part, h->anorm_seg, h->winv, h->ptasks, h->pdone,
+                    h->stasks[0], h->stasks[1], h->stasks[2], h->stasks[3], h->sdone,
+                    h->spoff[0], h->spoff[1], h->spoff[2], h->spoff[3], h->spart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (cur >= 0) cudaSetDevice(cur);

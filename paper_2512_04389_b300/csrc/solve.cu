@@ -16,6 +16,7 @@
 // recorded once per right-hand-side count as a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
+#include <exception>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -31,23 +32,29 @@ __device__ __forceinline__ C warp_sum(C v) {
 }
 
 constexpr int RC = 4;   // right-hand sides processed together
+
+// Loads of solution values and partial sums: read-only during a per-level
+// launch (__ldg), but written by other CTAs of the same launch in the
+// persistent sweep (COH: from L2, where those stores and atomics land).
+template <bool COH, typename V>
+__device__ __forceinline__ V ld_in(const V *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
 constexpr int kDenseRows = 64;   // rows of a dense source per pull CTA
 enum Sweep { FWD = 0, BWD = 1, FWD_T = 2, BWD_T = 3 };
 
 // Pull, scatter form (L y = b and U x = y): one CTA per source block B of
 // the level (rows = the diagonal block's rows); part = B * x(B's columns),
 // m x RC, reduced from per-warp partials in a fixed order.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_pull_scatter(const int32_t *__restrict__ pairs,
-               const int64_t *__restrict__ poff, BlockArgs a,
-               const T *__restrict__ val, const double *__restrict__ X,
-               int64_t ldx, int nc, double *__restrict__ part_d,
-               int rows_per_chunk) {
+template <typename T, bool COH>
+__device__ __forceinline__ void pull_scatter_body(
+    const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff, const BlockArgs &a,
+    const T *__restrict__ val, const double *X, int64_t ldx, int nc, double *part_d,
+    int rows_per_chunk, int qi, int yi, unsigned char *smem) {
     using C = T;
     C *part = reinterpret_cast<C *>(part_d);
-    extern __shared__ __align__(16) unsigned char smem[];
-    const BlockDesc db = a.bd[pairs[2 * blockIdx.x]];
+    const BlockDesc db = a.bd[pairs[2 * qi]];
     const int m = db.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     C *pw = reinterpret_cast<C *>(smem);
     constexpr int VW = 16 / sizeof(T);                  // rows per vector load
@@ -60,13 +67,13 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
         using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
         constexpr int NRG = kDenseRows / VW;            // row groups per chunk
         constexpr int NCG = kThreads / NRG;             // column slices
-        const int rbase = blockIdx.y * kDenseRows;
+        const int rbase = yi * kDenseRows;
         if (rbase >= m) return;
         C *xs = pw;                                     // cols x RC
         C *red = pw + (size_t)db.cols * RC;             // NCG x kDenseRows x RC
         for (int t = threadIdx.x; t < db.cols * RC; t += kThreads) {
             const int k = t / RC, c = t % RC;
-            xs[t] = c < nc ? X[(int64_t)c * ldx + db.c0 + k] : 0.0;
+            xs[t] = c < nc ? ld_in<COH>(X + (int64_t)c * ldx + db.c0 + k) : 0.0;
         }
         __syncthreads();
         const int rg = threadIdx.x % NRG, cg = threadIdx.x / NRG;
@@ -105,7 +112,7 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
             for (int c = 0; c < RC; ++c)
                 red[((size_t)cg * RC + c) * kDenseRows + rg * VW + i] = acc[i][c];
         __syncthreads();
-        C *out = part + poff[blockIdx.x] * RC;
+        C *out = part + poff[qi] * RC;
         const int mr = min(kDenseRows, m - rbase);
         for (int t = threadIdx.x; t < mr * RC; t += kThreads) {
             const int r = t % mr, c = t / mr;
@@ -115,8 +122,8 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
         }
         return;
     }
-    // rows [rc0, rc0 + mc) of the partial (one chunk per blockIdx.y)
-    const int mc = min(m, rows_per_chunk), rc0 = blockIdx.y * rows_per_chunk;
+    // rows [rc0, rc0 + mc) of the partial (chunk yi)
+    const int mc = min(m, rows_per_chunk), rc0 = yi * rows_per_chunk;
     if (rc0 >= m) return;
     const int mr = min(mc, m - rc0);
     for (int t = threadIdx.x; t < kWarps * mc * RC; t += kThreads) pw[t] = 0.0;
@@ -127,7 +134,7 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
         bool any = false;
 #pragma unroll
         for (int c = 0; c < RC; ++c) {
-            xv[c] = c < nc ? X[(int64_t)c * ldx + db.c0 + jj] : 0.0;
+            xv[c] = c < nc ? ld_in<COH>(X + (int64_t)c * ldx + db.c0 + jj) : 0.0;
             any |= xv[c] != 0.0;
         }
         if (any) {
@@ -147,7 +154,7 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
         __syncwarp();
     }
     __syncthreads();
-    C *out = part + poff[blockIdx.x] * RC;
+    C *out = part + poff[qi] * RC;
     for (int t = threadIdx.x; t < mr * RC; t += kThreads) {
         const int r = t % mr, c = t / mr;
         C sum = 0.0;
@@ -156,19 +163,30 @@ k_pull_scatter(const int32_t *__restrict__ pairs,
     }
 }
 
-// Pull, dot form (U^T z = g and L^T lam = z): one CTA per source block B
-// (columns = the diagonal block's columns); part(ii) = B(:, ii) . x(B's rows).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
-           BlockArgs a, const T *__restrict__ val,
-           const double *__restrict__ X, int64_t ldx, int nc,
-           double *__restrict__ part_d) {
+k_pull_scatter(const int32_t *__restrict__ pairs,
+               const int64_t *__restrict__ poff, BlockArgs a,
+               const T *__restrict__ val, const double *__restrict__ X,
+               int64_t ldx, int nc, double *__restrict__ part_d,
+               int rows_per_chunk) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    pull_scatter_body<T, false>(pairs, poff, a, val, X, ldx, nc, part_d, rows_per_chunk,
+                                (int)blockIdx.x, (int)blockIdx.y, smem);
+}
+
+// Pull, dot form (U^T z = g and L^T lam = z): one CTA per source block B
+// (columns = the diagonal block's columns); part(ii) = B(:, ii) . x(B's rows).
+template <typename T, bool COH>
+__device__ __forceinline__ void pull_dot_body(
+    const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff, const BlockArgs &a,
+    const T *__restrict__ val, const double *X, int64_t ldx, int nc, double *part_d,
+    int qi) {
     using C = T;
     C *part = reinterpret_cast<C *>(part_d);
-    const BlockDesc db = a.bd[pairs[2 * blockIdx.x]];
+    const BlockDesc db = a.bd[pairs[2 * qi]];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    C *out = part + poff[blockIdx.x] * RC;
+    C *out = part + poff[qi] * RC;
     constexpr int VW = 16 / sizeof(T);
     if (db.dense && db.ld % VW == 0) {
         // dense: thread per column, streaming its contiguous column with
@@ -183,7 +201,7 @@ k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
                 __syncthreads();
                 for (int t = threadIdx.x; t < nr * RC; t += kThreads) {
                     const int r = t / RC, c = t % RC;
-                    xs[t] = c < nc ? X[(int64_t)c * ldx + db.r0 + r0 + r] : 0.0;
+                    xs[t] = c < nc ? ld_in<COH>(X + (int64_t)c * ldx + db.r0 + r0 + r) : 0.0;
                 }
                 __syncthreads();
                 if (ii < db.cols) {
@@ -227,12 +245,21 @@ k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
             const int64_t r = db.r0 + rowat(rows, e);
 #pragma unroll
             for (int c = 0; c < RC; ++c)
-                if (c < nc) sv[c] += l * X[(int64_t)c * ldx + r];
+                if (c < nc) sv[c] += l * ld_in<COH>(X + (int64_t)c * ldx + r);
         }
 #pragma unroll
         for (int c = 0; c < RC; ++c) sv[c] = warp_sum(sv[c]);
         if (lane < RC) out[lane * db.cols + ii] = sv[lane];   // c * m + ii
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_pull_dot(const int32_t *__restrict__ pairs, const int64_t *__restrict__ poff,
+           BlockArgs a, const T *__restrict__ val,
+           const double *__restrict__ X, int64_t ldx, int nc,
+           double *__restrict__ part_d) {
+    pull_dot_body<T, false>(pairs, poff, a, val, X, ldx, nc, part_d, (int)blockIdx.x);
 }
 
 // One column step of a diagonal-block sweep; cv[e] is entry e of column jj
@@ -491,32 +518,16 @@ k_diag_inv(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
     }
 }
 
-// Diagonal part of a sweep: one CTA per diagonal block of the level.
-// y = x(block rows) minus the level's partials (fixed order), then the
-// chain over the block's columns by warp 0.  The block's index data is
-// staged in shared memory; its values too if they fit, otherwise they are
-// streamed through two column-panel buffers, warps 1-7 loading the next
-// panel while warp 0 works on the current one.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads)
-k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
-       const int64_t *__restrict__ pair0,
-       const int64_t *__restrict__ boff, const int64_t *__restrict__ poff,
-       BlockArgs a, const T *__restrict__ val, double *__restrict__ X,
-       int64_t ldx, int nc, const double *__restrict__ part_d,
-       const T *__restrict__ winv, const int64_t *__restrict__ woff,
-       RowLists rl) {
+// y (m x RC, row-major, shared memory) = x(block rows) minus the block's
+// partials, summed in the fixed order of its source list.
+template <typename T, bool COH>
+__device__ __forceinline__ void diag_load_y(const BlockDesc &dd, int64_t p0, int np,
+                                            const int64_t *__restrict__ poff,
+                                            const double *X, int64_t ldx, int nc,
+                                            const double *part_d, T *y) {
     using C = T;
     const C *part = reinterpret_cast<const C *>(part_d);
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int W = 16;
-    const int gpos = pos[blockIdx.x];
-    const BlockDesc dd = a.bd[ids[gpos]];
-    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    C *y = reinterpret_cast<C *>(smem);
-    const size_t ybytes = align16((size_t)m * RC * sizeof(C));
-    const int64_t p0 = pair0[gpos];
-    const int np = (int)(boff[dd.I + 1] - boff[dd.I]);
+    const int m = dd.rows;
     // partial offsets of this block's sources, staged once (the partials
     // themselves are then independent loads)
     __shared__ int64_t s_po[256];
@@ -538,7 +549,7 @@ k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
                         const int t = t0 + w * kThreads + threadIdx.x;
-                        v[u][w] = (q + u < nq && t < m * RC) ? part[s_po[q + u] + t] : 0.0;
+                        v[u][w] = (q + u < nq && t < m * RC) ? ld_in<COH>(part + s_po[q + u] + t) : 0.0;
                     }
 #pragma unroll
                 for (int w = 0; w < 4; ++w)
@@ -554,63 +565,100 @@ k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
             }
         }
     }
+}
+
+// Dense diagonal block with explicit inverses: x(block rows) = M y,
+//   L y -> L^{-1} y, U y -> U^{-1} y, U^T -> U^{-T}, L^T -> L^{-T}.
+template <typename T, int MODE>
+__device__ __forceinline__ void diag_inv_apply(const BlockDesc &dd, const T *__restrict__ winv,
+                                               const int64_t *__restrict__ woff, double *X,
+                                               int64_t ldx, int nc, T *y) {
+    using C = T;
+    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool useL = (MODE == FWD || MODE == BWD_T);
+    const T *M = winv + woff[dd.I] + (useL ? 0 : (int64_t)m * m);
+    C *o = y + m * RC;
+    __syncthreads();
+    if (MODE == FWD || MODE == BWD) {
+        // out(r) = sum_k M(r, k) y(k): thread per row, coalesced over r;
+        // loads issued 8 at a time ahead of their FMAs
+        for (int r = threadIdx.x; r < m; r += kThreads) {
+            C acc[RC] = {0.0, 0.0, 0.0, 0.0};
+            const int k0 = MODE == FWD ? 0 : r, k1 = MODE == FWD ? r + 1 : m;
+            for (int kb = k0; kb < k1; kb += 8) {
+                C mv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    mv[u] = kb + u < k1 ? (C)M[(int64_t)(kb + u) * m + r] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = min(kb + u, m - 1);
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < RC; ++c) o[r * RC + c] = acc[c];
+        }
+    } else {
+        // out(r) = sum_k M(k, r) y(k): warp per row, lanes over k
+        for (int r = warp; r < m; r += kWarps) {
+            C acc[RC] = {0.0, 0.0, 0.0, 0.0};
+            const int k0 = MODE == FWD_T ? 0 : r, k1 = MODE == FWD_T ? r + 1 : m;
+            for (int kb = k0; kb < k1; kb += 128) {
+                C mv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = kb + u * 32 + lane;
+                    mv[u] = k < k1 ? (C)M[(int64_t)r * m + k] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = min(kb + u * 32 + lane, m - 1);
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < RC; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane < RC) o[r * RC + lane] = acc[lane];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+        const int r = t / RC, c = t % RC;
+        if (c < nc) X[(int64_t)c * ldx + dd.r0 + r] = o[t];
+    }
+}
+
+// Diagonal part of a sweep: one CTA per diagonal block of the level.
+// y = x(block rows) minus the level's partials (fixed order), then the
+// chain over the block's columns by warp 0.  The block's index data is
+// staged in shared memory; its values too if they fit, otherwise they are
+// streamed through two column-panel buffers, warps 1-7 loading the next
+// panel while warp 0 works on the current one.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_diag(const int32_t *__restrict__ pos, const int32_t *__restrict__ ids,
+       const int64_t *__restrict__ pair0,
+       const int64_t *__restrict__ boff, const int64_t *__restrict__ poff,
+       BlockArgs a, const T *__restrict__ val, double *__restrict__ X,
+       int64_t ldx, int nc, const double *__restrict__ part_d,
+       const T *__restrict__ winv, const int64_t *__restrict__ woff,
+       RowLists rl) {
+    using C = T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int W = 16;
+    const int gpos = pos[blockIdx.x];
+    const BlockDesc dd = a.bd[ids[gpos]];
+    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    C *y = reinterpret_cast<C *>(smem);
+    const size_t ybytes = align16((size_t)m * RC * sizeof(C));
+    const int64_t p0 = pair0[gpos];
+    const int np = (int)(boff[dd.I + 1] - boff[dd.I]);
+    diag_load_y<T, false>(dd, p0, np, poff, X, ldx, nc, part_d, y);
     if (woff[dd.I] >= 0) {
-        // dense diagonal block with explicit inverses: one mat-vec
-        //   L y -> L^{-1} y, U y -> U^{-1} y, U^T -> U^{-T}, L^T -> L^{-T}
-        const bool useL = (MODE == FWD || MODE == BWD_T);
-        const T *M = winv + woff[dd.I] + (useL ? 0 : (int64_t)m * m);
-        C *o = y + m * RC;
-        __syncthreads();
-        if (MODE == FWD || MODE == BWD) {
-            // out(r) = sum_k M(r, k) y(k): thread per row, coalesced over r;
-            // loads issued 8 at a time ahead of their FMAs
-            for (int r = threadIdx.x; r < m; r += kThreads) {
-                C acc[RC] = {0.0, 0.0, 0.0, 0.0};
-                const int k0 = MODE == FWD ? 0 : r, k1 = MODE == FWD ? r + 1 : m;
-                for (int kb = k0; kb < k1; kb += 8) {
-                    C mv[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        mv[u] = kb + u < k1 ? (C)M[(int64_t)(kb + u) * m + r] : 0.0;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int k = min(kb + u, m - 1);
-#pragma unroll
-                        for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < RC; ++c) o[r * RC + c] = acc[c];
-            }
-        } else {
-            // out(r) = sum_k M(k, r) y(k): warp per row, lanes over k
-            for (int r = warp; r < m; r += kWarps) {
-                C acc[RC] = {0.0, 0.0, 0.0, 0.0};
-                const int k0 = MODE == FWD_T ? 0 : r, k1 = MODE == FWD_T ? r + 1 : m;
-                for (int kb = k0; kb < k1; kb += 128) {
-                    C mv[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int k = kb + u * 32 + lane;
-                        mv[u] = k < k1 ? (C)M[(int64_t)r * m + k] : 0.0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int k = min(kb + u * 32 + lane, m - 1);
-#pragma unroll
-                        for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < RC; ++c) acc[c] = warp_sum(acc[c]);
-                if (lane < RC) o[r * RC + lane] = acc[lane];
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < m * RC; t += kThreads) {
-            const int r = t / RC, c = t % RC;
-            if (c < nc) X[(int64_t)c * ldx + dd.r0 + r] = o[t];
-        }
+        diag_inv_apply<T, MODE>(dd, winv, woff, X, ldx, nc, y);
         return;
     }
     if (!dd.dense && 4 * dd.ngroups <= m) {
@@ -922,7 +970,302 @@ __global__ void k_add_cols(int64_t n, int nrhs, const double *__restrict__ D,
     }
 }
 
+// k_diag_inv's arithmetic in one CTA (the persistent sweep): the rows are
+// split into the cluster's kInvCluster row ranges only to reproduce its
+// operation order -- y = x minus the partials added one source after the
+// other; out(r) the sum over warps w = 0 .. 7, in order, of warp w's terms
+// k = k0 + w, k0 + w + 8, ... (k0 the start of r's row range for U, 0 for
+// L); the transposed forms lanes over k and a warp reduction, as there --
+// so the solutions are bit for bit those of the per-level sweep.
+template <typename T, int MODE, bool COH>
+__device__ __forceinline__ void diag_inv_cta(const BlockDesc &dd, int64_t p0, int np,
+                                             const int64_t *__restrict__ poff, double *X,
+                                             int64_t ldx, int nc, const double *part_d,
+                                             const T *__restrict__ winv,
+                                             const int64_t *__restrict__ woff,
+                                             unsigned char *smem) {
+    using C = T;
+    const C *part = reinterpret_cast<const C *>(part_d);
+    const int m = dd.rows, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int h = (m + kInvCluster - 1) / kInvCluster;
+    C *y = reinterpret_cast<C *>(smem);                  // m x RC
+    C *red = y + (size_t)m * RC;                         // kWarps x m x RC
+    for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+        const int r = t % m, c = t / m;
+        C acc = 0.0;
+        for (int q = 0; q < np; ++q)
+            acc += ld_in<COH>(part + poff[p0 + q] * RC + (int64_t)c * m + r);
+        const C xv = c < nc ? (C)X[(int64_t)c * ldx + dd.r0 + r] : C(0);
+        y[r * RC + c] = xv - acc;
+    }
+    __syncthreads();
+    const bool useL = (MODE == FWD || MODE == BWD_T);
+    const T *M = winv + woff[dd.I] + (useL ? 0 : (int64_t)m * m);
+    if (MODE == FWD || MODE == BWD) {
+        for (int r = lane; r < m; r += 32) {
+            const int ra = (r / h) * h, rb = min(m, ra + h);
+            const int k0 = MODE == FWD ? 0 : ra, k1 = MODE == FWD ? rb : m;
+            C acc[RC] = {0.0, 0.0, 0.0, 0.0};
+            for (int kb = k0 + warp; kb < k1; kb += kWarps * 4) {
+                C mv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = kb + kWarps * u;
+                    mv[u] = k < k1 ? (C)M[(int64_t)k * m + r] : C(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = min(kb + kWarps * u, m - 1);
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < RC; ++c) red[((size_t)warp * m + r) * RC + c] = acc[c];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < m * RC; t += kThreads) {
+            const int r = t / RC, c = t % RC;
+            C sum = 0.0;
+            for (int w = 0; w < kWarps; ++w) sum += red[((size_t)w * m + r) * RC + c];
+            if (c < nc) X[(int64_t)c * ldx + dd.r0 + r] = sum;
+        }
+    } else {
+        for (int r = warp; r < m; r += kWarps) {
+            C acc[RC] = {0.0, 0.0, 0.0, 0.0};
+            const int k0 = MODE == FWD_T ? 0 : r, k1 = MODE == FWD_T ? r + 1 : m;
+            for (int kb = k0; kb < k1; kb += 128) {
+                C mv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = kb + u * 32 + lane;
+                    mv[u] = k < k1 ? (C)M[(int64_t)r * m + k] : C(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = min(kb + u * 32 + lane, m - 1);
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) acc[c] += mv[u] * y[k * RC + c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < RC; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane < nc) X[(int64_t)lane * ldx + dd.r0 + r] = acc[lane];
+        }
+    }
+}
+
+// ------------------------------------------------------------ persistent
+// One sweep in one launch (slu_set_persistent_solve): persistent CTAs take
+// tickets in the order of the sweep's work list, which lists level by level
+// (in the sweep's order) the level's pull tasks (a source block and a row
+// chunk) and then its diagonal blocks.  A pull task waits (thread 0, an
+// acquire at GPU scope, bounded) until the diagonal block whose solution it
+// reads is done, a diagonal task until every pull into its block is; the
+// bodies are those of the per-level kernels (a diagonal block by one CTA
+// with the arithmetic of the cluster kernel); then barrier, fence and an
+// atomic increment of the task's counter.  Every ticket waited on was taken
+// earlier by a running CTA, so the sweep cannot deadlock; a wait that runs
+// out sets bit 2 of cnt[2] and the CTA leaves (the others then run out).
+enum : int32_t { kStPull = 0, kStDiag = 1 };
+constexpr int kStInts = 6;   // kind, index, chunk, wait counter (-1: none), need, done counter
+
+struct SolvePersistArgs {
+    const int32_t *tasks;
+    int ntasks;
+    int *done;                 // counters
+    int *ticket;
+    const int32_t *pairs;      // the sweep's (source, diagonal) pairs
+    const int64_t *poff;       // their partial offsets
+    const int32_t *ids;        // GETRF list (diagonal block ids)
+    const int64_t *pair0;      // first pair of each GETRF entry
+    const int64_t *boff;       // sources per block row
+    const int64_t *woff;
+    BlockArgs a;
+    unsigned long long *cnt;
+    long long budget_ns;
+    int rpc;                   // rows per chunk of a sparse source
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_solve_persistent(SolvePersistArgs p, const T *__restrict__ val, const T *__restrict__ winv,
+                   double *X, int64_t ldx, int nc, double *part) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_t, s_stop;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(p.ticket, 1);
+            int stop = t >= p.ntasks;
+            if (!stop) {
+                const int32_t *pt = p.tasks + kStInts * (int64_t)t;
+                if (pt[3] >= 0 && !wait_count(p.done + pt[3], pt[4], p.budget_ns)) {
+                    atomicOr(&p.cnt[2], 4ull);
+                    stop = 1;
+                }
+            }
+            s_t = t;
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_stop) break;                              // uniform
+        const int32_t *pt = p.tasks + kStInts * (int64_t)s_t;
+        if (pt[0] == kStPull) {
+            if (MODE == FWD || MODE == BWD)
+                pull_scatter_body<T, true>(p.pairs, p.poff, p.a, val, X, ldx, nc, part, p.rpc,
+                                           pt[1], pt[2], smem);
+            else
+                pull_dot_body<T, true>(p.pairs, p.poff, p.a, val, X, ldx, nc, part, pt[1]);
+        } else {
+            const int g = pt[1];
+            const BlockDesc dd = p.a.bd[p.ids[g]];
+            diag_inv_cta<T, MODE, true>(dd, p.pair0[g], (int)(p.boff[dd.I + 1] - p.boff[dd.I]),
+                                        p.poff, X, ldx, nc, part, winv, p.woff, smem);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(p.done + pt[5], 1);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host side
+
+// Work list of a persistent sweep, built once per handle and sweep: level
+// by level in the sweep's order, the level's pull tasks (only the row
+// chunks a source has), then its diagonal blocks.  Counters: [0, p) block
+// row solved, [p, 2p) pulls done into the block row.  Levels overlap in
+// the persistent launch, so the partial offsets of the per-level launches
+// (reused by every level) are rebased: level after level, past the end of
+// the previous levels' partials.
+template <typename T>
+static slu_status persistent_solve_tasks(slu_handle *h, int mode, int rpc) {
+    if (h->stasks[mode]) return SLU_OK;
+    const slu_plan *P = h->plan;
+    const int32_t p = P->p, L = P->nlevels;
+    constexpr int VW = 16 / sizeof(T);
+    const bool up = (mode == FWD || mode == FWD_T), scatter = (mode == FWD || mode == BWD);
+    const auto &pairs = P->sp_pairs[mode];
+    std::vector<int32_t> t;
+    std::vector<int32_t> need(p, 0);
+    std::vector<int64_t> off(pairs.size() / 2);    // partial offsets, all levels
+    int64_t base = 0;
+    try {
+        for (int k = 0; k < L; ++k) {
+            const int lv = up ? k : L - 1 - k;
+            int64_t top = base;
+            for (int64_t q = P->sp_off[mode][lv]; q < P->sp_off[mode][lv + 1]; ++q) {
+                off[q] = base + P->sp_poff[mode][q];
+                top = std::max<int64_t>(top, off[q] + P->blocks[pairs[2 * q + 1]].rows);
+            }
+            base = top;
+            for (int64_t q = P->sp_off[mode][lv]; q < P->sp_off[mode][lv + 1]; ++q) {
+                const BlockDesc &B = P->blocks[pairs[2 * q]];
+                const int32_t I = P->blocks[pairs[2 * q + 1]].I;
+                const int32_t src = scatter ? B.J : B.I;   // block row whose solution is read
+                int chunks = 1;
+                if (scatter) {
+                    const int per = B.dense && B.ld % VW == 0 ? kDenseRows : std::min(B.rows, rpc);
+                    chunks = (B.rows + per - 1) / per;
+                }
+                for (int y = 0; y < chunks; ++y) {
+                    const int32_t e[kStInts] = {kStPull, (int32_t)q, y, src, 1, p + I};
+                    t.insert(t.end(), e, e + kStInts);
+                }
+                need[I] += chunks;
+            }
+            for (int64_t g = P->getrf_off[lv]; g < P->getrf_off[lv + 1]; ++g) {
+                const int32_t I = P->blocks[P->getrf[g]].I;
+                const int32_t e[kStInts] = {kStDiag, (int32_t)g, 0, need[I] ? p + I : -1,
+                                            need[I], I};
+                t.insert(t.end(), e, e + kStInts);
+            }
+        }
+    } catch (const std::exception &) {
+        return fail(SLU_ERR_OUT_OF_MEMORY, "host allocation in the solve");
+    }
+    if (!h->sdone && !cuda_ok(cudaMalloc(&h->sdone, (2 * (size_t)p + 1) * sizeof(int)),
+                              "cudaMalloc(solve counters)"))
+        return SLU_ERR_OUT_OF_MEMORY;
+    if (base * RC > h->spart_elems) {             // partials of the whole sweep
+        if (h->spart) cudaFree(h->spart);
+        h->spart = nullptr;
+        h->spart_elems = 0;
+        if (!cuda_ok(cudaMalloc(&h->spart, std::max<int64_t>(1, base * RC) * sizeof(double)),
+                     "cudaMalloc(solve partials)"))
+            return SLU_ERR_OUT_OF_MEMORY;
+        h->spart_elems = base * RC;
+    }
+    int32_t *d = nullptr;
+    int64_t *o = nullptr;
+    if (!cuda_ok(cudaMalloc(&d, std::max<size_t>(1, t.size()) * sizeof(int32_t)),
+                 "cudaMalloc(solve tasks)") ||
+        !cuda_ok(cudaMalloc(&o, std::max<size_t>(1, off.size()) * sizeof(int64_t)),
+                 "cudaMalloc(solve offsets)")) {
+        if (d) cudaFree(d);
+        return SLU_ERR_OUT_OF_MEMORY;
+    }
+    if ((!t.empty() && !cuda_ok(cudaMemcpy(d, t.data(), t.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice), "cudaMemcpy(solve tasks)")) ||
+        (!off.empty() && !cuda_ok(cudaMemcpy(o, off.data(), off.size() * sizeof(int64_t),
+                                             cudaMemcpyHostToDevice), "cudaMemcpy(solve offsets)"))) {
+        cudaFree(d);
+        cudaFree(o);
+        return SLU_ERR_CUDA;
+    }
+    h->stasks[mode] = d;
+    h->spoff[mode] = o;
+    h->sntasks[mode] = (int64_t)t.size() / kStInts;
+    return SLU_OK;
+}
+
+// Rows per chunk of a sparse pull source and the pull kernels' shared
+// memory (as the per-level sweep computes them).
+template <typename T>
+static void pull_shape(const slu_plan *P, int *rpc, size_t *smem) {
+    *rpc = (int)std::min<int64_t>(P->maxb, kStageSmem / ((size_t)kWarps * RC * sizeof(double)));
+    constexpr size_t kSlices = kThreads / (kDenseRows / (16 / sizeof(T)));
+    *smem = std::max<size_t>((size_t)kWarps * *rpc * RC * sizeof(double),
+                             ((size_t)P->maxb + kSlices * kDenseRows) * RC * sizeof(T));
+}
+
+// The four sweeps' work lists, kernel attributes and grids (outside any
+// stream capture: allocations and copies).
+template <typename T, int MODE>
+static slu_status persistent_solve_setup(slu_handle *h) {
+    const slu_plan *P = h->plan;
+    int rpc;
+    size_t pull_smem;
+    pull_shape<T>(P, &rpc, &pull_smem);
+    if (pull_smem > kStageSmem) return fail(SLU_ERR_NOT_SUPPORTED, "block too large for the solve");
+    slu_status s = persistent_solve_tasks<T>(h, MODE, rpc);
+    if (s != SLU_OK) return s;
+    const size_t sm = std::max(pull_smem, (1 + kWarps) * (size_t)P->maxb * RC * sizeof(T));
+    int per_sm = 0, dev = 0, sms = 0;
+    if (!cuda_ok(cudaFuncSetAttribute(k_solve_persistent<T, MODE>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                 "attr") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &per_sm, k_solve_persistent<T, MODE>, kThreads, sm), "occupancy") ||
+        !cuda_ok(cudaGetDevice(&dev), "device") ||
+        !cuda_ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device"))
+        return SLU_ERR_CUDA;
+    if (per_sm < 1) return fail(SLU_ERR_NOT_SUPPORTED, "block too large for the solve");
+    h->ssmem[MODE] = sm;
+    h->sgrid[MODE] = (int)std::min<int64_t>((int64_t)sms * per_sm,
+                                            std::max<int64_t>(1, h->sntasks[MODE]));
+    return SLU_OK;
+}
+
+template <typename T>
+static slu_status persistent_solve_setup_all(slu_handle *h) {
+    slu_status s = persistent_solve_setup<T, FWD>(h);
+    if (s == SLU_OK) s = persistent_solve_setup<T, BWD>(h);
+    if (s == SLU_OK) s = persistent_solve_setup<T, FWD_T>(h);
+    if (s == SLU_OK) s = persistent_solve_setup<T, BWD_T>(h);
+    return s;
+}
 
 // One sweep over the levels (ascending for L and U^T, descending for U and
 // L^T), in chunks of RC right-hand sides; per level a pull launch (one CTA
@@ -951,6 +1294,29 @@ static slu_status sweep_t(const slu_handle *h, double *X, int64_t ldx,
     const int64_t *boff = MODE == FWD ? D->lrow_off : MODE == BWD ? D->urow_off
                         : MODE == FWD_T ? D->ucol_off : D->lcol_off;
     const bool up = (MODE == FWD || MODE == FWD_T);
+    if (h->persistent_solve) {
+        // work list, grid and shared memory set up by slu_set_persistent_solve
+        const size_t sm = h->ssmem[MODE];
+        if (!h->stasks[MODE] || h->sgrid[MODE] < 1)
+            return fail(SLU_ERR_INVALID_ARG, "persistent solve not set up");
+        const int64_t budget = P->opts.wait_budget_ms > 0 ? P->opts.wait_budget_ms : 2000;
+        const int ntasks = (int)h->sntasks[MODE];
+        SolvePersistArgs pa{h->stasks[MODE], ntasks, h->sdone, h->sdone + 2 * P->p,
+                            D->sp_pairs[MODE], h->spoff[MODE], D->getrf, D->sd_pair0[MODE],
+                            boff, D->woff, a, h->cnt, budget * 1000000ll, rpc};
+        const int grid = h->sgrid[MODE];
+        for (int c0 = 0; c0 < nrhs; c0 += RC) {
+            const int nc = std::min(RC, nrhs - c0);
+            if (!cuda_ok(cudaMemsetAsync(h->sdone, 0, (2 * (size_t)P->p + 1) * sizeof(int), st),
+                         "cudaMemsetAsync"))
+                return SLU_ERR_CUDA;
+            LaunchScope ls_(h, SLU_KC_PERSIST, st, grid);
+            k_solve_persistent<T, MODE><<<grid, kThreads, sm, st>>>(
+                pa, val, static_cast<const T *>(h->winv), X + (int64_t)c0 * ldx, ldx, nc,
+                h->spart);
+        }
+        return cuda_ok(cudaGetLastError(), "solve launch") ? SLU_OK : SLU_ERR_CUDA;
+    }
     for (int c0 = 0; c0 < nrhs; c0 += RC) {
         const int nc = std::min(RC, nrhs - c0);
         double *Xc = X + (int64_t)c0 * ldx;
@@ -1152,13 +1518,18 @@ static slu_status backward_error(slu_handle *h, const double *B, int64_t ldb,
                 reinterpret_cast<unsigned long long *>(h->red));
     }
     std::vector<double> hr(3 * (size_t)nseg * nrhs), an(nseg);
-    if (!cuda_ok(cudaMemcpyAsync(hr.data(), h->red, hr.size() * sizeof(double),
+    unsigned long long flags = 0;
+    if (!cuda_ok(cudaMemcpyAsync(&flags, h->cnt + 2, sizeof(flags), cudaMemcpyDeviceToHost, st),
+                 "cudaMemcpyAsync") ||
+        !cuda_ok(cudaMemcpyAsync(hr.data(), h->red, hr.size() * sizeof(double),
                                  cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
         !cuda_ok(cudaMemcpyAsync(an.data(), nseg > 1 ? h->anorm_seg : h->scal + 1,
                                  nseg * sizeof(double), cudaMemcpyDeviceToHost, st),
                  "cudaMemcpyAsync") ||
         !cuda_ok(cudaStreamSynchronize(st), "residual"))
         return SLU_ERR_CUDA;
+    if (flags & 4)
+        return fail(SLU_ERR_TIMEOUT, "a wait of the persistent solve exceeded its bound");
     double worst = 0.0;
     for (int q = 0; q < nseg; ++q)
         for (int c = 0; c < nrhs; ++c) {
@@ -1174,6 +1545,36 @@ static slu_status backward_error(slu_handle *h, const double *B, int64_t ldb,
 }  // namespace slu
 
 using namespace slu;
+
+extern "C" slu_status slu_set_persistent_solve(slu_handle *h, int32_t on) {
+    if (!h) return fail(SLU_ERR_INVALID_ARG, "NULL handle");
+    const slu_plan *P = h->plan;
+    if (on)
+        for (int32_t I = 0; I < P->p; ++I)
+            if (P->woff[I] < 0)
+                return fail(SLU_ERR_NOT_SUPPORTED,
+                            "the persistent solve needs the explicit inverses of every "
+                            "diagonal block (dense, at most 384 rows)");
+    if (h->persistent_solve != (on != 0)) {       // recorded graphs hold the other form
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (h->device >= 0) cudaSetDevice(h->device);
+        for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.exec);
+        h->sgraphs.clear();
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    if (on && P->n > 0) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (h->device >= 0) cudaSetDevice(h->device);
+        const slu_status s = h->prec == SLU_PREC_FP64 ? persistent_solve_setup_all<double>(h)
+                                                      : persistent_solve_setup_all<float>(h);
+        if (cur >= 0) cudaSetDevice(cur);
+        if (s != SLU_OK) return s;
+    }
+    h->persistent_solve = on != 0;
+    return SLU_OK;
+}
 
 extern "C" slu_status slu_solve(const slu_handle *ch, const double *B,
                                 int64_t ldb, int32_t nrhs, double *X,

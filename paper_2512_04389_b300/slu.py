@@ -86,6 +86,7 @@ EXPORTS = ["slu_opts_default", "slu_analyze", "slu_analyze_batch",
            "slu_plan_flops", "slu_handle_trace", "slu_set_graph", "slu_solve_refine_noalloc",
            "slu_factor_batch", "slu_select_regular_block",
            "slu_set_persistent", "slu_persistent_tasks", "slu_set_persistent_tasks",
+           "slu_set_persistent_solve",
            "slu_reorder", "slu_reorder_apply", "slu_permute_scale",
            "slu_plan_serialize", "slu_plan_deserialize", "slu_plan_digest", "slu_plan_check",
            "slu_plan_destroy",
@@ -115,6 +116,7 @@ def _load():
     lib.slu_refactor.argtypes = [P, P, P, C.POINTER(FactorInfo)]
     lib.slu_factor_batch.argtypes = [C.c_int32, P, P, P, P, C.POINTER(FactorInfo)]
     lib.slu_set_persistent.argtypes = [P, C.c_int32]
+    lib.slu_set_persistent_solve.argtypes = [P, C.c_int32]
     lib.slu_persistent_tasks.argtypes = [P, P, C.c_int64, P]
     lib.slu_set_persistent_tasks.argtypes = [P, P, C.c_int64]
     lib.slu_reorder.argtypes = [C.c_int64, P, P, P, C.c_int32, C.c_int32, P, P, P, P]
@@ -570,6 +572,10 @@ class Factor:
     def set_persistent(self, enable=True):
         """Run refactor()'s level walk as one persistent launch."""
         _check(lib.slu_set_persistent(self._h, 1 if enable else 0))
+
+    def set_persistent_solve(self, enable=True):
+        """Run every solve sweep as one persistent launch (per 4 RHS)."""
+        _check(lib.slu_set_persistent_solve(self._h, 1 if enable else 0))
 
     def persistent_tasks(self):
         """The persistent launch's work list, int32 array (tasks, 7)."""
