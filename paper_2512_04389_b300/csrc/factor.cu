@@ -375,6 +375,119 @@ __device__ void lu_dense_smem(T *S, int b, int ls, double tau,
     __syncthreads();
 }
 
+// Dense LU of an FP64 block held whole in shared memory with no CTA barrier
+// between steps.  Column c belongs to warp c % nw, which alone updates it.
+// Step k needs the pivot's reciprocal and the list of the nonzeros below the
+// pivot in column k (rows and unscaled values), published by the owner of
+// column k: in step k - 1 that warp updates column k first, fixes the pivot
+// (the FP64 test on the bit pattern), forms the reciprocal, lists the column,
+// scales it in place (L(:, k)) and sets `ready` = k -- while the other warps
+// still update their columns of step k - 1, so the reciprocal's latency is
+// off their path.  Every warp waits (lane 0, bounded) for ready >= k, then
+// updates its columns c > k over the listed rows: A(r, c) -= a(r, k) u with
+// u = U(k, c) / pivot.  A warp can fall behind only until it reaches the next
+// column it owns, at most nw steps ahead of it, so kLuRing >= nw + 2 list
+// slots are never written while still read.  A wait that runs out sets bit
+// 3 of cnt[2] and the warp stops.
+constexpr int kLuRing = 32;
+__host__ __device__ constexpr size_t lu_owner_bytes(int b) {
+    return (size_t)b * (b | 1) * sizeof(double) + (size_t)kLuRing * b * (sizeof(double) + 2);
+}
+
+__device__ void lu_owner(double *S, int b, int ls, double tau, unsigned long long *cnt,
+                         unsigned char *ring) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    double *Lv = reinterpret_cast<double *>(ring);                       // kLuRing x b
+    uint16_t *R = reinterpret_cast<uint16_t *>(Lv + (size_t)kLuRing * b); // kLuRing x b
+    __shared__ double s_rcp[kLuRing];
+    __shared__ int s_n[kLuRing];
+    __shared__ volatile int s_ready;
+    if (threadIdx.x == 0) s_ready = -1;
+    __syncthreads();
+    // the owner of column k, whole warp: the pivot's division is issued
+    // first and runs while the unscaled column is listed; the list and the
+    // reciprocal are published, and the column is scaled (L(:, k)) after
+    auto publish = [&](int k) {
+        double rc = 0.0;
+        if (lane == 0) {
+            double &p = S[(int64_t)k * ls + k];
+            const double pv = fix_pivot(p, tau, cnt);
+            p = pv;
+            rc = 1.0 / pv;
+        }
+        const int slot = k % kLuRing;
+        double *lv = Lv + (size_t)slot * b;
+        uint16_t *rr = R + (size_t)slot * b;
+        double *col = S + (int64_t)k * ls;
+        int n = 0;
+        for (int i0 = k + 1; i0 < b; i0 += 32) {
+            const int i = i0 + lane;
+            const double v = i < b ? col[i] : 0.0;
+            const bool live = i < b && nz(v);
+            const unsigned m = __ballot_sync(0xffffffffu, live);
+            if (live) {
+                const int q = n + __popc(m & lt);
+                rr[q] = (uint16_t)i;
+                lv[q] = v;
+            }
+            n += __popc(m);
+        }
+        rc = __shfl_sync(0xffffffffu, rc, 0);
+        if (lane == 0) {
+            s_rcp[slot] = rc;
+            s_n[slot] = n;
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) s_ready = k;
+        for (int q = lane; q < n; q += 32) col[rr[q]] = lv[q] * rc;
+    };
+    if (warp == 0 && b > 0) publish(0);
+    for (int k = 0; k + 1 < b; ++k) {
+        int ok = 1;
+        if (lane == 0) {
+            // the owner of column k + 1 is on the step chain and spins hot;
+            // the other warps back off, leaving it the issue slots
+            const bool next = warp == (k + 1) % nw;
+            for (int it = 0; s_ready < k; ++it) {
+                if (it >= (1 << 22)) {
+                    atomicOr(&cnt[2], 8ull);
+                    ok = 0;
+                    break;
+                }
+                if (!next || it >= 4096) __nanosleep(next ? 64 : 200);
+            }
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+        __syncwarp();
+        __threadfence_block();
+        const int slot = k % kLuRing;
+        const int nR = s_n[slot];
+        const double rc = s_rcp[slot];
+        const double *lv = Lv + (size_t)slot * b;
+        const uint16_t *rr = R + (size_t)slot * b;
+        // this warp's columns c > k, the first of them k + 1 when owned
+        const int c0 = k + 1 + (((warp - (k + 1)) % nw) + nw) % nw;
+        for (int c = c0; c < b; c += nw) {
+            double *cc = S + (int64_t)c * ls;
+            const double a = cc[k];                     // U(k, c), final
+            if (nR > 0 && nz(a)) {                      // uniform across the warp
+                const double u = a * rc;
+                for (int ri = lane; ri < nR; ri += 32) {
+                    const int r = rr[ri];
+                    cc[r] -= lv[ri] * u;
+                }
+            }
+            if (c == k + 1) {
+                __syncwarp();
+                publish(k + 1);
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // Dense diagonal block b x b at g (leading dimension ld): stage the largest
 // trailing square that fits next to the step lists, factor, write back.
 template <typename T>
@@ -387,6 +500,21 @@ __device__ void getrf_dense(T *g, int b, int64_t ld, double tau,
         ms = (int)sqrt((double)((cap - lb) / sizeof(T)));
         while (ms > 0 && (size_t)ms * (ms | 1) * sizeof(T) > cap - lb) --ms;
         ms = min(ms, b);
+    }
+    if constexpr (sizeof(T) == 8) {
+        if (b <= 128 && lu_owner_bytes(b) <= cap) {
+            // FP64 block that fits whole with the list ring: owned columns,
+            // no barrier between steps
+            const int ls = b | 1;
+            double *S = reinterpret_cast<double *>(smem);
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x)
+                S[(e / b) * ls + e % b] = g[(int64_t)(e / b) * ld + e % b];
+            __syncthreads();
+            lu_owner(S, b, ls, tau, cnt, smem + (size_t)b * ls * sizeof(double));
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x)
+                g[(int64_t)(e / b) * ld + e % b] = S[(e / b) * ls + e % b];
+            return;
+        }
     }
     if (sizeof(T) == 4 && (size_t)b * b * sizeof(T) <= cap) {
         // FP32 block that fits whole: dense steps with one barrier each
@@ -2465,6 +2593,8 @@ static slu_status finish_info(slu_handle *h, cudaStream_t st,
     if (c[2] & 2)
         return fail(SLU_ERR_TIMEOUT,
                     "a dependency wait of the persistent launch exceeded wait_budget_ms");
+    if (c[2] & 8)
+        return fail(SLU_ERR_TIMEOUT, "a step wait of the dense diagonal LU exceeded its bound");
     if (c[2]) return fail(SLU_ERR_TIMEOUT, "a tensor-core wait exceeded its bound");
     if (c[1]) return fail(SLU_ERR_SINGULAR, "zero pivot (perturbation off)");
     return SLU_OK;
