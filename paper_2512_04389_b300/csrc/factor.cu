@@ -2145,8 +2145,10 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
 }
 
 // One CTA per tile; blockIdx.y picks the 64-row half of a 128-row tile.
+// Four CTAs per SM (64 registers, no spills): a CTA staging its next slice
+// or waiting at its barrier leaves the FP64 pipe to three others.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
              const BlockDesc *__restrict__ bd, T *__restrict__ val) {
     extern __shared__ __align__(16) unsigned char gemm_raw[];   // sizeof(GemmSmem<T>)
