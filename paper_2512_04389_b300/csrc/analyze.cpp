@@ -718,7 +718,29 @@ static void build_levels_and_tasks(slu_plan &P) {
         std::vector<int64_t> srcend;  // per target, end of its pairs in src
         std::vector<int32_t> gm_task, gm_src, gg_tgt, gg_src;
         std::vector<int64_t> gg_srcend;
+        std::vector<uint32_t> gm_mask;    // per dense tile and source pair
         int64_t gm_mid = 0, gg_mid = 0;
+    };
+    // Live slices of the FP64 dense tiles: for the tile of target (K, J)
+    // with rows r0 .. r0 + 63 and columns c0 .. c0 + 63 and its source pair
+    // (K, I), (I, J), bit s is set when some column k of slice s (columns
+    // 16 s .. 16 s + 15 of block I) holds, in the filled pattern, a row in the
+    // tile's rows and one in its columns (U(k, c) is nonzero exactly when
+    // column k holds row c, the pattern being symmetric); slices from 32 on
+    // always count as live.  A slice without its bit holds only exact zeros
+    // in the product, so the tile skips it.  Tiles are indexed globally:
+    // tile (X, t) = rows 64 t .. 64 t + 63 of block X.
+    const bool masks = P.opts.precision == SLU_PREC_FP64;
+    std::vector<int64_t> tile_base(p + 1, 0);
+    int32_t max_sl = 1;
+    for (int32_t X = 0; X < p; ++X) {
+        const int32_t rows = (int32_t)(P.ptr[X + 1] - P.ptr[X]);
+        tile_base[X + 1] = tile_base[X] + (rows + 63) / 64;
+        max_sl = std::max(max_sl, std::min(32, (rows + 15) / 16));
+    }
+    auto tile_of = [&](int32_t r) -> int64_t {
+        const int32_t X = P.rowblk[r];
+        return tile_base[X] + (r - P.ptr[X]) / 64;
     };
     std::vector<Lvl> lvl(L);
     std::atomic<int32_t> next_lv{0};
@@ -726,6 +748,12 @@ static void build_levels_and_tasks(slu_plan &P) {
         std::vector<int32_t> slot(nb, -1), trip, pairs, dense_pairs, other;
         std::vector<int64_t> at;
         std::vector<Tgt> vec;
+        // mask entries to fill: (block row I, entry, tile of the rows, tile
+        // of the columns); per-slice masks of the columns of one block I
+        struct MaskReq { int32_t I; int64_t e, tk, tj; };
+        std::vector<MaskReq> req;
+        std::vector<uint16_t> tab(masks ? (size_t)tile_base[p] * max_sl : 0, 0);
+        std::vector<int64_t> touched;
         for (int32_t lv; (lv = next_lv.fetch_add(1)) < L;) {
             Lvl &o = lvl[lv];
             vec.clear();
@@ -812,6 +840,13 @@ static void build_levels_and_tasks(slu_plan &P) {
                             for (int32_t c0 = 0; c0 < td.cols; c0 += 64) {
                                 const int32_t t5[5] = {tb, s0, s1, r0, c0};
                                 o.gm_task.insert(o.gm_task.end(), t5, t5 + 5);
+                                if (!masks) continue;
+                                const int64_t tk = tile_of(td.r0 + r0), tj = tile_of(td.c0 + c0);
+                                for (size_t q = 0; q < dense_pairs.size(); q += 2) {
+                                    req.push_back({P.blocks[dense_pairs[q]].J,
+                                                   (int64_t)o.gm_mask.size(), tk, tj});
+                                    o.gm_mask.push_back(0);
+                                }
                             }
                     }
                     if (!other.empty()) {
@@ -820,6 +855,42 @@ static void build_levels_and_tasks(slu_plan &P) {
                         o.gg_srcend.push_back((int64_t)o.gg_src.size() / 2);
                     }
                 }
+            }
+            if (masks && !req.empty()) {
+                std::stable_sort(req.begin(), req.end(),
+                                 [](const MaskReq &x, const MaskReq &y) { return x.I < y.I; });
+                for (size_t a0 = 0; a0 < req.size();) {
+                    const int32_t I = req[a0].I;
+                    size_t a1 = a0;
+                    while (a1 < req.size() && req[a1].I == I) ++a1;
+                    // per tile and slice: the columns of block I (bit k mod
+                    // 16) holding a row of the tile below block I
+                    const int64_t k0 = P.ptr[I], k1 = P.ptr[I + 1];
+                    for (int64_t k = k0; k < k1; ++k) {
+                        const int32_t sl = (int32_t)((k - k0) / 16);
+                        if (sl >= 32) break;
+                        const uint16_t bit = (uint16_t)(1u << ((k - k0) % 16));
+                        for (int64_t f = P.f_colptr[k]; f < P.f_colptr[k + 1]; ++f) {
+                            const int32_t r = P.f_rowidx[f];
+                            if (r < k1) continue;
+                            const int64_t at = tile_of(r) * max_sl + sl;
+                            if (!tab[at]) touched.push_back(at);
+                            tab[at] |= bit;
+                        }
+                    }
+                    const int32_t nsl = std::min<int32_t>(32, (int32_t)((k1 - k0 + 15) / 16));
+                    for (size_t a = a0; a < a1; ++a) {
+                        uint32_t m = 0;
+                        for (int32_t sl = 0; sl < nsl; ++sl)
+                            if (tab[req[a].tk * max_sl + sl] & tab[req[a].tj * max_sl + sl])
+                                m |= 1u << sl;
+                        o.gm_mask[req[a].e] = m;
+                    }
+                    for (int64_t at : touched) tab[at] = 0;
+                    touched.clear();
+                    a0 = a1;
+                }
+                req.clear();
             }
         }
     });
@@ -895,6 +966,23 @@ static void build_levels_and_tasks(slu_plan &P) {
             tat += (int64_t)o.gm_task.size();
             sat += (int64_t)o.gm_src.size();
             P.gm_off[lv + 1] = tat / 5;
+        }
+    }
+    // slice masks in task order; gm_moff[t] = first mask of task t (one
+    // mask per source pair of the task)
+    P.gm_mask.clear();
+    P.gm_moff.clear();
+    if (masks) {
+        int64_t nm = 0;
+        for (const Lvl &o : lvl) nm += (int64_t)o.gm_mask.size();
+        P.gm_mask.resize((size_t)nm);
+        P.gm_moff.assign(P.gm_task.size() / 5 + 1, 0);
+        int64_t at = 0, t = 0;
+        for (const Lvl &o : lvl) {
+            std::copy(o.gm_mask.begin(), o.gm_mask.end(), P.gm_mask.begin() + at);
+            for (size_t q = 0; q < o.gm_task.size(); q += 5, ++t)
+                P.gm_moff[t + 1] = P.gm_moff[t] + (o.gm_task[q + 2] - o.gm_task[q + 1]);
+            at += (int64_t)o.gm_mask.size();
         }
     }
     std::vector<Lvl>().swap(lvl);

@@ -28,6 +28,8 @@ struct DevPlan {
     int64_t *srcoff = nullptr;
     int32_t *gm_task = nullptr, *gm_src = nullptr, *gg_tgt = nullptr,
             *gg_src = nullptr;
+    uint32_t *gm_mask = nullptr;        // slice masks (FP64 plans), or null
+    int64_t *gm_moff = nullptr;
     int64_t *gg_srcoff = nullptr;
     int64_t *a2s = nullptr, *f2s = nullptr;
     int64_t *a_rowptr = nullptr, *a_vpos = nullptr;

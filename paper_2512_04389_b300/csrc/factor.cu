@@ -2002,10 +2002,12 @@ struct GemmSmem {
 
 // rsub: rows of the task's tile to skip (0, or 64 for the lower half of
 // a 128-row FP32 tile when it runs as two 64-row tiles on the FP32 pipe)
+// mk: the task's slice masks (one per source pair; null: every slice live)
 template <typename T>
 __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
                                           const BlockDesc *bd, T *val,
-                                          GemmSmem<T> &sm, int rsub = 0) {
+                                          GemmSmem<T> &sm, int rsub = 0,
+                                          const uint32_t *mk = nullptr) {
     constexpr int TM = GemmSmem<T>::TM, TN = GemmSmem<T>::TN, KT = GemmSmem<T>::KT;
     constexpr int NQ = KT * TM / 256;              // staged elements per thread
     using Mask = typename std::conditional<KT == 64, unsigned long long, unsigned>::type;
@@ -2021,8 +2023,23 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
 #pragma unroll
     for (int g = 0; g < TN / 4; ++g) acc[g] = T(0);
     if (s0 >= s1) return;
+    // slice (pair ss, first column kk0) can contribute (slices of 16 columns)
+    auto live = [&](int ss, int kk0) -> bool {
+        if (!mk) return true;
+        const int sl = kk0 / 16;
+        return sl >= 32 || ((mk[ss - s0] >> sl) & 1u);
+    };
     int s = s0, k0 = 0;
     BlockDesc dl = bd[src[2 * s]], du = bd[src[2 * s + 1]];
+    while (!live(s, k0)) {                         // uniform: the first live slice
+        k0 += KT;
+        if (k0 >= dl.cols) {
+            if (++s >= s1) return;                 // nothing to add
+            k0 = 0;
+            dl = bd[src[2 * s]];
+            du = bd[src[2 * s + 1]];
+        }
+    }
     T ra[NQ], rb[NQ];
     auto load = [&](const BlockDesc &L, const BlockDesc &U, int kk0) {
         const T *A = val + L.voff;
@@ -2077,20 +2094,27 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
         }
     };
     const int rr = 8 * warp + (lane & 7), cc = lane >> 3;
-    load(dl, du, 0);
+    load(dl, du, k0);
     store(0);
     __syncthreads();
     int buf = 0;
     for (;;) {
-        // advance to the next slice
+        // advance to the next live slice
         int ns = s, nk0 = k0 + KT;
-        if (nk0 >= dl.cols) { ++ns; nk0 = 0; }
-        const bool more = ns < s1;
         BlockDesc nl = dl, nu = du;
-        if (more) {
-            if (ns != s) { nl = bd[src[2 * ns]]; nu = bd[src[2 * ns + 1]]; }
-            load(nl, nu, nk0);
+        for (;;) {
+            if (nk0 >= nl.cols) {
+                ++ns;
+                nk0 = 0;
+                if (ns >= s1) break;
+                nl = bd[src[2 * ns]];
+                nu = bd[src[2 * ns + 1]];
+            }
+            if (live(ns, nk0)) break;
+            nk0 += KT;
         }
+        const bool more = ns < s1;
+        if (more) load(nl, nu, nk0);
         // k mask of this warp's row group (lane k of the first KT reads it)
         Mask amk = __ballot_sync(
             0xffffffffu, lane < KT && ((sAg[buf][lane & (KT - 1)][warp >> 2] >> (warp & 3)) & 1u));
@@ -2150,10 +2174,12 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
 template <typename T>
 __global__ void __launch_bounds__(256, 4)
 k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
-             const BlockDesc *__restrict__ bd, T *__restrict__ val) {
+             const BlockDesc *__restrict__ bd, T *__restrict__ val,
+             const uint32_t *__restrict__ mask, const int64_t *__restrict__ moff) {
     extern __shared__ __align__(16) unsigned char gemm_raw[];   // sizeof(GemmSmem<T>)
     gemm_body<T>(task + 5 * (int64_t)blockIdx.x, src, bd, val,
-                 *reinterpret_cast<GemmSmem<T> *>(gemm_raw), 64 * (int)blockIdx.y);
+                 *reinterpret_cast<GemmSmem<T> *>(gemm_raw), 64 * (int)blockIdx.y,
+                 mask ? mask + moff[blockIdx.x] : nullptr);
 }
 
 // ------------------------------------------------------------ persistent
@@ -2182,6 +2208,8 @@ struct PersistArgs {
     int *done;                          // counters
     int *ticket;
     const int32_t *gd, *inv_task, *pd_task, *gm_task, *gm_src;
+    const uint32_t *gm_mask;            // slice masks, or null
+    const int64_t *gm_moff;
     const BlockDesc *bd;
     BlockArgs a;
     const int64_t *woff;
@@ -2256,7 +2284,8 @@ k_factor_persistent(PersistArgs p, T *val, T *winv) {
                 }
             } else
                 gemm_body<T>(p.gm_task + 5 * (int64_t)idx, p.gm_src, p.bd, val,
-                             *reinterpret_cast<GemmSmem<T> *>(smem));
+                             *reinterpret_cast<GemmSmem<T> *>(smem), 0,
+                             p.gm_mask ? p.gm_mask + p.gm_moff[idx] : nullptr);
         }
         __syncthreads();
         if (tid == 0) {
@@ -2291,7 +2320,8 @@ void free_dev_plan(slu_plan *P) {
                     D->gd, D->gs, D->dv_pos, D->dn_pos, D->lr_ptr, D->lr_pos,
                     D->ps_task, D->lr_col, D->ne_col, D->ne_off, D->pv_task,
                     D->ur_ptr, D->ur_pos, D->ur_col,
-                    D->gm_task, D->gm_src, D->gg_tgt, D->gg_src, D->gg_srcoff,
+                    D->gm_task, D->gm_src, D->gm_mask, D->gm_moff, D->gg_tgt, D->gg_src,
+                    D->gg_srcoff,
                     D->a2s, D->f2s, D->a_rowptr, D->a_vpos, D->a_colidx,
                     D->a_ri, D->a_ci, D->row_seg, D->woff, D->inv_task,
                     D->pd_task, D->pg_gessm, D->pg_tstrf,
@@ -2334,6 +2364,7 @@ slu_status ensure_dev_plan(const slu_plan *cP) {
         upload(P->tstrf, &D->tstrf) && upload(P->tgt, &D->tgt) &&
         upload(P->src, &D->src) && upload(P->srcoff, &D->srcoff) &&
         upload(P->gm_task, &D->gm_task) && upload(P->gm_src, &D->gm_src) &&
+        upload(P->gm_mask, &D->gm_mask) && upload(P->gm_moff, &D->gm_moff) &&
         upload(P->gg_tgt, &D->gg_tgt) && upload(P->gg_src, &D->gg_src) &&
         upload(P->gg_srcoff, &D->gg_srcoff) &&
         upload(P->a2s, &D->a2s) && upload(P->f2s, &D->f2s) &&
@@ -2453,7 +2484,8 @@ static slu_status run_factor(slu_handle *h, const double *values,
         nsm *= sizeof(T) == 4 ? 2 : 1;       // resident CTAs per SM
         const int64_t budget_ms = P->opts.wait_budget_ms > 0 ? P->opts.wait_budget_ms : 2000;
         PersistArgs pa{h->ptasks, (int)h->pntasks, h->pdone, h->pdone + h->pcounters,
-                       D->gd, D->inv_task, D->pd_task, D->gm_task, D->gm_src, D->bd, a,
+                       D->gd, D->inv_task, D->pd_task, D->gm_task, D->gm_src, D->gm_mask,
+                       D->gm_moff, D->bd, a,
                        D->woff, h->scal, h->tau_rel, h->cnt, budget_ms * 1000000ll,
                        P->opts.tc_passes};
         {
@@ -2546,10 +2578,12 @@ static slu_status run_factor(slu_handle *h, const double *values,
                         reinterpret_cast<float *>(val), h->cnt + 2, P->opts.tc_passes);
                 else if (sizeof(T) == 4)   // 128-row tiles as two 64-row halves
                     k_ssssm_gemm<T><<<dim3((unsigned)(mb - ma), 2), 256, sizeof(GemmSmem<T>), ss>>>(
-                        D->gm_task + 5 * ma, D->gm_src, D->bd, val);
+                        D->gm_task + 5 * ma, D->gm_src, D->bd, val, D->gm_mask,
+                        D->gm_moff ? D->gm_moff + ma : nullptr);
                 else
                     k_ssssm_gemm<T><<<(int)(mb - ma), 256, sizeof(GemmSmem<T>), ss>>>(
-                        D->gm_task + 5 * ma, D->gm_src, D->bd, val);
+                        D->gm_task + 5 * ma, D->gm_src, D->bd, val, D->gm_mask,
+                        D->gm_moff ? D->gm_moff + ma : nullptr);
             }
             if (sb > sa) {
                 LaunchScope ls_(h, SLU_KC_SSSSM, ss, -(int)(sb - sa));

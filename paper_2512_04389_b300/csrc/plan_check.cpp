@@ -243,6 +243,14 @@ std::string plan_violation(const slu_plan &P) {
             REQ(source(tb, lb, ub) && B[lb].dense && B[ub].dense, "dense SSSSM source");
         }
     }
+    // slice masks: none, or one per source pair of every dense tile
+    if (!P.gm_moff.empty() || !P.gm_mask.empty()) {
+        REQ(offsets(P.gm_moff, P.gm_task.size() / 5 + 1, (int64_t)P.gm_mask.size()),
+            "slice mask offsets");
+        for (size_t t = 0; t < P.gm_task.size(); t += 5)
+            REQ(P.gm_moff[t / 5 + 1] - P.gm_moff[t / 5] == P.gm_task[t + 2] - P.gm_task[t + 1],
+                "slice masks per tile");
+    }
     for (size_t k = 0; k < P.gg_tgt.size(); ++k) {
         REQ(blk(P.gg_tgt[k]), "generic SSSSM target");
         for (int64_t q = P.gg_srcoff[k]; q < P.gg_srcoff[k + 1]; ++q)

@@ -36,7 +36,7 @@ namespace {
     X(getrf_off) X(gessm_off) X(tstrf_off) X(tgt_off) X(getrf)                \
     X(gd_off) X(gs_off) X(gd) X(gs) X(dv_off) X(dn_off) X(dv_pos) X(dn_pos)   \
     X(gessm) X(tstrf) X(tgt) X(srcoff) X(src)                                 \
-    X(gm_off) X(gm_task) X(gm_src) X(gg_off) X(gg_tgt) X(gg_srcoff) X(gg_src) \
+    X(gm_off) X(gm_task) X(gm_src) X(gm_mask) X(gm_moff) X(gg_off) X(gg_tgt) X(gg_srcoff) X(gg_src) \
     X(gm_mid) X(gg_mid) X(ps_off) X(ps_task) X(pv_off) X(pv_task)             \
     X(woff) X(wsize) X(inv_maxb) X(inv_off) X(inv_task) X(pd_off) X(pd_task)  \
     X(pg_off) X(pg_gessm) X(pg_tstrf) X(pg_goff) X(pg_toff)                   \
@@ -45,7 +45,7 @@ namespace {
     X(lrow_blk) X(urow_blk) X(ucol_blk) X(lcol_blk) X(a2s) X(f2s)
 
 // Changes whenever the meaning of a field changes without a change of layout.
-constexpr uint32_t kPlanFormat = 3;
+constexpr uint32_t kPlanFormat = 4;
 constexpr char kPlanMagic[8] = {'S', 'L', 'U', 'P', 'L', 'A', 'N', 0};
 constexpr uint32_t kEndian = 0x01020304u;
 

@@ -152,6 +152,11 @@ struct slu_plan {
     std::vector<int64_t> gm_off;         // per level, into gm_task
     slu::big_vector<int32_t> gm_task;    // 5 per tile: tgt, s0, s1, r0, c0
     slu::big_vector<int32_t> gm_src;     // pairs (blk(K,I), blk(I,J))
+    // FP64 plans: per tile and source pair a mask of the live 16-deep
+    // slices (bit s: columns 16 s .. 16 s + 15 of block I can contribute);
+    // the masks of task t start at gm_moff[t] (empty for FP32 plans)
+    slu::big_vector<uint32_t> gm_mask;
+    std::vector<int64_t> gm_moff;
     std::vector<int64_t> gg_off;         // per level, into gg_tgt
     slu::big_vector<int32_t> gg_tgt;
     std::vector<int64_t> gg_srcoff;
