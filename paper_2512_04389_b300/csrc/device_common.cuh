@@ -269,6 +269,10 @@ struct slu_handle {
     // second stream for the deferred Schur updates, fork / join events
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the level walk runs on a stream of the greatest priority, forked from
+    // and joined back to the caller's stream
+    cudaStream_t hi = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     // solve graphs: the level sweeps of one solve, recorded once per
     // (right-hand side count, transposed) on a private stream over the
     // handle's vector buffer and replayed on the caller's stream

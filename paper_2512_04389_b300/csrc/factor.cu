@@ -608,11 +608,10 @@ template <typename T>
 __global__ void __launch_bounds__(kDenseLuThreads, 1)
 k_getrf_dense(const int32_t *__restrict__ ids, const BlockDesc *__restrict__ bd,
               T *__restrict__ val, const double *__restrict__ scal,
-              double tau_rel, unsigned long long *__restrict__ cnt) {
+              double tau_rel, unsigned long long *__restrict__ cnt, size_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     const BlockDesc d = bd[ids[blockIdx.x]];
-    getrf_dense<T>(val + d.voff, d.rows, d.ld, tau_rel * scal[0], cnt, smem,
-                   kStageSmem);
+    getrf_dense<T>(val + d.voff, d.rows, d.ld, tau_rel * scal[0], cnt, smem, cap);
 }
 
 // GETRF on sparse-stored diagonal blocks, one CTA per block: by height
@@ -2501,13 +2500,31 @@ static slu_status run_factor(slu_handle *h, const double *values,
     // generic SSSSM: per-warp accumulators plus room to stage a sparse source
     const size_t smem_g = ssssm_smem(P, sizeof(Acc));
     bool deferred = false;
+    // the level walk on the handle's high-priority stream: when the deferred
+    // Schur tiles of the side stream hold the SMs, the block scheduler takes
+    // the chain's kernels first as resources free up
+    const cudaStream_t caller = st;
+    if (h->hi) {
+        if (!cuda_ok(cudaEventRecord(h->ev_in, caller), "cudaEventRecord") ||
+            !cuda_ok(cudaStreamWaitEvent(h->hi, h->ev_in, 0), "cudaStreamWaitEvent"))
+            return SLU_ERR_CUDA;
+        st = h->hi;
+    }
     for (int lv = 0; lv < P->nlevels; ++lv) {
         h->cur_level = lv;
         const int64_t g0 = P->gd_off[lv], g1 = P->gd_off[lv + 1];
         if (g1 > g0) {
+            // shared memory for the level's largest dense diagonal block
+            int mb = 0;
+            for (int64_t g = g0; g < g1; ++g) mb = std::max(mb, P->blocks[P->gd[g]].rows);
+            size_t cap = kStageSmem;
+            if (sizeof(T) == 8 && mb <= 128 && lu_owner_bytes(mb) <= kStageSmem)
+                cap = lu_owner_bytes(mb);
+            else if (sizeof(T) == 4 && (size_t)mb * mb * sizeof(T) <= kStageSmem)
+                cap = (size_t)mb * mb * sizeof(T);
             LaunchScope ls_(h, SLU_KC_GETRF, st, (int)(g1 - g0));
-            k_getrf_dense<T><<<(int)(g1 - g0), kDenseLuThreads, kStageSmem, st>>>(
-                D->gd + g0, D->bd, val, h->scal, h->tau_rel, h->cnt);
+            k_getrf_dense<T><<<(int)(g1 - g0), kDenseLuThreads, cap, st>>>(
+                D->gd + g0, D->bd, val, h->scal, h->tau_rel, h->cnt, cap);
         }
         const int64_t q0 = P->gs_off[lv], q1 = P->gs_off[lv + 1];
         if (q1 > q0) {
@@ -2606,9 +2623,25 @@ static slu_status run_factor(slu_handle *h, const double *values,
     if (deferred &&
         !cuda_ok(cudaStreamWaitEvent(st, h->ev_join, 0), "cudaStreamWaitEvent"))
         return SLU_ERR_CUDA;
+    if (st != caller &&
+        (!cuda_ok(cudaEventRecord(h->ev_out, st), "cudaEventRecord") ||
+         !cuda_ok(cudaStreamWaitEvent(caller, h->ev_out, 0), "cudaStreamWaitEvent")))
+        return SLU_ERR_CUDA;
     h->cur_level = -1;
     if (!cuda_ok(cudaGetLastError(), "factor launch")) return SLU_ERR_CUDA;
     return SLU_OK;
+}
+
+// The handle's stream of the greatest priority and its fork / join events.
+static bool create_hi_stream(slu_handle *h) {
+    int least = 0, greatest = 0;
+    return cuda_ok(cudaDeviceGetStreamPriorityRange(&least, &greatest), "priorities") &&
+           cuda_ok(cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, greatest),
+                   "cudaStreamCreateWithPriority") &&
+           cuda_ok(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming),
+                   "cudaEventCreate") &&
+           cuda_ok(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming),
+                   "cudaEventCreate");
 }
 
 static slu_status finish_info(slu_handle *h, cudaStream_t st,
@@ -2677,6 +2710,9 @@ extern "C" void slu_handle_destroy(slu_handle *h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->side) cudaStreamDestroy(h->side);
+    if (h->hi) cudaStreamDestroy(h->hi);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     void *ptrs[] = {h->storage, h->a_vals, h->scal, h->cnt, h->work, h->red,
                     h->part, h->anorm_seg, h->winv, h->ptasks, h->pdone,
@@ -2740,7 +2776,8 @@ extern "C" slu_status slu_factor(const slu_plan *P, const double *values,
         !cuda_ok(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming),
                  "cudaEventCreate") ||
         !cuda_ok(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming),
-                 "cudaEventCreate")) {
+                 "cudaEventCreate") ||
+        !create_hi_stream(h)) {
         slu_handle_destroy(h);
         return SLU_ERR_CUDA;
     }
@@ -2910,7 +2947,8 @@ extern "C" slu_status slu_factor_batch(int32_t count, const slu_plan *const *pla
             cuda_ok(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming),
                     "cudaEventCreate") &&
             cuda_ok(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming),
-                    "cudaEventCreate");
+                    "cudaEventCreate") &&
+            create_hi_stream(h);
         out[q] = h;
         if (!ok) st = SLU_ERR_CUDA;
     }
