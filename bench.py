@@ -575,7 +575,13 @@ def main():
                 "host_phase_ms": host_plan.info["phase_ms"]}
     del host_plan
     fl = step_flops(plan, s.nrhs)
+    # the step runs on a created stream: the level walk is replayed from the
+    # CUDA graph recorded at the first refactor (slu_set_graph; the solves
+    # are always replayed from theirs)
+    step_stream = torch.cuda.Stream()
+    torch.cuda.set_stream(step_stream)
     F = S.Factor(plan, vals_d)
+    F.set_graph(True)
 
     def step():
         F.refactor(vals_d)
@@ -588,6 +594,10 @@ def main():
     with Clocks(local) as clk:
         ms = timed(torch, step, args.steps, 0, barrier, nvtx="bench_step")
     launches = (F.stats()["launches"] - l0) // max(1, args.steps)
+    # the same step with the level walk launched kernel by kernel
+    F.set_graph(False)
+    ms_direct = timed(torch, step, args.steps, 1)
+    F.set_graph(True)
     ms = max_over_ranks(ms, world, device="cuda")
     value = job_gflops(fl, ms, world)
     if rank != 0:
@@ -612,6 +622,8 @@ def main():
                       "levels": plan.info["nlevels"],
                       "analyze_ms": plan.info["analyze_ms"], "analysis": analysis,
                       "factor_ms": ms_factor, "solve_ms": ms_solve,
+                      "launch": "level walk replayed from a CUDA graph",
+                      "ms_per_step_kernel_by_kernel": ms_direct,
                       "tuned": best64, "tuning_ms": tun64,
                       "backward_error": sinfo["backward_error"],
                       "l2": "no flush: factors (340 MB) exceed L2",
@@ -620,11 +632,14 @@ def main():
            "clocks": clk.summary()}
 
     # per-kernel-class times by CUDA events over the same number of steps
+    # (kernel by kernel: a replayed graph records no per-launch events)
+    F.set_graph(False)
     F.set_profiling(True)
     for _ in range(args.steps):
         step()
     st = F.stats()
     F.set_profiling(False)
+    F.set_graph(True)
     # the paper's three classes; the explicit diagonal inverses are part of
     # how GESSM / TSTRF run here, so their time counts under the panel
     fcls = plan.flops_by_class()

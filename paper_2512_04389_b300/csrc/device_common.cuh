@@ -285,6 +285,7 @@ struct slu_handle {
     bool use_graph = false;
     cudaGraphExec_t graph_exec = nullptr;
     const double *graph_values = nullptr;
+    int64_t graph_launches = 0;         // kernels recorded in graph_exec
     bool capturing = false;
     // launch accounting and optional per-launch event timing
     int64_t launches = 0;

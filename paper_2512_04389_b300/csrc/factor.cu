@@ -2990,16 +2990,22 @@ extern "C" slu_status slu_refactor(slu_handle *h, const double *values,
             if (!cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal),
                          "cudaStreamBeginCapture"))
                 return SLU_ERR_CUDA;
+            const int64_t l0 = h->launches;
             h->capturing = true;
             st = factor_into(h, values, s);
             h->capturing = false;
+            h->graph_launches = h->launches - l0;   // counted per replay below
+            h->launches = l0;
             const cudaError_t e = cudaStreamEndCapture(s, &g);
             if (st != SLU_OK) {
                 if (g) cudaGraphDestroy(g);
                 return st;
             }
             if (!cuda_ok(e, "cudaStreamEndCapture")) return SLU_ERR_CUDA;
-            const bool ok = cuda_ok(cudaGraphInstantiate(&h->graph_exec, g, 0),
+            // the nodes keep the priorities of the streams they were
+            // recorded on (the level walk's high priority)
+            const bool ok = cuda_ok(cudaGraphInstantiate(&h->graph_exec, g,
+                                                         cudaGraphInstantiateFlagUseNodePriority),
                                     "cudaGraphInstantiate");
             cudaGraphDestroy(g);
             if (!ok) return SLU_ERR_CUDA;
@@ -3007,6 +3013,7 @@ extern "C" slu_status slu_refactor(slu_handle *h, const double *values,
         }
         if (!cuda_ok(cudaGraphLaunch(h->graph_exec, s), "cudaGraphLaunch"))
             return SLU_ERR_CUDA;
+        h->launches += h->graph_launches;
     } else {
         st = factor_into(h, values, s);
         if (st != SLU_OK) return st;
