@@ -708,7 +708,9 @@ def main():
                                      "levels": preg.info["nlevels"]}
         del Freg
         # the regular blocking tuned over block size and threshold (as many
-        # candidates as the irregular search), FP64 and FP32 + refinement
+        # candidates as the irregular search), FP64 and FP32 + refinement;
+        # these legs launch kernel by kernel, so the FP64 ratios are taken
+        # against the irregular step launched the same way
         from paper_2512_04389_b300.tune import candidates
         for prec in ("fp64", "fp32"):
             bt, tt = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d, precision=prec,
@@ -723,7 +725,7 @@ def main():
             extras[f"regular_tuned_{prec}"] = {
                 "ms_per_step": mst, "tuned": bt, "gflops": fl / (mst * 1e-3) / 1e9,
                 "levels": pt.info["nlevels"], "tuning_ms": tt,
-                "irregular_speedup": mst / (ms if prec == "fp64" else ms32)}
+                "irregular_speedup": mst / (ms_direct if prec == "fp64" else ms32)}
             del Ft, pt
             # the regular-size selection policy (no timing runs): its size
             # and threshold 0, the tuned choice on these grids
@@ -738,7 +740,7 @@ def main():
             extras[f"regular_select_{prec}"] = {
                 "ms_per_step": mss, "regular_block": ps_.info["regular_block"],
                 "gflops": fl / (mss * 1e-3) / 1e9,
-                "irregular_speedup": mss / (ms if prec == "fp64" else ms32)}
+                "irregular_speedup": mss / (ms_direct if prec == "fp64" else ms32)}
             del Fs, ps_
         bestr32, _ = tune(s.n, s.colptr, s.rowidx, vals_d, rhs_d,
                           precision="fp32", blocking="regular", regular_block=128)
