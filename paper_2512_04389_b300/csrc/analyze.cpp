@@ -892,6 +892,53 @@ static void build_levels_and_tasks(slu_plan &P) {
                 }
                 req.clear();
             }
+            // Inside each of the level's two tile launches the tiles run
+            // longest first (live slices x 8 x 4 sub-tiles of the tile), so a
+            // launch does not end on a few long tiles started last (list
+            // scheduling, longest processing time first).  Every tile writes
+            // only its own rows and columns of its target, so the order
+            // changes no result.
+            const int64_t nt = (int64_t)o.gm_task.size() / 5;
+            if (nt > 1) {
+                std::vector<int64_t> mo(nt + 1, 0);
+                for (int64_t t = 0; t < nt; ++t)
+                    mo[t + 1] = mo[t] + (o.gm_task[5 * t + 2] - o.gm_task[5 * t + 1]);
+                std::vector<double> cost(nt);
+                for (int64_t t = 0; t < nt; ++t) {
+                    const int32_t *tk = &o.gm_task[5 * t];
+                    const BlockDesc &td = P.blocks[tk[0]];
+                    int64_t live = 0;
+                    for (int32_t q = tk[1]; q < tk[2]; ++q) {
+                        const int32_t nsl = (P.blocks[o.gm_src[2 * q]].cols + 15) / 16;
+                        live += masks ? __builtin_popcount(o.gm_mask[mo[t] + (q - tk[1])]) +
+                                            std::max(0, nsl - 32)
+                                      : nsl;
+                    }
+                    const int32_t rt = std::min(kTile, td.rows - tk[3]);
+                    const int32_t ct = std::min(64, td.cols - tk[4]);
+                    cost[t] = (double)live * ((rt + 7) / 8) * ((ct + 3) / 4);
+                }
+                std::vector<int64_t> perm(nt);
+                for (int64_t t = 0; t < nt; ++t) perm[t] = t;
+                auto longest_first = [&](int64_t x, int64_t y) { return cost[x] > cost[y]; };
+                std::stable_sort(perm.begin(), perm.begin() + o.gm_mid, longest_first);
+                std::stable_sort(perm.begin() + o.gm_mid, perm.end(), longest_first);
+                std::vector<int32_t> task2(o.gm_task.size());
+                std::vector<uint32_t> mask2(o.gm_mask.size());
+                int64_t m = 0;
+                for (int64_t t = 0; t < nt; ++t) {
+                    const int64_t u = perm[t];
+                    std::copy(o.gm_task.begin() + 5 * u, o.gm_task.begin() + 5 * u + 5,
+                              task2.begin() + 5 * t);
+                    if (masks) {
+                        std::copy(o.gm_mask.begin() + mo[u], o.gm_mask.begin() + mo[u + 1],
+                                  mask2.begin() + m);
+                        m += mo[u + 1] - mo[u];
+                    }
+                }
+                o.gm_task.swap(task2);
+                o.gm_mask.swap(mask2);
+            }
         }
     });
     // concatenation in level order (each level's slice copied by a thread

@@ -1981,8 +1981,8 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
 // of A(:, k) and group g of B(k, :) hold one (set bits of a 16-bit mask,
 // warp-uniform, so no FP64 instruction is issued for a skipped product).
 // The terms left out are exact zeros: the result is the dense one.  Slices
-// are double-buffered (the next slice's global loads are in flight in
-// registers while the current one is multiplied), sources run in ascending
+// are double-buffered (the next slice's cp.async copies are in flight while
+// the current one is multiplied), sources run in ascending
 // I and k ascending within them, so the result is deterministic.
 // Shared memory of one dense Schur tile: the double-buffered slices and
 // their masks.  sAg[buf][k][h] bit j: rows 32h + 8j .. +7 of A(:, k) hold a
@@ -1990,6 +1990,15 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
 // 32-deep half of the slice).  Slices are 16 deep (the body also takes 64:
 // measured on B300, 64-deep FP32 slices were slower, 132 against 91 ms for
 // the 40^3 FP32 + refinement step, with fewer resident CTAs).
+// One element copied global -> shared by cp.async (sizeof(T) bytes, 4 or 8);
+// with in == false nothing is read and the element is zero-filled.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool in) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;"
+                 :: "r"(tc::smem_u32(dst)), "l"(src), "n"((int)sizeof(T)), "r"(in ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+
 template <typename T>
 struct GemmSmem {
     static constexpr int TM = 64, TN = 64, KT = 16, PAD = 16 / sizeof(T);
@@ -2039,8 +2048,11 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
             du = bd[src[2 * s + 1]];
         }
     }
-    T ra[NQ], rb[NQ];
-    auto load = [&](const BlockDesc &L, const BlockDesc &U, int kk0) {
+    // Slices are copied into shared memory by cp.async (no register round
+    // trip, so the tile fits five CTAs per SM): element e = tid + 256 q of
+    // the A slice is (row e % 64, k e / 64), of the B slice (k e % KT,
+    // column e / KT); elements outside the blocks are zero-filled.
+    auto issue = [&](const BlockDesc &L, const BlockDesc &U, int kk0, int b) {
         const T *A = val + L.voff;
         const T *B = val + U.voff;
         const int K = L.cols;
@@ -2049,52 +2061,54 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
             const int e = tid + 256 * q;
             const int r = e % TM, k = e / TM;
             const int gr = r0 + r, gk = kk0 + k;
-            ra[q] = (gr < d.rows && gk < K) ? A[(int64_t)gk * L.ld + gr] : T(0);
+            const bool in = gr < d.rows && gk < K;
+            cp_async_elem(&As[b][k][r], in ? A + (int64_t)gk * L.ld + gr : A, in);
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int e = tid + 256 * q;
             const int k = e % KT, c = e / KT;
             const int gk = kk0 + k, gc = c0 + c;
-            rb[q] = (gk < K && gc < d.cols) ? B[(int64_t)gc * U.ld + gk] : T(0);
+            const bool in = gk < K && gc < d.cols;
+            cp_async_elem(&Bs[b][k][c], in ? B + (int64_t)gc * U.ld + gk : B, in);
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    // Staging map: A element e = tid + 256 q is (row e % 64, k e / 64), so
-    // warp w's lanes are rows 32 (w & 1) .. + 31 of k = (w + 8 q) / 2 and its
-    // ballot gives four 8-row groups.  B element e is (k e % KT, column
-    // e / KT): for KT = 16 the warp holds columns 2 (w + 8 q) and + 1, lanes
-    // 0-15 and 16-31 over k = 0 .. 15; for KT = 64 it holds column
-    // (w + 8 q) / 2 over k = 32 ((w + 8 q) & 1) + lane.
-    auto store = [&](int buf) {
+    // After the thread's own copies landed: masks of the slice in buffer b.
+    // Warp w's lanes hold rows 32 (w & 1) .. + 31 of A column k = (w + 8 q)
+    // / 2, whose ballot gives four 8-row groups; for KT = 16 the warp holds
+    // B columns 2 (w + 8 q) and + 1, lanes 0-15 and 16-31 over k = 0 .. 15;
+    // for KT = 64 it holds column (w + 8 q) / 2 over k = 32 ((w + 8 q) & 1)
+    // + lane.
+    auto mark = [&](int b) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int e = tid + 256 * q;
-            As[buf][e / TM][e % TM] = ra[q];
-            const unsigned m = __ballot_sync(0xffffffffu, nz(ra[q]));
+            const unsigned m = __ballot_sync(0xffffffffu, nz(As[b][e / TM][e % TM]));
             if (lane == 0)
-                sAg[buf][(warp + 8 * q) >> 1][warp & 1] =
+                sAg[b][(warp + 8 * q) >> 1][warp & 1] =
                     (unsigned char)(((m & 0xffu) ? 1u : 0u) | ((m & 0xff00u) ? 2u : 0u) |
                                     ((m & 0xff0000u) ? 4u : 0u) | ((m & 0xff000000u) ? 8u : 0u));
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int e = tid + 256 * q;
-            Bs[buf][e % KT][e / KT] = rb[q];
-            const unsigned m = __ballot_sync(0xffffffffu, nz(rb[q]));
+            const unsigned m = __ballot_sync(0xffffffffu, nz(Bs[b][e % KT][e / KT]));
             if (lane == 0) {
                 const int wq = warp + 8 * q;
                 if (KT == 64) {
-                    sBc[buf][wq >> 1][wq & 1] = m;
+                    sBc[b][wq >> 1][wq & 1] = m;
                 } else {
-                    sBc[buf][2 * wq][0] = m & 0xffffu;
-                    sBc[buf][2 * wq + 1][0] = m >> 16;
+                    sBc[b][2 * wq][0] = m & 0xffffu;
+                    sBc[b][2 * wq + 1][0] = m >> 16;
                 }
             }
         }
     };
     const int rr = 8 * warp + (lane & 7), cc = lane >> 3;
-    load(dl, du, k0);
-    store(0);
+    issue(dl, du, k0, 0);
+    mark(0);
     __syncthreads();
     int buf = 0;
     for (;;) {
@@ -2113,7 +2127,9 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
             nk0 += KT;
         }
         const bool more = ns < s1;
-        if (more) load(nl, nu, nk0);
+        // the other buffer was last read before the barrier that ended the
+        // previous slice
+        if (more) issue(nl, nu, nk0, buf ^ 1);
         // k mask of this warp's row group (lane k of the first KT reads it)
         Mask amk = __ballot_sync(
             0xffffffffu, lane < KT && ((sAg[buf][lane & (KT - 1)][warp >> 2] >> (warp & 3)) & 1u));
@@ -2149,7 +2165,7 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
             }
         }
         if (!more) break;
-        store(buf ^ 1);
+        mark(buf ^ 1);
         __syncthreads();
         buf ^= 1;
         s = ns;
@@ -2168,10 +2184,10 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
 }
 
 // One CTA per tile; blockIdx.y picks the 64-row half of a 128-row tile.
-// Four CTAs per SM (64 registers, no spills): a CTA staging its next slice
-// or waiting at its barrier leaves the FP64 pipe to three others.
+// Five CTAs per SM: a CTA waiting for its next slice or at its barrier
+// leaves the FP64 pipe to four others.
 template <typename T>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 5)
 k_ssssm_gemm(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
              const BlockDesc *__restrict__ bd, T *__restrict__ val,
              const uint32_t *__restrict__ mask, const int64_t *__restrict__ moff) {
