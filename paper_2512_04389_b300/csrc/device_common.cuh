@@ -102,6 +102,24 @@ __device__ __forceinline__ bool nz(float v) {
     return (__float_as_uint(v) & 0x7fffffffu) != 0;
 }
 
+// One element copied global -> shared by cp.async (sizeof(T) bytes, 4 or 8);
+// with in == false nothing is read and the element is zero-filled.  The
+// copies of a thread land by cp_async_wait_all; other threads see them after
+// a barrier that follows it.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool in = true) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "n"((int)sizeof(T)),
+                    "r"(in ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 

@@ -508,7 +508,8 @@ __device__ void getrf_dense(T *g, int b, int64_t ld, double tau,
             const int ls = b | 1;
             double *S = reinterpret_cast<double *>(smem);
             for (int e = threadIdx.x; e < b * b; e += blockDim.x)
-                S[(e / b) * ls + e % b] = g[(int64_t)(e / b) * ld + e % b];
+                cp_async_elem(&S[(e / b) * ls + e % b], &g[(int64_t)(e / b) * ld + e % b]);
+            cp_async_wait_all();
             __syncthreads();
             lu_owner(S, b, ls, tau, cnt, smem + (size_t)b * ls * sizeof(double));
             for (int e = threadIdx.x; e < b * b; e += blockDim.x)
@@ -520,7 +521,8 @@ __device__ void getrf_dense(T *g, int b, int64_t ld, double tau,
         // FP32 block that fits whole: dense steps with one barrier each
         T *S = reinterpret_cast<T *>(smem);
         for (int e = threadIdx.x; e < b * b; e += blockDim.x)
-            S[e] = g[(int64_t)(e / b) * ld + e % b];
+            cp_async_elem(&S[e], &g[(int64_t)(e / b) * ld + e % b]);
+        cp_async_wait_all();
         __syncthreads();
         lu_dense_smem<T>(S, b, b, tau, cnt);
         for (int e = threadIdx.x; e < b * b; e += blockDim.x)
@@ -531,8 +533,9 @@ __device__ void getrf_dense(T *g, int b, int64_t ld, double tau,
     T *S = reinterpret_cast<T *>(smem + lb);
     for (int e = threadIdx.x; e < ms * ms; e += blockDim.x) {
         const int r = e % ms, c = e / ms;
-        S[c * ls + r] = g[(int64_t)(p0 + c) * ld + p0 + r];
+        cp_async_elem(&S[c * ls + r], &g[(int64_t)(p0 + c) * ld + p0 + r]);
     }
+    cp_async_wait_all();
     __syncthreads();
     const SplitBlock<T> B{g, ld, S, ls, p0, b};
     lu_skip<T>(B, b, smem, tau, cnt);
@@ -1158,7 +1161,9 @@ __device__ __forceinline__ void inv_body(const int32_t *tk, const BlockDesc *bd,
     T *staged = s_rcp + inv_smem_elems(b);
     const bool fits = (inv_smem_elems(b) + (size_t)b * b) * sizeof(T) <= cap;
     if (fits) {
-        for (int64_t e = threadIdx.x; e < (int64_t)b * b; e += blockDim.x) staged[e] = F[e];
+        for (int64_t e = threadIdx.x; e < (int64_t)b * b; e += blockDim.x)
+            cp_async_elem(&staged[e], &F[e]);
+        cp_async_wait_all();
         F = staged;
     }
     __syncthreads();
@@ -1172,20 +1177,24 @@ __device__ __forceinline__ void inv_body(const int32_t *tk, const BlockDesc *bd,
     for (int r = lane; r < bs; r += 32) x[r] = (r == j) ? T(1) : T(0);
     const int nq = bs >> 5;
     // column mm into c (rows the step uses, zeros elsewhere); returns the
-    // mask of its nonzero chunks.  All loads are issued before any vote.
+    // mask of its nonzero chunks.  All loads are issued before any vote; the
+    // unrolled loops leave at the block's chunk count (warp-uniform), so a
+    // step issues no instruction for chunks beyond the block.
     auto fetch = [&](int mm, T *c) -> unsigned {
         const T *col = F + (int64_t)mm * b;
         T v[kInvRows];
 #pragma unroll
         for (int q = 0; q < kInvRows; ++q) {
+            if (q >= nq) break;
             const int r = q * 32 + lane;
-            const bool in = q < nq && (which == 0 ? (r > mm && r < b) : (r < mm));
+            const bool in = which == 0 ? (r > mm && r < b) : (r < mm);
             v[q] = in ? col[r] : T(0);
         }
         unsigned m = 0;
 #pragma unroll
         for (int q = 0; q < kInvRows; ++q) {
-            if (q < nq) c[q * 32 + lane] = v[q];
+            if (q >= nq) break;
+            c[q * 32 + lane] = v[q];
             if (__ballot_sync(~0u, nz(v[q]))) m |= 1u << q;
         }
         return m;
@@ -1330,10 +1339,10 @@ __device__ __forceinline__ void panel_inv_body(const int32_t *tk, const BlockDes
     const int c0 = tk[3], m = dd.rows, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     T *X = reinterpret_cast<T *>(smem);                 // m x 64 chunk, X[k * 64 + c]
-    T *Ts = X + (size_t)m * 64;                          // 16 x 64 inverse slice
+    T *Ts = X + (size_t)m * 64;                          // 2 x 16 x 64 inverse slices
     const int nsl = (m + KT - 1) / KT;
-    unsigned short *xpm = reinterpret_cast<unsigned short *>(Ts + KT * 64);  // [nsl][32]
-    unsigned short *tpm = xpm + (size_t)nsl * 32;                           // [32]
+    unsigned short *xpm = reinterpret_cast<unsigned short *>(Ts + 2 * KT * 64);  // [nsl][32]
+    unsigned short *tpm = xpm + (size_t)nsl * 32;                               // [2][32]
     const int64_t ld = d.ld;
     T *Bg = val + d.voff;
     const T *Inv = winv + woff[dd.I] + (type == 0 ? 0 : (int64_t)m * m);
@@ -1343,11 +1352,12 @@ __device__ __forceinline__ void panel_inv_body(const int32_t *tk, const BlockDes
     if (d.dense) {
         for (int e = tid; e < m * 64; e += 256) {
             const int k = e / 64, c = e % 64;
-            T v = T(0);
-            if (c < nv)
-                v = type == 0 ? Bg[(int64_t)(c0 + c) * ld + k] : Bg[(int64_t)k * ld + c0 + c];
-            X[e] = v;
+            const T *src = c < nv ? (type == 0 ? &Bg[(int64_t)(c0 + c) * ld + k]
+                                               : &Bg[(int64_t)k * ld + c0 + c])
+                                  : Bg;
+            cp_async_elem(&X[e], src, c < nv);
         }
+        cp_async_wait_all();
     } else {
         // sparse panel block: scatter its pattern into the zeroed chunk
         for (int e = tid; e < m * 64; e += 256) X[e] = T(0);
@@ -1378,42 +1388,63 @@ __device__ __forceinline__ void panel_inv_body(const int32_t *tk, const BlockDes
         slice_pair_masks<T>(X + (size_t)sl * KT * 64, min(KT, m - sl * KT), xpm + sl * 32);
     __syncthreads();
     const int rr = 8 * warp + (lane & 7), cc = lane >> 3;
+    // inverse slice (output chunk ob, rows k0 .. k0 + 15) into buffer bf by
+    // cp.async, entries outside the inverse zero-filled:
+    //   GESSM: Ts[kk][ii] = Linv(ob + ii, k0 + kk)
+    //   TSTRF: Ts[kk][ii] = Uinv(k0 + kk, ob + ii)
+    auto issue = [&](int ob, int k0, int bf) {
+        T *D = Ts + (size_t)bf * KT * 64;
+        for (int e = tid; e < KT * 64; e += 256) {
+            int kk, ii;
+            if (type == 0) { ii = e % 64; kk = e / 64; }
+            else           { kk = e % KT; ii = e / KT; }
+            const int gi = ob + ii, gk = k0 + kk;
+            const bool in = gi < m && gk < m;
+            const T *src = !in ? Inv : type == 0 ? &Inv[(int64_t)gk * m + gi]
+                                                 : &Inv[(int64_t)gi * m + gk];
+            cp_async_elem(&D[kk * 64 + ii], src, in);
+        }
+        cp_async_commit();
+    };
+    // first slice from k0 on, below kend, whose slice of X holds a nonzero
+    // (kend: none); a slice of X without one adds nothing
+    auto next_live = [&](int k0, int kend) {
+        for (; k0 < kend; k0 += KT) {
+            const unsigned short *xp = xpm + (k0 / KT) * 32;
+            bool any = false;
+#pragma unroll
+            for (int p = 0; p < 32; ++p) any |= xp[p] != 0;
+            if (any) break;
+        }
+        return min(k0, kend);
+    };
     for (int ob = 0; ob < m; ob += 64) {       // output chunk along m
         T acc[16];
 #pragma unroll
         for (int g = 0; g < 16; ++g) acc[g] = T(0);
         // GESSM: out(i, c) = sum_{k <= i} Linv(i, k) X(k, c), i in [ob, ob+64)
         // TSTRF: out(r, i) = sum_{k <= i} X(r, k) Uinv(k, i), i in [ob, ob+64)
+        // The inverse slices are double-buffered: the next live slice's
+        // copies are in flight while the current one is multiplied.
         const int kend = min(m, ob + 64);
-        for (int k0 = 0; k0 < kend; k0 += KT) {
+        __syncthreads();                          // buffers of the previous chunk read
+        int k0 = next_live(0, kend), buf = 0;
+        if (k0 < kend) issue(ob, k0, 0);
+        while (k0 < kend) {
+            cp_async_wait_all();
+            __syncthreads();                      // slice k0 in buffer buf for all
+            const T *TsB = Ts + (size_t)buf * KT * 64;
+            unsigned short *tpB = tpm + buf * 32;
+            slice_pair_masks<T>(TsB, min(KT, m - k0), tpB);
+            __syncthreads();
+            // the other buffer was last read before the first barrier above
+            const int k1 = next_live(k0 + KT, kend);
+            if (k1 < kend) issue(ob, k1, buf ^ 1);
             const unsigned short *xp = xpm + (k0 / KT) * 32;
-            // uniform across the CTA: a slice of X without a nonzero adds nothing
-            bool any = false;
-#pragma unroll
-            for (int p = 0; p < 32; ++p) any |= xp[p] != 0;
-            if (!any) continue;
-            const int kn = min(KT, m - k0);
-            for (int e = tid; e < KT * 64; e += 256) {
-                int kk, ii;
-                T v = T(0);
-                if (type == 0) {               // Ts[kk][ii] = Linv(ob + ii, k0 + kk)
-                    ii = e % 64; kk = e / 64;
-                    const int gi = ob + ii, gk = k0 + kk;
-                    if (gi < m && gk < m) v = Inv[(int64_t)gk * m + gi];
-                } else {                       // Ts[kk][ii] = Uinv(k0 + kk, ob + ii)
-                    kk = e % KT; ii = e / KT;
-                    const int gi = ob + ii, gk = k0 + kk;
-                    if (gi < m && gk < m) v = Inv[(int64_t)gi * m + gk];
-                }
-                Ts[kk * 64 + ii] = v;
-            }
-            __syncthreads();
-            slice_pair_masks<T>(Ts, kn, tpm);
-            __syncthreads();
-            const unsigned short *apm = type == 0 ? tpm : xp;
-            const unsigned short *bpm = type == 0 ? xp : tpm;
-            const T *A = type == 0 ? Ts : X + (size_t)k0 * 64;
-            const T *B = type == 0 ? X + (size_t)k0 * 64 : Ts;
+            const unsigned short *apm = type == 0 ? tpB : xp;
+            const unsigned short *bpm = type == 0 ? xp : tpB;
+            const T *A = type == 0 ? TsB : X + (size_t)k0 * 64;
+            const T *B = type == 0 ? X + (size_t)k0 * 64 : TsB;
             const unsigned amk = apm[4 * warp] | apm[4 * warp + 1] | apm[4 * warp + 2] |
                                  apm[4 * warp + 3];
             if (amk) {
@@ -1436,7 +1467,8 @@ __device__ __forceinline__ void panel_inv_body(const int32_t *tk, const BlockDes
                     }
                 }
             }
-            __syncthreads();                              // Ts and tpm are rewritten next
+            k0 = k1;
+            buf ^= 1;
         }
 #pragma unroll
         for (int g = 0; g < 16; ++g) {
@@ -1990,15 +2022,6 @@ k_ssssm_tc(const int32_t *__restrict__ task, const int32_t *__restrict__ src,
 // 32-deep half of the slice).  Slices are 16 deep (the body also takes 64:
 // measured on B300, 64-deep FP32 slices were slower, 132 against 91 ms for
 // the 40^3 FP32 + refinement step, with fewer resident CTAs).
-// One element copied global -> shared by cp.async (sizeof(T) bytes, 4 or 8);
-// with in == false nothing is read and the element is zero-filled.
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool in) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;"
-                 :: "r"(tc::smem_u32(dst)), "l"(src), "n"((int)sizeof(T)), "r"(in ? (int)sizeof(T) : 0)
-                 : "memory");
-}
-
 template <typename T>
 struct GemmSmem {
     static constexpr int TM = 64, TN = 64, KT = 16, PAD = 16 / sizeof(T);
@@ -2072,7 +2095,7 @@ __device__ __forceinline__ void gemm_body(const int32_t *tk, const int32_t *src,
             const bool in = gk < K && gc < d.cols;
             cp_async_elem(&Bs[b][k][c], in ? B + (int64_t)gc * U.ld + gk : B, in);
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        cp_async_commit();
     };
     // After the thread's own copies landed: masks of the slice in buffer b.
     // Warp w's lanes hold rows 32 (w & 1) .. + 31 of A column k = (w + 8 q)
@@ -2566,7 +2589,7 @@ static slu_status run_factor(slu_handle *h, const double *values,
         if (d1 > d0) {
             LaunchScope ls_(h, SLU_KC_PANEL, st, (int)(d1 - d0));
             k_panel_inv<T><<<(int)(d1 - d0), 256,
-                             ((size_t)P->inv_maxb * 64 + 16 * 64) * sizeof(T) +
+                             ((size_t)P->inv_maxb * 64 + 2 * 16 * 64) * sizeof(T) +
                                  8 * (size_t)P->inv_maxb + 256, st>>>(
                 D->pd_task + 4 * d0, D->bd, val, static_cast<const T *>(h->winv),
                 D->woff, a);
