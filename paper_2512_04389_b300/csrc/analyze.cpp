@@ -738,10 +738,12 @@ static void build_levels_and_tasks(slu_plan &P) {
         tile_base[X + 1] = tile_base[X] + (rows + 63) / 64;
         max_sl = std::max(max_sl, std::min(32, (rows + 15) / 16));
     }
-    auto tile_of = [&](int32_t r) -> int64_t {
-        const int32_t X = P.rowblk[r];
-        return tile_base[X] + (r - P.ptr[X]) / 64;
-    };
+    // tile of every row (rows 64 t .. 64 t + 63 of a block form its tile t)
+    std::vector<int32_t> row_tile(masks ? (size_t)P.n : 0);
+    for (int32_t X = 0; masks && X < p; ++X)
+        for (int64_t r = P.ptr[X]; r < P.ptr[X + 1]; ++r)
+            row_tile[r] = (int32_t)(tile_base[X] + (r - P.ptr[X]) / 64);
+    auto tile_of = [&](int32_t r) -> int64_t { return row_tile[r]; };
     std::vector<Lvl> lvl(L);
     std::atomic<int32_t> next_lv{0};
     run_threads(std::min<int>(host_threads(nb), std::max(1, L)), [&](int) {
@@ -751,9 +753,19 @@ static void build_levels_and_tasks(slu_plan &P) {
         // mask entries to fill: (block row I, entry, tile of the rows, tile
         // of the columns); per-slice masks of the columns of one block I
         struct MaskReq { int32_t I; int64_t e, tk, tj; };
-        std::vector<MaskReq> req;
+        std::vector<MaskReq> req, req2;
+        std::vector<Tgt> vec2;
         std::vector<uint16_t> tab(masks ? (size_t)tile_base[p] * max_sl : 0, 0);
         std::vector<int64_t> touched;
+        // stable counting sort of src into dst by key(x) in [0, p)
+        std::vector<int64_t> cnt(p + 1);
+        auto by_key = [&](const auto &src, auto &dst, auto key) {
+            std::fill(cnt.begin(), cnt.end(), 0);
+            for (const auto &x : src) cnt[key(x) + 1]++;
+            for (int32_t i = 0; i < p; ++i) cnt[i + 1] += cnt[i];
+            dst.resize(src.size());
+            for (const auto &x : src) dst[cnt[key(x)]++] = x;
+        };
         for (int32_t lv; (lv = next_lv.fetch_add(1)) < L;) {
             Lvl &o = lvl[lv];
             vec.clear();
@@ -800,9 +812,16 @@ static void build_levels_and_tasks(slu_plan &P) {
                 pairs[2 * q + 1] = trip[t + 2];
             }
             for (const Tgt &t : vec) slot[t.tb] = -1;
-            std::sort(vec.begin(), vec.end(), [](const Tgt &x, const Tgt &y) {
-                return x.K != y.K ? x.K < y.K : x.J < y.J;
-            });
+            // targets by (K, J) (unique per level): a comparison sort for a
+            // few, else counting sorts by J, then stably by K
+            if ((int64_t)vec.size() <= 64) {
+                std::sort(vec.begin(), vec.end(), [](const Tgt &x, const Tgt &y) {
+                    return x.K != y.K ? x.K < y.K : x.J < y.J;
+                });
+            } else {
+                by_key(vec, vec2, [](const Tgt &t) { return t.J; });
+                by_key(vec2, vec, [](const Tgt &t) { return t.K; });
+            }
             o.tgt.reserve(vec.size());
             o.srcend.reserve(vec.size());
             o.src.reserve(pairs.size());
@@ -857,8 +876,8 @@ static void build_levels_and_tasks(slu_plan &P) {
                 }
             }
             if (masks && !req.empty()) {
-                std::stable_sort(req.begin(), req.end(),
-                                 [](const MaskReq &x, const MaskReq &y) { return x.I < y.I; });
+                by_key(req, req2, [](const MaskReq &x) { return x.I; });
+                req.swap(req2);
                 for (size_t a0 = 0; a0 < req.size();) {
                     const int32_t I = req[a0].I;
                     size_t a1 = a0;
@@ -870,10 +889,11 @@ static void build_levels_and_tasks(slu_plan &P) {
                         const int32_t sl = (int32_t)((k - k0) / 16);
                         if (sl >= 32) break;
                         const uint16_t bit = (uint16_t)(1u << ((k - k0) % 16));
-                        for (int64_t f = P.f_colptr[k]; f < P.f_colptr[k + 1]; ++f) {
-                            const int32_t r = P.f_rowidx[f];
-                            if (r < k1) continue;
-                            const int64_t at = tile_of(r) * max_sl + sl;
+                        // rows below block I: the column's rows ascend
+                        const int32_t *c0 = P.f_rowidx.data() + P.f_colptr[k];
+                        const int32_t *c1 = P.f_rowidx.data() + P.f_colptr[k + 1];
+                        for (const int32_t *f = std::lower_bound(c0, c1, (int32_t)k1); f < c1; ++f) {
+                            const int64_t at = (int64_t)row_tile[*f] * max_sl + sl;
                             if (!tab[at]) touched.push_back(at);
                             tab[at] |= bit;
                         }
@@ -903,7 +923,7 @@ static void build_levels_and_tasks(slu_plan &P) {
                 std::vector<int64_t> mo(nt + 1, 0);
                 for (int64_t t = 0; t < nt; ++t)
                     mo[t + 1] = mo[t] + (o.gm_task[5 * t + 2] - o.gm_task[5 * t + 1]);
-                std::vector<double> cost(nt);
+                std::vector<uint64_t> cost(nt);
                 for (int64_t t = 0; t < nt; ++t) {
                     const int32_t *tk = &o.gm_task[5 * t];
                     const BlockDesc &td = P.blocks[tk[0]];
@@ -916,13 +936,16 @@ static void build_levels_and_tasks(slu_plan &P) {
                     }
                     const int32_t rt = std::min(kTile, td.rows - tk[3]);
                     const int32_t ct = std::min(64, td.cols - tk[4]);
-                    cost[t] = (double)live * ((rt + 7) / 8) * ((ct + 3) / 4);
+                    // key: cost descending, then task ascending (unique keys)
+                    const uint64_t c = std::min<uint64_t>(
+                        (uint64_t)live * ((rt + 7) / 8) * ((ct + 3) / 4), 0xffffffffull);
+                    cost[t] = ((0xffffffffull - c) << 32) | (uint64_t)(t - (t < o.gm_mid ? 0 : o.gm_mid));
                 }
+                std::sort(cost.begin(), cost.begin() + o.gm_mid);
+                std::sort(cost.begin() + o.gm_mid, cost.end());
                 std::vector<int64_t> perm(nt);
-                for (int64_t t = 0; t < nt; ++t) perm[t] = t;
-                auto longest_first = [&](int64_t x, int64_t y) { return cost[x] > cost[y]; };
-                std::stable_sort(perm.begin(), perm.begin() + o.gm_mid, longest_first);
-                std::stable_sort(perm.begin() + o.gm_mid, perm.end(), longest_first);
+                for (int64_t t = 0; t < nt; ++t)
+                    perm[t] = (int64_t)(cost[t] & 0xffffffffull) + (t < o.gm_mid ? 0 : o.gm_mid);
                 std::vector<int32_t> task2(o.gm_task.size());
                 std::vector<uint32_t> mask2(o.gm_mask.size());
                 int64_t m = 0;
@@ -983,54 +1006,58 @@ static void build_levels_and_tasks(slu_plan &P) {
             gb += (int64_t)o.gg_src.size() / 2;
         }
     }
-    // dense tiles: source pair indices become global
+    // dense tiles: source pair indices become global; slice masks in task
+    // order, gm_moff[t] = first mask of task t (one mask per source pair of
+    // the task).  Offsets per level first, then each level's slices copied
+    // by a thread of its own (first touching their pages).
     P.gm_off.assign(L + 1, 0);
     P.gm_mid.assign(L, 0);
     P.gg_mid.assign(L, 0);
-    {
-        int64_t nt5 = 0, nsrc = 0;
-        for (const Lvl &o : lvl) {
-            nt5 += (int64_t)o.gm_task.size();
-            nsrc += (int64_t)o.gm_src.size();
-        }
-        P.gm_task.resize((size_t)nt5);
-        P.gm_src.resize((size_t)nsrc);
-        int64_t tat = 0, sat = 0;
-        for (int32_t lv = 0; lv < L; ++lv) {
-            const Lvl &o = lvl[lv];
-            const int32_t base = (int32_t)(sat / 2);
-            for (size_t t = 0; t < o.gm_task.size(); t += 5) {
-                int32_t *d = P.gm_task.data() + tat + t;
-                d[0] = o.gm_task[t];
-                d[1] = o.gm_task[t + 1] + base;
-                d[2] = o.gm_task[t + 2] + base;
-                d[3] = o.gm_task[t + 3];
-                d[4] = o.gm_task[t + 4];
-            }
-            std::copy(o.gm_src.begin(), o.gm_src.end(), P.gm_src.begin() + sat);
-            P.gm_mid[lv] = tat / 5 + o.gm_mid;
-            P.gg_mid[lv] = P.gg_off[lv] + o.gg_mid;
-            tat += (int64_t)o.gm_task.size();
-            sat += (int64_t)o.gm_src.size();
-            P.gm_off[lv + 1] = tat / 5;
-        }
-    }
-    // slice masks in task order; gm_moff[t] = first mask of task t (one
-    // mask per source pair of the task)
     P.gm_mask.clear();
     P.gm_moff.clear();
-    if (masks) {
-        int64_t nm = 0;
-        for (const Lvl &o : lvl) nm += (int64_t)o.gm_mask.size();
-        P.gm_mask.resize((size_t)nm);
-        P.gm_moff.assign(P.gm_task.size() / 5 + 1, 0);
-        int64_t at = 0, t = 0;
-        for (const Lvl &o : lvl) {
-            std::copy(o.gm_mask.begin(), o.gm_mask.end(), P.gm_mask.begin() + at);
-            for (size_t q = 0; q < o.gm_task.size(); q += 5, ++t)
-                P.gm_moff[t + 1] = P.gm_moff[t] + (o.gm_task[q + 2] - o.gm_task[q + 1]);
-            at += (int64_t)o.gm_mask.size();
+    {
+        std::vector<int64_t> tat(L + 1, 0), sat(L + 1, 0), mat(L + 1, 0);
+        for (int32_t lv = 0; lv < L; ++lv) {
+            const Lvl &o = lvl[lv];
+            tat[lv + 1] = tat[lv] + (int64_t)o.gm_task.size();
+            sat[lv + 1] = sat[lv] + (int64_t)o.gm_src.size();
+            mat[lv + 1] = mat[lv] + (int64_t)o.gm_mask.size();
+            P.gm_mid[lv] = tat[lv] / 5 + o.gm_mid;
+            P.gg_mid[lv] = P.gg_off[lv] + o.gg_mid;
+            P.gm_off[lv + 1] = tat[lv + 1] / 5;
         }
+        P.gm_task.resize((size_t)tat[L]);
+        P.gm_src.resize((size_t)sat[L]);
+        if (masks) {
+            P.gm_mask.resize((size_t)mat[L]);
+            P.gm_moff.resize(P.gm_task.size() / 5 + 1);
+            P.gm_moff[0] = 0;
+        }
+        std::atomic<int32_t> nx{0};
+        run_threads(ntc, [&](int) {
+            for (int32_t lv; (lv = nx.fetch_add(1)) < L;) {
+                const Lvl &o = lvl[lv];
+                const int32_t base = (int32_t)(sat[lv] / 2);
+                for (size_t t = 0; t < o.gm_task.size(); t += 5) {
+                    int32_t *d = P.gm_task.data() + tat[lv] + t;
+                    d[0] = o.gm_task[t];
+                    d[1] = o.gm_task[t + 1] + base;
+                    d[2] = o.gm_task[t + 2] + base;
+                    d[3] = o.gm_task[t + 3];
+                    d[4] = o.gm_task[t + 4];
+                }
+                std::copy(o.gm_src.begin(), o.gm_src.end(), P.gm_src.begin() + sat[lv]);
+                if (!masks) continue;
+                std::copy(o.gm_mask.begin(), o.gm_mask.end(), P.gm_mask.begin() + mat[lv]);
+                // gm_moff[t + 1] for the level's tasks: the level's first
+                // mask is mat[lv], its tasks' masks follow in task order
+                int64_t m = mat[lv], t = tat[lv] / 5;
+                for (size_t q = 0; q < o.gm_task.size(); q += 5, ++t) {
+                    m += o.gm_task[q + 2] - o.gm_task[q + 1];
+                    P.gm_moff[t + 1] = m;
+                }
+            }
+        });
     }
     std::vector<Lvl>().swap(lvl);
     auto flat = [&](std::vector<std::vector<int32_t>> &v,
